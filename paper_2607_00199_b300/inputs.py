@@ -1,0 +1,130 @@
+"""Seeded synthetic inputs: meshes, motion parameters, initial flows, request streams.
+
+This module holds none of the method's arithmetic.  It is the one piece shared
+by the CUDA library's tests and benchmark and by the CPU oracle's tests: it
+only generates the inputs both sides receive.
+
+Random numbers come from splitmix64 (Steele, Lea and Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) used as a counter-based
+generator: draw k of stream `seed` is mix(seed + (k + 1) * 0x9E3779B97F4A7C15).
+"""
+import math
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+DEFAULT_SEED = 260700199
+
+
+def splitmix64(counter, seed=DEFAULT_SEED):
+    """splitmix64 output for integer counters (array), as uint64."""
+    with np.errstate(over='ignore'):
+        z = np.uint64(seed) + (np.asarray(counter, dtype=np.uint64) + np.uint64(1)) * GOLDEN
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        z = z ^ (z >> np.uint64(31))
+    return z
+
+
+def uniform(counter, seed=DEFAULT_SEED, lo=0.0, hi=1.0):
+    """Uniform doubles in [lo, hi) from the top 53 bits of splitmix64."""
+    u = (splitmix64(counter, seed) >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+    return lo + (hi - lo) * u
+
+
+def periodic_square_mesh(n, L=2.0 * math.pi, jitter=0.0, seed=DEFAULT_SEED):
+    """Periodic [0, L]^2 with n x n square cells, each split along its (0,0)-(1,1)
+    diagonal into two counter-clockwise triangles; K = 2 n^2.
+
+    Unique vertices are the n^2 grid points (periodic images share an id).
+    jitter > 0 moves every unique vertex by independent U[-jitter h, jitter h]
+    offsets in x and y (h = L/n), drawn with splitmix64 (x: counter 2 id,
+    y: counter 2 id + 1).
+
+    Returns a dict: X (n^2, 2) float64 vertex coordinates, EToV (K, 3) int32,
+    shift (K, 3, 2) float64 periodic unwrap offsets (element vertex k of
+    element e sits at X[EToV[e, k]] + shift[e, k]), L (2,) periods, n.
+    """
+    if n < 3:
+        raise ValueError('n >= 3 is needed so that every face has a unique vertex pair')
+    h = L / n
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing='ij')
+    X = np.zeros((n * n, 2))
+    vid = (ii + n * jj).ravel()
+    X[vid, 0] = (ii * h).ravel()
+    X[vid, 1] = (jj * h).ravel()
+    if jitter > 0.0:
+        ids = np.arange(n * n, dtype=np.uint64)
+        X[:, 0] += uniform(2 * ids, seed, -jitter * h, jitter * h)
+        X[:, 1] += uniform(2 * ids + 1, seed, -jitter * h, jitter * h)
+    EToV = np.zeros((2 * n * n, 3), dtype=np.int32)
+    shift = np.zeros((2 * n * n, 3, 2))
+    k = 0
+    for j in range(n):
+        for i in range(n):
+            c00, c10, c11, c01 = (i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)
+            for tri in ((c00, c10, c11), (c00, c11, c01)):
+                for v, (a, b) in enumerate(tri):
+                    EToV[k, v] = (a % n) + n * (b % n)
+                    shift[k, v] = ((a // n) * L, (b // n) * L)
+                k += 1
+    return {'X': X, 'EToV': EToV, 'shift': shift, 'L': np.array([L, L]), 'n': n}
+
+
+def min_altitude(mesh):
+    """Smallest triangle altitude of the mesh at its Lagrangian positions."""
+    P = mesh['X'][mesh['EToV']] + mesh['shift']
+    e = [P[:, (k + 1) % 3] - P[:, k] for k in range(3)]
+    area2 = np.abs(e[0][:, 0] * e[1][:, 1] - e[0][:, 1] * e[1][:, 0])
+    longest = np.max(np.stack([np.hypot(v[:, 0], v[:, 1]) for v in e]), axis=0)
+    return float(np.min(area2 / longest))
+
+
+def cfl_dt(mesh, N, c, cfl):
+    """Run parameter: dt = cfl * h_min / (sqrt(3) c (N+1)^2), with sqrt(3) c the
+    largest characteristic speed and h_min the smallest altitude.  The paper does
+    not define its time step; this helper fixes one, passed to both sides."""
+    return cfl * min_altitude(mesh) / (math.sqrt(3.0) * c * (N + 1) ** 2)
+
+
+def taylor_green(x, y, Ma):
+    """Incompressible 2D Taylor-Green vortex: u = sin x cos y, v = -cos x sin y,
+    rho = 1 + Ma^2/4 (cos 2x + cos 2y).  Returns (rho, u, v)."""
+    u = np.sin(x) * np.cos(y)
+    v = -np.cos(x) * np.sin(y)
+    rho = 1.0 + Ma * Ma * 0.25 * (np.cos(2.0 * x) + np.cos(2.0 * y))
+    return rho, u, v
+
+
+def free_stream(x, y, u0=1.0, v0=0.0):
+    """Uniform flow rho = 1, (u, v) = (u0, v0)."""
+    return np.ones_like(x), np.full_like(x, u0), np.full_like(x, v0)
+
+
+def random_flow(x, y, seed, amp=0.05):
+    """Smooth seeded periodic perturbation of the rest state (for parity tests)."""
+    k = uniform(np.arange(12), seed)
+    rho = 1.0 + amp * (np.sin(x + 6.0 * k[0]) * np.cos(y + 6.0 * k[1]) + 0.5 * np.sin(2 * x + 6.0 * k[2]))
+    u = 0.5 * np.sin(y + 6.0 * k[3]) + 0.3 * np.cos(x + 2 * y + 6.0 * k[4])
+    v = 0.5 * np.cos(x + 6.0 * k[5]) - 0.3 * np.sin(2 * x - y + 6.0 * k[6])
+    return rho, u, v
+
+
+def serving_requests(n=256, rate=50.0, seed=1):
+    """Request stream: Poisson arrivals (mean `rate`/s) with K in
+    {2048, 8192, 32768, 131072} (as n x n x 2 meshes), N in {2, 3, 4, 5},
+    motion amplitude U[0.01, 0.08], period U[0.5, 2], Re U[100, 2000], Ma = 0.1."""
+    ids = np.arange(n, dtype=np.uint64)
+    u = [uniform(8 * ids + k, seed) for k in range(6)]
+    gaps = -np.log1p(-u[0]) / rate
+    arrival = np.cumsum(gaps)
+    Ks = np.array([2048, 8192, 32768, 131072])
+    Ns = np.array([2, 3, 4, 5])
+    out = []
+    for r in range(n):
+        K = int(Ks[min(int(u[1][r] * 4), 3)])
+        out.append({'id': r, 'arrival': float(arrival[r]), 'K': K, 'n': int(round(math.sqrt(K / 2))),
+                    'N': int(Ns[min(int(u[2][r] * 4), 3)]),
+                    'A': 0.01 + 0.07 * float(u[3][r]), 'T': 0.5 + 1.5 * float(u[4][r]),
+                    'Re': 100.0 + 1900.0 * float(u[5][r]), 'Ma': 0.1})
+    return out
