@@ -1,0 +1,149 @@
+/*
+ * gb.h -- C ABI of libgb, the B300 (sm_103a) solver for the arbitrary
+ * Lagrangian-Eulerian (ALE) nodal discontinuous Galerkin form of the 2D
+ * Galerkin-Boltzmann equations with semi-analytic Runge-Kutta (SARK) time
+ * stepping (arXiv 2607.00199, Secs. 2-6).
+ *
+ * Conventions (every entry point):
+ *  - Returns GB_OK (0) or a negative GB_E* code; gb_last_error() gives a
+ *    one-line message for the solver (or the last failed create, with NULL).
+ *  - No call takes ownership of caller memory.  Host pointers are read or
+ *    written during the call only.  The library allocates and owns all of
+ *    the solver's device memory (cudaMalloc in gb_create, freed by
+ *    gb_destroy).
+ *  - All device work is enqueued on the CUDA stream given to gb_create
+ *    (NULL = the legacy default stream).  Calls that return host data
+ *    synchronise that stream; gb_step and gb_rhs only enqueue.
+ *  - Field layout ("canonical"): q[k][f][i], k < n_elem elements, f < 6
+ *    fields, i < Np nodes, row-major, FP64.  Node order: Warp & Blend nodes
+ *    (Warburton 2006) on the reference triangle (-1,-1), (1,-1), (-1,1),
+ *    by rows of constant barycentric coordinate of (-1,1) (bottom row
+ *    first), left to right inside a row; Np = (N+1)(N+2)/2.
+ *  - Fields (Sec. 2): q1 = rho, q2 = rho u / c, q3 = rho v / c, q4..q6 the
+ *    second-order Hermite coefficients; c = sqrt(RT) = 1/Ma, tau = Ma^2/Re
+ *    (lengths and the reference velocity scaled to 1, rho0 = 1).
+ *  - There is no CPU fallback: every computation runs in the library's CUDA
+ *    kernels; without a usable GPU the calls fail with GB_ECUDA.
+ */
+#ifndef GB_H
+#define GB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GB_OK       0
+#define GB_EINVAL  (-1)  /* bad argument (NULL pointer, unsupported N, non-positive Ma/Re/dt ...) */
+#define GB_ENOMEM  (-2)  /* device or host allocation failed */
+#define GB_ECUDA   (-3)  /* a CUDA call failed (message in gb_last_error) */
+#define GB_EMESH   (-4)  /* invalid mesh, or an element with J <= 0 at some stage */
+#define GB_ENAN    (-5)  /* a NaN or Inf appeared in the fields */
+
+#define GB_FP64   0      /* FP64 everywhere (the reference form) */
+#define GB_MIXED  1      /* FP32 perturbation fields around the rest state; FP64 geometry and SARK coefficients */
+
+#define GB_MOTION_STATIC 0
+#define GB_MOTION_SINXY  1
+
+typedef struct gb_solver gb_solver;   /* opaque */
+
+/* Straight-sided periodic triangle mesh (Sec. 3: affine simplices, fixed topology). */
+typedef struct {
+  int32_t dim;               /* must be 2 */
+  int64_t n_vert;            /* number of unique vertices (periodic images share one id) */
+  const double *X;           /* n_vert x 2, Lagrangian (initial) vertex coordinates, host */
+  int64_t n_elem;            /* K */
+  const int32_t *EToV;       /* n_elem x 3 vertex ids, counter-clockwise, host */
+  const double *elem_shift;  /* n_elem x 3 x 2 periodic unwrap offsets (element vertex j of element k
+                                sits at X[EToV[k][j]] + elem_shift[k][j]); NULL = no offsets.  Every
+                                offset must be an integer multiple (|m| <= 7) of one period per direction. */
+} gb_mesh;
+
+/* Prescribed grid motion (Sec. 5 and the free-stream test of Sec. 7.1):
+ * GB_MOTION_SINXY displaces both coordinates of a vertex with Lagrangian
+ * position X by A sin(2 pi t / T) sin(2 pi X / Lx) sin(2 pi Y / Ly). */
+typedef struct {
+  int32_t kind;              /* GB_MOTION_STATIC or GB_MOTION_SINXY */
+  double A, T, Lx, Ly;
+} gb_motion;
+
+/* gb_create: validate the mesh (GB_EMESH if a face is not shared by exactly two
+ * elements or an element has J <= 0), build the order-N reference operators in
+ * FP64 (Sec. 3), upload mesh and operators, allocate the state.  N in 1..6.
+ * Ma > 0, Re > 0.  precision is GB_FP64 or GB_MIXED.  cuda_stream is a
+ * cudaStream_t (NULL = default stream).  The fields start at zero, the vertices
+ * at X, the time at 0, the motion static.  On success *out owns the solver. */
+int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision,
+              void *cuda_stream, gb_solver **out);
+
+/* gb_set_motion: prescribe the vertex velocity d/dt of the displacement above,
+ * evaluated at the Lagrangian X (Sec. 5).  Copied; takes effect at the next step. */
+int gb_set_motion(gb_solver *s, const gb_motion *m);
+
+/* gb_set_fields: upload q (host, canonical layout, K*6*Np doubles) and set the time t. */
+int gb_set_fields(gb_solver *s, const double *q_host, double t);
+
+/* gb_fields: synchronise, check the device status, copy q (canonical FP64) and t
+ * to the host.  In GB_MIXED mode q is the FP32 perturbation plus the rest state,
+ * widened to FP64.  Returns GB_ENAN / GB_EMESH if a step flagged one. */
+int gb_fields(gb_solver *s, double *q_host_out, double *t_out);
+
+/* gb_set_vertices / gb_vertices: current vertex positions x_n (n_vert x 2, host). */
+int gb_set_vertices(gb_solver *s, const double *x_host);
+int gb_vertices(gb_solver *s, double *x_host_out);
+
+/* gb_nodes: physical node coordinates at the current vertex positions, host,
+ * n_elem x Np x 2 (the P1 map of Sec. 3). */
+int gb_nodes(gb_solver *s, double *xy_out);
+
+/* gb_rhs: F = L(q) + Ntilde(q) (Sec. 4 splitting; the stiff -Lambda q part is not
+ * included) for device arrays q_dev, F_dev in canonical layout (K*6*Np; FP64 in
+ * GB_FP64 mode, FP32 perturbation values in GB_MIXED mode), at the current vertex
+ * positions with the grid velocity of time t.  Both arrays are caller-owned
+ * device memory, used on the solver's stream; enqueue only. */
+int gb_rhs(gb_solver *s, double t, const void *q_dev, void *F_dev);
+
+/* gb_step: enqueue nsteps SARK steps of size dt (Sec. 4): per stage, the vertex
+ * positions and velocities (Sec. 5), the geometric factors (GCL), the volume,
+ * surface and cubature terms and the SARK combination.  Enqueue only; errors of
+ * the device computation are reported by gb_sync / gb_fields. */
+int gb_step(gb_solver *s, double dt, int64_t nsteps);
+
+/* gb_sync: synchronise the stream, return and clear the device status
+ * (GB_OK, GB_ENAN or GB_EMESH). */
+int gb_sync(gb_solver *s);
+
+/* gb_info: sizes and derived constants.  Any output pointer may be NULL. */
+int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *n_vert,
+            double *c, double *tau, int64_t *device_bytes);
+
+/* gb_state_ptr: the device address of the current fields (canonical layout, FP64 in
+ * GB_FP64 mode, FP32 perturbations in GB_MIXED mode), owned by the solver, valid
+ * until gb_destroy. */
+int gb_state_ptr(gb_solver *s, void **q_dev);
+
+int gb_destroy(gb_solver *s);
+const char *gb_last_error(gb_solver *s);
+
+/* ---- host-side queries (no GPU needed) ---------------------------------- */
+
+/* gb_reference_operators: the library's order-N reference operators (Sec. 3),
+ * row-major FP64: r, s [Np]; Dr, Ds [Np x Np]; LIFT [Np x 3 Nfp] (face nodes
+ * counter-clockwise: face 0 from (-1,-1) to (1,-1), face 1 to (-1,1), face 2 back);
+ * Icub [Nc x Np]; Pcub [Np x Nc]; cubature points/weights cr, cs, cw [Nc].  Any
+ * output may be NULL; *Nc_out receives Nc (the degree-3N Stroud rule). */
+int gb_reference_operators(int N, double *r, double *s, double *Dr, double *Ds, double *LIFT,
+                           double *Icub, double *Pcub, double *cr, double *cs, double *cw,
+                           int *Nc_out);
+
+/* gb_sark_coefficients: SARK-4 coefficients of Sec. 4 for gamma = -dt/tau <= 0:
+ * E[5] = exp(c_i gamma) (i = 0..3) and exp(gamma); A[16] row-major atilde (strictly
+ * lower); B[4] btilde.  Evaluated through phi-functions (series for |gamma| < 1). */
+int gb_sark_coefficients(double gamma, double *E, double *A, double *B);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB_H */

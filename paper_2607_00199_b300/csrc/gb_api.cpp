@@ -1,0 +1,467 @@
+// C ABI of libgb (declared in include/gb.h): solver lifetime, mesh validation
+// and connectivity, state transfer, and the SARK step driver (Sec. 4) that
+// enqueues the fused stage kernels of gb_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "gb.h"
+#include "gb_internal.h"
+
+namespace gb {
+size_t ops_float_offset(int N);
+}
+
+using gb::MeshRec;
+
+struct gb_solver {
+  int N = 0, Np = 0, Nfp = 0, Nc = 0, precision = GB_FP64;
+  int64_t K = 0, nv = 0;
+  double c = 0, tau = 0, period[2] = {0, 0};
+  cudaStream_t stream = nullptr;
+  int num_sms = 1;
+  std::string err;
+  gb::RefOps ref;
+  gb_motion motion{GB_MOTION_STATIC, 0, 1, 1, 1};
+  double coef_dt = -1.0;
+  gb::SarkCoef co{};
+  size_t elem_bytes = 8;
+  // device memory
+  double *d_ops = nullptr;     // FP64 operator block followed by the FP32 copy
+  MeshRec *d_mesh = nullptr;
+  double *d_X = nullptr, *d_xn = nullptr, *d_shape = nullptr, *d_clock = nullptr;
+  int *d_status = nullptr;
+  void *d_qn = nullptr, *d_b1 = nullptr, *d_b2 = nullptr, *d_F0 = nullptr, *d_acc = nullptr;
+  double *d_tmp = nullptr;     // FP64 staging (GB_MIXED transfers, node coordinates)
+  size_t tmp_bytes = 0;
+  int64_t device_bytes = 0;
+};
+
+static std::string g_create_error;
+
+static int fail(gb_solver *s, int code, const std::string &msg) {
+  if (s) s->err = msg; else g_create_error = msg;
+  return code;
+}
+
+static int cuda_fail(gb_solver *s, cudaError_t e, const char *where) {
+  return fail(s, GB_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+static int dev_alloc(gb_solver *s, void **p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return fail(s, GB_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  s->device_bytes += (int64_t)bytes;
+  return GB_OK;
+}
+
+static void free_all(gb_solver *s) {
+  void *ptrs[] = {s->d_ops, s->d_mesh, s->d_X, s->d_xn, s->d_shape, s->d_clock, s->d_status,
+                  s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+}
+
+static int ensure_tmp(gb_solver *s, size_t bytes) {
+  if (s->tmp_bytes >= bytes) return GB_OK;
+  if (s->d_tmp) {
+    cudaFree(s->d_tmp);
+    s->device_bytes -= (int64_t)s->tmp_bytes;
+    s->d_tmp = nullptr;
+    s->tmp_bytes = 0;
+  }
+  int rc = dev_alloc(s, (void **)&s->d_tmp, bytes);
+  if (rc == GB_OK) s->tmp_bytes = bytes;
+  return rc;
+}
+
+static const double *ops_for(const gb_solver *s) {
+  if (s->precision == GB_FP64) return s->d_ops;
+  return reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(s->d_ops) + gb::ops_float_offset(s->N));
+}
+
+static gb::StageArgs base_args(gb_solver *s) {
+  gb::StageArgs a;
+  memset(&a, 0, sizeof(a));
+  a.xn = s->d_xn;
+  a.shape = s->d_shape;
+  a.mesh = s->d_mesh;
+  a.ops = ops_for(s);
+  a.clock = s->d_clock;
+  a.status = s->d_status;
+  a.K = s->K;
+  a.period[0] = s->period[0];
+  a.period[1] = s->period[1];
+  a.c = s->c;
+  a.inv_tau = 1.0 / s->tau;
+  a.motion_A = (s->motion.kind == GB_MOTION_SINXY) ? s->motion.A : 0.0;
+  a.motion_w = (s->motion.kind == GB_MOTION_SINXY) ? 2.0 * M_PI / s->motion.T : 0.0;
+  a.co = s->co;
+  return a;
+}
+
+static int launch_stage(gb_solver *s, const gb::StageArgs &a) {
+  int rc = s->precision == GB_FP64 ? gb::launch_stage_fp64(s->N, a, s->stream, s->num_sms)
+                                   : gb::launch_stage_fp32(s->N, a, s->stream, s->num_sms);
+  if (rc != 0) return cuda_fail(s, (cudaError_t)rc, "stage kernel launch");
+  return GB_OK;
+}
+
+extern "C" {
+
+int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, void *cuda_stream, gb_solver **out) {
+  if (!out) return fail(nullptr, GB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !mesh->X || !mesh->EToV) return fail(nullptr, GB_EINVAL, "mesh, X or EToV is NULL");
+  if (mesh->dim != 2) return fail(nullptr, GB_EINVAL, "only dim = 2 is supported");
+  if (mesh->n_vert <= 0 || mesh->n_elem <= 0) return fail(nullptr, GB_EINVAL, "empty mesh");
+  if (mesh->n_elem >= (int64_t(1) << 29)) return fail(nullptr, GB_EINVAL, "n_elem must be < 2^29");
+  if (mesh->n_vert >= (int64_t(1) << 31)) return fail(nullptr, GB_EINVAL, "n_vert must be < 2^31");
+  if (N < 1 || N > GB_MAX_N) return fail(nullptr, GB_EINVAL, "N must be in 1..6");
+  if (!(Ma > 0.0) || !(Re > 0.0) || !std::isfinite(Ma) || !std::isfinite(Re))
+    return fail(nullptr, GB_EINVAL, "Ma and Re must be positive and finite");
+  if (precision != GB_FP64 && precision != GB_MIXED) return fail(nullptr, GB_EINVAL, "precision must be GB_FP64 or GB_MIXED");
+
+  const int64_t K = mesh->n_elem, nv = mesh->n_vert;
+  for (int64_t i = 0; i < 3 * K; ++i)
+    if (mesh->EToV[i] < 0 || mesh->EToV[i] >= nv) return fail(nullptr, GB_EINVAL, "EToV entry out of range");
+
+  // periods and integer shift codes
+  std::vector<double> sh(6 * K, 0.0);
+  if (mesh->elem_shift) memcpy(sh.data(), mesh->elem_shift, sizeof(double) * 6 * K);
+  double period[2] = {0.0, 0.0};
+  for (int64_t i = 0; i < 6 * K; ++i) {
+    double v = fabs(sh[i]);
+    int d = (int)(i & 1);
+    if (!std::isfinite(sh[i])) return fail(nullptr, GB_EINVAL, "non-finite elem_shift");
+    if (v > 0.0 && (period[d] == 0.0 || v < period[d])) period[d] = v;
+  }
+  std::vector<MeshRec> rec(K);
+  for (int64_t e = 0; e < K; ++e) {
+    MeshRec &r = rec[e];
+    memset(&r, 0, sizeof(r));
+    for (int k = 0; k < 3; ++k) r.v[k] = mesh->EToV[3 * e + k];
+    for (int k = 0; k < 6; ++k) {
+      double p = period[k & 1];
+      double v = sh[6 * e + k];
+      long m = p > 0.0 ? lround(v / p) : 0;
+      if (labs(m) > 7 || fabs(v - m * p) > 1e-12 * (1.0 + fabs(v)))
+        return fail(nullptr, GB_EINVAL, "elem_shift entries must be small integer multiples of one period per direction");
+      r.shift[k] = (int8_t)m;
+    }
+  }
+  auto vx = [&](int64_t e, int k, int d) { return mesh->X[2 * (int64_t)rec[e].v[k] + d] + rec[e].shift[2 * k + d] * period[d]; };
+  // positive orientation (Sec. 3: all elements positively oriented)
+  for (int64_t e = 0; e < K; ++e) {
+    double J = (vx(e, 1, 0) - vx(e, 0, 0)) * (vx(e, 2, 1) - vx(e, 0, 1)) - (vx(e, 2, 0) - vx(e, 0, 0)) * (vx(e, 1, 1) - vx(e, 0, 1));
+    if (!(J > 0.0)) {
+      char buf[128];
+      snprintf(buf, sizeof(buf), "element %lld is not positively oriented (J <= 0)", (long long)e);
+      return fail(nullptr, GB_EMESH, buf);
+    }
+  }
+  // face connectivity: face f of element e runs from local vertex f to f+1;
+  // every unordered vertex pair must occur on exactly two faces
+  std::unordered_map<uint64_t, int64_t> first;   // key -> 3 e + f of the first face, -1 once paired
+  first.reserve((size_t)(3 * K));
+  for (int64_t e = 0; e < K; ++e)
+    for (int f = 0; f < 3; ++f) {
+      uint64_t a = (uint32_t)rec[e].v[f], b = (uint32_t)rec[e].v[(f + 1) % 3];
+      if (a == b) return fail(nullptr, GB_EMESH, "degenerate face (repeated vertex id)");
+      uint64_t key = a < b ? (a << 32 | b) : (b << 32 | a);
+      auto it = first.find(key);
+      if (it == first.end()) {
+        first.emplace(key, e * 3 + f);
+        continue;
+      }
+      if (it->second < 0) return fail(nullptr, GB_EMESH, "a face is shared by more than two elements");
+      const int64_t e2 = it->second / 3;
+      const int f2 = (int)(it->second % 3);
+      it->second = -1;
+      // opposite traversal and a single translation between the two copies of the edge
+      if (rec[e2].v[f2] != rec[e].v[(f + 1) % 3] || rec[e2].v[(f2 + 1) % 3] != rec[e].v[f])
+        return fail(nullptr, GB_EMESH, "neighbouring elements are not consistently oriented");
+      for (int d = 0; d < 2; ++d) {
+        double ta = vx(e, f, d) - vx(e2, (f2 + 1) % 3, d);
+        double tb = vx(e, (f + 1) % 3, d) - vx(e2, f2, d);
+        if (fabs(ta - tb) > 1e-9 * (1.0 + fabs(period[d]))) return fail(nullptr, GB_EMESH, "periodic face copies do not match");
+      }
+      rec[e].nbr[f] = (int32_t)((e2 << 2) | f2);
+      rec[e2].nbr[f2] = (int32_t)((e << 2) | f);
+    }
+  for (const auto &kv : first)
+    if (kv.second >= 0)
+      return fail(nullptr, GB_EMESH, "the mesh is not closed: a face has no neighbour (only periodic meshes are supported)");
+
+  gb_solver *s = new gb_solver();
+  s->N = N;
+  s->Np = (N + 1) * (N + 2) / 2;
+  s->Nfp = N + 1;
+  s->K = K;
+  s->nv = nv;
+  s->precision = precision;
+  s->c = 1.0 / Ma;
+  s->tau = Ma * Ma / Re;
+  s->period[0] = period[0];
+  s->period[1] = period[1];
+  s->stream = (cudaStream_t)cuda_stream;
+  s->elem_bytes = precision == GB_FP64 ? sizeof(double) : sizeof(float);
+  if (!gb::build_reference(N, s->ref)) {
+    delete s;
+    return fail(nullptr, GB_EINVAL, "reference operator construction failed");
+  }
+  s->Nc = s->ref.Nc;
+
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ce != cudaSuccess) {
+    delete s;
+    return fail(nullptr, GB_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(ce));
+  }
+  int rc = gb::upload_ops(N, s->ref, &s->d_ops, s->stream);
+  if (rc != 0) {
+    std::string m = std::string("operator upload: ") + cudaGetErrorString((cudaError_t)rc);
+    delete s;
+    return fail(nullptr, GB_ECUDA, m);
+  }
+  const size_t fbytes = (size_t)K * 6 * s->Np * s->elem_bytes;
+  void **fields[] = {&s->d_qn, &s->d_b1, &s->d_b2, &s->d_F0, &s->d_acc};
+  int arc = GB_OK;
+  arc = arc ? arc : dev_alloc(s, (void **)&s->d_mesh, sizeof(MeshRec) * K);
+  arc = arc ? arc : dev_alloc(s, (void **)&s->d_X, sizeof(double) * 2 * nv);
+  arc = arc ? arc : dev_alloc(s, (void **)&s->d_xn, sizeof(double) * 2 * nv);
+  arc = arc ? arc : dev_alloc(s, (void **)&s->d_shape, sizeof(double) * 2 * nv);
+  arc = arc ? arc : dev_alloc(s, (void **)&s->d_clock, sizeof(double) * 2);
+  arc = arc ? arc : dev_alloc(s, (void **)&s->d_status, sizeof(int));
+  for (void **p : fields) arc = arc ? arc : dev_alloc(s, p, fbytes);
+  if (arc != GB_OK) {
+    g_create_error = s->err;
+    free_all(s);
+    delete s;
+    return arc;
+  }
+  double clock0[2] = {0.0, 0.0};
+  int zero = 0;
+  ce = cudaMemcpyAsync(s->d_mesh, rec.data(), sizeof(MeshRec) * K, cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_X, mesh->X, sizeof(double) * 2 * nv, cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_xn, mesh->X, sizeof(double) * 2 * nv, cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->d_shape, 0, sizeof(double) * 2 * nv, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_clock, clock0, sizeof(clock0), cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream);
+  for (void **p : fields)
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(*p, 0, fbytes, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) {
+    cuda_fail(s, ce, "gb_create upload");
+    g_create_error = s->err;
+    free_all(s);
+    delete s;
+    return GB_ECUDA;
+  }
+  *out = s;
+  return GB_OK;
+}
+
+int gb_set_motion(gb_solver *s, const gb_motion *m) {
+  if (!s || !m) return fail(s, GB_EINVAL, "NULL argument");
+  if (m->kind != GB_MOTION_STATIC && m->kind != GB_MOTION_SINXY) return fail(s, GB_EINVAL, "unknown motion kind");
+  if (m->kind == GB_MOTION_SINXY) {
+    if (!(m->T > 0.0) || !(m->Lx != 0.0) || !(m->Ly != 0.0) || !std::isfinite(m->A) || !std::isfinite(m->T))
+      return fail(s, GB_EINVAL, "GB_MOTION_SINXY needs T > 0, Lx != 0, Ly != 0 and finite A");
+  }
+  s->motion = *m;
+  int rc = gb::launch_shape(s->d_X, s->d_shape, s->nv, m->kind, m->Lx, m->Ly, s->stream);
+  if (rc != 0) return cuda_fail(s, (cudaError_t)rc, "shape kernel");
+  return GB_OK;
+}
+
+int gb_set_fields(gb_solver *s, const double *q_host, double t) {
+  if (!s || !q_host) return fail(s, GB_EINVAL, "NULL argument");
+  if (!std::isfinite(t)) return fail(s, GB_EINVAL, "t must be finite");
+  const size_t n = (size_t)s->K * 6 * s->Np;
+  cudaError_t ce;
+  if (s->precision == GB_FP64) {
+    ce = cudaMemcpyAsync(s->d_qn, q_host, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  } else {
+    int rc = ensure_tmp(s, n * sizeof(double));
+    if (rc) return rc;
+    ce = cudaMemcpyAsync(s->d_tmp, q_host, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
+    if (ce == cudaSuccess) {
+      int lr = gb::launch_to_fp32_perturbation(s->d_tmp, (float *)s->d_qn, s->K, s->Np, s->stream);
+      if (lr) ce = (cudaError_t)lr;
+    }
+  }
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_clock, &t, sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_fields");
+  return GB_OK;
+}
+
+int gb_sync(gb_solver *s) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  int status = 0, zero = 0;
+  cudaError_t ce = cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_sync");
+  if (status & GB_STATUS_MESH) return fail(s, GB_EMESH, "an element reached J <= 0 during a stage");
+  if (status & GB_STATUS_NAN) return fail(s, GB_ENAN, "a NaN or Inf appeared in the fields");
+  return GB_OK;
+}
+
+int gb_fields(gb_solver *s, double *q_host_out, double *t_out) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  int st = gb_sync(s);
+  const size_t n = (size_t)s->K * 6 * s->Np;
+  cudaError_t ce = cudaSuccess;
+  if (q_host_out) {
+    if (s->precision == GB_FP64) {
+      ce = cudaMemcpyAsync(q_host_out, s->d_qn, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    } else {
+      int rc = ensure_tmp(s, n * sizeof(double));
+      if (rc) return rc;
+      int lr = gb::launch_from_fp32_perturbation((const float *)s->d_qn, s->d_tmp, s->K, s->Np, s->stream);
+      ce = lr ? (cudaError_t)lr : cudaMemcpyAsync(q_host_out, s->d_tmp, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+    }
+  }
+  double clk[2] = {0, 0};
+  if (ce == cudaSuccess) ce = cudaMemcpyAsync(clk, s->d_clock, sizeof(clk), cudaMemcpyDeviceToHost, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_fields");
+  if (t_out) *t_out = clk[0];
+  return st;
+}
+
+int gb_set_vertices(gb_solver *s, const double *x_host) {
+  if (!s || !x_host) return fail(s, GB_EINVAL, "NULL argument");
+  cudaError_t ce = cudaMemcpyAsync(s->d_xn, x_host, sizeof(double) * 2 * s->nv, cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_vertices");
+  return GB_OK;
+}
+
+int gb_vertices(gb_solver *s, double *x_host_out) {
+  if (!s || !x_host_out) return fail(s, GB_EINVAL, "NULL argument");
+  cudaError_t ce = cudaMemcpyAsync(x_host_out, s->d_xn, sizeof(double) * 2 * s->nv, cudaMemcpyDeviceToHost, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_vertices");
+  return GB_OK;
+}
+
+int gb_nodes(gb_solver *s, double *xy_out) {
+  if (!s || !xy_out) return fail(s, GB_EINVAL, "NULL argument");
+  const size_t n = (size_t)s->K * s->Np * 2;
+  int rc = ensure_tmp(s, n * sizeof(double));
+  if (rc) return rc;
+  int lr = gb::launch_nodes(s->N, s->d_ops, s->d_xn, s->d_mesh, s->period[0], s->period[1], s->K, s->d_tmp, s->stream);
+  cudaError_t ce = lr ? (cudaError_t)lr : cudaMemcpyAsync(xy_out, s->d_tmp, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_nodes");
+  return GB_OK;
+}
+
+int gb_rhs(gb_solver *s, double t, const void *q_dev, void *F_dev) {
+  if (!s || !q_dev || !F_dev) return fail(s, GB_EINVAL, "NULL argument");
+  if (!std::isfinite(t)) return fail(s, GB_EINVAL, "t must be finite");
+  gb::StageArgs a = base_args(s);
+  a.stage = -1;
+  a.qin = q_dev;
+  a.qn = q_dev;
+  a.Fout = F_dev;
+  a.rhs_time = t;
+  return launch_stage(s, a);
+}
+
+int gb_step(gb_solver *s, double dt, int64_t nsteps) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(s, GB_EINVAL, "dt must be positive and finite");
+  if (nsteps < 0) return fail(s, GB_EINVAL, "nsteps must be >= 0");
+  if (dt != s->coef_dt) {
+    double E[5], A[16], B[4];
+    gb::sark_coefficients(0.0, E, A, B);
+    memcpy(s->co.E[0], E, sizeof(E)); memcpy(s->co.A[0], A, sizeof(A)); memcpy(s->co.B[0], B, sizeof(B));
+    gb::sark_coefficients(-dt / s->tau, E, A, B);
+    memcpy(s->co.E[1], E, sizeof(E)); memcpy(s->co.A[1], A, sizeof(A)); memcpy(s->co.B[1], B, sizeof(B));
+    s->coef_dt = dt;
+  }
+  gb::StageArgs a = base_args(s);
+  a.dt = dt;
+  void *bufs_in[4] = {s->d_qn, s->d_b1, s->d_b2, s->d_b1};
+  void *bufs_out[4] = {s->d_b1, s->d_b2, s->d_b1, s->d_qn};
+  for (int64_t k = 0; k < nsteps; ++k) {
+    for (int st = 0; st < 4; ++st) {
+      a.stage = st;
+      a.qin = bufs_in[st];
+      a.qn = s->d_qn;
+      a.qout = bufs_out[st];
+      a.F0 = s->d_F0;
+      a.acc = s->d_acc;
+      int rc = launch_stage(s, a);
+      if (rc) return rc;
+    }
+    int rc = gb::launch_vertex_update(a, s->nv, s->stream);
+    if (rc) return cuda_fail(s, (cudaError_t)rc, "vertex update launch");
+  }
+  return GB_OK;
+}
+
+int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *n_vert, double *c, double *tau,
+            int64_t *device_bytes) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (Np) *Np = s->Np;
+  if (Nfp) *Nfp = s->Nfp;
+  if (Nc) *Nc = s->Nc;
+  if (n_elem) *n_elem = s->K;
+  if (n_vert) *n_vert = s->nv;
+  if (c) *c = s->c;
+  if (tau) *tau = s->tau;
+  if (device_bytes) *device_bytes = s->device_bytes;
+  return GB_OK;
+}
+
+int gb_state_ptr(gb_solver *s, void **q_dev) {
+  if (!s || !q_dev) return fail(s, GB_EINVAL, "NULL argument");
+  *q_dev = s->d_qn;
+  return GB_OK;
+}
+
+int gb_destroy(gb_solver *s) {
+  if (!s) return GB_OK;
+  if (s->stream) cudaStreamSynchronize(s->stream); else cudaDeviceSynchronize();
+  free_all(s);
+  delete s;
+  return GB_OK;
+}
+
+const char *gb_last_error(gb_solver *s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+
+int gb_reference_operators(int N, double *r, double *s_, double *Dr, double *Ds, double *LIFT, double *Icub,
+                           double *Pcub, double *cr, double *cs, double *cw, int *Nc_out) {
+  gb::RefOps R;
+  if (!gb::build_reference(N, R)) return GB_EINVAL;
+  auto put = [](const std::vector<double> &v, double *o) {
+    if (o) memcpy(o, v.data(), v.size() * sizeof(double));
+  };
+  put(R.r, r); put(R.s, s_); put(R.Dr, Dr); put(R.Ds, Ds); put(R.LIFT, LIFT);
+  put(R.I, Icub); put(R.P, Pcub); put(R.cr, cr); put(R.cs, cs); put(R.cw, cw);
+  if (Nc_out) *Nc_out = R.Nc;
+  return GB_OK;
+}
+
+int gb_sark_coefficients(double gamma, double *E, double *A, double *B) {
+  if (!E || !A || !B) return GB_EINVAL;
+  if (!(gamma <= 0.0) || !std::isfinite(gamma)) return GB_EINVAL;
+  gb::sark_coefficients(gamma, E, A, B);
+  return GB_OK;
+}
+
+}  // extern "C"

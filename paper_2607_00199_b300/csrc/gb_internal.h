@@ -1,0 +1,92 @@
+// Internal declarations shared by the host API (gb_api.cpp), the reference
+// builder (gb_reference.cpp) and the CUDA kernels (gb_kernels.cu).
+#ifndef GB_INTERNAL_H
+#define GB_INTERNAL_H
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "gb.h"
+
+#define GB_MAX_N 6
+
+// device status bits (OR-ed by the kernels, read by gb_sync / gb_fields)
+#define GB_STATUS_NAN  1
+#define GB_STATUS_MESH 2
+
+namespace gb {
+
+// Reference operators of order N, FP64, row-major (see gb_reference.cpp).
+struct RefOps {
+  int N = 0, Np = 0, Nfp = 0, Nc = 0;
+  std::vector<double> r, s;      // Np
+  std::vector<double> Dr, Ds;    // Np x Np
+  std::vector<double> LIFT;      // Np x 3Nfp
+  std::vector<double> I, P;      // Nc x Np, Np x Nc
+  std::vector<double> cr, cs, cw;
+  std::vector<int> fmask;        // 3 x Nfp, counter-clockwise along each face
+};
+
+bool build_reference(int N, RefOps &R);
+void sark_coefficients(double gamma, double E[5], double A[16], double B[4]);
+
+// Per-element mesh record, 32 bytes: vertex ids, face neighbours packed as
+// (neighbour element << 2 | neighbour face), and periodic shifts of the three
+// vertices as signed multiples of the periods (x then y per vertex).
+struct __attribute__((aligned(16))) MeshRec {
+  int32_t v[3];
+  int32_t nbr[3];
+  int8_t shift[6];
+  int8_t pad[2];
+};
+static_assert(sizeof(MeshRec) == 32, "MeshRec must be 32 bytes");
+
+// SARK coefficients for the two field classes (0: fields 1-3, gamma = 0;
+// 1: fields 4-6, gamma = -dt/tau), plus the RK4 vertex tableau factors.
+struct SarkCoef {
+  double E[2][5];
+  double A[2][16];
+  double B[2][4];
+};
+
+// Everything a stage kernel needs, passed by value.
+struct StageArgs {
+  const void *qin;      // q_i: self values and neighbour traces
+  const void *qn;       // q_n
+  void *qout;           // q_{i+1}, or q_{n+1} at the last stage (may alias qn)
+  void *F0;             // F_0 (written at stage 0, read at stages 1-2)
+  void *acc;            // running btilde combination
+  void *Fout;           // right-hand side output (rhs-only mode)
+  const double *xn;     // current vertex positions, n_vert x 2
+  const double *shape;  // vertex velocity shape S(X), n_vert x 2
+  const MeshRec *mesh;
+  const double *ops;    // device copy of the operators (layout in gb_kernels.cu)
+  const double *clock;  // device time t_n
+  int *status;
+  int64_t K;
+  double period[2];
+  double c, inv_tau;
+  double dt;
+  // grid velocity of stage i at a vertex: gfac[i] * S(X); stage position
+  // x_i = x_n + xfac[i] * S(X).  Derived per block from the clock.
+  double motion_A, motion_w;   // A and 2 pi / T (A = 0: static)
+  int stage;                   // -1: rhs only, 0..3: SARK stage
+  double rhs_time;             // rhs-only mode: evaluate the grid velocity at this time
+  SarkCoef co;
+};
+
+// Launchers (gb_kernels.cu).  Return a cudaError_t value as int.
+int launch_stage_fp64(int N, const StageArgs &a, void *stream, int num_sms);
+int launch_stage_fp32(int N, const StageArgs &a, void *stream, int num_sms);
+int launch_vertex_update(const StageArgs &a, int64_t n_vert, void *stream);
+int launch_shape(const double *X, double *shape, int64_t n_vert, int kind, double Lx, double Ly, void *stream);
+int launch_nodes(int N, const double *ops, const double *xn, const MeshRec *mesh, double px, double py,
+                 int64_t K, double *out, void *stream);
+int launch_to_fp32_perturbation(const double *q64, float *q32, int64_t K, int Np, void *stream);
+int launch_from_fp32_perturbation(const float *q32, double *q64, int64_t K, int Np, void *stream);
+int upload_ops(int N, const RefOps &R, double **dev_ops, void *stream);
+
+}  // namespace gb
+
+#endif

@@ -1,0 +1,203 @@
+"""Thin ctypes binding of libgb (C ABI in include/gb.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Importing this module loads libgb.so and fails loudly if the
+library has not been built (python -m paper_2607_00199_b300.build); there is
+no fallback implementation.
+
+Device arrays may be passed as torch CUDA tensors (their data_ptr() is used)
+or as raw integer addresses.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, 'libgb.so')
+
+GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_EMESH, GB_ENAN = 0, -1, -2, -3, -4, -5
+GB_FP64, GB_MIXED = 0, 1
+GB_MOTION_STATIC, GB_MOTION_SINXY = 0, 1
+_NAMES = {GB_EINVAL: 'GB_EINVAL', GB_ENOMEM: 'GB_ENOMEM', GB_ECUDA: 'GB_ECUDA', GB_EMESH: 'GB_EMESH', GB_ENAN: 'GB_ENAN'}
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class GbMesh(ctypes.Structure):
+    _fields_ = [('dim', ctypes.c_int32), ('n_vert', ctypes.c_int64), ('X', _dp),
+                ('n_elem', ctypes.c_int64), ('EToV', _ip), ('elem_shift', _dp)]
+
+
+class GbMotion(ctypes.Structure):
+    _fields_ = [('kind', ctypes.c_int32), ('A', ctypes.c_double), ('T', ctypes.c_double),
+                ('Lx', ctypes.c_double), ('Ly', ctypes.c_double)]
+
+
+class GBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__('%s: %s' % (_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError('libgb.so is not built (run python -m paper_2607_00199_b300.build): %s' % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, c_int, c_double = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        'gb_create': ([ctypes.POINTER(GbMesh), c_int, c_double, c_double, c_int, vp, ctypes.POINTER(vp)], c_int),
+        'gb_set_motion': ([vp, ctypes.POINTER(GbMotion)], c_int),
+        'gb_set_fields': ([vp, _dp, c_double], c_int),
+        'gb_fields': ([vp, _dp, _dp], c_int),
+        'gb_set_vertices': ([vp, _dp], c_int),
+        'gb_vertices': ([vp, _dp], c_int),
+        'gb_nodes': ([vp, _dp], c_int),
+        'gb_rhs': ([vp, c_double, vp, vp], c_int),
+        'gb_step': ([vp, c_double, i64], c_int),
+        'gb_sync': ([vp], c_int),
+        'gb_info': ([vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                     ctypes.POINTER(i64), ctypes.POINTER(i64), _dp, _dp, ctypes.POINTER(i64)], c_int),
+        'gb_state_ptr': ([vp, ctypes.POINTER(vp)], c_int),
+        'gb_destroy': ([vp], c_int),
+        'gb_last_error': ([vp], ctypes.c_char_p),
+        'gb_reference_operators': ([c_int] + [_dp] * 10 + [ctypes.POINTER(c_int)], c_int),
+        'gb_sark_coefficients': ([c_double, _dp, _dp, _dp], c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+lib = _load()
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _addr(x):
+    """Device address of a torch tensor or an int."""
+    if x is None:
+        return None
+    if hasattr(x, 'data_ptr'):
+        return ctypes.c_void_p(x.data_ptr())
+    return ctypes.c_void_p(int(x))
+
+
+def _check(rc, handle=None):
+    if rc != GB_OK:
+        raise GBError(rc, lib.gb_last_error(handle).decode())
+    return rc
+
+
+def reference_operators(N):
+    """The library's order-N reference operators (host computation, no GPU)."""
+    Np, Nfp = (N + 1) * (N + 2) // 2, N + 1
+    nc = ctypes.c_int(0)
+    _check(lib.gb_reference_operators(N, *([None] * 10), ctypes.byref(nc)))
+    Nc = nc.value
+    out = {'r': np.zeros(Np), 's': np.zeros(Np), 'Dr': np.zeros((Np, Np)), 'Ds': np.zeros((Np, Np)),
+           'LIFT': np.zeros((Np, 3 * Nfp)), 'I': np.zeros((Nc, Np)), 'P': np.zeros((Np, Nc)),
+           'cr': np.zeros(Nc), 'cs': np.zeros(Nc), 'cw': np.zeros(Nc)}
+    keys = ['r', 's', 'Dr', 'Ds', 'LIFT', 'I', 'P', 'cr', 'cs', 'cw']
+    _check(lib.gb_reference_operators(N, *[_ptr(out[k]) for k in keys], ctypes.byref(nc)))
+    out['Nc'] = Nc
+    return out
+
+
+def sark_coefficients(gamma):
+    """(E[5], A[4,4], B[4]) from the library (host computation, no GPU)."""
+    E, A, B = np.zeros(5), np.zeros(16), np.zeros(4)
+    _check(lib.gb_sark_coefficients(float(gamma), _ptr(E), _ptr(A), _ptr(B)))
+    return E, A.reshape(4, 4), B
+
+
+class Solver:
+    """Owns one gb_solver.  mesh is a dict with X, EToV, shift (see inputs.py)."""
+
+    def __init__(self, mesh, N, Ma, Re, precision=GB_FP64, stream=None):
+        self._X = np.ascontiguousarray(mesh['X'], dtype=np.float64)
+        self._EToV = np.ascontiguousarray(mesh['EToV'], dtype=np.int32)
+        shift = mesh.get('shift')
+        self._shift = None if shift is None else np.ascontiguousarray(shift, dtype=np.float64)
+        m = GbMesh(2, self._X.shape[0], _ptr(self._X), self._EToV.shape[0],
+                   self._EToV.ctypes.data_as(_ip), None if self._shift is None else _ptr(self._shift))
+        h = ctypes.c_void_p(None)
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        _check(lib.gb_create(ctypes.byref(m), int(N), float(Ma), float(Re), int(precision), st, ctypes.byref(h)))
+        self.h = h
+        self.N = int(N)
+        self.precision = int(precision)
+        np_, nfp, nc = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        K, nv, c, tau, nb = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+        _check(lib.gb_info(h, ctypes.byref(np_), ctypes.byref(nfp), ctypes.byref(nc), ctypes.byref(K),
+                           ctypes.byref(nv), ctypes.byref(c), ctypes.byref(tau), ctypes.byref(nb)), h)
+        self.Np, self.Nfp, self.Nc = np_.value, nfp.value, nc.value
+        self.K, self.nv, self.c, self.tau = K.value, nv.value, c.value, tau.value
+        self.device_bytes = nb.value
+
+    def _c(self, rc):
+        return _check(rc, self.h)
+
+    def set_motion(self, A=0.0, T=1.0, Lx=2 * np.pi, Ly=2 * np.pi, kind=None):
+        if kind is None:
+            kind = GB_MOTION_SINXY if A != 0.0 else GB_MOTION_STATIC
+        m = GbMotion(kind, float(A), float(T), float(Lx), float(Ly))
+        self._c(lib.gb_set_motion(self.h, ctypes.byref(m)))
+
+    def set_fields(self, q, t=0.0):
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        if q.size != self.K * 6 * self.Np:
+            raise ValueError('q must hold K*6*Np values')
+        self._c(lib.gb_set_fields(self.h, _ptr(q), float(t)))
+
+    def fields(self, out=None):
+        q = out if out is not None else np.empty((self.K, 6, self.Np))
+        t = ctypes.c_double()
+        self._c(lib.gb_fields(self.h, _ptr(q), ctypes.byref(t)))
+        return q, t.value
+
+    def set_vertices(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        if x.size != 2 * self.nv:
+            raise ValueError('x must hold n_vert*2 values')
+        self._c(lib.gb_set_vertices(self.h, _ptr(x)))
+
+    def vertices(self):
+        x = np.empty((self.nv, 2))
+        self._c(lib.gb_vertices(self.h, _ptr(x)))
+        return x
+
+    def nodes(self):
+        xy = np.empty((self.K, self.Np, 2))
+        self._c(lib.gb_nodes(self.h, _ptr(xy)))
+        return xy
+
+    def rhs(self, t, q_dev, F_dev):
+        self._c(lib.gb_rhs(self.h, float(t), _addr(q_dev), _addr(F_dev)))
+
+    def step(self, dt, nsteps=1):
+        self._c(lib.gb_step(self.h, float(dt), int(nsteps)))
+
+    def sync(self):
+        self._c(lib.gb_sync(self.h))
+
+    def state_ptr(self):
+        p = ctypes.c_void_p()
+        self._c(lib.gb_state_ptr(self.h, ctypes.byref(p)))
+        return p.value
+
+    def close(self):
+        if getattr(self, 'h', None) is not None and self.h.value is not None:
+            lib.gb_destroy(self.h)
+            self.h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,212 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle,
+element by element on the same seeded inputs.
+
+Tolerances (FP64 path): relative L2 <= 1e-12 for one right-hand side and
+<= 1e-10 after 100 SARK steps.  Mixed path: relative L2 of the fields against
+the FP64 oracle <= 1e-5 (also reported relative to the perturbation size).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import physics
+from oracle.solver import Motion, OracleSolver
+from paper_2607_00199_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip('torch')
+if not torch.cuda.is_available():
+    pytest.skip('needs a CUDA GPU', allow_module_level=True)
+
+from paper_2607_00199_b300 import gb  # noqa: E402  (loads libgb.so; fails loudly if missing)
+
+REST = np.array([1.0, 0, 0, 0, 0, 0])
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def oracle_state(o, xv, flow):
+    xn = o.node_coords(xv)
+    rho, u, v = flow(xn[..., 0], xn[..., 1])
+    return np.ascontiguousarray(physics.equilibrium_state(rho, u, v, o.c).transpose(0, 2, 1))
+
+
+def make_pair(n, N, Ma, Re, A, T, jitter=0.0, precision=gb.GB_FP64, L=2 * math.pi):
+    mesh = inputs.periodic_square_mesh(n, L=L, jitter=jitter)
+    o = OracleSolver(mesh, N, Ma=Ma, Re=Re, motion=Motion(A, T, L, L))
+    s = gb.Solver(mesh, N, Ma, Re, precision=precision, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_motion(A, T, L, L)
+    return mesh, o, s
+
+
+def gpu_rhs(s, q, t):
+    dt = torch.float64 if s.precision == gb.GB_FP64 else torch.float32
+    qq = q - REST[None, :, None] if s.precision == gb.GB_MIXED else q
+    qd = torch.from_numpy(np.ascontiguousarray(qq)).to('cuda', dt)
+    Fd = torch.empty_like(qd)
+    s.rhs(t, qd, Fd)
+    torch.cuda.synchronize()
+    return Fd.double().cpu().numpy()
+
+
+@pytest.mark.parametrize('N', [1, 2, 3, 4, 5, 6])
+def test_rhs_parity_all_orders_ragged(N):
+    # n = 5: K = 50 elements, not a multiple of any tile size; jittered, moved vertices
+    mesh, o, s = make_pair(5, N, 0.1, 100.0, 0.05, 1.0, jitter=0.1)
+    t = 0.3
+    xv = o.X + o.motion.displacement(o.X, t)
+    s.set_vertices(xv)
+    q = oracle_state(o, xv, lambda x, y: inputs.random_flow(x, y, 11 + N))
+    F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
+    F_gpu = gpu_rhs(s, q, t)
+    assert rel_l2(F_gpu, F_or) <= 1e-12
+    for f in range(6):
+        assert rel_l2(F_gpu[:, f], F_or[:, f]) <= 1e-11, f
+
+
+def test_rhs_parity_cfg1():
+    # 2D moving Taylor-Green vortex: 16x16 quads -> K = 512, N = 3, Ma 0.1, Re 100
+    mesh, o, s = make_pair(16, 3, 0.1, 100.0, 0.05, 1.0)
+    t = 0.17
+    xv = o.X + o.motion.displacement(o.X, t)
+    s.set_vertices(xv)
+    q = oracle_state(o, xv, lambda x, y: inputs.taylor_green(x, y, 0.1))
+    F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
+    assert rel_l2(gpu_rhs(s, q, t), F_or) <= 1e-12
+
+
+def test_nodes_match_oracle():
+    mesh, o, s = make_pair(6, 4, 0.1, 100.0, 0.05, 1.0, jitter=0.1)
+    xv = o.X + o.motion.displacement(o.X, 0.2)
+    s.set_vertices(xv)
+    np.testing.assert_allclose(s.nodes(), o.node_coords(xv), atol=1e-14)
+
+
+def run_both(n, N, Ma, Re, A, T, nsteps, flow, jitter=0.0, precision=gb.GB_FP64, cfl=0.5):
+    mesh, o, s = make_pair(n, N, Ma, Re, A, T, jitter=jitter, precision=precision)
+    q0 = oracle_state(o, o.X, flow)
+    dt = inputs.cfl_dt(mesh, N, o.c, cfl)
+    s.set_fields(q0, 0.0)
+    s.step(dt, nsteps)
+    q_gpu, t_gpu = s.fields()
+    x_gpu = s.vertices()
+    q_or, x_or, t_or = o.run(q0, o.X.copy(), 0.0, dt, nsteps)
+    return q_gpu, q_or, x_gpu, x_or, t_gpu, t_or, q0
+
+
+def test_step_parity_cfg1_100_steps():
+    tg = lambda x, y: inputs.taylor_green(x, y, 0.1)
+    q_gpu, q_or, x_gpu, x_or, t_gpu, t_or, q0 = run_both(16, 3, 0.1, 100.0, 0.05, 1.0, 100, tg)
+    assert abs(t_gpu - t_or) <= 1e-15 * max(1.0, t_or)
+    np.testing.assert_allclose(x_gpu, x_or, atol=1e-13)
+    assert rel_l2(q_gpu, q_or) <= 1e-10
+    assert rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-10
+
+
+@pytest.mark.parametrize('u0,v0', [(1.0, 0.0), (1.0, 1.0)])
+def test_free_stream_gcl_gpu(u0, v0):
+    fs = lambda x, y: inputs.free_stream(x, y, u0, v0)
+    q_gpu, q_or, x_gpu, x_or, t_gpu, t_or, q0 = run_both(16, 3, 0.1, 100.0, 0.05, 1.0, 100, fs)
+    assert np.abs(x_gpu - x_or).max() < 1e-13 and np.abs(x_gpu - mesh_X(16)).max() > 1e-3
+    assert np.abs(q_gpu - q0).max() <= 1e-13
+
+
+def mesh_X(n):
+    return inputs.periodic_square_mesh(n)['X']
+
+
+def test_full_size_cfg2_rhs_and_step():
+    # 256x256 quads -> K = 131072 jittered triangles, N = 4, Ma 0.1, Re 1000: the benchmark workload
+    mesh, o, s = make_pair(256, 4, 0.1, 1000.0, 0.05, 1.0, jitter=0.1)
+    q0 = oracle_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1))
+    t = 0.0
+    F_or = o.rhs(q0, o.X, o.motion.velocity(o.X, t))
+    assert rel_l2(gpu_rhs(s, q0, t), F_or) <= 1e-12
+    dt = inputs.cfl_dt(mesh, 4, o.c, 0.5)
+    s.set_fields(q0, 0.0)
+    s.step(dt, 1)
+    q_gpu, _ = s.fields()
+    q_or, x_or = o.step(q0, o.X.copy(), 0.0, dt)
+    assert rel_l2(q_gpu, q_or) <= 1e-11
+    np.testing.assert_allclose(s.vertices(), x_or, atol=1e-13)
+
+
+@pytest.mark.parametrize('N', [2, 5])
+def test_step_parity_other_orders(N):
+    flow = lambda x, y: inputs.random_flow(x, y, 3)
+    q_gpu, q_or, *_ = run_both(7, N, 0.1, 300.0, 0.04, 0.6, 20, flow, jitter=0.1)
+    assert rel_l2(q_gpu, q_or) <= 1e-10
+
+
+def test_smallest_mesh():
+    # n = 3: K = 18, every element is on the periodic boundary
+    flow = lambda x, y: inputs.random_flow(x, y, 5)
+    q_gpu, q_or, *_ = run_both(3, 3, 0.1, 100.0, 0.05, 1.0, 10, flow)
+    assert rel_l2(q_gpu, q_or) <= 1e-11
+
+
+def test_mixed_precision_error_cfg1():
+    tg = lambda x, y: inputs.taylor_green(x, y, 0.1)
+    q_gpu, q_or, x_gpu, x_or, *_ = run_both(16, 3, 0.1, 100.0, 0.05, 1.0, 100, tg, precision=gb.GB_MIXED)
+    np.testing.assert_allclose(x_gpu, x_or, atol=1e-13)     # geometry stays FP64
+    assert rel_l2(q_gpu, q_or) <= 1e-5
+    assert rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
+
+
+def test_mixed_rhs_matches_fp64_rhs():
+    mesh, o, s = make_pair(8, 4, 0.1, 100.0, 0.05, 1.0, jitter=0.1, precision=gb.GB_MIXED)
+    xv = o.X + o.motion.displacement(o.X, 0.1)
+    s.set_vertices(xv)
+    q = oracle_state(o, xv, lambda x, y: inputs.taylor_green(x, y, 0.1))
+    F_or = o.rhs(q, xv, o.motion.velocity(o.X, 0.1))
+    assert rel_l2(gpu_rhs(s, q, 0.1), F_or) <= 1e-5
+
+
+def test_nan_is_reported():
+    mesh, o, s = make_pair(6, 3, 0.1, 100.0, 0.0, 1.0)
+    q = oracle_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1))
+    q[3, 2, 1] = np.nan
+    s.set_fields(q, 0.0)
+    s.step(1e-4, 2)
+    with pytest.raises(gb.GBError) as ei:
+        s.fields()
+    assert ei.value.code == gb.GB_ENAN
+    s.set_fields(oracle_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1)), 0.0)
+    s.step(1e-4, 1)
+    s.fields()       # status was cleared; the solver is usable again
+
+
+def test_tangled_mesh_is_reported():
+    # amplitude larger than the cell size tangles the mesh within a quarter period
+    mesh, o, s = make_pair(8, 2, 0.1, 100.0, 1.5, 1.0)
+    s.set_fields(oracle_state(o, o.X, lambda x, y: inputs.free_stream(x, y)), 0.0)
+    s.step(0.01, 30)
+    with pytest.raises(gb.GBError) as ei:
+        s.fields()
+    assert ei.value.code == gb.GB_EMESH
+
+
+def test_checkpoint_resume_is_bitwise():
+    mesh, o, s = make_pair(10, 3, 0.1, 100.0, 0.05, 1.0, jitter=0.1)
+    q0 = oracle_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1))
+    dt = inputs.cfl_dt(mesh, 3, o.c, 0.5)
+    s.set_fields(q0, 0.0)
+    s.step(dt, 100)
+    q100, t100 = s.fields()
+    s.set_fields(q0, 0.0)
+    s.set_vertices(o.X)
+    s.step(dt, 50)
+    q50, t50 = s.fields()
+    x50 = s.vertices()
+    s2 = gb.Solver(mesh, 3, 0.1, 100.0, stream=torch.cuda.current_stream().cuda_stream)
+    s2.set_motion(0.05, 1.0)
+    s2.set_fields(q50, t50)
+    s2.set_vertices(x50)
+    s2.step(dt, 50)
+    q100b, t100b = s2.fields()
+    assert t100b == t100
+    assert np.array_equal(q100b, q100)
