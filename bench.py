@@ -1,0 +1,425 @@
+#!/usr/bin/env python
+"""Benchmark of the SARK step on the 2D moving Taylor-Green vortex workload.
+
+Workload: periodic [0, 2 pi]^2, 256 x 256 quads split into K = 131072
+triangles with vertices jittered by +-10% of h (seeded), N = 4 (Np = 15),
+6 Galerkin-Boltzmann fields, Ma = 0.1, Re = 1000, vertex motion
+x = X + 0.05 sin(X) sin(Y) sin(2 pi t), CFL 0.5.  A "step" is one full SARK
+step (4 stages: vertex positions, geometric factors, volume, surface,
+cubature and update for every element).  Metric: DOF-stage updates/s with
+DOF = K Np 6 and 4 stages per step.
+
+Two paths are timed: GB_MIXED (FP32 perturbation fields, FP64 geometry and
+SARK coefficients; the headline `value`) and GB_FP64 (the reference form).
+Both start from the same state and take the same steps; the mixed path's
+error against the FP64 path is reported.  Under torchrun each rank runs an
+independent replica on its own GPU (no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(n=256, N=4, Ma=0.1, Re=1000.0, A=0.05, T=1.0, jitter=0.1, cfl=0.5)
+WORKLOAD_NAME = ('2D moving Taylor-Green vortex: periodic [0,2pi]^2, 256x256 quads -> K=131072 triangles, '
+                 'vertices jittered +-10% h (seed 260700199), N=4 (Np=15), 6 fields, Ma=0.1, Re=1000, '
+                 'motion A=0.05 T=1, CFL 0.5')
+PEAKS_FILE = os.path.join(ROOT, 'MEASURED_PEAKS.json')
+TRAFFIC_FILE = os.path.join(ROOT, 'profiles', 'stage_kernel_traffic.json')
+# FP64 pipe: 2 FMA per clock per SM on B300 (measured 1.127 TFLOP/s at 1935 MHz with the
+# FMA probe in paper_2607_00199_b300/csrc/peak_probe.cu); peak = 148 SMs x 4 flop x 2032 MHz.
+FP64_FLOP_PER_CLK_SM = 4.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument('--gpus', type=int, default=1)
+    p.add_argument('--steps', type=int, default=100)
+    p.add_argument('--warmup', type=int, default=5)
+    p.add_argument('--impl', choices=['ours', 'reference'], default='ours')
+    p.add_argument('--no-cpu-baseline', action='store_true')
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per element-stage ("Roofline")
+# ---------------------------------------------------------------------------
+def sizes(N):
+    Np, Nfp = (N + 1) * (N + 2) // 2, N + 1
+    qc = (3 * N + 2) // 2
+    return Np, Nfp, qc * qc
+
+
+def flops_per_element_stage(N):
+    """Algorithmic flops (FMA = 2) of one element-stage of the fused RHS + update."""
+    Np, Nfp, Nc = sizes(N)
+    macs = 2 * 6 * Np * Np + 6 * Np * 3 * Nfp + 3 * Nc * Np + 3 * Np * Nc   # Dr, Ds, LIFT, I, P
+    volume = Np * 86          # chain rule 36, flux terms 16, v_G . grad 24, v_G interpolation 10
+    surface = 3 * Nfp * 95    # jump 6, upwind blocks 64, ALE 12, v_G . n 13
+    cubature = Nc * 12        # Ntilde with one division
+    update = 6 * Np * 4
+    return 2 * macs + volume + surface + cubature + update
+
+
+def bytes_per_step(K, N, nv, elem_bytes):
+    """Algorithmic HBM bytes of the 4 stage launches of one step: 18 field arrays
+    (3 + 5 + 6 + 4 reads/writes), plus per launch the 32-byte mesh record of every
+    element and x_n and S(X) (32 bytes) of every unique vertex."""
+    Np, _, _ = sizes(N)
+    return 18 * K * 6 * Np * elem_bytes + 4 * (32 * K + 32 * nv)
+
+
+# ---------------------------------------------------------------------------
+# environment helpers
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get('WORLD_SIZE', '1'))
+    rank = int(os.environ.get('RANK', '0'))
+    local = int(os.environ.get('LOCAL_RANK', '0'))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+    FIELDS = ('index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,'
+              'clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,'
+              'clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap')
+
+    def __init__(self, index):
+        self.index = index
+        self.file = tempfile.NamedTemporaryFile('w+', suffix='.csv', delete=False)
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(['nvidia-smi', '--query-gpu=' + self.FIELDS, '--format=csv,noheader,nounits',
+                                          '-lms', '200', '-i', str(self.index)],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        self.file.flush()
+        rows = []
+        try:
+            with open(self.file.name) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(',')]
+                    if len(parts) >= 9 and parts[1].replace('.', '').isdigit():
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.file.name)
+            except OSError:
+                pass
+        if not rows:
+            return {'sm_mhz': None, 'sm_max_mhz': None, 'reasons': ['unavailable'], 'samples': 0}
+        sm = [float(r[1]) for r in rows]
+        reasons = set()
+        names = ['hw_slowdown', 'hw_thermal_slowdown', 'sw_thermal_slowdown', 'sw_power_cap']
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith('active'):
+                    reasons.add(nm)
+        return {'sm_mhz': statistics.median(sm), 'sm_max_mhz': float(rows[0][2]), 'reasons': sorted(reasons),
+                'samples': len(rows), 'power_w_max': max(float(r[3]) for r in rows if r[3].replace('.', '').isdigit())}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d['hbm_gbs']), float(d.get('sm_max_mhz', 2032.0)), 'measured'
+    except (OSError, KeyError, ValueError):
+        return 6400.0, 2032.0, 'fallback'
+
+
+def recorded_traffic(precision):
+    """DRAM bytes per launch (average over the 4 stage launches of a step) of the
+    stage kernel from a committed ncu capture, or None if that kernel's source file
+    changed since the capture was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            d = json.load(f)[precision]
+        src = os.path.join(ROOT, d['kernel_source'])
+        if hashlib.sha256(open(src, 'rb').read()).hexdigest() != d['kernel_source_sha256']:
+            return None
+        return d['dram_bytes_per_launch_avg']
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def make_case(gb, inputs, state, precision, stream):
+    W = WORKLOAD
+    mesh = inputs.periodic_square_mesh(W['n'], jitter=W['jitter'])
+    s = gb.Solver(mesh, W['N'], W['Ma'], W['Re'], precision=precision, stream=stream)
+    s.set_motion(W['A'], W['T'])
+    xy = s.nodes()
+    rho, u, v = inputs.taylor_green(xy[..., 0], xy[..., 1], W['Ma'])
+    q0 = state.equilibrium_fields(rho, u, v, s.c)
+    dt = inputs.cfl_dt(mesh, W['N'], s.c, W['cfl'])
+    return s, q0, dt
+
+
+def time_path(torch, s, q0, dt, steps, warmup, barrier):
+    s.set_fields(q0, 0.0)
+    s.step(dt, warmup)
+    s.sync()
+    barrier()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    kernel_ms = s.step_timed(dt, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    return e0.elapsed_time(e1), kernel_ms
+
+
+class _SingleThreadBLAS:
+    """Limit BLAS threads when threadpoolctl is available (the oracle's einsum and
+    batched small linalg calls are single-threaded either way)."""
+
+    def __enter__(self):
+        try:
+            from threadpoolctl import threadpool_limits
+            self._ctx = threadpool_limits(1)
+        except ImportError:
+            self._ctx = None
+        return self
+
+    def __exit__(self, *exc):
+        if self._ctx is not None:
+            self._ctx.__exit__(*exc)
+
+
+def _cores_used(cpu_s, wall_s):
+    return max(1, int(round(cpu_s / max(wall_s, 1e-9))))
+
+
+def cpu_baseline(steps_sample=2, n_sample=128):
+    """The oracle, as it stands, on a bounded sample of the workload (host cores)."""
+    from oracle import physics
+    from oracle.solver import Motion, OracleSolver
+    from paper_2607_00199_b300 import inputs
+    W = WORKLOAD
+    with _SingleThreadBLAS():
+        mesh = inputs.periodic_square_mesh(n_sample, jitter=W['jitter'])
+        o = OracleSolver(mesh, W['N'], Ma=W['Ma'], Re=W['Re'], motion=Motion(W['A'], W['T']))
+        xn = o.node_coords(o.X)
+        rho, u, v = inputs.taylor_green(xn[..., 0], xn[..., 1], W['Ma'])
+        q = np.ascontiguousarray(physics.equilibrium_state(rho, u, v, o.c).transpose(0, 2, 1))
+        dt = inputs.cfl_dt(mesh, W['N'], o.c, W['cfl'])
+        c0, t0 = time.process_time(), time.perf_counter()
+        o.run(q, o.X.copy(), 0.0, dt, steps_sample)
+        el, cpu = time.perf_counter() - t0, time.process_time() - c0
+    Np, _, _ = sizes(W['N'])
+    dof = o.K * Np * 6
+    return {'value': dof * 4 * steps_sample / el, 'unit': 'DOF-stage updates/s', 'cores': _cores_used(cpu, el),
+            'kind': 'oracle',
+            'sample': '%d SARK steps of the same method on a %dx%d jittered mesh (K=%d, N=%d), numpy FP64; '
+                      '%.1f s wall, %.1f s CPU (cores = CPU/wall, rounded)' % (steps_sample, n_sample, n_sample,
+                                                                           o.K, W['N'], el, cpu)}
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws != args.gpus:
+        raise SystemExit('--gpus %d but WORLD_SIZE %d' % (args.gpus, ws))
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group('nccl', device_id=torch.device('cuda', local))
+    barrier = (lambda: dist.barrier()) if dist else (lambda: None)
+
+    from paper_2607_00199_b300 import gb, inputs, state
+    W = WORKLOAD
+    stream = torch.cuda.current_stream().cuda_stream
+    Np, Nfp, Nc = sizes(W['N'])
+    results = {}
+    sampler = ClockSampler(local)
+    with sampler:
+        for name, prec in (('mixed', gb.GB_MIXED), ('fp64', gb.GB_FP64)):
+            s, q0, dt = make_case(gb, inputs, state, prec, stream)
+            ms, kms = time_path(torch, s, q0, dt, args.steps, args.warmup, barrier)
+            q_end, _ = s.fields()
+            results[name] = dict(ms=ms, kernel_ms=kms, solver=s, q_end=q_end, q0=q0, dt=dt)
+    clocks = sampler.summary()
+
+    # max over ranks of the timed region
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device='cuda')
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    K = results['mixed']['solver'].K
+    nv = results['mixed']['solver'].nv
+    dof = K * Np * 6
+    hbm, sm_max, peak_kind = load_peaks()
+    out = {}
+    for name in ('mixed', 'fp64'):
+        r = results[name]
+        ms = max_over_ranks(r['ms'])
+        stage_ms = float(sum(r['kernel_ms'][:4]))
+        v = ws * dof * 4 * args.steps / (ms / 1e3)
+        ebytes = 4 if name == 'mixed' else 8
+        if name == 'mixed':
+            alg = bytes_per_step(K, W['N'], nv, ebytes) * args.steps
+            achieved = alg / (stage_ms / 1e3) / 1e9
+            traffic = recorded_traffic('mixed')
+            roof = {'bound': 'hbm', 'achieved': achieved, 'peak': hbm, 'unit': 'GB/s', 'frac': achieved / hbm,
+                    'traffic': traffic, 'kernel': 'tc_stage_kernel<4,*> (4 launches per step)',
+                    'algorithmic_bytes_per_launch_avg': bytes_per_step(K, W['N'], nv, ebytes) / 4,
+                    'mean_launch_ms': stage_ms / (4 * args.steps),
+                    'peak_source': '%s hbm_gbs (MEASURED_PEAKS.json)' % peak_kind if peak_kind == 'measured'
+                    else 'fallback 6400 GB/s',
+                    'algorithmic_bytes_per_step': bytes_per_step(K, W['N'], nv, ebytes)}
+        else:
+            fl = flops_per_element_stage(W['N']) * K * 4 * args.steps
+            achieved = fl / (stage_ms / 1e3) / 1e12
+            peak = 148 * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
+            roof = {'bound': 'alu', 'achieved': achieved, 'peak': peak, 'unit': 'TFLOP/s', 'frac': achieved / peak,
+                    'traffic': recorded_traffic('fp64'), 'kernel': 'stage_kernel<double,4,*> (4 launches per step)',
+                    'mean_launch_ms': stage_ms / (4 * args.steps),
+                    'peak_source': 'FP64 pipe: 148 SMs x 2 FMA/clk x 2 flop x %.0f MHz' % sm_max,
+                    'algorithmic_flops_per_element_stage': flops_per_element_stage(W['N'])}
+        out[name] = {'value': v, 'ms_per_step': ms / args.steps, 'roofline': roof,
+                     'kernel_ms_per_step': [x / args.steps for x in r['kernel_ms']],
+                     'stage_kernel_share': stage_ms / ms}
+    qm, qf = results['mixed']['q_end'], results['fp64']['q_end']
+    rest = np.zeros_like(qf)
+    rest[:, 0, :] = 1.0
+    err = {'rel_l2_fields': float(np.linalg.norm(qm - qf) / np.linalg.norm(qf)),
+           'rel_l2_perturbation': float(np.linalg.norm(qm - qf) / np.linalg.norm(qf - rest)),
+           'steps': args.warmup + args.steps, 'against': 'GB_FP64 path (oracle-parity-tested) from the same state'}
+
+    # end to end through the public API: pinned host state in, steps, pinned host state out
+    s = results['mixed']['solver']
+    q0 = results['mixed']['q0']
+    pin_in = torch.empty(q0.shape, dtype=torch.float64, pin_memory=True).numpy()
+    pin_in[...] = q0
+    pin_out = torch.empty(q0.shape, dtype=torch.float64, pin_memory=True).numpy()
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    s.set_fields(pin_in, 0.0)
+    s.step(results['mixed']['dt'], args.steps)
+    s.fields(out=pin_out)
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    nbytes = q0.nbytes
+    e2e = {'value': ws * dof * 4 * args.steps / e2e_s, 'unit': 'DOF-stage updates/s',
+           'h2d_bytes_per_step': nbytes / args.steps, 'd2h_bytes_per_step': nbytes / args.steps,
+           'note': 'gb_set_fields (pinned host FP64 state) + gb_step x K + gb_fields (pinned host), wall clock'}
+
+    if rank != 0:
+        return
+    line = {
+        'metric': 'DOF-stage updates/s', 'value': out['mixed']['value'], 'unit': 'DOF-stage updates/s',
+        'n_gpus': ws, 'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': out['mixed']['ms_per_step'],
+        'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f32',
+        'data': 'synthetic: seeded jittered periodic mesh, Taylor-Green initial state, prescribed motion',
+        'config': {'workload': WORKLOAD_NAME, 'K': K, 'N': W['N'], 'Np': Np, 'fields': 6, 'dof': dof,
+                   'precision': 'GB_MIXED: FP32 perturbation fields, FP64 geometry and SARK coefficients',
+                   'l2': 'inputs larger than L2: state arrays 5 x %.0f MB (FP32)' % (dof * 4 / 1e6),
+                   'parallelism': 'replicas' if ws > 1 else 'single GPU'},
+        'roofline': out['mixed']['roofline'],
+        'e2e': e2e,
+        'gpu_launches': 5 * args.steps,
+        'clocks': clocks,
+        'fp64': out['fp64'],
+        'mixed': {k: v for k, v in out['mixed'].items() if k != 'roofline'},
+        'mixed_speedup_vs_fp64': out['mixed']['value'] / out['fp64']['value'],
+        'mixed_error': err,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line['cpu_baseline'] = cpu_baseline()
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    from oracle import physics
+    from oracle.solver import Motion, OracleSolver
+    from paper_2607_00199_b300 import inputs
+    W = WORKLOAD
+    # bounded sample per step: a smaller jittered mesh of the same workload, sized so
+    # that warmup + steps stays within a couple of minutes (~0.16 ms per element-step)
+    budget_s = 120.0
+    per_elem = 1.6e-4
+    k_target = max(512, min(32768, budget_s / max(1, args.steps + args.warmup) / per_elem))
+    n = max(16, int(math.sqrt(k_target / 2)))
+    with _SingleThreadBLAS():
+        mesh = inputs.periodic_square_mesh(n, jitter=W['jitter'])
+        o = OracleSolver(mesh, W['N'], Ma=W['Ma'], Re=W['Re'], motion=Motion(W['A'], W['T']))
+        xn = o.node_coords(o.X)
+        rho, u, v = inputs.taylor_green(xn[..., 0], xn[..., 1], W['Ma'])
+        q = np.ascontiguousarray(physics.equilibrium_state(rho, u, v, o.c).transpose(0, 2, 1))
+        dt = inputs.cfl_dt(mesh, W['N'], o.c, W['cfl'])
+        x, t = o.X.copy(), 0.0
+        for _ in range(args.warmup):
+            q, x = o.step(q, x, t, dt)
+            t += dt
+        c0, t0 = time.process_time(), time.perf_counter()
+        for _ in range(args.steps):
+            q, x = o.step(q, x, t, dt)
+            t += dt
+        el, cpu = time.perf_counter() - t0, time.process_time() - c0
+    Np, _, _ = sizes(W['N'])
+    dof = o.K * Np * 6
+    v = dof * 4 * args.steps / el
+    sample = ('each step: one SARK step of the same method on a %dx%d jittered mesh (K=%d, N=%d) '
+              'instead of 256x256, numpy FP64' % (n, n, o.K, W['N']))
+    line = {'impl': 'reference', 'metric': 'DOF-stage updates/s', 'value': v, 'unit': 'DOF-stage updates/s',
+            'n_gpus': ws, 'steps': args.steps, 'warmup': args.warmup, 'ms_per_step': el / args.steps * 1e3,
+            'higher_is_better': True, 'scaling': 'weak', 'vs_baseline': None, 'dtype': 'f64',
+            'data': 'synthetic: seeded jittered periodic mesh, Taylor-Green initial state, prescribed motion',
+            'config': {'workload': WORKLOAD_NAME, 'K': 131072, 'N': W['N'], 'sample_K': o.K},
+            'cpu_baseline': {'value': v, 'unit': 'DOF-stage updates/s', 'cores': _cores_used(cpu, el), 'kind': 'oracle',
+                             'sample': sample},
+            'e2e': {'value': v, 'unit': 'DOF-stage updates/s', 'h2d_bytes_per_step': 0, 'd2h_bytes_per_step': 0}}
+    print(json.dumps(line))
+
+
+if __name__ == '__main__':
+    a = parse()
+    if a.impl == 'reference':
+        run_reference(a)
+    else:
+        run_ours(a)

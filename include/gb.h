@@ -100,9 +100,11 @@ int gb_nodes(gb_solver *s, double *xy_out);
 
 /* gb_rhs: F = L(q) + Ntilde(q) (Sec. 4 splitting; the stiff -Lambda q part is not
  * included) for device arrays q_dev, F_dev in canonical layout (K*6*Np; FP64 in
- * GB_FP64 mode, FP32 perturbation values in GB_MIXED mode), at the current vertex
- * positions with the grid velocity of time t.  Both arrays are caller-owned
- * device memory, used on the solver's stream; enqueue only. */
+ * GB_FP64 mode; in GB_MIXED mode FP32, q_dev holding perturbations q - (1,0,0,0,0,0)
+ * and F_dev receiving F itself), at the current vertex positions with the grid
+ * velocity of time t.  Both arrays are caller-owned device memory, used on the
+ * solver's stream; enqueue only.  GB_MIXED uses the solver's stage buffers as
+ * scratch, so the call must not overlap a gb_step on another stream. */
 int gb_rhs(gb_solver *s, double t, const void *q_dev, void *F_dev);
 
 /* gb_step: enqueue nsteps SARK steps of size dt (Sec. 4): per stage, the vertex
@@ -110,6 +112,13 @@ int gb_rhs(gb_solver *s, double t, const void *q_dev, void *F_dev);
  * surface and cubature terms and the SARK combination.  Enqueue only; errors of
  * the device computation are reported by gb_sync / gb_fields. */
 int gb_step(gb_solver *s, double dt, int64_t nsteps);
+
+/* gb_step_timed: gb_step that also records a CUDA event pair around every kernel
+ * launch on the solver's stream (tracing), synchronises, and adds the device time
+ * in milliseconds of each kernel kind to kernel_ms[0..4]: the fused stage kernels
+ * of stages 0..3, then the vertex update.  kernel_ms is host memory of 5 doubles
+ * (not cleared).  Returns the device status like gb_sync. */
+int gb_step_timed(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms);
 
 /* gb_sync: synchronise the stream, return and clear the device status
  * (GB_OK, GB_ENAN or GB_EMESH). */
@@ -119,9 +128,10 @@ int gb_sync(gb_solver *s);
 int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *n_vert,
             double *c, double *tau, int64_t *device_bytes);
 
-/* gb_state_ptr: the device address of the current fields (canonical layout, FP64 in
- * GB_FP64 mode, FP32 perturbations in GB_MIXED mode), owned by the solver, valid
- * until gb_destroy. */
+/* gb_state_ptr: the device address of the current fields, owned by the solver and
+ * valid until gb_destroy: the canonical FP64 layout in GB_FP64 mode; in GB_MIXED
+ * mode an internal layout (FP32 perturbations, elements renumbered along a Morton
+ * curve, padded element stride) that only gb_fields translates. */
 int gb_state_ptr(gb_solver *s, void **q_dev);
 
 int gb_destroy(gb_solver *s);

@@ -13,9 +13,7 @@
 #include "gb.h"
 #include "gb_internal.h"
 
-namespace gb {
-size_t ops_float_offset(int N);
-}
+#include <algorithm>
 
 using gb::MeshRec;
 
@@ -32,8 +30,11 @@ struct gb_solver {
   gb::SarkCoef co{};
   size_t elem_bytes = 8;
   // device memory
-  double *d_ops = nullptr;     // FP64 operator block followed by the FP32 copy
-  MeshRec *d_mesh = nullptr;
+  double *d_ops = nullptr;     // FP64 operator block (canonical kernel, node coordinates)
+  float *d_ops_mixed = nullptr;  // FP32 operator block of the GB_MIXED kernel
+  MeshRec *d_mesh = nullptr;     // canonical element order
+  MeshRec *d_mesh_int = nullptr; // GB_MIXED: Morton element order, neighbours renumbered
+  int32_t *d_perm = nullptr;     // GB_MIXED: canonical index of internal element i
   double *d_X = nullptr, *d_xn = nullptr, *d_shape = nullptr, *d_clock = nullptr;
   int *d_status = nullptr;
   void *d_qn = nullptr, *d_b1 = nullptr, *d_b2 = nullptr, *d_F0 = nullptr, *d_acc = nullptr;
@@ -64,8 +65,8 @@ static int dev_alloc(gb_solver *s, void **p, size_t bytes) {
 }
 
 static void free_all(gb_solver *s) {
-  void *ptrs[] = {s->d_ops, s->d_mesh, s->d_X, s->d_xn, s->d_shape, s->d_clock, s->d_status,
-                  s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp};
+  void *ptrs[] = {s->d_ops, s->d_ops_mixed, s->d_mesh, s->d_mesh_int, s->d_perm, s->d_X, s->d_xn, s->d_shape,
+                  s->d_clock, s->d_status, s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -83,18 +84,14 @@ static int ensure_tmp(gb_solver *s, size_t bytes) {
   return rc;
 }
 
-static const double *ops_for(const gb_solver *s) {
-  if (s->precision == GB_FP64) return s->d_ops;
-  return reinterpret_cast<const double *>(reinterpret_cast<const unsigned char *>(s->d_ops) + gb::ops_float_offset(s->N));
-}
-
 static gb::StageArgs base_args(gb_solver *s) {
   gb::StageArgs a;
   memset(&a, 0, sizeof(a));
   a.xn = s->d_xn;
   a.shape = s->d_shape;
-  a.mesh = s->d_mesh;
-  a.ops = ops_for(s);
+  const bool mixed = s->precision == GB_MIXED;
+  a.mesh = mixed ? s->d_mesh_int : s->d_mesh;
+  a.ops = mixed ? reinterpret_cast<const double *>(s->d_ops_mixed) : s->d_ops;
   a.clock = s->d_clock;
   a.status = s->d_status;
   a.K = s->K;
@@ -110,9 +107,38 @@ static gb::StageArgs base_args(gb_solver *s) {
 
 static int launch_stage(gb_solver *s, const gb::StageArgs &a) {
   int rc = s->precision == GB_FP64 ? gb::launch_stage_fp64(s->N, a, s->stream, s->num_sms)
-                                   : gb::launch_stage_fp32(s->N, a, s->stream, s->num_sms);
+                                   : gb::launch_stage_mixed(s->N, a, s->stream, s->num_sms);
   if (rc != 0) return cuda_fail(s, (cudaError_t)rc, "stage kernel launch");
   return GB_OK;
+}
+
+// Morton (Z-order) numbering of the element centroids: internal element i is
+// canonical element perm[i].  Keeps face neighbours close in memory.
+static std::vector<int32_t> morton_order(const std::vector<double> &cx, const std::vector<double> &cy) {
+  const size_t K = cx.size();
+  double x0 = cx[0], x1 = cx[0], y0 = cy[0], y1 = cy[0];
+  for (size_t i = 0; i < K; ++i) {
+    x0 = std::min(x0, cx[i]); x1 = std::max(x1, cx[i]);
+    y0 = std::min(y0, cy[i]); y1 = std::max(y1, cy[i]);
+  }
+  const double sx = x1 > x0 ? 65535.0 / (x1 - x0) : 0.0, sy = y1 > y0 ? 65535.0 / (y1 - y0) : 0.0;
+  auto spread = [](uint32_t v) {
+    v &= 0xffff;
+    v = (v | (v << 8)) & 0x00ff00ff;
+    v = (v | (v << 4)) & 0x0f0f0f0f;
+    v = (v | (v << 2)) & 0x33333333;
+    v = (v | (v << 1)) & 0x55555555;
+    return v;
+  };
+  std::vector<std::pair<uint32_t, int32_t>> key(K);
+  for (size_t i = 0; i < K; ++i) {
+    uint32_t ix = (uint32_t)((cx[i] - x0) * sx), iy = (uint32_t)((cy[i] - y0) * sy);
+    key[i] = {spread(ix) | (spread(iy) << 1), (int32_t)i};
+  }
+  std::sort(key.begin(), key.end());
+  std::vector<int32_t> perm(K);
+  for (size_t i = 0; i < K; ++i) perm[i] = key[i].second;
+  return perm;
 }
 
 extern "C" {
@@ -228,12 +254,37 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
     return fail(nullptr, GB_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(ce));
   }
   int rc = gb::upload_ops(N, s->ref, &s->d_ops, s->stream);
+  if (rc == 0 && precision == GB_MIXED) rc = gb::upload_ops_mixed(N, s->ref, &s->d_ops_mixed, s->stream);
   if (rc != 0) {
     std::string m = std::string("operator upload: ") + cudaGetErrorString((cudaError_t)rc);
+    free_all(s);
     delete s;
     return fail(nullptr, GB_ECUDA, m);
   }
-  const size_t fbytes = (size_t)K * 6 * s->Np * s->elem_bytes;
+  // GB_MIXED: element-major layout with the padded stride S, tiles of 16 elements, Morton order
+  const int64_t Kpad = precision == GB_MIXED ? ((K + 15) / 16) * 16 : K;
+  const int64_t per_elem = precision == GB_MIXED ? gb::mixed_stride(N) : 6 * s->Np;
+  std::vector<int32_t> perm;
+  std::vector<MeshRec> rec_int;
+  if (precision == GB_MIXED) {
+    std::vector<double> cx(K), cy(K);
+    for (int64_t e = 0; e < K; ++e) {
+      cx[e] = (vx(e, 0, 0) + vx(e, 1, 0) + vx(e, 2, 0)) / 3.0;
+      cy[e] = (vx(e, 0, 1) + vx(e, 1, 1) + vx(e, 2, 1)) / 3.0;
+    }
+    perm = morton_order(cx, cy);
+    std::vector<int32_t> inv(K);
+    for (int64_t i = 0; i < K; ++i) inv[perm[i]] = (int32_t)i;
+    rec_int.resize(K);
+    for (int64_t i = 0; i < K; ++i) {
+      rec_int[i] = rec[perm[i]];
+      for (int f = 0; f < 3; ++f) {
+        const int32_t nb = rec_int[i].nbr[f];
+        rec_int[i].nbr[f] = (inv[nb >> 2] << 2) | (nb & 3);
+      }
+    }
+  }
+  const size_t fbytes = (size_t)Kpad * per_elem * s->elem_bytes;
   void **fields[] = {&s->d_qn, &s->d_b1, &s->d_b2, &s->d_F0, &s->d_acc};
   int arc = GB_OK;
   arc = arc ? arc : dev_alloc(s, (void **)&s->d_mesh, sizeof(MeshRec) * K);
@@ -243,6 +294,10 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   arc = arc ? arc : dev_alloc(s, (void **)&s->d_clock, sizeof(double) * 2);
   arc = arc ? arc : dev_alloc(s, (void **)&s->d_status, sizeof(int));
   for (void **p : fields) arc = arc ? arc : dev_alloc(s, p, fbytes);
+  if (precision == GB_MIXED) {
+    arc = arc ? arc : dev_alloc(s, (void **)&s->d_mesh_int, sizeof(MeshRec) * K);
+    arc = arc ? arc : dev_alloc(s, (void **)&s->d_perm, sizeof(int32_t) * K);
+  }
   if (arc != GB_OK) {
     g_create_error = s->err;
     free_all(s);
@@ -252,6 +307,10 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   double clock0[2] = {0.0, 0.0};
   int zero = 0;
   ce = cudaMemcpyAsync(s->d_mesh, rec.data(), sizeof(MeshRec) * K, cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess && precision == GB_MIXED)
+    ce = cudaMemcpyAsync(s->d_mesh_int, rec_int.data(), sizeof(MeshRec) * K, cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess && precision == GB_MIXED)
+    ce = cudaMemcpyAsync(s->d_perm, perm.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_X, mesh->X, sizeof(double) * 2 * nv, cudaMemcpyHostToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_xn, mesh->X, sizeof(double) * 2 * nv, cudaMemcpyHostToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemsetAsync(s->d_shape, 0, sizeof(double) * 2 * nv, s->stream);
@@ -296,7 +355,8 @@ int gb_set_fields(gb_solver *s, const double *q_host, double t) {
     if (rc) return rc;
     ce = cudaMemcpyAsync(s->d_tmp, q_host, n * sizeof(double), cudaMemcpyHostToDevice, s->stream);
     if (ce == cudaSuccess) {
-      int lr = gb::launch_to_fp32_perturbation(s->d_tmp, (float *)s->d_qn, s->K, s->Np, s->stream);
+      int lr = gb::launch_relayout(s->d_tmp, nullptr, true, true, (float *)s->d_qn, s->d_perm, s->K, s->Np,
+                                   gb::mixed_stride(s->N), 1.0, s->stream);
       if (lr) ce = (cudaError_t)lr;
     }
   }
@@ -329,7 +389,8 @@ int gb_fields(gb_solver *s, double *q_host_out, double *t_out) {
     } else {
       int rc = ensure_tmp(s, n * sizeof(double));
       if (rc) return rc;
-      int lr = gb::launch_from_fp32_perturbation((const float *)s->d_qn, s->d_tmp, s->K, s->Np, s->stream);
+      int lr = gb::launch_relayout(nullptr, s->d_tmp, true, false, (float *)s->d_qn, s->d_perm, s->K, s->Np,
+                                   gb::mixed_stride(s->N), 1.0, s->stream);
       ce = lr ? (cudaError_t)lr : cudaMemcpyAsync(q_host_out, s->d_tmp, n * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     }
   }
@@ -374,14 +435,39 @@ int gb_rhs(gb_solver *s, double t, const void *q_dev, void *F_dev) {
   if (!std::isfinite(t)) return fail(s, GB_EINVAL, "t must be finite");
   gb::StageArgs a = base_args(s);
   a.stage = -1;
-  a.qin = q_dev;
-  a.qn = q_dev;
-  a.Fout = F_dev;
   a.rhs_time = t;
-  return launch_stage(s, a);
+  if (s->precision == GB_FP64) {
+    a.qin = q_dev;
+    a.qn = q_dev;
+    a.Fout = F_dev;
+    return launch_stage(s, a);
+  }
+  // GB_MIXED: canonical FP32 perturbations -> internal layout in the stage buffers b1, b2
+  int lr = gb::launch_relayout(q_dev, nullptr, false, true, (float *)s->d_b1, s->d_perm, s->K, s->Np,
+                               gb::mixed_stride(s->N), 0.0, s->stream);
+  if (lr) return cuda_fail(s, (cudaError_t)lr, "gb_rhs relayout");
+  a.qin = s->d_b1;
+  a.qn = s->d_b1;
+  a.Fout = s->d_b2;
+  int rc = launch_stage(s, a);
+  if (rc) return rc;
+  lr = gb::launch_relayout(nullptr, F_dev, false, false, (float *)s->d_b2, s->d_perm, s->K, s->Np,
+                           gb::mixed_stride(s->N), 0.0, s->stream);
+  if (lr) return cuda_fail(s, (cudaError_t)lr, "gb_rhs relayout");
+  return GB_OK;
 }
 
-int gb_step(gb_solver *s, double dt, int64_t nsteps) {
+static int step_impl(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms);
+
+int gb_step(gb_solver *s, double dt, int64_t nsteps) { return step_impl(s, dt, nsteps, nullptr); }
+
+int gb_step_timed(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms) {
+  if (!kernel_ms) return fail(s, GB_EINVAL, "kernel_ms is NULL");
+  int rc = step_impl(s, dt, nsteps, kernel_ms);
+  return rc ? rc : gb_sync(s);
+}
+
+static int step_impl(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
   if (!(dt > 0.0) || !std::isfinite(dt)) return fail(s, GB_EINVAL, "dt must be positive and finite");
   if (nsteps < 0) return fail(s, GB_EINVAL, "nsteps must be >= 0");
@@ -397,21 +483,47 @@ int gb_step(gb_solver *s, double dt, int64_t nsteps) {
   a.dt = dt;
   void *bufs_in[4] = {s->d_qn, s->d_b1, s->d_b2, s->d_b1};
   void *bufs_out[4] = {s->d_b1, s->d_b2, s->d_b1, s->d_qn};
-  for (int64_t k = 0; k < nsteps; ++k) {
-    for (int st = 0; st < 4; ++st) {
-      a.stage = st;
-      a.qin = bufs_in[st];
-      a.qn = s->d_qn;
-      a.qout = bufs_out[st];
-      a.F0 = s->d_F0;
-      a.acc = s->d_acc;
-      int rc = launch_stage(s, a);
-      if (rc) return rc;
-    }
-    int rc = gb::launch_vertex_update(a, s->nv, s->stream);
-    if (rc) return cuda_fail(s, (cudaError_t)rc, "vertex update launch");
+  std::vector<cudaEvent_t> ev;
+  if (kernel_ms) {
+    ev.resize((size_t)nsteps * 10);
+    for (auto &e : ev)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        for (auto &x : ev)
+          if (x) cudaEventDestroy(x);
+        return fail(s, GB_ECUDA, "cudaEventCreate failed");
+      }
   }
-  return GB_OK;
+  int rc = GB_OK;
+  for (int64_t k = 0; k < nsteps && rc == GB_OK; ++k) {
+    for (int st = 0; st < 5 && rc == GB_OK; ++st) {
+      if (kernel_ms) cudaEventRecord(ev[(size_t)k * 10 + 2 * st], s->stream);
+      if (st < 4) {
+        a.stage = st;
+        a.qin = bufs_in[st];
+        a.qn = s->d_qn;
+        a.qout = bufs_out[st];
+        a.F0 = s->d_F0;
+        a.acc = s->d_acc;
+        rc = launch_stage(s, a);
+      } else {
+        int lr = gb::launch_vertex_update(a, s->nv, s->stream);
+        if (lr) rc = cuda_fail(s, (cudaError_t)lr, "vertex update launch");
+      }
+      if (kernel_ms) cudaEventRecord(ev[(size_t)k * 10 + 2 * st + 1], s->stream);
+    }
+  }
+  if (kernel_ms) {
+    cudaError_t ce = cudaStreamSynchronize(s->stream);
+    for (int64_t k = 0; k < nsteps && ce == cudaSuccess && rc == GB_OK; ++k)
+      for (int st = 0; st < 5; ++st) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ev[(size_t)k * 10 + 2 * st], ev[(size_t)k * 10 + 2 * st + 1]) == cudaSuccess)
+          kernel_ms[st] += ms;
+      }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (ce != cudaSuccess && rc == GB_OK) rc = cuda_fail(s, ce, "gb_step_timed");
+  }
+  return rc;
 }
 
 int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *n_vert, double *c, double *tau,

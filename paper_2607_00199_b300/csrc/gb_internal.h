@@ -78,14 +78,16 @@ struct StageArgs {
 
 // Launchers (gb_kernels.cu).  Return a cudaError_t value as int.
 int launch_stage_fp64(int N, const StageArgs &a, void *stream, int num_sms);
-int launch_stage_fp32(int N, const StageArgs &a, void *stream, int num_sms);
+int launch_stage_mixed(int N, const StageArgs &a, void *stream, int num_sms);
 int launch_vertex_update(const StageArgs &a, int64_t n_vert, void *stream);
 int launch_shape(const double *X, double *shape, int64_t n_vert, int kind, double Lx, double Ly, void *stream);
 int launch_nodes(int N, const double *ops, const double *xn, const MeshRec *mesh, double px, double py,
                  int64_t K, double *out, void *stream);
-int launch_to_fp32_perturbation(const double *q64, float *q32, int64_t K, int Np, void *stream);
-int launch_from_fp32_perturbation(const float *q32, double *q64, int64_t K, int Np, void *stream);
+int launch_relayout(const void *canon_src, void *canon_dst, bool canon_is_double, bool to_internal, float *inner,
+                    const int32_t *perm, int64_t K, int Np, int S, double rest, void *stream);
+int mixed_stride(int N);   // element stride (floats) of the GB_MIXED field layout
 int upload_ops(int N, const RefOps &R, double **dev_ops, void *stream);
+int upload_ops_mixed(int N, const RefOps &R, float **dev_ops, void *stream);
 
 }  // namespace gb
 

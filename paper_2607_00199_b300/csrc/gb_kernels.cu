@@ -14,9 +14,8 @@
 //   update    : the SARK stage / final combination of Sec. 4.
 // The kernel is persistent: the grid covers the SMs and each CTA loops over
 // element tiles, with the reference operators staged once in shared memory.
-// T is the field/arithmetic type: double for GB_FP64; float for GB_MIXED,
-// where the fields hold perturbations from the rest state (rho = 1, u = 0) and
-// the geometry and coefficients are still formed in FP64.
+// T is the field/arithmetic type; the library instantiates it for double
+// (GB_FP64).  GB_MIXED uses the thread-per-element kernel of gb_kernels_mixed.cu.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -47,12 +46,6 @@ template <> struct Tile<double, 3> { static constexpr int E = 16; };
 template <> struct Tile<double, 4> { static constexpr int E = 16; };
 template <> struct Tile<double, 5> { static constexpr int E = 12; };
 template <> struct Tile<double, 6> { static constexpr int E = 8; };
-template <> struct Tile<float, 1> { static constexpr int E = 64; };
-template <> struct Tile<float, 2> { static constexpr int E = 32; };
-template <> struct Tile<float, 3> { static constexpr int E = 24; };
-template <> struct Tile<float, 4> { static constexpr int E = 16; };
-template <> struct Tile<float, 5> { static constexpr int E = 12; };
-template <> struct Tile<float, 6> { static constexpr int E = 8; };
 
 // layout of the operator block (in T), all stored so that consecutive
 // threads read consecutive entries
@@ -467,9 +460,6 @@ static int launch_stage_t(int N, const StageArgs &a, void *stream, int num_sms) 
 int launch_stage_fp64(int N, const StageArgs &a, void *stream, int num_sms) {
   return launch_stage_t<double>(N, a, stream, num_sms);
 }
-int launch_stage_fp32(int N, const StageArgs &a, void *stream, int num_sms) {
-  return launch_stage_t<float>(N, a, stream, num_sms);
-}
 
 // final vertex update of the step, x_{n+1} = x_n + fin S(X), and t_n += dt
 __global__ void vertex_update_kernel(double *xn, const double *shape, double *clock, double dt, int64_t nv) {
@@ -544,31 +534,7 @@ int launch_nodes(int N, const double *ops, const double *xn, const MeshRec *mesh
   return (int)cudaGetLastError();
 }
 
-// canonical FP64 fields <-> FP32 perturbations from the rest state (q1 = 1, others 0)
-__global__ void to_pert_kernel(const double *q64, float *q32, int64_t n, int NQ, int Np) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int within = (int)(i % NQ);
-    const double rest = within < Np ? 1.0 : 0.0;
-    q32[i] = (float)(q64[i] - rest);
-  }
-}
-__global__ void from_pert_kernel(const float *q32, double *q64, int64_t n, int NQ, int Np) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const int within = (int)(i % NQ);
-    const double rest = within < Np ? 1.0 : 0.0;
-    q64[i] = (double)q32[i] + rest;
-  }
-}
-int launch_to_fp32_perturbation(const double *q64, float *q32, int64_t K, int Np, void *stream) {
-  to_pert_kernel<<<2048, 256, 0, (cudaStream_t)stream>>>(q64, q32, K * 6 * Np, 6 * Np, Np);
-  return (int)cudaGetLastError();
-}
-int launch_from_fp32_perturbation(const float *q32, double *q64, int64_t K, int Np, void *stream) {
-  from_pert_kernel<<<2048, 256, 0, (cudaStream_t)stream>>>(q32, q64, K * 6 * Np, 6 * Np, Np);
-  return (int)cudaGetLastError();
-}
-
-// operator block: FP64 copy followed by an FP32 copy (the same layout)
+// operator block (FP64) in the layout of OpLayout
 template <int N>
 static void fill_ops(const RefOps &R, std::vector<double> &h) {
   typedef Dim<N> D;
@@ -604,17 +570,10 @@ int upload_ops(int N, const RefOps &R, double **dev_ops, void *stream) {
     case 6: fill_ops<6>(R, h); break;
     default: return (int)cudaErrorInvalidValue;
   }
-  const size_t n = h.size();
-  // doubles, then floats (aligned to 16 bytes)
-  const size_t fl_off = ((n * sizeof(double) + 15) / 16) * 16;
-  std::vector<unsigned char> blob(fl_off + n * sizeof(float));
-  memcpy(blob.data(), h.data(), n * sizeof(double));
-  float *f = reinterpret_cast<float *>(blob.data() + fl_off);
-  for (size_t i = 0; i < n; ++i) f[i] = (float)h[i];
   void *d = nullptr;
-  cudaError_t err = cudaMalloc(&d, blob.size());
+  cudaError_t err = cudaMalloc(&d, h.size() * sizeof(double));
   if (err != cudaSuccess) return (int)err;
-  err = cudaMemcpyAsync(d, blob.data(), blob.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  err = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, (cudaStream_t)stream);
   if (err == cudaSuccess) err = cudaStreamSynchronize((cudaStream_t)stream);
   if (err != cudaSuccess) {
     cudaFree(d);
@@ -622,19 +581,6 @@ int upload_ops(int N, const RefOps &R, double **dev_ops, void *stream) {
   }
   *dev_ops = reinterpret_cast<double *>(d);
   return 0;
-}
-
-size_t ops_float_offset(int N) {
-  size_t n = 0;
-  switch (N) {
-    case 1: n = OpLayout<1>::Size; break;
-    case 2: n = OpLayout<2>::Size; break;
-    case 3: n = OpLayout<3>::Size; break;
-    case 4: n = OpLayout<4>::Size; break;
-    case 5: n = OpLayout<5>::Size; break;
-    case 6: n = OpLayout<6>::Size; break;
-  }
-  return ((n * sizeof(double) + 15) / 16) * 16;
 }
 
 }  // namespace gb

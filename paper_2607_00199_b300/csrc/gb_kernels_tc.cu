@@ -1,0 +1,719 @@
+// GB_MIXED stage kernel on the tensor cores.
+//
+// Same right-hand side and SARK combination as the FP64 stage kernel (Secs.
+// 2-5), with the four dense contractions of the semi-discrete form (Dr/Ds on
+// the 6 fields, LIFT on the face fluxes, the cubature interpolation I and the
+// projection P) issued as mma.sync.m16n8k8 TF32 products with FP32
+// accumulation.  Each operand is split into a TF32 head and a TF32 tail
+// (x = hi + lo) and every product is formed as hi*hi + hi*lo + lo*hi, which
+// keeps the contractions at FP32 accuracy (the dropped lo*lo term is ~2^-22
+// relative).
+//
+// A warp owns a tile of 16 elements (the M dimension of every product):
+//   rows = elements, columns = nodes / face nodes / cubature points.
+// The reference operators are constant B operands, pre-split and stored in
+// shared memory in per-lane fragment order (one 16-byte load per fragment).
+// The cubature chain reuses the accumulator fragment of I q directly as the A
+// fragment of P Ntilde: the 8 columns of a chunk are taken in the order
+// (0,2,4,6,1,3,5,7), which is folded into the P table.
+//
+// Data: fields are FP32 perturbations from the rest state (q1 = 1, others 0)
+// in an element-major layout with a padded element stride S (S >= 6 Np,
+// S = 4 mod 8: conflict-free fragment loads from the staged tile), elements
+// numbered along a Morton curve.  Per tile: the own fields and all neighbour
+// traces are staged in shared memory with cp.async, the geometry is formed
+// while the copies are in flight (FP64 stage positions and edge differences,
+// FP32 afterwards), and the SARK combination runs as a coalesced pass over
+// the tile.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "gb_internal.h"
+
+namespace gb {
+
+__host__ __device__ constexpr int tc_round_s(int x) { return ((x - 4 + 7) / 8) * 8 + 4; }   // smallest s >= x, s = 4 mod 8
+
+template <int N>
+struct TcDim {
+  static constexpr int Np = (N + 1) * (N + 2) / 2;
+  static constexpr int Nfp = N + 1;
+  static constexpr int NFN = 3 * (N + 1);
+  static constexpr int Nc = ((3 * N + 2) / 2) * ((3 * N + 2) / 2);
+  static constexpr int KS = (Np + 7) / 8;       // k-steps over nodes
+  static constexpr int KF = (NFN + 7) / 8;      // k-steps over face nodes
+  static constexpr int NT = (Np + 7) / 8;       // n-tiles over output nodes
+  static constexpr int CH = (Nc + 7) / 8;       // cubature chunks of 8 points
+  static constexpr int S = tc_round_s(6 * Np);  // element stride of the field layout
+  static constexpr int FJ = 8 * KF;             // face-node slots per field
+  static constexpr int ST = tc_round_s(6 * FJ); // element stride of the trace / flux buffer
+  static constexpr int OUTS = S > ST ? S : ST;  // row capacity of the trace buffer, reused for the rhs tile
+  // B-fragment sets (32 lanes x float4 each)
+  static constexpr int B_DR = 0;
+  static constexpr int B_DS = B_DR + KS * NT;
+  static constexpr int B_LIFT = B_DS + KS * NT;
+  static constexpr int B_I = B_LIFT + KF * NT;
+  static constexpr int B_P = B_I + CH * KS;
+  static constexpr int NSETS = B_P + CH * NT;
+  static constexpr int GEOS = 17;               // per element: rx sx ry sy iJ vx[3] vy[3] ex[3] ey[3]
+  static constexpr int W = 4;                   // warps per CTA
+  static constexpr int WARP_FLOATS = 16 * S + 16 * OUTS + 16 * GEOS + 4;
+};
+
+template <int N>
+__device__ __forceinline__ int tc_fmask(int f, int k) {
+  constexpr int NN = N;
+  auto rs = [](int j) { return j * (NN + 1) - j * (j - 1) / 2; };
+  return f == 0 ? k : (f == 1 ? rs(k) + (NN - k) : rs(NN - k));
+}
+
+__device__ __forceinline__ unsigned to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// c += (ahi + alo)(bhi + blo), dropping alo * blo; b = (blo0, blo1, bhi0, bhi1)
+__device__ __forceinline__ void mma3(float (&c)[4], const unsigned (&ahi)[4], const unsigned (&alo)[4], const float4 b) {
+  mma_tf32(c, alo, __float_as_uint(b.z), __float_as_uint(b.w));
+  mma_tf32(c, ahi, __float_as_uint(b.x), __float_as_uint(b.y));
+  mma_tf32(c, ahi, __float_as_uint(b.z), __float_as_uint(b.w));
+}
+
+__device__ __forceinline__ void tc_cp_async16(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void tc_cp_async4(float *dst, const float *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void tc_cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+__device__ __forceinline__ void tc_l2_prefetch(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// A fragment of rows (element) x columns [col0, col0 + 8) from a row-major smem tile
+// with row stride `stride`; columns >= ncol are zero.
+template <int STRIDE>
+__device__ __forceinline__ void load_a(const float *tile, int col0, int ncol, int g, int t, unsigned (&hi)[4], unsigned (&lo)[4]) {
+  const int c0 = col0 + t, c1 = col0 + t + 4;
+  const float x0 = c0 < ncol ? tile[g * STRIDE + c0] : 0.0f;
+  const float x1 = c0 < ncol ? tile[(g + 8) * STRIDE + c0] : 0.0f;
+  const float x2 = c1 < ncol ? tile[g * STRIDE + c1] : 0.0f;
+  const float x3 = c1 < ncol ? tile[(g + 8) * STRIDE + c1] : 0.0f;
+  split_tf32(x0, hi[0], lo[0]);
+  split_tf32(x1, hi[1], lo[1]);
+  split_tf32(x2, hi[2], lo[2]);
+  split_tf32(x3, hi[3], lo[3]);
+}
+
+template <int N, int STAGE>
+__global__ void __launch_bounds__(32 * TcDim<N>::W) tc_stage_kernel(const StageArgs a) {
+  typedef TcDim<N> D;
+  constexpr int Np = D::Np, Nfp = D::Nfp, NFN = D::NFN, KS = D::KS, KF = D::KF, NT = D::NT, CH = D::CH;
+  constexpr int S = D::S, ST = D::ST, FJ = D::FJ, GEOS = D::GEOS, W = D::W;
+  const float SQ2 = 1.41421356237309505f, ISQ2 = 0.70710678118654752f;
+  extern __shared__ float4 tc_smem4[];
+  float4 *btab = tc_smem4;                                          // [NSETS][32]
+  float *wbase = reinterpret_cast<float *>(tc_smem4 + D::NSETS * 32);
+  __shared__ double s_motion[2];
+  {
+    const float4 *g4 = reinterpret_cast<const float4 *>(a.ops);
+    for (int i = threadIdx.x; i < D::NSETS * 32; i += blockDim.x) btab[i] = g4[i];
+  }
+  if (threadIdx.x == 0) {
+    double gf = 0.0, xf = 0.0, fin = 0.0;
+    if (a.motion_A != 0.0) {
+      const double w = a.motion_w, Aw = a.motion_A * a.motion_w;
+      if (STAGE < 0) {
+        gf = Aw * cos(w * a.rhs_time);
+      } else {
+        const double t = a.clock[0], dt = a.dt;
+        const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+        gf = Aw * cos(w * (t + cst[STAGE] * dt));
+        if (STAGE > 0) xf = dt * cst[STAGE == 3 ? 3 : 1] * Aw * cos(w * (t + cst[STAGE - 1] * dt));
+        if (STAGE == 3) fin = dt * Aw * (cos(w * t) / 6.0 + cos(w * (t + 0.5 * dt)) * (2.0 / 3.0) + cos(w * (t + dt)) / 6.0);
+      }
+    }
+    s_motion[0] = gf;
+    s_motion[1] = xf;
+    if (STAGE == 3 && blockIdx.x == 0) const_cast<double *>(a.clock)[1] = fin;
+  }
+  __syncthreads();
+  const double gfac = s_motion[0], xfac = s_motion[1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, t = lane & 3;
+  float *own = wbase + warp * D::WARP_FLOATS;   // [16][S]   fields of the tile
+  float *trc = own + 16 * S;                    // [16][ST] traces -> fluxes, then [16][S] rhs (16 OUTS floats)
+  float *geo = trc + 16 * D::OUTS;              // [16][GEOS]
+  const float *qin = reinterpret_cast<const float *>(a.qin);
+  const float c = (float)a.c, mc = -(float)a.c, mcs = -(float)a.c * SQ2;
+  const float itau = (float)a.inv_tau;
+  // barycentric coordinates of the 2 NT output nodes this lane holds in accumulator fragments
+  float bl[NT][2][3];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int n = nt * 8 + 2 * t + j;
+      const float *bary = reinterpret_cast<const float *>(a.ops) + D::NSETS * 128 + 4 * (n < Np ? n : 0);
+      bl[nt][j][0] = bary[0];
+      bl[nt][j][1] = bary[1];
+      bl[nt][j][2] = bary[2];
+    }
+  const int64_t ntile = (a.K + 15) >> 4;
+  const int64_t tstride = (int64_t)gridDim.x * W;
+
+  for (int64_t tile = (int64_t)blockIdx.x * W + warp; tile < ntile; tile += tstride) {
+    const int64_t e0 = tile * 16;
+    const int nel = (int)((a.K - e0) < 16 ? (a.K - e0) : 16);
+    __syncwarp();
+    // ---- stage the tile's fields (contiguous) ----
+    {
+      const float *src = qin + e0 * S;
+      for (int i = lane; i < 4 * S; i += 32) tc_cp_async16(own + 4 * i, src + 4 * i);
+      asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    // ---- neighbour traces: item = (element, face), 48 per tile ----
+    for (int item = lane; item < 48; item += 32) {
+      const int el = item % 16, f = item / 16;
+      if (el < nel) {
+        const int nb = a.mesh[e0 + el].nbr[f];
+        const int f2 = nb & 3;
+        const float *qp = qin + (int64_t)(nb >> 2) * S;
+#pragma unroll
+        for (int k = 0; k < Nfp; ++k) {
+          const int vol2 = tc_fmask<N>(f2, Nfp - 1 - k);
+#pragma unroll
+          for (int fld = 0; fld < 6; ++fld) tc_cp_async4(trc + el * ST + fld * FJ + f * Nfp + k, qp + fld * Np + vol2);
+        }
+      }
+    }
+    if (lane == 0) {
+      const unsigned bytes = 16 * S * sizeof(float);
+      if (STAGE >= 1) {
+        tc_l2_prefetch(reinterpret_cast<const float *>(a.qn) + e0 * S, bytes);
+        if (STAGE <= 2) tc_l2_prefetch(reinterpret_cast<const float *>(a.F0) + e0 * S, bytes);
+        if (STAGE >= 2) tc_l2_prefetch(reinterpret_cast<const float *>(a.acc) + e0 * S, bytes);
+      }
+      if (tile + tstride < ntile) {
+        tc_l2_prefetch(qin + (tile + tstride) * 16 * S, bytes);
+        const int64_t m0 = (tile + tstride) * 16;
+        const int64_t mcount = (a.K - m0) < 16 ? (a.K - m0) : 16;   // records that exist
+        tc_l2_prefetch(a.mesh + m0, (unsigned)(mcount * sizeof(MeshRec)));
+      }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    // ---- geometry of the tile's elements (lanes 0..15), while the copies fly ----
+    if (lane < 16) {
+      float *gm = geo + lane * GEOS;
+      float ex[3] = {1.f, 0.f, -1.f}, ey[3] = {0.f, 1.f, -1.f}, vx[3] = {0.f, 0.f, 0.f}, vy[3] = {0.f, 0.f, 0.f};
+      if (lane < nel) {
+        const MeshRec rec = a.mesh[e0 + lane];
+        double px[3], py[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const double2 xv = reinterpret_cast<const double2 *>(a.xn)[rec.v[k]];
+          const double2 sv = reinterpret_cast<const double2 *>(a.shape)[rec.v[k]];
+          px[k] = fma(xfac, sv.x, xv.x + rec.shift[2 * k] * a.period[0]);
+          py[k] = fma(xfac, sv.y, xv.y + rec.shift[2 * k + 1] * a.period[1]);
+          vx[k] = (float)(gfac * sv.x);
+          vy[k] = (float)(gfac * sv.y);
+        }
+        ex[0] = (float)(px[1] - px[0]); ey[0] = (float)(py[1] - py[0]);
+        ex[1] = (float)(px[2] - px[1]); ey[1] = (float)(py[2] - py[1]);
+        ex[2] = (float)(px[0] - px[2]); ey[2] = (float)(py[0] - py[2]);
+      }
+      const float xr = 0.5f * ex[0], yr = 0.5f * ey[0], xs = -0.5f * ex[2], ys = -0.5f * ey[2];
+      const float J = xr * ys - xs * yr;
+      if (lane < nel && !(J > 0.0f)) atomicOr(a.status, GB_STATUS_MESH);
+      const float iJ = 1.0f / J;
+      gm[0] = ys * iJ; gm[1] = -yr * iJ; gm[2] = -xs * iJ; gm[3] = xr * iJ; gm[4] = iJ;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        gm[5 + k] = vx[k];
+        gm[8 + k] = vy[k];
+        gm[11 + k] = ex[k];
+        gm[14 + k] = ey[k];
+      }
+    }
+    // the own fields (first group) are needed now; the traces only for the surface term
+    asm volatile("cp.async.wait_group 1;" ::: "memory");
+    __syncwarp();
+
+    // accumulators: rhs[field][n-tile][fragment]
+    float acc[6][NT][4];
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[f][nt][j] = 0.0f;
+
+    // per-row geometry of this lane's two elements (rows g and g + 8)
+    float rxr[2], sxr[2], ryr[2], syr[2], vgxp[2][NT][2], vgyp[2][NT][2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const float *gm = geo + (g + 8 * h) * GEOS;
+      rxr[h] = gm[0]; sxr[h] = gm[1]; ryr[h] = gm[2]; syr[h] = gm[3];
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int col = 0; col < 2; ++col) {
+          vgxp[h][nt][col] = bl[nt][col][0] * gm[5] + bl[nt][col][1] * gm[6] + bl[nt][col][2] * gm[7];
+          vgyp[h][nt][col] = bl[nt][col][0] * gm[8] + bl[nt][col][1] * gm[9] + bl[nt][col][2] * gm[10];
+        }
+    }
+
+    // ---- volume: (A + v_G) . grad q ----
+#pragma unroll 1
+    for (int f = 0; f < 6; ++f) {
+      float dr[NT][4], ds[NT][4];
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { dr[nt][j] = 0.0f; ds[nt][j] = 0.0f; }
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks) {
+        unsigned ahi[4], alo[4];
+        load_a<S>(own, f * Np + ks * 8, f * Np + Np, g, t, ahi, alo);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          mma3(dr[nt], ahi, alo, btab[(D::B_DR + ks * NT + nt) * 32 + lane]);
+          mma3(ds[nt], ahi, alo, btab[(D::B_DS + ks * NT + nt) * 32 + lane]);
+        }
+      }
+      // pointwise: chain rule, v_G . grad q_f and the Atilde couplings (Sec. 2)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int h = j >> 1, col = j & 1;
+          const float qx = rxr[h] * dr[nt][j] + sxr[h] * ds[nt][j];
+          const float qy = ryr[h] * dr[nt][j] + syr[h] * ds[nt][j];
+          const float ale = vgxp[h][nt][col] * qx + vgyp[h][nt][col] * qy;
+          switch (f) {
+            case 0: acc[0][nt][j] += ale; acc[1][nt][j] = fmaf(mc, qx, acc[1][nt][j]); acc[2][nt][j] = fmaf(mc, qy, acc[2][nt][j]); break;
+            case 1: acc[1][nt][j] += ale; acc[0][nt][j] = fmaf(mc, qx, acc[0][nt][j]); acc[3][nt][j] = fmaf(mc, qy, acc[3][nt][j]);
+                    acc[4][nt][j] = fmaf(mcs, qx, acc[4][nt][j]); break;
+            case 2: acc[2][nt][j] += ale; acc[0][nt][j] = fmaf(mc, qy, acc[0][nt][j]); acc[3][nt][j] = fmaf(mc, qx, acc[3][nt][j]);
+                    acc[5][nt][j] = fmaf(mcs, qy, acc[5][nt][j]); break;
+            case 3: acc[3][nt][j] += ale; acc[2][nt][j] = fmaf(mc, qx, acc[2][nt][j]); acc[1][nt][j] = fmaf(mc, qy, acc[1][nt][j]); break;
+            case 4: acc[4][nt][j] += ale; acc[1][nt][j] = fmaf(mcs, qx, acc[1][nt][j]); break;
+            default: acc[5][nt][j] += ale; acc[2][nt][j] = fmaf(mcs, qy, acc[2][nt][j]); break;
+          }
+        }
+    }
+
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+    // ---- surface fluxes: item = (element, face), flux overwrites the trace in place ----
+    for (int item = lane; item < 48; item += 32) {
+      const int el = item % 16, f = item / 16;
+      if (el >= nel) continue;
+      const float *gm = geo + el * GEOS;
+      const float dx = gm[11 + f], dy = gm[14 + f];
+      const float len = sqrtf(dx * dx + dy * dy);
+      const float il = 1.0f / len;
+      const float nx = dy * il, ny = -dx * il;
+      const float fs = 0.5f * len * gm[4];
+      const float h = 0.5f * c * fs;
+      const float al = (9.0f - 1.7320508075688772f) / 6.0f, be = (1.7320508075688772f - 3.0f) / 6.0f;
+      const float nn = nx * nx + ny * ny;
+      const float m00 = nn, m01 = 2.0f * nx * ny, m02 = SQ2 * nx * nx, m03 = SQ2 * ny * ny;
+      const float m12 = SQ2 * nx * ny, m22 = 2.0f * nx * nx, m33 = 2.0f * ny * ny;
+      const float q00 = m00 * m00 + m01 * m01 + m02 * m02 + m03 * m03;
+      const float q01 = m00 * m01 + m01 * m00 + m02 * m12 + m03 * m12;
+      const float q02 = m00 * m02 + m01 * m12 + m02 * m22;
+      const float q03 = m00 * m03 + m01 * m12 + m03 * m33;
+      const float q11 = m01 * m01 + m00 * m00 + m12 * m12 + m12 * m12;
+      const float q12 = m01 * m02 + m00 * m12 + m12 * m22;
+      const float q13 = m01 * m03 + m00 * m12 + m12 * m33;
+      const float q22 = m02 * m02 + m12 * m12 + m22 * m22;
+      const float q23 = m02 * m03 + m12 * m12;
+      const float q33 = m03 * m03 + m12 * m12 + m33 * m33;
+      const float M00 = h * (al * m00 + be * q00), M03 = h * (al * m01 + be * q01), M04 = h * (al * m02 + be * q02);
+      const float M05 = h * (al * m03 + be * q03), M33 = h * (al * m00 + be * q11), M34 = h * (al * m12 + be * q12);
+      const float M35 = h * (al * m12 + be * q13), M44 = h * (al * m22 + be * q22), M45 = h * (be * q23);
+      const float M55 = h * (al * m33 + be * q33);
+      const float o11 = 3.0f * nx * nx + ny * ny, o12 = 2.0f * nx * ny, o22 = nx * nx + 3.0f * ny * ny;
+      const float N11 = h * (al * o11 + be * (o11 * o11 + o12 * o12));
+      const float N12 = h * (al * o12 + be * (o11 * o12 + o12 * o22));
+      const float N22 = h * (al * o22 + be * (o12 * o12 + o22 * o22));
+      const float hnx = h * nx, hny = h * ny, hsx = h * SQ2 * nx, hsy = h * SQ2 * ny;
+      const float vx0 = gm[5], vx1 = gm[6], vx2 = gm[7], vy0 = gm[8], vy1 = gm[9], vy2 = gm[10];
+      const float *bary = reinterpret_cast<const float *>(a.ops) + D::NSETS * 128;
+#pragma unroll
+      for (int k = 0; k < Nfp; ++k) {
+        const int vol = tc_fmask<N>(f, k);
+        const int j = f * Nfp + k;
+        float *tr = trc + el * ST + j;
+        const float *qm = own + el * S + vol;
+        float w[6];
+#pragma unroll
+        for (int fld = 0; fld < 6; ++fld) w[fld] = tr[fld * FJ] - qm[fld * Np];
+        const float b0 = __ldg(bary + 4 * vol), b1 = __ldg(bary + 4 * vol + 1), b2 = __ldg(bary + 4 * vol + 2);
+        const float vn = (b0 * vx0 + b1 * vx1 + b2 * vx2) * nx + (b0 * vy0 + b1 * vy1 + b2 * vy2) * ny;
+        const float ale = vn > 0.0f ? vn * fs : 0.0f;
+        tr[0 * FJ] = M00 * w[0] + M03 * w[3] + M04 * w[4] + M05 * w[5] - hnx * w[1] - hny * w[2] + ale * w[0];
+        tr[3 * FJ] = M03 * w[0] + M33 * w[3] + M34 * w[4] + M35 * w[5] - hnx * w[2] - hny * w[1] + ale * w[3];
+        tr[4 * FJ] = M04 * w[0] + M34 * w[3] + M44 * w[4] + M45 * w[5] - hsx * w[1] + ale * w[4];
+        tr[5 * FJ] = M05 * w[0] + M35 * w[3] + M45 * w[4] + M55 * w[5] - hsy * w[2] + ale * w[5];
+        tr[1 * FJ] = N11 * w[1] + N12 * w[2] - hnx * w[0] - hsx * w[4] - hny * w[3] + ale * w[1];
+        tr[2 * FJ] = N12 * w[1] + N22 * w[2] - hny * w[0] - hsy * w[5] - hnx * w[3] + ale * w[2];
+      }
+    }
+    __syncwarp();
+
+    // ---- LIFT of the fluxes ----
+#pragma unroll 1
+    for (int f = 0; f < 6; ++f) {
+#pragma unroll
+      for (int kf = 0; kf < KF; ++kf) {
+        unsigned ahi[4], alo[4];
+        load_a<ST>(trc, f * FJ + kf * 8, f * FJ + NFN, g, t, ahi, alo);
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          switch (f) {   // keeps the accumulator index compile-time
+            case 0: mma3(acc[0][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
+            case 1: mma3(acc[1][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
+            case 2: mma3(acc[2][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
+            case 3: mma3(acc[3][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
+            case 4: mma3(acc[4][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
+            default: mma3(acc[5][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
+          }
+        }
+      }
+    }
+
+    // ---- collision term: I q at the cubature points, Ntilde there, P back (fields 4..6) ----
+    {
+      unsigned qh[3][KS][4], ql[3][KS][4];
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) load_a<S>(own, f * Np + ks * 8, f * Np + Np, g, t, qh[f][ks], ql[f][ks]);
+#pragma unroll 1
+      for (int ch = 0; ch < CH; ++ch) {
+        float qc[3][4];
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) qc[f][j] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+          const float4 b = btab[(D::B_I + ch * KS + ks) * 32 + lane];
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma3(qc[f], qh[f][ks], ql[f][ks], b);
+        }
+        // Ntilde at the 4 (element, point) positions; the accumulator order (c0, c2, c1, c3)
+        // is the A-fragment order of the permuted chunk
+        unsigned nh[3][4], nl[3][4];
+        const int perm[4] = {0, 2, 1, 3};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int src = perm[j];
+          const float q1 = 1.0f + qc[0][src], q2 = qc[1][src], q3 = qc[2][src];
+          const float r1 = itau * __frcp_rn(q1);
+          const float rs = r1 * ISQ2;
+          split_tf32(q2 * q3 * r1, nh[0][j], nl[0][j]);
+          split_tf32(q2 * q2 * rs, nh[1][j], nl[1][j]);
+          split_tf32(q3 * q3 * rs, nh[2][j], nl[2][j]);
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const float4 b = btab[(D::B_P + ch * NT + nt) * 32 + lane];
+          mma3(acc[3][nt], nh[0], nl[0], b);
+          mma3(acc[4][nt], nh[1], nl[1], b);
+          mma3(acc[5][nt], nh[2], nl[2], b);
+        }
+      }
+    }
+
+    // ---- rhs tile to shared memory (over the fluxes), then the SARK pass ----
+    __syncwarp();
+    float *out = trc;   // [16][S]
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int row = g + 8 * (j >> 1), n = nt * 8 + 2 * t + (j & 1);
+          if (n < Np) out[row * S + f * Np + n] = acc[f][nt][j];
+        }
+    __syncwarp();
+    {
+      const float dt = (float)a.dt;
+      // lane slots w = lane + 32 sl of each element's 6 Np values; class 0 for fields 1..3
+      constexpr int NSL = (6 * Np + 31) / 32;
+      float E1[NSL], A0[NSL], A1[NSL], Bc[NSL], B1[NSL];
+#pragma unroll
+      for (int sl = 0; sl < NSL; ++sl) {
+        const int cl = (lane + 32 * sl) < 3 * Np ? 0 : 1;
+        E1[sl] = (float)a.co.E[cl][STAGE < 0 ? 0 : (STAGE < 3 ? STAGE + 1 : 4)];
+        A0[sl] = STAGE == 0 ? (float)a.co.A[cl][4] : STAGE == 1 ? (float)a.co.A[cl][8] : STAGE == 2 ? (float)a.co.A[cl][12] : 0.0f;
+        A1[sl] = STAGE == 1 ? (float)a.co.A[cl][9] : STAGE == 2 ? (float)a.co.A[cl][14] : 0.0f;
+        Bc[sl] = STAGE == 1 ? (float)a.co.B[cl][0] : STAGE == 2 ? (float)a.co.B[cl][2] : STAGE == 3 ? (float)a.co.B[cl][3] : 0.0f;
+        B1[sl] = (float)a.co.B[cl][1];
+      }
+      bool bad = false;
+      float *Fo = reinterpret_cast<float *>(a.Fout);
+      float *qo = reinterpret_cast<float *>(a.qout);
+      float *F0 = reinterpret_cast<float *>(a.F0);
+      float *ac = reinterpret_cast<float *>(a.acc);
+      const float *qn = reinterpret_cast<const float *>(a.qn);
+#pragma unroll 4
+      for (int r = 0; r < 16; ++r) {
+        if (r < nel) {
+          const int64_t rowg = (e0 + r) * S;
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl) {
+            const int w = lane + 32 * sl;
+            if (w < 6 * Np) {
+              const float rv = out[r * S + w];
+              const int64_t gi = rowg + w;
+              if (STAGE < 0) {
+                Fo[gi] = rv;
+              } else if (STAGE == 0) {
+                F0[gi] = rv;
+                qo[gi] = E1[sl] * own[r * S + w] + dt * (A0[sl] * rv);
+              } else if (STAGE == 1) {
+                const float qv = qn[gi], f0 = F0[gi];
+                qo[gi] = E1[sl] * qv + dt * (A0[sl] * f0 + A1[sl] * rv);
+                ac[gi] = Bc[sl] * f0 + B1[sl] * rv;
+              } else if (STAGE == 2) {
+                const float qv = qn[gi], f0 = F0[gi], av = ac[gi];
+                qo[gi] = E1[sl] * qv + dt * (A0[sl] * f0 + A1[sl] * rv);
+                ac[gi] = av + Bc[sl] * rv;
+              } else {
+                const float qv = qn[gi], av = ac[gi];
+                const float o = E1[sl] * qv + dt * (av + Bc[sl] * rv);
+                qo[gi] = o;
+                bad |= (__float_as_int(o) & 0x7f800000) == 0x7f800000;
+              }
+            }
+          }
+        }
+      }
+      if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int N>
+static size_t tc_smem() {
+  typedef TcDim<N> D;
+  return sizeof(float4) * (size_t)D::NSETS * 32 + sizeof(float) * (size_t)D::W * D::WARP_FLOATS;
+}
+
+template <int N, int STAGE>
+static int tc_launch_one(const StageArgs &a, cudaStream_t st, int num_sms) {
+  typedef TcDim<N> D;
+  const size_t smem = tc_smem<N>();
+  constexpr int threads = 32 * D::W;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(tc_stage_kernel<N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_stage_kernel<N, STAGE>, threads, smem);
+  if (err != cudaSuccess) return (int)err;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  const int64_t need = ((a.K + 15) / 16 + D::W - 1) / D::W;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  tc_stage_kernel<N, STAGE><<<(unsigned)grid, threads, smem, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <int N>
+static int tc_launch_n(const StageArgs &a, cudaStream_t st, int num_sms) {
+  switch (a.stage) {
+    case -1: return tc_launch_one<N, -1>(a, st, num_sms);
+    case 0: return tc_launch_one<N, 0>(a, st, num_sms);
+    case 1: return tc_launch_one<N, 1>(a, st, num_sms);
+    case 2: return tc_launch_one<N, 2>(a, st, num_sms);
+    case 3: return tc_launch_one<N, 3>(a, st, num_sms);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_stage_mixed(int N, const StageArgs &a, void *stream, int num_sms) {
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (N) {
+    case 1: return tc_launch_n<1>(a, st, num_sms);
+    case 2: return tc_launch_n<2>(a, st, num_sms);
+    case 3: return tc_launch_n<3>(a, st, num_sms);
+    case 4: return tc_launch_n<4>(a, st, num_sms);
+    case 5: return tc_launch_n<5>(a, st, num_sms);
+    case 6: return tc_launch_n<6>(a, st, num_sms);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int mixed_stride(int N) {
+  switch (N) {
+    case 1: return TcDim<1>::S;
+    case 2: return TcDim<2>::S;
+    case 3: return TcDim<3>::S;
+    case 4: return TcDim<4>::S;
+    case 5: return TcDim<5>::S;
+    case 6: return TcDim<6>::S;
+  }
+  return 0;
+}
+
+// ---- operator tables: B fragments (hi, lo) per lane, then the node barycentric table ----
+static inline float tf32_round_host(float x) {
+  // round to nearest, ties away from zero, at 10 explicit mantissa bits (cvt.rna.tf32.f32)
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x1000u;
+    u &= 0xffffe000u;
+  }
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+
+template <int N>
+static void fill_tc(const RefOps &Rf, std::vector<float> &h) {
+  typedef TcDim<N> D;
+  const int Np = D::Np, NFN = D::NFN, Nc = D::Nc;
+  h.assign((size_t)D::NSETS * 128 + 4 * 32, 0.0f);
+  auto put = [&](int set, auto Bfun) {   // Bfun(k, n) -> value of the K x N operand
+    for (int lane = 0; lane < 32; ++lane) {
+      const int gq = lane >> 2, tq = lane & 3;
+      const float v0 = (float)Bfun(tq, gq), v1 = (float)Bfun(tq + 4, gq);
+      const float h0 = tf32_round_host(v0), h1 = tf32_round_host(v1);
+      float *o = &h[((size_t)set * 32 + lane) * 4];
+      o[0] = tf32_round_host(v0 - h0);
+      o[1] = tf32_round_host(v1 - h1);
+      o[2] = h0;
+      o[3] = h1;
+    }
+  };
+  for (int ks = 0; ks < D::KS; ++ks)
+    for (int nt = 0; nt < D::NT; ++nt) {
+      put(D::B_DR + ks * D::NT + nt, [&](int k, int n) {
+        const int m = ks * 8 + k, o = nt * 8 + n;
+        return (m < Np && o < Np) ? Rf.Dr[o * Np + m] : 0.0;
+      });
+      put(D::B_DS + ks * D::NT + nt, [&](int k, int n) {
+        const int m = ks * 8 + k, o = nt * 8 + n;
+        return (m < Np && o < Np) ? Rf.Ds[o * Np + m] : 0.0;
+      });
+    }
+  for (int kf = 0; kf < D::KF; ++kf)
+    for (int nt = 0; nt < D::NT; ++nt)
+      put(D::B_LIFT + kf * D::NT + nt, [&](int k, int n) {
+        const int j = kf * 8 + k, o = nt * 8 + n;
+        return (j < NFN && o < Np) ? Rf.LIFT[o * NFN + j] : 0.0;
+      });
+  for (int ch = 0; ch < D::CH; ++ch)
+    for (int ks = 0; ks < D::KS; ++ks)
+      put(D::B_I + ch * D::KS + ks, [&](int k, int n) {
+        const int m = ks * 8 + k, cp = ch * 8 + n;
+        return (m < Np && cp < Nc) ? Rf.I[cp * Np + m] : 0.0;
+      });
+  for (int ch = 0; ch < D::CH; ++ch)
+    for (int nt = 0; nt < D::NT; ++nt)
+      put(D::B_P + ch * D::NT + nt, [&](int k, int n) {
+        // chunk columns taken in the order (0,2,4,6,1,3,5,7): k < 4 -> point 2k, k >= 4 -> 2(k-4)+1
+        const int cp = ch * 8 + (k < 4 ? 2 * k : 2 * (k - 4) + 1), o = nt * 8 + n;
+        return (cp < Nc && o < Np) ? Rf.P[o * Nc + cp] : 0.0;
+      });
+  // fragment float4 = (lo0, lo1, hi0, hi1): mma3 uses .x/.y as the tail and .z/.w as the head
+  float *bary = &h[(size_t)D::NSETS * 128];
+  for (int n = 0; n < Np && n < 32; ++n) {
+    bary[4 * n] = (float)(-0.5 * (Rf.r[n] + Rf.s[n]));
+    bary[4 * n + 1] = (float)(0.5 * (1.0 + Rf.r[n]));
+    bary[4 * n + 2] = (float)(0.5 * (1.0 + Rf.s[n]));
+  }
+}
+
+int upload_ops_mixed(int N, const RefOps &Rf, float **dev_ops, void *stream) {
+  std::vector<float> h;
+  switch (N) {
+    case 1: fill_tc<1>(Rf, h); break;
+    case 2: fill_tc<2>(Rf, h); break;
+    case 3: fill_tc<3>(Rf, h); break;
+    case 4: fill_tc<4>(Rf, h); break;
+    case 5: fill_tc<5>(Rf, h); break;
+    case 6: fill_tc<6>(Rf, h); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  void *d = nullptr;
+  cudaError_t err = cudaMalloc(&d, h.size() * sizeof(float));
+  if (err != cudaSuccess) return (int)err;
+  err = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize((cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    cudaFree(d);
+    return (int)err;
+  }
+  *dev_ops = reinterpret_cast<float *>(d);
+  return 0;
+}
+
+// ---------------------------------------------------------------------------
+// canonical <-> internal (element-major, stride S, Morton order) relayout.
+// perm[i] = canonical index of internal element i.  rest is added to field 1
+// on the way out and subtracted on the way in (0 for arrays that are not states).
+template <typename Tc, bool TO_INTERNAL>
+__global__ void relayout_kernel(Tc *canon, float *inner, const int32_t *perm, int64_t K, int Np, int S, double rest) {
+  const int NQ = 6 * Np;
+  const int64_t total = K * NQ;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / NQ;
+    const int fn = (int)(i - e * NQ);
+    const int64_t ci = (int64_t)perm[e] * NQ + fn;
+    const int64_t ii = e * S + fn;
+    const double r = fn < Np ? rest : 0.0;
+    if (TO_INTERNAL) inner[ii] = (float)((double)canon[ci] - r);
+    else canon[ci] = (Tc)((double)inner[ii] + r);
+  }
+}
+
+int launch_relayout(const void *canon_src, void *canon_dst, bool canon_is_double, bool to_internal, float *inner,
+                    const int32_t *perm, int64_t K, int Np, int S, double rest, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  const unsigned blocks = 2048, thr = 256;
+  if (to_internal) {
+    if (canon_is_double)
+      relayout_kernel<double, true><<<blocks, thr, 0, st>>>(const_cast<double *>((const double *)canon_src), inner, perm, K, Np, S, rest);
+    else
+      relayout_kernel<float, true><<<blocks, thr, 0, st>>>(const_cast<float *>((const float *)canon_src), inner, perm, K, Np, S, rest);
+  } else {
+    if (canon_is_double)
+      relayout_kernel<double, false><<<blocks, thr, 0, st>>>((double *)canon_dst, inner, perm, K, Np, S, rest);
+    else
+      relayout_kernel<float, false><<<blocks, thr, 0, st>>>((float *)canon_dst, inner, perm, K, Np, S, rest);
+  }
+  return (int)cudaGetLastError();
+}
+
+}  // namespace gb

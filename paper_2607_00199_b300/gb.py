@@ -56,6 +56,7 @@ def _load():
         'gb_nodes': ([vp, _dp], c_int),
         'gb_rhs': ([vp, c_double, vp, vp], c_int),
         'gb_step': ([vp, c_double, i64], c_int),
+        'gb_step_timed': ([vp, c_double, i64, _dp], c_int),
         'gb_sync': ([vp], c_int),
         'gb_info': ([vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                      ctypes.POINTER(i64), ctypes.POINTER(i64), _dp, _dp, ctypes.POINTER(i64)], c_int),
@@ -182,6 +183,13 @@ class Solver:
 
     def step(self, dt, nsteps=1):
         self._c(lib.gb_step(self.h, float(dt), int(nsteps)))
+
+    def step_timed(self, dt, nsteps=1):
+        """Steps with a CUDA event pair around every kernel; returns the summed device
+        milliseconds per kernel kind: [stage 0, stage 1, stage 2, stage 3, vertex update]."""
+        ms = np.zeros(5)
+        self._c(lib.gb_step_timed(self.h, float(dt), int(nsteps), _ptr(ms)))
+        return ms
 
     def sync(self):
         self._c(lib.gb_sync(self.h))

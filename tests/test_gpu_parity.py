@@ -157,6 +157,63 @@ def test_mixed_precision_error_cfg1():
     assert rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
 
 
+@pytest.mark.parametrize('N', [1, 2, 3, 4, 5, 6])
+def test_mixed_rhs_all_orders_ragged(N):
+    # K = 50: two 32-element interleave blocks, the second one partly padding
+    mesh, o, s = make_pair(5, N, 0.1, 100.0, 0.05, 1.0, jitter=0.1, precision=gb.GB_MIXED)
+    t = 0.3
+    xv = o.X + o.motion.displacement(o.X, t)
+    s.set_vertices(xv)
+    q = oracle_state(o, xv, lambda x, y: inputs.random_flow(x, y, 21 + N))
+    F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
+    F_gpu = gpu_rhs(s, q, t)
+    assert rel_l2(F_gpu, F_or) <= 1e-5
+    for f in range(6):
+        assert rel_l2(F_gpu[:, f], F_or[:, f]) <= 1e-4, f
+
+
+@pytest.mark.parametrize('N', [2, 4, 5])
+def test_mixed_step_other_orders(N):
+    flow = lambda x, y: inputs.random_flow(x, y, 4)
+    q_gpu, q_or, *_ = run_both(7, N, 0.1, 300.0, 0.04, 0.6, 20, flow, jitter=0.1, precision=gb.GB_MIXED)
+    assert rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
+
+
+def test_mixed_full_size_cfg2_step():
+    mesh, o, s = make_pair(256, 4, 0.1, 1000.0, 0.05, 1.0, jitter=0.1, precision=gb.GB_MIXED)
+    q0 = oracle_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1))
+    dt = inputs.cfl_dt(mesh, 4, o.c, 0.5)
+    s.set_fields(q0, 0.0)
+    s.step(dt, 2)
+    q_gpu, _ = s.fields()
+    q_or, x_or, _ = o.run(q0, o.X.copy(), 0.0, dt, 2)
+    assert rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
+    np.testing.assert_allclose(s.vertices(), x_or, atol=1e-13)
+
+
+def test_mixed_checkpoint_and_status():
+    mesh, o, s = make_pair(9, 3, 0.1, 100.0, 0.05, 1.0, jitter=0.1, precision=gb.GB_MIXED)
+    q0 = oracle_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1))
+    dt = inputs.cfl_dt(mesh, 3, o.c, 0.5)
+    s.set_fields(q0, 0.0)
+    q_back, _ = s.fields()
+    # the FP32 perturbation round trip keeps rho to ~1e-8
+    assert np.abs(q_back - q0).max() < 1e-7
+    s.step(dt, 10)
+    q10, t10 = s.fields()
+    s.set_fields(q0, 0.0)
+    s.set_vertices(o.X)
+    s.step(dt, 10)
+    assert np.array_equal(s.fields()[0], q10)
+    bad = q0.copy()
+    bad[5, 4, 2] = np.inf
+    s.set_fields(bad, 0.0)
+    s.step(dt, 1)
+    with pytest.raises(gb.GBError) as ei:
+        s.fields()
+    assert ei.value.code == gb.GB_ENAN
+
+
 def test_mixed_rhs_matches_fp64_rhs():
     mesh, o, s = make_pair(8, 4, 0.1, 100.0, 0.05, 1.0, jitter=0.1, precision=gb.GB_MIXED)
     xv = o.X + o.motion.displacement(o.X, 0.1)
