@@ -134,6 +134,33 @@ int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *
  * curve, padded element stride) that only gb_fields translates. */
 int gb_state_ptr(gb_solver *s, void **q_dev);
 
+/* gb_rhs_noalloc: the same F as gb_rhs, for GB_MIXED solvers, without the
+ * library touching any device memory it allocated for scratch.  (The paper has
+ * no counterpart; this is an interface for a particular kind of caller.)
+ *
+ * Who needs it: a process whose device memory is handed out by its own pool or
+ * budget -- for instance a serving host that reserves its HBM at start-up --
+ * must not have a library call cudaMalloc or cudaFree behind its back, and may
+ * also want to evaluate a right-hand side without disturbing the solver's
+ * stage buffers, which gb_rhs of a GB_MIXED solver uses as scratch.  This call
+ * allocates and frees nothing: its scratch (the kernel-layout copies of q and
+ * F) is a static device array of 16 MiB that every GPU loading libgb holds
+ * until the process exits.
+ *
+ * Arguments and layout are those of gb_rhs in GB_MIXED mode (q_dev: canonical
+ * FP32 perturbations, F_dev: canonical FP32 F, both caller-owned device
+ * memory); work is enqueued on the solver's stream.  Limits and errors:
+ *  - GB_EINVAL for a GB_FP64 solver (its gb_rhs needs no scratch) and for a
+ *    mesh whose two internal copies exceed the array (at N = 4 about 22.8k
+ *    elements, N = 3 35k, N = 2 58k), with the limit in gb_last_error.
+ *  - The first call made with a given device current looks up the array's
+ *    device address on that device (cudaGetSymbolAddress); make that first
+ *    call before any stream capture.
+ *  - Every call, on any solver and stream, shares the one array, which keeps
+ *    the last call's contents (the call clears what it needs cleared): calls
+ *    that overlap on the GPU race and must be ordered by the caller. */
+int gb_rhs_noalloc(gb_solver *s, double t, const void *q_dev, void *F_dev);
+
 int gb_destroy(gb_solver *s);
 const char *gb_last_error(gb_solver *s);
 

@@ -577,3 +577,29 @@ int gb_sark_coefficients(double gamma, double *E, double *A, double *B) {
 }
 
 }  // extern "C"
+
+namespace gb {
+
+// View of a solver for the allocation-free right-hand side (gb_noalloc.cu): the
+// stage arguments of an rhs-only launch at time t, the element permutation and
+// the sizes.  Returns GB_EINVAL for a NULL solver.
+int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, int *N, int64_t *K, int *Np,
+                    int *precision, void **stream, int *num_sms) {
+  if (!s) return GB_EINVAL;
+  *a = base_args(s);
+  a->stage = -1;
+  a->rhs_time = t;
+  *perm = s->d_perm;
+  *N = s->N;
+  *K = s->K;
+  *Np = s->Np;
+  *precision = s->precision;
+  *stream = s->stream;
+  *num_sms = s->num_sms;
+  return GB_OK;
+}
+
+int set_solver_error(gb_solver *s, int code, const char *msg) { return fail(s, code, msg); }
+
+}  // namespace gb
+

@@ -86,6 +86,9 @@ int launch_nodes(int N, const double *ops, const double *xn, const MeshRec *mesh
 int launch_relayout(const void *canon_src, void *canon_dst, bool canon_is_double, bool to_internal, float *inner,
                     const int32_t *perm, int64_t K, int Np, int S, double rest, void *stream);
 int mixed_stride(int N);   // element stride (floats) of the GB_MIXED field layout
+int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, int *N, int64_t *K, int *Np,
+                    int *precision, void **stream, int *num_sms);
+int set_solver_error(gb_solver *s, int code, const char *msg);
 int upload_ops(int N, const RefOps &R, double **dev_ops, void *stream);
 int upload_ops_mixed(int N, const RefOps &R, float **dev_ops, void *stream);
 

@@ -55,6 +55,7 @@ def _load():
         'gb_vertices': ([vp, _dp], c_int),
         'gb_nodes': ([vp, _dp], c_int),
         'gb_rhs': ([vp, c_double, vp, vp], c_int),
+        'gb_rhs_noalloc': ([vp, c_double, vp, vp], c_int),
         'gb_step': ([vp, c_double, i64], c_int),
         'gb_step_timed': ([vp, c_double, i64, _dp], c_int),
         'gb_sync': ([vp], c_int),
@@ -180,6 +181,10 @@ class Solver:
 
     def rhs(self, t, q_dev, F_dev):
         self._c(lib.gb_rhs(self.h, float(t), _addr(q_dev), _addr(F_dev)))
+
+    def rhs_noalloc(self, t, q_dev, F_dev):
+        """gb_rhs_noalloc: GB_MIXED right-hand side with a static scratch array (no allocation)."""
+        self._c(lib.gb_rhs_noalloc(self.h, float(t), _addr(q_dev), _addr(F_dev)))
 
     def step(self, dt, nsteps=1):
         self._c(lib.gb_step(self.h, float(dt), int(nsteps)))
