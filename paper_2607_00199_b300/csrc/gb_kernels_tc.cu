@@ -125,7 +125,7 @@ __device__ __forceinline__ void load_a(const float *tile, int col0, int ncol, in
 }
 
 template <int N, int STAGE>
-__global__ void __launch_bounds__(32 * TcDim<N>::W) tc_stage_kernel(const StageArgs a) {
+__global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_kernel(const StageArgs a) {
   typedef TcDim<N> D;
   constexpr int Np = D::Np, Nfp = D::Nfp, NFN = D::NFN, KS = D::KS, KF = D::KF, NT = D::NT, CH = D::CH;
   constexpr int S = D::S, ST = D::ST, FJ = D::FJ, GEOS = D::GEOS, W = D::W;
@@ -480,38 +480,54 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W) tc_stage_kernel(const StageA
       float *F0 = reinterpret_cast<float *>(a.F0);
       float *ac = reinterpret_cast<float *>(a.acc);
       const float *qn = reinterpret_cast<const float *>(a.qn);
-#pragma unroll 4
-      for (int r = 0; r < 16; ++r) {
-        if (r < nel) {
-          const int64_t rowg = (e0 + r) * S;
+      // Batches of RB rows: every load of a batch is issued before any store of it
+      // (outputs may alias inputs: q_{n+1} overwrites q_n in place), so a batch costs
+      // one memory round trip instead of one per row.
+      constexpr int RB = 8;
+#pragma unroll 1
+      for (int r0 = 0; r0 < 16; r0 += RB) {
+        float rv[RB][NSL], x0[RB][NSL], x1[RB][NSL], x2[RB][NSL];
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
 #pragma unroll
           for (int sl = 0; sl < NSL; ++sl) {
-            const int w = lane + 32 * sl;
-            if (w < 6 * Np) {
-              const float rv = out[r * S + w];
-              const int64_t gi = rowg + w;
-              if (STAGE < 0) {
-                Fo[gi] = rv;
-              } else if (STAGE == 0) {
-                F0[gi] = rv;
-                qo[gi] = E1[sl] * own[r * S + w] + dt * (A0[sl] * rv);
-              } else if (STAGE == 1) {
-                const float qv = qn[gi], f0 = F0[gi];
-                qo[gi] = E1[sl] * qv + dt * (A0[sl] * f0 + A1[sl] * rv);
-                ac[gi] = Bc[sl] * f0 + B1[sl] * rv;
-              } else if (STAGE == 2) {
-                const float qv = qn[gi], f0 = F0[gi], av = ac[gi];
-                qo[gi] = E1[sl] * qv + dt * (A0[sl] * f0 + A1[sl] * rv);
-                ac[gi] = av + Bc[sl] * rv;
-              } else {
-                const float qv = qn[gi], av = ac[gi];
-                const float o = E1[sl] * qv + dt * (av + Bc[sl] * rv);
-                qo[gi] = o;
-                bad |= (__float_as_int(o) & 0x7f800000) == 0x7f800000;
-              }
+            const int r = r0 + rr, w = lane + 32 * sl;
+            const bool ok = r < nel && w < 6 * Np;
+            const int64_t gi = (e0 + r) * S + w;
+            rv[rr][sl] = ok ? out[r * S + w] : 0.0f;
+            x0[rr][sl] = x1[rr][sl] = x2[rr][sl] = 0.0f;
+            if (ok) {
+              if (STAGE == 0) x0[rr][sl] = own[r * S + w];
+              if (STAGE >= 1) x0[rr][sl] = qn[gi];
+              if (STAGE == 1 || STAGE == 2) x1[rr][sl] = F0[gi];
+              if (STAGE >= 2) x2[rr][sl] = ac[gi];
             }
           }
-        }
+#pragma unroll
+        for (int rr = 0; rr < RB; ++rr)
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl) {
+            const int r = r0 + rr, w = lane + 32 * sl;
+            if (!(r < nel && w < 6 * Np)) continue;
+            const int64_t gi = (e0 + r) * S + w;
+            const float r_ = rv[rr][sl], qv = x0[rr][sl], f0 = x1[rr][sl], av = x2[rr][sl];
+            if (STAGE < 0) {
+              Fo[gi] = r_;
+            } else if (STAGE == 0) {
+              F0[gi] = r_;
+              qo[gi] = E1[sl] * qv + dt * (A0[sl] * r_);
+            } else if (STAGE == 1) {
+              qo[gi] = E1[sl] * qv + dt * (A0[sl] * f0 + A1[sl] * r_);
+              ac[gi] = Bc[sl] * f0 + B1[sl] * r_;
+            } else if (STAGE == 2) {
+              qo[gi] = E1[sl] * qv + dt * (A0[sl] * f0 + A1[sl] * r_);
+              ac[gi] = av + Bc[sl] * r_;
+            } else {
+              const float o = E1[sl] * qv + dt * (av + Bc[sl] * r_);
+              qo[gi] = o;
+              bad |= (__float_as_int(o) & 0x7f800000) == 0x7f800000;
+            }
+          }
       }
       if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
     }
