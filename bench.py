@@ -44,6 +44,50 @@ TRAFFIC_FILE = os.path.join(ROOT, 'profiles', 'stage_kernel_traffic.json')
 FP64_FLOP_PER_CLK_SM = 4.0
 
 
+def run_serving(torch, n_req=256, steps=500, rate=50.0, budget_gib=16.0):
+    """Serving stream (configuration 5): n_req requests with Poisson
+    arrivals, K in {2048 .. 131072}, N in {2 .. 5}, random motion and Re, `steps` SARK
+    steps each, admitted against a device-memory budget and stepped together per
+    order by the continuous-batching loop (GB_MIXED).  Baselines: the same requests
+    run one after another alone, in GB_FP64 and in GB_MIXED, from per-(K, N) step
+    times measured here."""
+    from paper_2607_00199_b300 import gb, inputs, serve, state
+    reqs = inputs.serving_requests(n_req, rate=rate, seed=1)
+    stream = torch.cuda.Stream()
+    setup = torch.cuda.Stream()
+    srv = serve.Server(int(budget_gib * 2 ** 30), stream.cuda_stream, steps_per_request=steps,
+                       setup_stream=setup.cuda_stream)
+    stats = srv.run(reqs, sync=stream.synchronize)
+    # per-bucket step times of a request running alone
+    alone = {}
+    for prec, name, nst in ((gb.GB_FP64, 'fp64', 2), (gb.GB_MIXED, 'mixed', 10)):
+        for K in sorted({r['K'] for r in reqs}):
+            for N in sorted({r['N'] for r in reqs}):
+                spec = {'id': -1, 'arrival': 0.0, 'n': int(round(math.sqrt(K / 2))), 'N': N, 'A': 0.05, 'T': 1.0,
+                        'Re': 1000.0, 'Ma': 0.1}
+                rq = serve.Request(spec, stream.cuda_stream, precision=prec)
+                rq.solver.step(rq.dt, 1)
+                stream.synchronize()
+                t0 = time.perf_counter()
+                rq.solver.step(rq.dt, nst)
+                rq.solver.sync()
+                alone[(name, K, N)] = (time.perf_counter() - t0) / nst
+                rq.solver.close()
+    work = sum(2 * r['n'] ** 2 * ((r['N'] + 1) * (r['N'] + 2) // 2) * 6 * 4 * steps for r in reqs)
+    t_fp64 = sum(alone[('fp64', r['K'], r['N'])] * steps for r in reqs)
+    t_mixed = sum(alone[('mixed', r['K'], r['N'])] * steps for r in reqs)
+    return {'workload': '%d requests, Poisson %.0f/s (seed 1), K in {2048,8192,32768,131072}, N in {2,3,4,5}, '
+                        'A~U[0.01,0.08], T~U[0.5,2], Re~U[100,2000], Ma 0.1, %d SARK steps each, '
+                        'HBM budget %.0f GiB, GB_MIXED grouped by N' % (n_req, rate, steps, budget_gib),
+            'dof_stage_per_s': stats['dof_stage_per_s'], 'wall_s': stats['wall_s'], 'ticks': stats['ticks'],
+            'step_latency_ms': stats['step_latency_ms'], 'completion_latency_s': stats['completion_latency_s'],
+            'peak_device_bytes': stats['peak_device_bytes'], 'budget_bytes': stats['budget_bytes'],
+            'alone_fp64_dof_stage_per_s': work / t_fp64, 'alone_mixed_dof_stage_per_s': work / t_mixed,
+            'speedup_vs_alone_fp64': (work / stats['wall_s']) / (work / t_fp64),
+            'note': 'aggregate rate = all DOF-stage updates / wall time from the first arrival to the last '
+                    'completion (includes set-up of each request and idle time before arrivals)'}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument('--gpus', type=int, default=1)
@@ -51,6 +95,10 @@ def parse():
     p.add_argument('--warmup', type=int, default=5)
     p.add_argument('--impl', choices=['ours', 'reference'], default='ours')
     p.add_argument('--no-cpu-baseline', action='store_true')
+    p.add_argument('--no-serve', action='store_true', help='skip the serving-stream measurement')
+    p.add_argument('--serve-only', action='store_true', help='only the serving-stream measurement')
+    p.add_argument('--serve-requests', type=int, default=256)
+    p.add_argument('--serve-steps', type=int, default=500)
     return p.parse_args()
 
 
@@ -363,6 +411,8 @@ def run_ours(args):
         'mixed_speedup_vs_fp64': out['mixed']['value'] / out['fp64']['value'],
         'mixed_error': err,
     }
+    if ws == 1 and not args.no_serve:
+        line['serving'] = run_serving(torch, args.serve_requests, args.serve_steps)
     if ws == 1 and not args.no_cpu_baseline:
         line['cpu_baseline'] = cpu_baseline()
     print(json.dumps(line))
@@ -419,7 +469,10 @@ def run_reference(args):
 
 if __name__ == '__main__':
     a = parse()
-    if a.impl == 'reference':
+    if a.serve_only:
+        import torch
+        print(json.dumps(run_serving(torch, a.serve_requests, a.serve_steps)))
+    elif a.impl == 'reference':
         run_reference(a)
     else:
         run_ours(a)

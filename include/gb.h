@@ -124,9 +124,31 @@ int gb_step_timed(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms);
  * (GB_OK, GB_ENAN or GB_EMESH). */
 int gb_sync(gb_solver *s);
 
+/* gb_set_stream: finish the work enqueued on the solver's current stream, then use
+ * cuda_stream for all later work (e.g. set a solver up on one stream and step it
+ * in a group on another). */
+int gb_set_stream(gb_solver *s, void *cuda_stream);
+
 /* gb_info: sizes and derived constants.  Any output pointer may be NULL. */
 int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *n_vert,
             double *c, double *tau, int64_t *device_bytes);
+
+/* ---- groups (batched stepping of many simulations) --------------------------
+ * A group steps several GB_MIXED solvers of the same order N with one launch
+ * per SARK stage (a persistent kernel over the 16-element tiles of all of them)
+ * plus one vertex-update launch per step.  Every solver keeps its own fields,
+ * mesh, motion, time and step size; the result of each solver is bitwise the
+ * same as stepping it alone with gb_step.  gb_group_create allocates the
+ * descriptor buffers for up to `capacity` solvers (device and pinned host
+ * memory) and uses `cuda_stream` for all its work; the solvers of a group must
+ * have been created on that same stream.  gb_group_step enqueues nsteps steps
+ * of solvers[0..n-1] with step sizes dt[0..n-1] (enqueue only; per-solver
+ * device errors are reported by gb_sync / gb_fields of each solver). */
+typedef struct gb_group gb_group;
+int gb_group_create(int capacity, void *cuda_stream, gb_group **out);
+int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int n, int64_t nsteps);
+int gb_group_destroy(gb_group *g);
+const char *gb_group_last_error(gb_group *g);
 
 /* gb_state_ptr: the device address of the current fields, owned by the solver and
  * valid until gb_destroy: the canonical FP64 layout in GB_FP64 mode; in GB_MIXED

@@ -112,6 +112,26 @@ static int launch_stage(gb_solver *s, const gb::StageArgs &a) {
   return GB_OK;
 }
 
+struct gb_group {
+  int capacity = 0, num_sms = 1;
+  cudaStream_t stream = nullptr;
+  gb::StageArgs *d_args = nullptr, *h_args = nullptr;   // [4][capacity]
+  int64_t *d_prefix = nullptr, *h_prefix = nullptr;     // tile prefix (n+1), then vertex prefix (n+1)
+  cudaEvent_t uploaded = nullptr;
+  std::string err;
+};
+
+// SARK coefficients of both field classes for step size dt (cached per solver)
+static void set_coefficients(gb_solver *s, double dt) {
+  if (dt == s->coef_dt) return;
+  double E[5], A[16], B[4];
+  gb::sark_coefficients(0.0, E, A, B);
+  memcpy(s->co.E[0], E, sizeof(E)); memcpy(s->co.A[0], A, sizeof(A)); memcpy(s->co.B[0], B, sizeof(B));
+  gb::sark_coefficients(-dt / s->tau, E, A, B);
+  memcpy(s->co.E[1], E, sizeof(E)); memcpy(s->co.A[1], A, sizeof(A)); memcpy(s->co.B[1], B, sizeof(B));
+  s->coef_dt = dt;
+}
+
 // Morton (Z-order) numbering of the element centroids: internal element i is
 // canonical element perm[i].  Keeps face neighbours close in memory.
 static std::vector<int32_t> morton_order(const std::vector<double> &cx, const std::vector<double> &cy) {
@@ -524,6 +544,120 @@ static int step_impl(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms)
     if (ce != cudaSuccess && rc == GB_OK) rc = cuda_fail(s, ce, "gb_step_timed");
   }
   return rc;
+}
+
+// ---- groups: many GB_MIXED solvers of one order stepped by one launch per stage ----
+
+int gb_group_create(int capacity, void *cuda_stream, gb_group **out) {
+  if (!out || capacity < 1 || capacity > (1 << 20)) return fail(nullptr, GB_EINVAL, "gb_group_create: bad capacity or NULL out");
+  *out = nullptr;
+  gb_group *g = new gb_group();
+  g->capacity = capacity;
+  g->stream = (cudaStream_t)cuda_stream;
+  int dev = 0;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t args_bytes = sizeof(gb::StageArgs) * 4 * (size_t)capacity;
+  const size_t pre_bytes = sizeof(int64_t) * 2 * (size_t)(capacity + 1);
+  if (ce == cudaSuccess) ce = cudaMalloc(&g->d_args, args_bytes);
+  if (ce == cudaSuccess) ce = cudaMalloc(&g->d_prefix, pre_bytes);
+  if (ce == cudaSuccess) ce = cudaMallocHost(&g->h_args, args_bytes);
+  if (ce == cudaSuccess) ce = cudaMallocHost(&g->h_prefix, pre_bytes);
+  if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&g->uploaded, cudaEventDisableTiming);
+  if (ce != cudaSuccess) {
+    std::string m = std::string("gb_group_create: ") + cudaGetErrorString(ce);
+    gb_group_destroy(g);
+    return fail(nullptr, ce == cudaErrorMemoryAllocation ? GB_ENOMEM : GB_ECUDA, m);
+  }
+  *out = g;
+  return GB_OK;
+}
+
+int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int n, int64_t nsteps) {
+  if (!g) return fail(nullptr, GB_EINVAL, "gb_group_step: NULL group");
+  auto gfail = [&](int code, const std::string &m) { g->err = m; return code; };
+  if (!solvers || !dt || n < 1 || n > g->capacity) return gfail(GB_EINVAL, "gb_group_step: bad arguments or n > capacity");
+  if (nsteps < 0) return gfail(GB_EINVAL, "gb_group_step: nsteps < 0");
+  const int N = solvers[0] ? solvers[0]->N : 0;
+  for (int r = 0; r < n; ++r) {
+    gb_solver *s = solvers[r];
+    if (!s) return gfail(GB_EINVAL, "gb_group_step: NULL solver");
+    if (s->precision != GB_MIXED) return gfail(GB_EINVAL, "gb_group_step: only GB_MIXED solvers can be grouped");
+    if (s->N != N) return gfail(GB_EINVAL, "gb_group_step: all solvers of a group must have the same N");
+    if (s->stream != g->stream) return gfail(GB_EINVAL, "gb_group_step: solvers must use the group's stream");
+    if (!(dt[r] > 0.0) || !std::isfinite(dt[r])) return gfail(GB_EINVAL, "gb_group_step: dt must be positive and finite");
+  }
+  // the pinned staging buffers may still be read by the previous upload
+  cudaError_t ce = cudaEventSynchronize(g->uploaded);
+  if (ce != cudaSuccess) return gfail(GB_ECUDA, std::string("gb_group_step: ") + cudaGetErrorString(ce));
+  int64_t *tstart = g->h_prefix, *vstart = g->h_prefix + (n + 1);
+  tstart[0] = 0;
+  vstart[0] = 0;
+  for (int r = 0; r < n; ++r) {
+    gb_solver *s = solvers[r];
+    set_coefficients(s, dt[r]);
+    gb::StageArgs a = base_args(s);
+    a.dt = dt[r];
+    void *bufs_in[4] = {s->d_qn, s->d_b1, s->d_b2, s->d_b1};
+    void *bufs_out[4] = {s->d_b1, s->d_b2, s->d_b1, s->d_qn};
+    for (int st = 0; st < 4; ++st) {
+      a.stage = st;
+      a.qin = bufs_in[st];
+      a.qn = s->d_qn;
+      a.qout = bufs_out[st];
+      a.F0 = s->d_F0;
+      a.acc = s->d_acc;
+      g->h_args[(size_t)st * g->capacity + r] = a;
+    }
+    tstart[r + 1] = tstart[r] + (s->K + 15) / 16;
+    vstart[r + 1] = vstart[r] + s->nv;
+  }
+  ce = cudaMemcpyAsync(g->d_args, g->h_args, sizeof(gb::StageArgs) * 4 * (size_t)g->capacity, cudaMemcpyHostToDevice, g->stream);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(g->d_prefix, g->h_prefix, sizeof(int64_t) * 2 * (size_t)(n + 1), cudaMemcpyHostToDevice, g->stream);
+  if (ce == cudaSuccess) ce = cudaEventRecord(g->uploaded, g->stream);
+  if (ce != cudaSuccess) return gfail(GB_ECUDA, std::string("gb_group_step upload: ") + cudaGetErrorString(ce));
+  gb::GroupArgs ga;
+  ga.tile_start = g->d_prefix;
+  ga.vtx_start = g->d_prefix + (n + 1);
+  ga.n = n;
+  ga.total_tiles = tstart[n];
+  ga.total_vertices = vstart[n];
+  ga.ops = solvers[0]->d_ops_mixed;
+  for (int64_t k = 0; k < nsteps; ++k) {
+    for (int st = 0; st < 4; ++st) {
+      ga.args = g->d_args + (size_t)st * g->capacity;
+      int rc = gb::launch_group_mixed(N, st, ga, g->stream, g->num_sms);
+      if (rc) return gfail(GB_ECUDA, std::string("gb_group_step launch: ") + cudaGetErrorString((cudaError_t)rc));
+    }
+    ga.args = g->d_args + 3 * (size_t)g->capacity;
+    int rc = gb::launch_group_vertex_update(ga, g->stream);
+    if (rc) return gfail(GB_ECUDA, std::string("gb_group_step launch: ") + cudaGetErrorString((cudaError_t)rc));
+  }
+  return GB_OK;
+}
+
+int gb_group_destroy(gb_group *g) {
+  if (!g) return GB_OK;
+  if (g->uploaded) cudaEventSynchronize(g->uploaded);
+  if (g->stream) cudaStreamSynchronize(g->stream); else cudaDeviceSynchronize();
+  if (g->d_args) cudaFree(g->d_args);
+  if (g->d_prefix) cudaFree(g->d_prefix);
+  if (g->h_args) cudaFreeHost(g->h_args);
+  if (g->h_prefix) cudaFreeHost(g->h_prefix);
+  if (g->uploaded) cudaEventDestroy(g->uploaded);
+  delete g;
+  return GB_OK;
+}
+
+const char *gb_group_last_error(gb_group *g) { return g ? g->err.c_str() : g_create_error.c_str(); }
+
+int gb_set_stream(gb_solver *s, void *cuda_stream) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  cudaError_t ce = s->stream ? cudaStreamSynchronize(s->stream) : cudaDeviceSynchronize();
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_stream");
+  s->stream = (cudaStream_t)cuda_stream;
+  return GB_OK;
 }
 
 int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *n_vert, double *c, double *tau,

@@ -76,6 +76,20 @@ struct StageArgs {
   SarkCoef co;
 };
 
+// Several requests (solvers) of one order stepped by one launch per stage:
+// args[r] are their stage arguments, tile_start the exclusive prefix of their
+// 16-element tile counts (n + 1 entries), vtx_start the prefix of their vertex
+// counts (n + 1 entries); all three arrays live in device memory.
+struct GroupArgs {
+  const StageArgs *args;
+  const int64_t *tile_start;
+  const int64_t *vtx_start;
+  int n;
+  int64_t total_tiles;
+  int64_t total_vertices;
+  const void *ops;
+};
+
 // Launchers (gb_kernels.cu).  Return a cudaError_t value as int.
 int launch_stage_fp64(int N, const StageArgs &a, void *stream, int num_sms);
 int launch_stage_mixed(int N, const StageArgs &a, void *stream, int num_sms);
@@ -86,6 +100,8 @@ int launch_nodes(int N, const double *ops, const double *xn, const MeshRec *mesh
 int launch_relayout(const void *canon_src, void *canon_dst, bool canon_is_double, bool to_internal, float *inner,
                     const int32_t *perm, int64_t K, int Np, int S, double rest, void *stream);
 int mixed_stride(int N);   // element stride (floats) of the GB_MIXED field layout
+int launch_group_mixed(int N, int stage, const GroupArgs &g, void *stream, int num_sms);
+int launch_group_vertex_update(const GroupArgs &g, void *stream);
 int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, int *N, int64_t *K, int *Np,
                     int *precision, void **stream, int *num_sms);
 int set_solver_error(gb_solver *s, int code, const char *msg);

@@ -124,64 +124,22 @@ __device__ __forceinline__ void load_a(const float *tile, int col0, int ncol, in
   split_tf32(x3, hi[3], lo[3]);
 }
 
+// One 16-element tile of one request: staging, geometry, volume, surface, cubature and the SARK
+// combination.  gfac / xfac are the stage's motion factors of the request; next_tile (or -1) is the
+// tile this warp takes next in the same request (prefetched towards L2).
 template <int N, int STAGE>
-__global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_kernel(const StageArgs a) {
+__device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_t next_tile, double gfac, double xfac,
+                                        const float4 *btab, float *own, float *trc, float *geo,
+                                        const float (&bl)[TcDim<N>::NT][2][3], int lane) {
   typedef TcDim<N> D;
   constexpr int Np = D::Np, Nfp = D::Nfp, NFN = D::NFN, KS = D::KS, KF = D::KF, NT = D::NT, CH = D::CH;
-  constexpr int S = D::S, ST = D::ST, FJ = D::FJ, GEOS = D::GEOS, W = D::W;
+  constexpr int S = D::S, ST = D::ST, FJ = D::FJ, GEOS = D::GEOS;
   const float SQ2 = 1.41421356237309505f, ISQ2 = 0.70710678118654752f;
-  extern __shared__ float4 tc_smem4[];
-  float4 *btab = tc_smem4;                                          // [NSETS][32]
-  float *wbase = reinterpret_cast<float *>(tc_smem4 + D::NSETS * 32);
-  __shared__ double s_motion[2];
-  {
-    const float4 *g4 = reinterpret_cast<const float4 *>(a.ops);
-    for (int i = threadIdx.x; i < D::NSETS * 32; i += blockDim.x) btab[i] = g4[i];
-  }
-  if (threadIdx.x == 0) {
-    double gf = 0.0, xf = 0.0, fin = 0.0;
-    if (a.motion_A != 0.0) {
-      const double w = a.motion_w, Aw = a.motion_A * a.motion_w;
-      if (STAGE < 0) {
-        gf = Aw * cos(w * a.rhs_time);
-      } else {
-        const double t = a.clock[0], dt = a.dt;
-        const double cst[4] = {0.0, 0.5, 0.5, 1.0};
-        gf = Aw * cos(w * (t + cst[STAGE] * dt));
-        if (STAGE > 0) xf = dt * cst[STAGE == 3 ? 3 : 1] * Aw * cos(w * (t + cst[STAGE - 1] * dt));
-        if (STAGE == 3) fin = dt * Aw * (cos(w * t) / 6.0 + cos(w * (t + 0.5 * dt)) * (2.0 / 3.0) + cos(w * (t + dt)) / 6.0);
-      }
-    }
-    s_motion[0] = gf;
-    s_motion[1] = xf;
-    if (STAGE == 3 && blockIdx.x == 0) const_cast<double *>(a.clock)[1] = fin;
-  }
-  __syncthreads();
-  const double gfac = s_motion[0], xfac = s_motion[1];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
-  float *own = wbase + warp * D::WARP_FLOATS;   // [16][S]   fields of the tile
-  float *trc = own + 16 * S;                    // [16][ST] traces -> fluxes, then [16][S] rhs (16 OUTS floats)
-  float *geo = trc + 16 * D::OUTS;              // [16][GEOS]
   const float *qin = reinterpret_cast<const float *>(a.qin);
   const float c = (float)a.c, mc = -(float)a.c, mcs = -(float)a.c * SQ2;
   const float itau = (float)a.inv_tau;
-  // barycentric coordinates of the 2 NT output nodes this lane holds in accumulator fragments
-  float bl[NT][2][3];
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int n = nt * 8 + 2 * t + j;
-      const float *bary = reinterpret_cast<const float *>(a.ops) + D::NSETS * 128 + 4 * (n < Np ? n : 0);
-      bl[nt][j][0] = bary[0];
-      bl[nt][j][1] = bary[1];
-      bl[nt][j][2] = bary[2];
-    }
-  const int64_t ntile = (a.K + 15) >> 4;
-  const int64_t tstride = (int64_t)gridDim.x * W;
-
-  for (int64_t tile = (int64_t)blockIdx.x * W + warp; tile < ntile; tile += tstride) {
+  {
     const int64_t e0 = tile * 16;
     const int nel = (int)((a.K - e0) < 16 ? (a.K - e0) : 16);
     __syncwarp();
@@ -213,9 +171,9 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_k
         if (STAGE <= 2) tc_l2_prefetch(reinterpret_cast<const float *>(a.F0) + e0 * S, bytes);
         if (STAGE >= 2) tc_l2_prefetch(reinterpret_cast<const float *>(a.acc) + e0 * S, bytes);
       }
-      if (tile + tstride < ntile) {
-        tc_l2_prefetch(qin + (tile + tstride) * 16 * S, bytes);
-        const int64_t m0 = (tile + tstride) * 16;
+      if (next_tile >= 0) {
+        tc_l2_prefetch(qin + next_tile * 16 * S, bytes);
+        const int64_t m0 = next_tile * 16;
         const int64_t mcount = (a.K - m0) < 16 ? (a.K - m0) : 16;   // records that exist
         tc_l2_prefetch(a.mesh + m0, (unsigned)(mcount * sizeof(MeshRec)));
       }
@@ -534,6 +492,116 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_k
   }
 }
 
+// motion factors of a stage for one request: v_i = gfac S(X), x_i = x_n + xfac S(X),
+// and the factor of the final vertex update x_{n+1} = x_n + fin S(X) (RK4 nodes and weights)
+template <int STAGE>
+__device__ __forceinline__ void tc_stage_motion(const StageArgs &a, double &gf, double &xf, double &fin) {
+  gf = 0.0; xf = 0.0; fin = 0.0;
+  if (a.motion_A == 0.0) return;
+  const double w = a.motion_w, Aw = a.motion_A * a.motion_w;
+  if (STAGE < 0) {
+    gf = Aw * cos(w * a.rhs_time);
+    return;
+  }
+  const double tt = a.clock[0], dt = a.dt;
+  const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+  gf = Aw * cos(w * (tt + cst[STAGE] * dt));
+  if (STAGE > 0) xf = dt * cst[STAGE == 3 ? 3 : 1] * Aw * cos(w * (tt + cst[STAGE - 1] * dt));
+  if (STAGE == 3) fin = dt * Aw * (cos(w * tt) / 6.0 + cos(w * (tt + 0.5 * dt)) * (2.0 / 3.0) + cos(w * (tt + dt)) / 6.0);
+}
+
+template <int N>
+__device__ __forceinline__ void tc_load_bary(const void *ops, int lane, float (&bl)[TcDim<N>::NT][2][3]) {
+  typedef TcDim<N> D;
+  const int t = lane & 3;
+#pragma unroll
+  for (int nt = 0; nt < D::NT; ++nt)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int n = nt * 8 + 2 * t + j;
+      const float *bary = reinterpret_cast<const float *>(ops) + D::NSETS * 128 + 4 * (n < D::Np ? n : 0);
+      bl[nt][j][0] = bary[0];
+      bl[nt][j][1] = bary[1];
+      bl[nt][j][2] = bary[2];
+    }
+}
+
+template <int N, int STAGE>
+__global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_kernel(const StageArgs a) {
+  typedef TcDim<N> D;
+  constexpr int W = D::W;
+  extern __shared__ float4 tc_smem4[];
+  float4 *btab = tc_smem4;                                          // [NSETS][32]
+  float *wbase = reinterpret_cast<float *>(tc_smem4 + D::NSETS * 32);
+  __shared__ double s_motion[2];
+  {
+    const float4 *g4 = reinterpret_cast<const float4 *>(a.ops);
+    for (int i = threadIdx.x; i < D::NSETS * 32; i += blockDim.x) btab[i] = g4[i];
+  }
+  if (threadIdx.x == 0) {
+    double gf, xf, fin;
+    tc_stage_motion<STAGE>(a, gf, xf, fin);
+    s_motion[0] = gf;
+    s_motion[1] = xf;
+    if (STAGE == 3 && blockIdx.x == 0) const_cast<double *>(a.clock)[1] = fin;
+  }
+  __syncthreads();
+  const double gfac = s_motion[0], xfac = s_motion[1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *own = wbase + warp * D::WARP_FLOATS;   // [16][S]   fields of the tile
+  float *trc = own + 16 * D::S;                 // [16][ST] traces -> fluxes, then [16][S] rhs (16 OUTS floats)
+  float *geo = trc + 16 * D::OUTS;              // [16][GEOS]
+  float bl[D::NT][2][3];                        // barycentric coordinates of this lane's output nodes
+  tc_load_bary<N>(a.ops, lane, bl);
+  const int64_t ntile = (a.K + 15) >> 4;
+  const int64_t tstride = (int64_t)gridDim.x * W;
+  for (int64_t tile = (int64_t)blockIdx.x * W + warp; tile < ntile; tile += tstride)
+    tc_tile<N, STAGE>(a, tile, tile + tstride < ntile ? tile + tstride : -1, gfac, xfac, btab, own, trc, geo, bl, lane);
+}
+
+// Many requests of the same order in one launch: tile T of the launch is tile
+// T - tile_start[r] of request r (tile_start is the exclusive prefix of the
+// requests' tile counts).  Each warp derives its request's motion factors.
+template <int N, int STAGE>
+__global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_group_kernel(const GroupArgs gd) {
+  typedef TcDim<N> D;
+  constexpr int W = D::W;
+  extern __shared__ float4 tc_smem4[];
+  float4 *btab = tc_smem4;
+  float *wbase = reinterpret_cast<float *>(tc_smem4 + D::NSETS * 32);
+  {
+    const float4 *g4 = reinterpret_cast<const float4 *>(gd.ops);
+    for (int i = threadIdx.x; i < D::NSETS * 32; i += blockDim.x) btab[i] = g4[i];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float *own = wbase + warp * D::WARP_FLOATS;
+  float *trc = own + 16 * D::S;
+  float *geo = trc + 16 * D::OUTS;
+  float bl[D::NT][2][3];
+  tc_load_bary<N>(gd.ops, lane, bl);
+  const int64_t tstride = (int64_t)gridDim.x * W;
+  for (int64_t T = (int64_t)blockIdx.x * W + warp; T < gd.total_tiles; T += tstride) {
+    int lo = 0, hi = gd.n - 1;              // last r with tile_start[r] <= T
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (gd.tile_start[mid] <= T) lo = mid; else hi = mid - 1;
+    }
+    const StageArgs &a = gd.args[lo];
+    const int64_t tile = T - gd.tile_start[lo];
+    const int64_t ntile = gd.tile_start[lo + 1] - gd.tile_start[lo];
+    double gf = 0.0, xf = 0.0;
+    if (lane == 0) {
+      double fin;
+      tc_stage_motion<STAGE>(a, gf, xf, fin);
+      if (STAGE == 3 && tile == 0) const_cast<double *>(a.clock)[1] = fin;
+    }
+    gf = __shfl_sync(0xffffffffu, gf, 0);
+    xf = __shfl_sync(0xffffffffu, xf, 0);
+    tc_tile<N, STAGE>(a, tile, tile + tstride < ntile ? tile + tstride : -1, gf, xf, btab, own, trc, geo, bl, lane);
+  }
+}
+
 // ---------------------------------------------------------------------------
 template <int N>
 static size_t tc_smem() {
@@ -587,6 +655,80 @@ int launch_stage_mixed(int N, const StageArgs &a, void *stream, int num_sms) {
     case 6: return tc_launch_n<6>(a, st, num_sms);
   }
   return (int)cudaErrorInvalidValue;
+}
+
+template <int N, int STAGE>
+static int tc_group_launch_one(const GroupArgs &g, cudaStream_t st, int num_sms) {
+  typedef TcDim<N> D;
+  const size_t smem = tc_smem<N>();
+  constexpr int threads = 32 * D::W;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(tc_group_kernel<N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_group_kernel<N, STAGE>, threads, smem);
+  if (err != cudaSuccess) return (int)err;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  const int64_t need = (g.total_tiles + D::W - 1) / D::W;
+  if (grid > need) grid = need;
+  if (grid < 1) grid = 1;
+  tc_group_kernel<N, STAGE><<<(unsigned)grid, threads, smem, st>>>(g);
+  return (int)cudaGetLastError();
+}
+
+template <int N>
+static int tc_group_launch_n(int stage, const GroupArgs &g, cudaStream_t st, int num_sms) {
+  switch (stage) {
+    case 0: return tc_group_launch_one<N, 0>(g, st, num_sms);
+    case 1: return tc_group_launch_one<N, 1>(g, st, num_sms);
+    case 2: return tc_group_launch_one<N, 2>(g, st, num_sms);
+    case 3: return tc_group_launch_one<N, 3>(g, st, num_sms);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_group_mixed(int N, int stage, const GroupArgs &g, void *stream, int num_sms) {
+  cudaStream_t st = (cudaStream_t)stream;
+  switch (N) {
+    case 1: return tc_group_launch_n<1>(stage, g, st, num_sms);
+    case 2: return tc_group_launch_n<2>(stage, g, st, num_sms);
+    case 3: return tc_group_launch_n<3>(stage, g, st, num_sms);
+    case 4: return tc_group_launch_n<4>(stage, g, st, num_sms);
+    case 5: return tc_group_launch_n<5>(stage, g, st, num_sms);
+    case 6: return tc_group_launch_n<6>(stage, g, st, num_sms);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+// final vertex update of every request of a group: x_{n+1} = x_n + fin S(X), t += dt
+__global__ void group_vertex_update_kernel(const GroupArgs g) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < g.total_vertices;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = g.n - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (g.vtx_start[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const StageArgs &a = g.args[lo];
+    const int64_t v = i - g.vtx_start[lo];
+    double *xn = const_cast<double *>(a.xn);
+    const double fin = a.clock[1];
+    xn[2 * v] += fin * a.shape[2 * v];
+    xn[2 * v + 1] += fin * a.shape[2 * v + 1];
+    if (v == 0) const_cast<double *>(a.clock)[0] += a.dt;
+  }
+}
+
+int launch_group_vertex_update(const GroupArgs &g, void *stream) {
+  int64_t blocks = (g.total_vertices + 255) / 256;
+  if (blocks > 8192) blocks = 8192;
+  if (blocks < 1) blocks = 1;
+  group_vertex_update_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(g);
+  return (int)cudaGetLastError();
 }
 
 int mixed_stride(int N) {

@@ -59,6 +59,7 @@ def _load():
         'gb_step': ([vp, c_double, i64], c_int),
         'gb_step_timed': ([vp, c_double, i64, _dp], c_int),
         'gb_sync': ([vp], c_int),
+        'gb_set_stream': ([vp, vp], c_int),
         'gb_info': ([vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                      ctypes.POINTER(i64), ctypes.POINTER(i64), _dp, _dp, ctypes.POINTER(i64)], c_int),
         'gb_state_ptr': ([vp, ctypes.POINTER(vp)], c_int),
@@ -66,6 +67,10 @@ def _load():
         'gb_last_error': ([vp], ctypes.c_char_p),
         'gb_reference_operators': ([c_int] + [_dp] * 10 + [ctypes.POINTER(c_int)], c_int),
         'gb_sark_coefficients': ([c_double, _dp, _dp, _dp], c_int),
+        'gb_group_create': ([c_int, vp, ctypes.POINTER(vp)], c_int),
+        'gb_group_step': ([vp, ctypes.POINTER(vp), _dp, c_int, i64], c_int),
+        'gb_group_destroy': ([vp], c_int),
+        'gb_group_last_error': ([vp], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -196,6 +201,10 @@ class Solver:
         self._c(lib.gb_step_timed(self.h, float(dt), int(nsteps), _ptr(ms)))
         return ms
 
+    def set_stream(self, stream):
+        """Finish pending work, then use `stream` (a cudaStream_t address) from now on."""
+        self._c(lib.gb_set_stream(self.h, None if stream is None else ctypes.c_void_p(int(stream))))
+
     def sync(self):
         self._c(lib.gb_sync(self.h))
 
@@ -214,3 +223,36 @@ class Solver:
             self.close()
         except Exception:
             pass
+
+
+class Group:
+    """Owns one gb_group: steps several GB_MIXED solvers of one order together."""
+
+    def __init__(self, capacity, stream=None):
+        h = ctypes.c_void_p(None)
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        rc = lib.gb_group_create(int(capacity), st, ctypes.byref(h))
+        if rc != GB_OK:
+            raise GBError(rc, lib.gb_group_last_error(None).decode())
+        self.h = h
+        self.capacity = int(capacity)
+
+    def step(self, solvers, dts, nsteps=1):
+        n = len(solvers)
+        arr = (ctypes.c_void_p * n)(*[s.h.value for s in solvers])
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        rc = lib.gb_group_step(self.h, arr, _ptr(d), n, int(nsteps))
+        if rc != GB_OK:
+            raise GBError(rc, lib.gb_group_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, 'h', None) is not None and self.h.value is not None:
+            lib.gb_group_destroy(self.h)
+            self.h = ctypes.c_void_p(None)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

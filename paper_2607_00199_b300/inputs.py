@@ -57,17 +57,15 @@ def periodic_square_mesh(n, L=2.0 * math.pi, jitter=0.0, seed=DEFAULT_SEED):
         ids = np.arange(n * n, dtype=np.uint64)
         X[:, 0] += uniform(2 * ids, seed, -jitter * h, jitter * h)
         X[:, 1] += uniform(2 * ids + 1, seed, -jitter * h, jitter * h)
-    EToV = np.zeros((2 * n * n, 3), dtype=np.int32)
-    shift = np.zeros((2 * n * n, 3, 2))
-    k = 0
-    for j in range(n):
-        for i in range(n):
-            c00, c10, c11, c01 = (i, j), (i + 1, j), (i + 1, j + 1), (i, j + 1)
-            for tri in ((c00, c10, c11), (c00, c11, c01)):
-                for v, (a, b) in enumerate(tri):
-                    EToV[k, v] = (a % n) + n * (b % n)
-                    shift[k, v] = ((a // n) * L, (b // n) * L)
-                k += 1
+    # cells in row-major order (j outer, i inner), two triangles per cell
+    j, i = np.meshgrid(np.arange(n), np.arange(n), indexing='ij')
+    i = i.ravel()
+    j = j.ravel()
+    corners = np.array([[(0, 0), (1, 0), (1, 1)], [(0, 0), (1, 1), (0, 1)]])
+    a = i[:, None, None] + corners[None, :, :, 0]
+    b = j[:, None, None] + corners[None, :, :, 1]
+    EToV = ((a % n) + n * (b % n)).reshape(-1, 3).astype(np.int32)
+    shift = np.stack([(a // n) * L, (b // n) * L], axis=-1).reshape(-1, 3, 2).astype(np.float64)
     return {'X': X, 'EToV': EToV, 'shift': shift, 'L': np.array([L, L]), 'n': n}
 
 
