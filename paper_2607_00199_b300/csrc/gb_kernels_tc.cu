@@ -81,8 +81,9 @@ __device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) 
   lo = to_tf32(x - __uint_as_float(hi));
 }
 
+// not volatile: the compiler may interleave products into independent accumulators
 __device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
-  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
                : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
                : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
@@ -252,10 +253,27 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
       for (int ks = 0; ks < KS; ++ks) {
         unsigned ahi[4], alo[4];
         load_a<S>(own, f * Np + ks * 8, f * Np + Np, g, t, ahi, alo);
+        float4 br[NT], bs[NT];
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
-          mma3(dr[nt], ahi, alo, btab[(D::B_DR + ks * NT + nt) * 32 + lane]);
-          mma3(ds[nt], ahi, alo, btab[(D::B_DS + ks * NT + nt) * 32 + lane]);
+          br[nt] = btab[(D::B_DR + ks * NT + nt) * 32 + lane];
+          bs[nt] = btab[(D::B_DS + ks * NT + nt) * 32 + lane];
+        }
+        // split terms outermost: consecutive products go to independent accumulators
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          mma_tf32(dr[nt], alo, __float_as_uint(br[nt].z), __float_as_uint(br[nt].w));
+          mma_tf32(ds[nt], alo, __float_as_uint(bs[nt].z), __float_as_uint(bs[nt].w));
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          mma_tf32(dr[nt], ahi, __float_as_uint(br[nt].x), __float_as_uint(br[nt].y));
+          mma_tf32(ds[nt], ahi, __float_as_uint(bs[nt].x), __float_as_uint(bs[nt].y));
+        }
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          mma_tf32(dr[nt], ahi, __float_as_uint(br[nt].z), __float_as_uint(br[nt].w));
+          mma_tf32(ds[nt], ahi, __float_as_uint(bs[nt].z), __float_as_uint(bs[nt].w));
         }
       }
       // pointwise: chain rule, v_G . grad q_f and the Atilde couplings (Sec. 2)
@@ -340,24 +358,29 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
     }
     __syncwarp();
 
-    // ---- LIFT of the fluxes ----
-#pragma unroll 1
-    for (int f = 0; f < 6; ++f) {
+    // ---- LIFT of the fluxes: fields in two groups of three, split terms outermost ----
+#pragma unroll
+    for (int fg = 0; fg < 6; fg += 3) {
 #pragma unroll
       for (int kf = 0; kf < KF; ++kf) {
-        unsigned ahi[4], alo[4];
-        load_a<ST>(trc, f * FJ + kf * 8, f * FJ + NFN, g, t, ahi, alo);
+        unsigned ahi[3][4], alo[3][4];
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          switch (f) {   // keeps the accumulator index compile-time
-            case 0: mma3(acc[0][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
-            case 1: mma3(acc[1][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
-            case 2: mma3(acc[2][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
-            case 3: mma3(acc[3][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
-            case 4: mma3(acc[4][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
-            default: mma3(acc[5][nt], ahi, alo, btab[(D::B_LIFT + kf * NT + nt) * 32 + lane]); break;
-          }
-        }
+        for (int ff = 0; ff < 3; ++ff) load_a<ST>(trc, (fg + ff) * FJ + kf * 8, (fg + ff) * FJ + NFN, g, t, ahi[ff], alo[ff]);
+        float4 bq[NT];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) bq[nt] = btab[(D::B_LIFT + kf * NT + nt) * 32 + lane];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int ff = 0; ff < 3; ++ff) mma_tf32(acc[fg + ff][nt], alo[ff], __float_as_uint(bq[nt].z), __float_as_uint(bq[nt].w));
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int ff = 0; ff < 3; ++ff) mma_tf32(acc[fg + ff][nt], ahi[ff], __float_as_uint(bq[nt].x), __float_as_uint(bq[nt].y));
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int ff = 0; ff < 3; ++ff) mma_tf32(acc[fg + ff][nt], ahi[ff], __float_as_uint(bq[nt].z), __float_as_uint(bq[nt].w));
       }
     }
 
@@ -379,7 +402,11 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
         for (int ks = 0; ks < KS; ++ks) {
           const float4 b = btab[(D::B_I + ch * KS + ks) * 32 + lane];
 #pragma unroll
-          for (int f = 0; f < 3; ++f) mma3(qc[f], qh[f][ks], ql[f][ks], b);
+          for (int f = 0; f < 3; ++f) mma_tf32(qc[f], ql[f][ks], __float_as_uint(b.z), __float_as_uint(b.w));
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(qc[f], qh[f][ks], __float_as_uint(b.x), __float_as_uint(b.y));
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(qc[f], qh[f][ks], __float_as_uint(b.z), __float_as_uint(b.w));
         }
         // Ntilde at the 4 (element, point) positions; the accumulator order (c0, c2, c1, c3)
         // is the A-fragment order of the permuted chunk
@@ -395,13 +422,21 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
           split_tf32(q2 * q2 * rs, nh[1][j], nl[1][j]);
           split_tf32(q3 * q3 * rs, nh[2][j], nl[2][j]);
         }
+        float4 bp[NT];
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          const float4 b = btab[(D::B_P + ch * NT + nt) * 32 + lane];
-          mma3(acc[3][nt], nh[0], nl[0], b);
-          mma3(acc[4][nt], nh[1], nl[1], b);
-          mma3(acc[5][nt], nh[2], nl[2], b);
-        }
+        for (int nt = 0; nt < NT; ++nt) bp[nt] = btab[(D::B_P + ch * NT + nt) * 32 + lane];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(acc[3 + f][nt], nl[f], __float_as_uint(bp[nt].z), __float_as_uint(bp[nt].w));
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(acc[3 + f][nt], nh[f], __float_as_uint(bp[nt].x), __float_as_uint(bp[nt].y));
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(acc[3 + f][nt], nh[f], __float_as_uint(bp[nt].z), __float_as_uint(bp[nt].w));
       }
     }
 
