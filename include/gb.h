@@ -110,8 +110,20 @@ int gb_rhs(gb_solver *s, double t, const void *q_dev, void *F_dev);
 /* gb_step: enqueue nsteps SARK steps of size dt (Sec. 4): per stage, the vertex
  * positions and velocities (Sec. 5), the geometric factors (GCL), the volume,
  * surface and cubature terms and the SARK combination.  Enqueue only; errors of
- * the device computation are reported by gb_sync / gb_fields. */
+ * the device computation are reported by gb_sync / gb_fields.  On a non-default
+ * stream and for nsteps >= 2 one step is captured as a CUDA graph (after one
+ * direct step with the same dt) and replayed; the graph is rebuilt after a
+ * change of dt, motion or stream.  gb_set_graph(s, 0) turns this off. */
 int gb_step(gb_solver *s, double dt, int64_t nsteps);
+int gb_set_graph(gb_solver *s, int enable);
+
+/* gb_launch_config: the GB_MIXED kernel's warps per CTA (1, 2 or 4; 0 for GB_FP64).
+ * The first gb_step / gb_step_timed of a GB_MIXED solver tunes it: it times the
+ * right-hand-side kernel on the solver's own data for each shape (the state is not
+ * changed) and keeps the fastest; the choice is cached per (N, K) in the process. */
+int gb_launch_config(gb_solver *s, int *warps_per_cta);
+/* gb_set_launch_config: fix the GB_MIXED warps per CTA (1, 2 or 4) and skip the tuner. */
+int gb_set_launch_config(gb_solver *s, int warps_per_cta);
 
 /* gb_step_timed: gb_step that also records a CUDA event pair around every kernel
  * launch on the solver's stream (tracing), synchronises, and adds the device time

@@ -14,6 +14,8 @@
 #include "gb_internal.h"
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 using gb::MeshRec;
 
@@ -27,6 +29,12 @@ struct gb_solver {
   gb::RefOps ref;
   gb_motion motion{GB_MOTION_STATIC, 0, 1, 1, 1};
   double coef_dt = -1.0;
+  // one SARK step captured as a CUDA graph (gb_step); rebuilt when dt, the motion or the stream change
+  cudaGraphExec_t step_graph = nullptr;
+  double graph_dt = -1.0;
+  bool graph_warm = false;     // one uncaptured step ran with the current settings
+  bool use_graph = true;
+  int warps = 0;               // GB_MIXED warps per CTA chosen by tune_launch (0 = not tuned yet)
   gb::SarkCoef co{};
   size_t elem_bytes = 8;
   // device memory
@@ -102,6 +110,7 @@ static gb::StageArgs base_args(gb_solver *s) {
   a.motion_A = (s->motion.kind == GB_MOTION_SINXY) ? s->motion.A : 0.0;
   a.motion_w = (s->motion.kind == GB_MOTION_SINXY) ? 2.0 * M_PI / s->motion.T : 0.0;
   a.co = s->co;
+  a.warps_per_cta = s->warps;
   return a;
 }
 
@@ -130,6 +139,72 @@ static void set_coefficients(gb_solver *s, double dt) {
   gb::sark_coefficients(-dt / s->tau, E, A, B);
   memcpy(s->co.E[1], E, sizeof(E)); memcpy(s->co.A[1], A, sizeof(A)); memcpy(s->co.B[1], B, sizeof(B));
   s->coef_dt = dt;
+}
+
+// Launch-shape tuner (GB_MIXED): warps per CTA, 1, 2 or 4.  Fewer warps per CTA
+// spread the 16-element tiles of a small mesh over more SMs; more warps share
+// one copy of the operator tables.  The tuner times the rhs-only stage kernel
+// (which writes only the scratch buffer b2 and leaves the state alone) on the
+// solver's own data for each shape and keeps the fastest; a smaller shape must
+// win by 3%.  Choices are cached per (N, K) for the rest of the process.
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int64_t>, int> g_tuned;
+
+static int tune_launch(gb_solver *s) {
+  if (s->precision != GB_MIXED || s->warps != 0) return GB_OK;
+  const std::pair<int, int64_t> key(s->N, s->K);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(key);
+    if (it != g_tuned.end()) {
+      s->warps = it->second;
+      return GB_OK;
+    }
+  }
+  gb::StageArgs a = base_args(s);
+  a.stage = -1;
+  a.qin = s->d_qn;
+  a.qn = s->d_qn;
+  a.Fout = s->d_b2;
+  a.rhs_time = 0.0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  int best = 4;
+  float best_ms = 1e30f;
+  const int cand[3] = {4, 2, 1};
+  for (int i = 0; i < 3 && ce == cudaSuccess; ++i) {
+    a.warps_per_cta = cand[i];
+    int rc = gb::launch_stage_mixed(s->N, a, s->stream, s->num_sms);   // warm-up
+    if (rc) { ce = (cudaError_t)rc; break; }
+    ce = cudaEventRecord(e0, s->stream);
+    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) {
+      rc = gb::launch_stage_mixed(s->N, a, s->stream, s->num_sms);
+      if (rc) ce = (cudaError_t)rc;
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, s->stream);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce == cudaSuccess && ms < 0.97f * best_ms) {
+      best_ms = ms;
+      best = cand[i];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "launch tuning");
+  s->warps = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuned[key] = best;
+  return GB_OK;
+}
+
+static void drop_graph(gb_solver *s) {
+  if (s->step_graph) cudaGraphExecDestroy(s->step_graph);
+  s->step_graph = nullptr;
+  s->graph_dt = -1.0;
+  s->graph_warm = false;
 }
 
 // Morton (Z-order) numbering of the element centroids: internal element i is
@@ -358,6 +433,7 @@ int gb_set_motion(gb_solver *s, const gb_motion *m) {
       return fail(s, GB_EINVAL, "GB_MOTION_SINXY needs T > 0, Lx != 0, Ly != 0 and finite A");
   }
   s->motion = *m;
+  drop_graph(s);
   int rc = gb::launch_shape(s->d_X, s->d_shape, s->nv, m->kind, m->Lx, m->Ly, s->stream);
   if (rc != 0) return cuda_fail(s, (cudaError_t)rc, "shape kernel");
   return GB_OK;
@@ -479,10 +555,53 @@ int gb_rhs(gb_solver *s, double t, const void *q_dev, void *F_dev) {
 
 static int step_impl(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms);
 
-int gb_step(gb_solver *s, double dt, int64_t nsteps) { return step_impl(s, dt, nsteps, nullptr); }
+int gb_step(gb_solver *s, double dt, int64_t nsteps) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (nsteps > 0) {
+    int trc = tune_launch(s);
+    if (trc) return trc;
+  }
+  // the legacy default stream cannot be captured; tiny runs are not worth a capture
+  if (!s->use_graph || !s->stream || nsteps < 2 || !(dt > 0.0) || !std::isfinite(dt)) return step_impl(s, dt, nsteps, nullptr);
+  if (s->step_graph && s->graph_dt != dt) drop_graph(s);
+  if (!s->graph_warm || s->graph_dt != dt) {
+    // first step with these settings runs directly (kernel attributes, coefficients)
+    int rc = step_impl(s, dt, 1, nullptr);
+    if (rc) return rc;
+    s->graph_warm = true;
+    s->graph_dt = dt;
+    --nsteps;
+  }
+  if (!s->step_graph) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_step capture");
+    int rc = step_impl(s, dt, 1, nullptr);
+    ce = cudaStreamEndCapture(s->stream, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&s->step_graph, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      s->step_graph = nullptr;
+      return cuda_fail(s, ce, "gb_step graph");
+    }
+  }
+  for (int64_t k = 0; k < nsteps; ++k) {
+    cudaError_t ce = cudaGraphLaunch(s->step_graph, s->stream);
+    if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_step graph launch");
+  }
+  return GB_OK;
+}
 
 int gb_step_timed(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms) {
   if (!kernel_ms) return fail(s, GB_EINVAL, "kernel_ms is NULL");
+  if (s && nsteps > 0) {
+    int trc = tune_launch(s);
+    if (trc) return trc;
+  }
   int rc = step_impl(s, dt, nsteps, kernel_ms);
   return rc ? rc : gb_sync(s);
 }
@@ -652,10 +771,34 @@ int gb_group_destroy(gb_group *g) {
 
 const char *gb_group_last_error(gb_group *g) { return g ? g->err.c_str() : g_create_error.c_str(); }
 
+int gb_launch_config(gb_solver *s, int *warps_per_cta) {
+  if (!s || !warps_per_cta) return fail(s, GB_EINVAL, "NULL argument");
+  *warps_per_cta = s->precision == GB_MIXED ? (s->warps ? s->warps : 4) : 0;
+  return GB_OK;
+}
+
+int gb_set_launch_config(gb_solver *s, int warps_per_cta) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->precision != GB_MIXED) return fail(s, GB_EINVAL, "launch shapes apply to GB_MIXED solvers");
+  if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4)
+    return fail(s, GB_EINVAL, "warps_per_cta must be 1, 2 or 4");
+  s->warps = warps_per_cta;
+  drop_graph(s);
+  return GB_OK;
+}
+
+int gb_set_graph(gb_solver *s, int enable) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  s->use_graph = enable != 0;
+  drop_graph(s);
+  return GB_OK;
+}
+
 int gb_set_stream(gb_solver *s, void *cuda_stream) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
   cudaError_t ce = s->stream ? cudaStreamSynchronize(s->stream) : cudaDeviceSynchronize();
   if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_stream");
+  drop_graph(s);
   s->stream = (cudaStream_t)cuda_stream;
   return GB_OK;
 }
@@ -683,6 +826,7 @@ int gb_state_ptr(gb_solver *s, void **q_dev) {
 int gb_destroy(gb_solver *s) {
   if (!s) return GB_OK;
   if (s->stream) cudaStreamSynchronize(s->stream); else cudaDeviceSynchronize();
+  drop_graph(s);
   free_all(s);
   delete s;
   return GB_OK;

@@ -72,6 +72,7 @@ struct StageArgs {
   // x_i = x_n + xfac[i] * S(X).  Derived per block from the clock.
   double motion_A, motion_w;   // A and 2 pi / T (A = 0: static)
   int stage;                   // -1: rhs only, 0..3: SARK stage
+  int warps_per_cta;           // GB_MIXED launch shape (1, 2 or 4; 0 = 4), chosen by the tuner
   double rhs_time;             // rhs-only mode: evaluate the grid velocity at this time
   SarkCoef co;
 };

@@ -419,9 +419,11 @@ static int launch_one(const StageArgs &a, cudaStream_t st, int num_sms) {
     if (err != cudaSuccess) return (int)err;
     attr_set = true;
   }
-  int per_sm = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel<T, N, STAGE>, threads, smem);
-  if (err != cudaSuccess) return (int)err;
+  static int per_sm = 0;   // cached: no runtime queries while a graph is being captured
+  if (per_sm == 0) {
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel<T, N, STAGE>, threads, smem);
+    if (err != cudaSuccess) return (int)err;
+  }
   if (per_sm < 1) per_sm = 1;
   const int64_t ntiles = (a.K + E - 1) / E;
   int64_t grid = (int64_t)num_sms * per_sm;

@@ -59,7 +59,7 @@ struct TcDim {
   static constexpr int B_P = B_I + CH * KS;
   static constexpr int NSETS = B_P + CH * NT;
   static constexpr int GEOS = 17;               // per element: rx sx ry sy iJ vx[3] vy[3] ex[3] ey[3]
-  static constexpr int W = 4;                   // warps per CTA
+  static constexpr int W = 4;                   // most warps per CTA (the launch picks 1, 2 or 4)
   static constexpr int WARP_FLOATS = 16 * S + 16 * OUTS + 16 * GEOS + 4;
 };
 
@@ -564,7 +564,7 @@ __device__ __forceinline__ void tc_load_bary(const void *ops, int lane, float (&
 template <int N, int STAGE>
 __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_kernel(const StageArgs a) {
   typedef TcDim<N> D;
-  constexpr int W = D::W;
+  const int W = blockDim.x >> 5;                // warps per CTA: a launch parameter (1, 2 or 4)
   extern __shared__ float4 tc_smem4[];
   float4 *btab = tc_smem4;                                          // [NSETS][32]
   float *wbase = reinterpret_cast<float *>(tc_smem4 + D::NSETS * 32);
@@ -639,28 +639,32 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_group_k
 
 // ---------------------------------------------------------------------------
 template <int N>
-static size_t tc_smem() {
+static size_t tc_smem(int W = TcDim<N>::W) {
   typedef TcDim<N> D;
-  return sizeof(float4) * (size_t)D::NSETS * 32 + sizeof(float) * (size_t)D::W * D::WARP_FLOATS;
+  return sizeof(float4) * (size_t)D::NSETS * 32 + sizeof(float) * (size_t)W * D::WARP_FLOATS;
 }
 
 template <int N, int STAGE>
 static int tc_launch_one(const StageArgs &a, cudaStream_t st, int num_sms) {
   typedef TcDim<N> D;
-  const size_t smem = tc_smem<N>();
-  constexpr int threads = 32 * D::W;
+  const int W = (a.warps_per_cta == 1 || a.warps_per_cta == 2) ? a.warps_per_cta : D::W;
+  const size_t smem = tc_smem<N>(W);
+  const int threads = 32 * W;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(tc_stage_kernel<N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(tc_stage_kernel<N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<N>());
     if (err != cudaSuccess) return (int)err;
     attr_set = true;
   }
-  int per_sm = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_stage_kernel<N, STAGE>, threads, smem);
-  if (err != cudaSuccess) return (int)err;
-  if (per_sm < 1) per_sm = 1;
+  static int per_sm_w[5] = {0, 0, 0, 0, 0};   // cached: no runtime queries while a graph is being captured
+  int &per_sm = per_sm_w[W];
+  if (per_sm == 0) {
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_stage_kernel<N, STAGE>, threads, smem);
+    if (err != cudaSuccess) return (int)err;
+    if (per_sm < 1) per_sm = 1;
+  }
   int64_t grid = (int64_t)num_sms * per_sm;
-  const int64_t need = ((a.K + 15) / 16 + D::W - 1) / D::W;
+  const int64_t need = ((a.K + 15) / 16 + W - 1) / W;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   tc_stage_kernel<N, STAGE><<<(unsigned)grid, threads, smem, st>>>(a);
@@ -703,9 +707,11 @@ static int tc_group_launch_one(const GroupArgs &g, cudaStream_t st, int num_sms)
     if (err != cudaSuccess) return (int)err;
     attr_set = true;
   }
-  int per_sm = 0;
-  cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_group_kernel<N, STAGE>, threads, smem);
-  if (err != cudaSuccess) return (int)err;
+  static int per_sm = 0;   // cached: no runtime queries while a graph is being captured
+  if (per_sm == 0) {
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_group_kernel<N, STAGE>, threads, smem);
+    if (err != cudaSuccess) return (int)err;
+  }
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms * per_sm;
   const int64_t need = (g.total_tiles + D::W - 1) / D::W;

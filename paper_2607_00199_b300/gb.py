@@ -60,6 +60,9 @@ def _load():
         'gb_step_timed': ([vp, c_double, i64, _dp], c_int),
         'gb_sync': ([vp], c_int),
         'gb_set_stream': ([vp, vp], c_int),
+        'gb_set_graph': ([vp, c_int], c_int),
+        'gb_launch_config': ([vp, ctypes.POINTER(c_int)], c_int),
+        'gb_set_launch_config': ([vp, c_int], c_int),
         'gb_info': ([vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                      ctypes.POINTER(i64), ctypes.POINTER(i64), _dp, _dp, ctypes.POINTER(i64)], c_int),
         'gb_state_ptr': ([vp, ctypes.POINTER(vp)], c_int),
@@ -200,6 +203,20 @@ class Solver:
         ms = np.zeros(5)
         self._c(lib.gb_step_timed(self.h, float(dt), int(nsteps), _ptr(ms)))
         return ms
+
+    def launch_config(self):
+        """Warps per CTA of the GB_MIXED kernel (tuned at the first step; 0 for GB_FP64)."""
+        w = ctypes.c_int()
+        self._c(lib.gb_launch_config(self.h, ctypes.byref(w)))
+        return w.value
+
+    def set_launch_config(self, warps_per_cta):
+        """Fix the GB_MIXED warps per CTA (1, 2 or 4) instead of tuning."""
+        self._c(lib.gb_set_launch_config(self.h, int(warps_per_cta)))
+
+    def set_graph(self, enable):
+        """Capture each step as a CUDA graph in step() (default on)."""
+        self._c(lib.gb_set_graph(self.h, int(bool(enable))))
 
     def set_stream(self, stream):
         """Finish pending work, then use `stream` (a cudaStream_t address) from now on."""

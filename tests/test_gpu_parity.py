@@ -267,3 +267,55 @@ def test_checkpoint_resume_is_bitwise():
     q100b, t100b = s2.fields()
     assert t100b == t100
     assert np.array_equal(q100b, q100)
+
+
+@pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
+def test_graph_steps_equal_direct_steps(precision):
+    # gb_step on a non-default stream replays one captured step; it must match direct launches
+    stream = torch.cuda.Stream()
+    mesh = inputs.periodic_square_mesh(9, jitter=0.1)
+    outs = []
+    for use_graph in (True, False):
+        s = gb.Solver(mesh, 3, 0.1, 200.0, precision=precision, stream=stream.cuda_stream)
+        s.set_graph(use_graph)
+        s.set_motion(0.05, 0.8)
+        xy = s.nodes()
+        rho, u, v = inputs.taylor_green(xy[..., 0], xy[..., 1], 0.1)
+        from paper_2607_00199_b300 import state
+        s.set_fields(state.equilibrium_fields(rho, u, v, s.c), 0.0)
+        dt = inputs.cfl_dt(mesh, 3, s.c, 0.5)
+        s.step(dt, 7)
+        s.step(dt * 0.9, 5)          # a new dt rebuilds the graph
+        outs.append(s.fields() + (s.vertices(),))
+        s.close()
+    (qa, ta, xa), (qb, tb, xb) = outs
+    assert ta == tb and np.array_equal(qa, qb) and np.array_equal(xa, xb)
+
+
+def test_launch_shapes_give_identical_results_and_tuner_picks_one():
+    stream = torch.cuda.Stream()
+    mesh = inputs.periodic_square_mesh(11, jitter=0.1)
+    from paper_2607_00199_b300 import state
+    outs = []
+    for w in (1, 2, 4, None):
+        s = gb.Solver(mesh, 4, 0.1, 300.0, precision=gb.GB_MIXED, stream=stream.cuda_stream)
+        if w is not None:
+            s.set_launch_config(w)
+        s.set_motion(0.04, 0.9)
+        xy = s.nodes()
+        rho, u, v = inputs.taylor_green(xy[..., 0], xy[..., 1], 0.1)
+        s.set_fields(state.equilibrium_fields(rho, u, v, s.c), 0.0)
+        dt = inputs.cfl_dt(mesh, 4, s.c, 0.5)
+        s.step(dt, 6)
+        q, t = s.fields()
+        if w is None:
+            assert s.launch_config() in (1, 2, 4)
+        else:
+            assert s.launch_config() == w
+        outs.append(q)
+        s.close()
+    for q in outs[1:]:
+        assert np.array_equal(q, outs[0])
+    with pytest.raises(gb.GBError):
+        f = gb.Solver(mesh, 2, 0.1, 100.0, precision=gb.GB_FP64, stream=stream.cuda_stream)
+        f.set_launch_config(2)
