@@ -132,6 +132,14 @@ int gb_set_launch_config(gb_solver *s, int warps_per_cta);
  * (not cleared).  Returns the device status like gb_sync. */
 int gb_step_timed(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms);
 
+/* gb_diagnostics: integrals of the current state over the moving mesh (the kinetic
+ * energy diagnostic of Sec. 7.2 and conservation checks), each the exact integral
+ * of the degree-N nodal interpolant (J sum_i w_i f_i per element, w = 1^T Mhat):
+ * out[0] = int rho, out[1] = E_K = (1/|Omega|) int rho |u|^2 / 2 (rho_inf = 1),
+ * out[2] = int rho u, out[3] = int rho v, out[4] = |Omega|.  Host array of 5
+ * doubles; synchronises the stream.  Reductions in FP64 in both precisions. */
+int gb_diagnostics(gb_solver *s, double *out);
+
 /* gb_sync: synchronise the stream, return and clear the device status
  * (GB_OK, GB_ENAN or GB_EMESH). */
 int gb_sync(gb_solver *s);

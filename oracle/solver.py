@@ -233,3 +233,14 @@ class OracleSolver:
         """int f over the mesh for nodal f of shape (K, Np): sum_e J_e 1^T Mhat f_e."""
         _, J, _, _ = self.geometry(xv)
         return float(np.einsum('e,ij,ej->', J, self.ref.M, f))
+
+    def diagnostics(self, q, xv):
+        """Integrals of the state (Sec. 7.2 kinetic energy, rho_inf = 1), each the
+        exact integral of the nodal interpolant of its integrand:
+        mass int rho, E_K = (1/|Omega|) int rho |u|^2 / 2, momentum int rho u,
+        int rho v, and the area |Omega|.  q has shape (K, 6, Np)."""
+        rho, mu, mv = physics.macroscopic(np.moveaxis(q, 1, -1), self.c)
+        area = self.integral(np.ones_like(rho), xv)
+        ke = self.integral(0.5 * (mu * mu + mv * mv) / rho, xv)
+        return {'mass': self.integral(rho, xv), 'kinetic_energy': ke / area,
+                'momentum_x': self.integral(mu, xv), 'momentum_y': self.integral(mv, xv), 'area': area}

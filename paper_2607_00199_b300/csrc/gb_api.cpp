@@ -47,6 +47,7 @@ struct gb_solver {
   int *d_status = nullptr;
   void *d_qn = nullptr, *d_b1 = nullptr, *d_b2 = nullptr, *d_F0 = nullptr, *d_acc = nullptr;
   double *d_tmp = nullptr;     // FP64 staging (GB_MIXED transfers, node coordinates)
+  double *d_diag = nullptr;    // 1^T Mhat (Np), 5 result slots, block partials
   size_t tmp_bytes = 0;
   int64_t device_bytes = 0;
 };
@@ -74,7 +75,7 @@ static int dev_alloc(gb_solver *s, void **p, size_t bytes) {
 
 static void free_all(gb_solver *s) {
   void *ptrs[] = {s->d_ops, s->d_ops_mixed, s->d_mesh, s->d_mesh_int, s->d_perm, s->d_X, s->d_xn, s->d_shape,
-                  s->d_clock, s->d_status, s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp};
+                  s->d_clock, s->d_status, s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp, s->d_diag};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -770,6 +771,32 @@ int gb_group_destroy(gb_group *g) {
 }
 
 const char *gb_group_last_error(gb_group *g) { return g ? g->err.c_str() : g_create_error.c_str(); }
+
+int gb_diagnostics(gb_solver *s, double *out) {
+  if (!s || !out) return fail(s, GB_EINVAL, "NULL argument");
+  if (!s->d_diag) {
+    int rc = dev_alloc(s, (void **)&s->d_diag, sizeof(double) * (s->Np + 5 + gb::diagnostics_scratch_doubles()));
+    if (rc) return rc;
+    cudaError_t ce = cudaMemcpyAsync(s->d_diag, s->ref.wq.data(), sizeof(double) * s->Np, cudaMemcpyHostToDevice, s->stream);
+    if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_diagnostics");
+  }
+  const bool mixed = s->precision == GB_MIXED;
+  const int64_t stride = mixed ? gb::mixed_stride(s->N) : 6 * s->Np;
+  int lr = gb::launch_diagnostics(s->N, s->d_qn, mixed, mixed, stride, mixed ? s->d_mesh_int : s->d_mesh, s->d_xn,
+                                  s->period[0], s->period[1], s->d_diag, s->c, s->K, s->d_diag + s->Np + 5,
+                                  s->d_diag + s->Np, s->stream);
+  if (lr) return cuda_fail(s, (cudaError_t)lr, "gb_diagnostics");
+  double r[5];
+  cudaError_t ce = cudaMemcpyAsync(r, s->d_diag + s->Np, sizeof(r), cudaMemcpyDeviceToHost, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_diagnostics");
+  out[0] = r[0];
+  out[1] = r[1] / r[4];
+  out[2] = r[2];
+  out[3] = r[3];
+  out[4] = r[4];
+  return GB_OK;
+}
 
 int gb_launch_config(gb_solver *s, int *warps_per_cta) {
   if (!s || !warps_per_cta) return fail(s, GB_EINVAL, "NULL argument");

@@ -26,6 +26,7 @@ struct RefOps {
   std::vector<double> I, P;      // Nc x Np, Np x Nc
   std::vector<double> cr, cs, cw;
   std::vector<int> fmask;        // 3 x Nfp, counter-clockwise along each face
+  std::vector<double> wq;        // Np: 1^T Mhat, integral of each nodal basis function
 };
 
 bool build_reference(int N, RefOps &R);
@@ -101,6 +102,14 @@ int launch_nodes(int N, const double *ops, const double *xn, const MeshRec *mesh
 int launch_relayout(const void *canon_src, void *canon_dst, bool canon_is_double, bool to_internal, float *inner,
                     const int32_t *perm, int64_t K, int Np, int S, double rest, void *stream);
 int mixed_stride(int N);   // element stride (floats) of the GB_MIXED field layout
+// integrals over the mesh at the current vertices: out[0] = int rho, out[1] = int rho |u|^2 / 2,
+// out[2] = int rho u, out[3] = int rho v, out[4] = area; fields of element e at
+// q[e * stride + f * Np + n] (+ 1 on field 1 when perturbation), FP64 or FP32
+// part: diagnostics_scratch_doubles() doubles of block partials; out: 5 doubles (device)
+int launch_diagnostics(int N, const void *q, bool is_float, bool perturbation, int64_t stride, const MeshRec *mesh,
+                       const double *xn, double px, double py, const double *wq, double c, int64_t K, double *part,
+                       double *out, void *stream);
+int diagnostics_scratch_doubles();
 int launch_group_mixed(int N, int stage, const GroupArgs &g, void *stream, int num_sms);
 int launch_group_vertex_update(const GroupArgs &g, void *stream);
 int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, int *N, int64_t *K, int *Np,

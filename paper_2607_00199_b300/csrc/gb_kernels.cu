@@ -15,7 +15,7 @@
 // The kernel is persistent: the grid covers the SMs and each CTA loops over
 // element tiles, with the reference operators staged once in shared memory.
 // T is the field/arithmetic type; the library instantiates it for double
-// (GB_FP64).  GB_MIXED uses the thread-per-element kernel of gb_kernels_mixed.cu.
+// (GB_FP64).  GB_MIXED uses the tensor-core kernel of gb_kernels_tc.cu.
 #include <cuda_runtime.h>
 
 #include <cstdint>

@@ -322,12 +322,18 @@ bool build_reference(int N, RefOps &R) {
   for (int i = 0; i < Np; ++i)
     for (int k = 0; k < Nc; ++k) ITW[(size_t)i * Nc + k] *= cw[k];
   std::vector<ld> P = matmul(Minv, ITW, Np, Np, Nc);
+  // integral of each nodal basis function: 1^T Mhat, Mhat = (V V^T)^-1
+  std::vector<ld> Mhat;
+  if (!invert(Minv, Np, Mhat)) return false;
+  std::vector<ld> wq(Np, 0.0L);
+  for (int i = 0; i < Np; ++i)
+    for (int j = 0; j < Np; ++j) wq[j] += Mhat[(size_t)i * Np + j];
   auto cp = [](const std::vector<ld> &a, std::vector<double> &b) {
     b.resize(a.size());
     for (size_t i = 0; i < a.size(); ++i) b[i] = (double)a[i];
   };
   cp(r, R.r); cp(s, R.s); cp(Dr, R.Dr); cp(Ds, R.Ds); cp(LIFT, R.LIFT);
-  cp(I, R.I); cp(P, R.P); cp(cr, R.cr); cp(cs, R.cs); cp(cw, R.cw);
+  cp(I, R.I); cp(P, R.P); cp(cr, R.cr); cp(cs, R.cs); cp(cw, R.cw); cp(wq, R.wq);
   return true;
 }
 

@@ -61,6 +61,7 @@ def _load():
         'gb_sync': ([vp], c_int),
         'gb_set_stream': ([vp, vp], c_int),
         'gb_set_graph': ([vp, c_int], c_int),
+        'gb_diagnostics': ([vp, _dp], c_int),
         'gb_launch_config': ([vp, ctypes.POINTER(c_int)], c_int),
         'gb_set_launch_config': ([vp, c_int], c_int),
         'gb_info': ([vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
@@ -203,6 +204,12 @@ class Solver:
         ms = np.zeros(5)
         self._c(lib.gb_step_timed(self.h, float(dt), int(nsteps), _ptr(ms)))
         return ms
+
+    def diagnostics(self):
+        """dict: mass, kinetic_energy (per unit area), momentum_x, momentum_y, area."""
+        out = np.zeros(5)
+        self._c(lib.gb_diagnostics(self.h, _ptr(out)))
+        return {'mass': out[0], 'kinetic_energy': out[1], 'momentum_x': out[2], 'momentum_y': out[3], 'area': out[4]}
 
     def launch_config(self):
         """Warps per CTA of the GB_MIXED kernel (tuned at the first step; 0 for GB_FP64)."""

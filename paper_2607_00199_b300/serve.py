@@ -23,12 +23,12 @@ from . import gb, inputs, state
 def predicted_device_bytes(K, N):
     """Device memory of a GB_MIXED solver of K elements and order N (from the
     library's layout: 5 field arrays of ceil16(K) x S floats, mesh records,
-    permutation, vertex arrays, operator tables)."""
+    permutation, vertex arrays, operator tables, diagnostics scratch)."""
     Np = (N + 1) * (N + 2) // 2
     S = ((6 * Np - 4 + 7) // 8) * 8 + 4
     Kpad = (K + 15) // 16 * 16
     nv = K // 2
-    return 5 * Kpad * S * 4 + 2 * 32 * K + 4 * K + 3 * 16 * nv + 16 + 4 + (1 << 17)
+    return 5 * Kpad * S * 4 + 2 * 32 * K + 4 * K + 3 * 16 * nv + 16 + 4 + (1 << 17) + 8 * (Np + 5 + 5 * 1184)
 
 
 class Admission:

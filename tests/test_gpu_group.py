@@ -73,6 +73,7 @@ def test_predicted_footprint_is_conservative():
     for n, N in ((32, 2), (16, 5), (64, 4)):
         s, _, _ = _solver(n, N, 0.05, 1.0, 100.0, jitter=0.0)
         s.fields()
+        s.diagnostics()
         assert serve.predicted_device_bytes(2 * n * n, N) >= s.device_bytes
         s.close()
 

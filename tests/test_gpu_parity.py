@@ -214,6 +214,45 @@ def test_mixed_checkpoint_and_status():
     assert ei.value.code == gb.GB_ENAN
 
 
+@pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
+@pytest.mark.parametrize('N', [2, 4])
+def test_diagnostics_parity(precision, N):
+    # Sec. 7.2 kinetic energy and the conserved integrals of the GPU state after
+    # a few steps (ragged K = 98, jittered, moved mesh) against the oracle's on
+    # the same fields and vertices; both reduce in FP64
+    mesh, o, s = make_pair(7, N, 0.1, 200.0, 0.05, 1.0, jitter=0.1, precision=precision)
+    q0 = oracle_state(o, o.X, lambda x, y: inputs.random_flow(x, y, 5 + N))
+    s.set_fields(q0, 0.0)
+    d0 = s.diagnostics()
+    want0 = o.diagnostics(s.fields()[0], s.vertices())
+    s.step(inputs.cfl_dt(mesh, N, o.c, 0.5), 7)
+    d1 = s.diagnostics()
+    want1 = o.diagnostics(s.fields()[0], s.vertices())
+    for d, want in ((d0, want0), (d1, want1)):
+        for k in want:
+            assert abs(d[k] - want[k]) <= 1e-13 * max(1.0, abs(want[k])), (k, d[k], want[k])
+    # the stepping itself conserves mass to rounding over such a short run
+    assert abs(d1['mass'] - d0['mass']) <= (1e-11 if precision == gb.GB_FP64 else 1e-5) * d0['mass']
+    assert s.diagnostics() == d1        # deterministic reduction order
+
+
+def test_diagnostics_full_size_cfg2():
+    # K = 131072, N = 4 moving Taylor-Green vortex: closed forms at t = 0
+    # (mass 4 pi^2, E_K = 1/4) and oracle parity on the stepped state
+    for precision in (gb.GB_FP64, gb.GB_MIXED):
+        mesh, o, s = make_pair(256, 4, 0.1, 1000.0, 0.05, 1.0, jitter=0.1, precision=precision)
+        s.set_fields(oracle_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1)), 0.0)
+        d = s.diagnostics()
+        tol = 1e-12 if precision == gb.GB_FP64 else 1e-6
+        assert abs(d['mass'] - 4 * math.pi ** 2) <= tol * 40 and abs(d['kinetic_energy'] - 0.25) <= tol
+        s.step(inputs.cfl_dt(mesh, 4, o.c, 0.5), 3)
+        d = s.diagnostics()
+        want = o.diagnostics(s.fields()[0], s.vertices())
+        for k in want:
+            assert abs(d[k] - want[k]) <= 1e-12 * max(1.0, abs(want[k])), (precision, k)
+        s.close()
+
+
 def test_mixed_rhs_matches_fp64_rhs():
     mesh, o, s = make_pair(8, 4, 0.1, 100.0, 0.05, 1.0, jitter=0.1, precision=gb.GB_MIXED)
     xv = o.X + o.motion.displacement(o.X, 0.1)

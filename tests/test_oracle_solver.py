@@ -108,8 +108,7 @@ def test_planted_anti_upwind_flux_is_caught(monkeypatch):
 
 
 def _kinetic_energy(o, q, xv):
-    rho, ru, rv = physics.macroscopic(q.transpose(0, 2, 1), o.c)
-    return o.integral(0.5 * (ru ** 2 + rv ** 2) / rho, xv) / (4 * math.pi ** 2)
+    return o.diagnostics(q, xv)['kinetic_energy']
 
 
 @pytest.mark.parametrize('A', [0.0, 0.05])
@@ -137,3 +136,51 @@ def test_mass_conserved_on_static_mesh():
     dt = inputs.cfl_dt(mesh, 3, o.c, 0.5)
     q, xv, t = o.run(q, o.X.copy(), 0.0, dt, 30)
     assert abs(o.integral(q[:, 0], xv) - m0) < 1e-13 * abs(m0)
+
+
+def test_diagnostics_closed_forms_taylor_green():
+    # Sec. 7.2 E_K for the 2D vortex u = sin x cos y, v = -cos x sin y with
+    # rho = 1 + Ma^2/4 (cos 2x + cos 2y) on [0, 2 pi]^2: the rho perturbation
+    # integrates to zero against |u|^2, so int rho = 4 pi^2 and E_K = 1/4 exactly;
+    # both momenta vanish.  The nodal-interpolant integrals converge as h^(N+1).
+    errs = []
+    for n in (8, 16):
+        mesh = inputs.periodic_square_mesh(n, jitter=0.1)
+        o = OracleSolver(mesh, 4, Ma=0.1, Re=1000.0)
+        d = o.diagnostics(_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1)), o.X)
+        assert abs(d['area'] - 4 * math.pi ** 2) < 1e-12
+        errs.append(max(abs(d['mass'] - 4 * math.pi ** 2), abs(d['kinetic_energy'] - 0.25),
+                        abs(d['momentum_x']), abs(d['momentum_y'])))
+    assert errs[1] < 1e-7 and errs[1] < errs[0] / 16, errs
+
+
+def test_diagnostics_uniform_flow_exact():
+    # constant integrands are integrated exactly on any affine mesh
+    mesh = inputs.periodic_square_mesh(5, L=3.0, jitter=0.2)
+    o = OracleSolver(mesh, 3, Ma=0.2, Re=50.0)
+    d = o.diagnostics(_state(o, o.X, lambda x, y: inputs.free_stream(x, y, 0.6, -0.8)), o.X)
+    assert abs(d['area'] - 9.0) < 1e-13
+    assert abs(d['mass'] - 9.0) < 1e-13
+    assert abs(d['kinetic_energy'] - 0.5) < 1e-13          # |u|^2 / 2 = (0.36 + 0.64) / 2
+    assert abs(d['momentum_x'] - 9.0 * 0.6) < 1e-13 and abs(d['momentum_y'] + 9.0 * 0.8) < 1e-13
+
+
+def test_mass_and_momentum_conserved_on_moving_mesh():
+    # d/dt int q J = int (-div F + v_G . grad q + q div v_G) = 0 on the periodic
+    # domain and the collision leaves the conserved moments q1..q3 unchanged
+    # (Sec. 2): the semi-discrete scheme conserves them, the SARK step with
+    # stage geometry (Sec. 6) up to its own O(dt^4) error, so the drift over a
+    # fixed time falls at least 8x when dt halves; the torus area is exact.
+    mesh = inputs.periodic_square_mesh(6, jitter=0.1)
+    o = OracleSolver(mesh, 3, Ma=0.1, Re=100, motion=Motion(0.1, 0.1))
+    q0 = _state(o, o.X, lambda x, y: inputs.random_flow(x, y, 3))
+    d0 = o.diagnostics(q0, o.X)
+    dt = inputs.cfl_dt(mesh, 3, o.c, 0.5)
+    drift = []
+    for k in (1, 2):
+        q, xv, t = o.run(q0, o.X.copy(), 0.0, dt / k, 20 * k)
+        assert np.abs(xv - o.X).max() > 0.01
+        d1 = o.diagnostics(q, xv)
+        assert abs(d1['area'] - d0['area']) < 1e-12 * d0['area']
+        drift.append(max(abs(d1[k] - d0[k]) for k in ('mass', 'momentum_x', 'momentum_y')))
+    assert drift[0] < 1e-7 * d0['mass'] and drift[1] < drift[0] / 8, drift
