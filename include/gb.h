@@ -122,7 +122,8 @@ int gb_set_graph(gb_solver *s, int enable);
  * right-hand-side kernel on the solver's own data for each shape (the state is not
  * changed) and keeps the fastest; the choice is cached per (N, K) in the process. */
 int gb_launch_config(gb_solver *s, int *warps_per_cta);
-/* gb_set_launch_config: fix the GB_MIXED warps per CTA (1, 2 or 4) and skip the tuner. */
+/* gb_set_launch_config: fix the GB_MIXED warps per CTA (1, 2 or 4) and skip the
+ * tuner.  GB_EINVAL for other values and for GB_FP64 solvers. */
 int gb_set_launch_config(gb_solver *s, int warps_per_cta);
 
 /* gb_step_timed: gb_step that also records a CUDA event pair around every kernel

@@ -143,11 +143,11 @@ static void set_coefficients(gb_solver *s, double dt) {
 }
 
 // Launch-shape tuner (GB_MIXED): warps per CTA, 1, 2 or 4.  Fewer warps per CTA
-// spread the 16-element tiles of a small mesh over more SMs; more warps share
-// one copy of the operator tables.  The tuner times the rhs-only stage kernel
-// (which writes only the scratch buffer b2 and leaves the state alone) on the
-// solver's own data for each shape and keeps the fastest; a smaller shape must
-// win by 3%.  Choices are cached per (N, K) for the rest of the process.
+// spread the 16-element tiles of a small mesh over more SMs; more warps share one
+// copy of the operator tables.  The tuner times the rhs-only stage
+// kernel (which writes only the scratch buffer b2 and leaves the state alone) on
+// the solver's own data for each shape and keeps the fastest; a candidate after
+// the first must win by 3%.  Choices are cached per (N, K) for the process.
 static std::mutex g_tune_mu;
 static std::map<std::pair<int, int64_t>, int> g_tuned;
 
@@ -173,6 +173,7 @@ static int tune_launch(gb_solver *s) {
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
   int best = 4;
   float best_ms = 1e30f;
+  // later candidates must beat the best so far by 3%
   const int cand[3] = {4, 2, 1};
   for (int i = 0; i < 3 && ce == cudaSuccess; ++i) {
     a.warps_per_cta = cand[i];

@@ -220,7 +220,69 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
     // accumulators: rhs[field][n-tile][fragment]
     float acc[6][NT][4];
 #pragma unroll
-    for (int f = 0; f < 6; ++f)
+    for (int f = 3; f < 6; ++f)
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[f][nt][j] = 0.0f;
+    // ---- collision term: I q at the cubature points, Ntilde there, P back (fields 4..6) ----
+    {
+      unsigned qh[3][KS][4], ql[3][KS][4];
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) load_a<S>(own, f * Np + ks * 8, f * Np + Np, g, t, qh[f][ks], ql[f][ks]);
+#pragma unroll 1
+      for (int ch = 0; ch < CH; ++ch) {
+        float qc[3][4];
+#pragma unroll
+        for (int f = 0; f < 3; ++f)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) qc[f][j] = 0.0f;
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+          const float4 b = btab[(D::B_I + ch * KS + ks) * 32 + lane];
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(qc[f], ql[f][ks], __float_as_uint(b.z), __float_as_uint(b.w));
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(qc[f], qh[f][ks], __float_as_uint(b.x), __float_as_uint(b.y));
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(qc[f], qh[f][ks], __float_as_uint(b.z), __float_as_uint(b.w));
+        }
+        // Ntilde at the 4 (element, point) positions; the accumulator order (c0, c2, c1, c3)
+        // is the A-fragment order of the permuted chunk
+        unsigned nh[3][4], nl[3][4];
+        const int perm[4] = {0, 2, 1, 3};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int src = perm[j];
+          const float q1 = 1.0f + qc[0][src], q2 = qc[1][src], q3 = qc[2][src];
+          const float r1 = itau * __frcp_rn(q1);
+          const float rs = r1 * ISQ2;
+          split_tf32(q2 * q3 * r1, nh[0][j], nl[0][j]);
+          split_tf32(q2 * q2 * rs, nh[1][j], nl[1][j]);
+          split_tf32(q3 * q3 * rs, nh[2][j], nl[2][j]);
+        }
+        float4 bp[NT];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) bp[nt] = btab[(D::B_P + ch * NT + nt) * 32 + lane];
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(acc[3 + f][nt], nl[f], __float_as_uint(bp[nt].z), __float_as_uint(bp[nt].w));
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(acc[3 + f][nt], nh[f], __float_as_uint(bp[nt].x), __float_as_uint(bp[nt].y));
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+          for (int f = 0; f < 3; ++f) mma_tf32(acc[3 + f][nt], nh[f], __float_as_uint(bp[nt].z), __float_as_uint(bp[nt].w));
+      }
+    }
+
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
@@ -381,62 +443,6 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
         for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
           for (int ff = 0; ff < 3; ++ff) mma_tf32(acc[fg + ff][nt], ahi[ff], __float_as_uint(bq[nt].z), __float_as_uint(bq[nt].w));
-      }
-    }
-
-    // ---- collision term: I q at the cubature points, Ntilde there, P back (fields 4..6) ----
-    {
-      unsigned qh[3][KS][4], ql[3][KS][4];
-#pragma unroll
-      for (int f = 0; f < 3; ++f)
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks) load_a<S>(own, f * Np + ks * 8, f * Np + Np, g, t, qh[f][ks], ql[f][ks]);
-#pragma unroll 1
-      for (int ch = 0; ch < CH; ++ch) {
-        float qc[3][4];
-#pragma unroll
-        for (int f = 0; f < 3; ++f)
-#pragma unroll
-          for (int j = 0; j < 4; ++j) qc[f][j] = 0.0f;
-#pragma unroll
-        for (int ks = 0; ks < KS; ++ks) {
-          const float4 b = btab[(D::B_I + ch * KS + ks) * 32 + lane];
-#pragma unroll
-          for (int f = 0; f < 3; ++f) mma_tf32(qc[f], ql[f][ks], __float_as_uint(b.z), __float_as_uint(b.w));
-#pragma unroll
-          for (int f = 0; f < 3; ++f) mma_tf32(qc[f], qh[f][ks], __float_as_uint(b.x), __float_as_uint(b.y));
-#pragma unroll
-          for (int f = 0; f < 3; ++f) mma_tf32(qc[f], qh[f][ks], __float_as_uint(b.z), __float_as_uint(b.w));
-        }
-        // Ntilde at the 4 (element, point) positions; the accumulator order (c0, c2, c1, c3)
-        // is the A-fragment order of the permuted chunk
-        unsigned nh[3][4], nl[3][4];
-        const int perm[4] = {0, 2, 1, 3};
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int src = perm[j];
-          const float q1 = 1.0f + qc[0][src], q2 = qc[1][src], q3 = qc[2][src];
-          const float r1 = itau * __frcp_rn(q1);
-          const float rs = r1 * ISQ2;
-          split_tf32(q2 * q3 * r1, nh[0][j], nl[0][j]);
-          split_tf32(q2 * q2 * rs, nh[1][j], nl[1][j]);
-          split_tf32(q3 * q3 * rs, nh[2][j], nl[2][j]);
-        }
-        float4 bp[NT];
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) bp[nt] = btab[(D::B_P + ch * NT + nt) * 32 + lane];
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-          for (int f = 0; f < 3; ++f) mma_tf32(acc[3 + f][nt], nl[f], __float_as_uint(bp[nt].z), __float_as_uint(bp[nt].w));
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-          for (int f = 0; f < 3; ++f) mma_tf32(acc[3 + f][nt], nh[f], __float_as_uint(bp[nt].x), __float_as_uint(bp[nt].y));
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-          for (int f = 0; f < 3; ++f) mma_tf32(acc[3 + f][nt], nh[f], __float_as_uint(bp[nt].z), __float_as_uint(bp[nt].w));
       }
     }
 

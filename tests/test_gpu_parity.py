@@ -331,24 +331,27 @@ def test_graph_steps_equal_direct_steps(precision):
     assert ta == tb and np.array_equal(qa, qb) and np.array_equal(xa, xb)
 
 
-def test_launch_shapes_give_identical_results_and_tuner_picks_one():
+@pytest.mark.parametrize('N', [3, 4])
+def test_launch_shapes_give_identical_results_and_tuner_picks_one(N):
+    # every shape computes the same tiles in the same order: bitwise equal results
     stream = torch.cuda.Stream()
     mesh = inputs.periodic_square_mesh(11, jitter=0.1)
     from paper_2607_00199_b300 import state
     outs = []
-    for w in (1, 2, 4, None):
-        s = gb.Solver(mesh, 4, 0.1, 300.0, precision=gb.GB_MIXED, stream=stream.cuda_stream)
+    shapes = [1, 2, 4]
+    for w in shapes + [None]:
+        s = gb.Solver(mesh, N, 0.1, 300.0, precision=gb.GB_MIXED, stream=stream.cuda_stream)
         if w is not None:
             s.set_launch_config(w)
         s.set_motion(0.04, 0.9)
         xy = s.nodes()
         rho, u, v = inputs.taylor_green(xy[..., 0], xy[..., 1], 0.1)
         s.set_fields(state.equilibrium_fields(rho, u, v, s.c), 0.0)
-        dt = inputs.cfl_dt(mesh, 4, s.c, 0.5)
+        dt = inputs.cfl_dt(mesh, N, s.c, 0.5)
         s.step(dt, 6)
         q, t = s.fields()
         if w is None:
-            assert s.launch_config() in (1, 2, 4)
+            assert s.launch_config() in shapes
         else:
             assert s.launch_config() == w
         outs.append(q)
@@ -358,3 +361,6 @@ def test_launch_shapes_give_identical_results_and_tuner_picks_one():
     with pytest.raises(gb.GBError):
         f = gb.Solver(mesh, 2, 0.1, 100.0, precision=gb.GB_FP64, stream=stream.cuda_stream)
         f.set_launch_config(2)
+    for bad in (3, 8, 0, 16):
+        with pytest.raises(gb.GBError):
+            gb.Solver(mesh, N, 0.1, 100.0, precision=gb.GB_MIXED, stream=stream.cuda_stream).set_launch_config(bad)
