@@ -141,6 +141,20 @@ int gb_step_timed(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms);
  * doubles; synchronises the stream.  Reductions in FP64 in both precisions. */
 int gb_diagnostics(gb_solver *s, double *out);
 
+/* gb_set_diagnostics: record the integrals of gb_diagnostics after every `every`-th
+ * step of gb_step, gb_step_timed and gb_group_step, on the device and without host
+ * synchronisation (the launches join the step, and its CUDA graph), into a ring of
+ * `capacity` records of 6 doubles: t, int rho, E_K, int rho u, int rho v, |Omega|.
+ * Counting starts at this call; every = 0 stops recording and frees the ring.
+ * Synchronises the stream.  GB_EINVAL for every < 0 or capacity outside 1 .. 2^32. */
+int gb_set_diagnostics(gb_solver *s, int every, int64_t capacity);
+
+/* gb_diagnostics_history: copy the most recent records (at most max; host array of
+ * max x 6 doubles), oldest first; *count = records copied, *total (may be NULL) =
+ * records written since recording began (those beyond `capacity` are overwritten).
+ * Synchronises the stream; *count = 0 when recording is off. */
+int gb_diagnostics_history(gb_solver *s, double *out, int64_t max, int64_t *count, int64_t *total);
+
 /* gb_sync: synchronise the stream, return and clear the device status
  * (GB_OK, GB_ENAN or GB_EMESH). */
 int gb_sync(gb_solver *s);

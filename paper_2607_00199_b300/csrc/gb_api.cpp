@@ -48,6 +48,11 @@ struct gb_solver {
   void *d_qn = nullptr, *d_b1 = nullptr, *d_b2 = nullptr, *d_F0 = nullptr, *d_acc = nullptr;
   double *d_tmp = nullptr;     // FP64 staging (GB_MIXED transfers, node coordinates)
   double *d_diag = nullptr;    // 1^T Mhat (Np), 5 result slots, block partials
+  // recorded diagnostics: every diag_every steps into a ring of diag_cap records
+  int diag_every = 0;
+  int64_t diag_cap = 0;
+  double *d_hist = nullptr;
+  int64_t *d_hctl = nullptr;   // steps since enabled, records written
   size_t tmp_bytes = 0;
   int64_t device_bytes = 0;
 };
@@ -75,9 +80,38 @@ static int dev_alloc(gb_solver *s, void **p, size_t bytes) {
 
 static void free_all(gb_solver *s) {
   void *ptrs[] = {s->d_ops, s->d_ops_mixed, s->d_mesh, s->d_mesh_int, s->d_perm, s->d_X, s->d_xn, s->d_shape,
-                  s->d_clock, s->d_status, s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp, s->d_diag};
+                  s->d_clock, s->d_status, s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp, s->d_diag,
+                  s->d_hist, s->d_hctl};
   for (void *p : ptrs)
     if (p) cudaFree(p);
+}
+
+static void dev_free(gb_solver *s, void **p, size_t bytes) {
+  if (*p) {
+    cudaFree(*p);
+    s->device_bytes -= (int64_t)bytes;
+    *p = nullptr;
+  }
+}
+
+// integration weights and scratch of the diagnostics (allocated on first use)
+static int ensure_diag(gb_solver *s) {
+  if (s->d_diag) return GB_OK;
+  int rc = dev_alloc(s, (void **)&s->d_diag, sizeof(double) * (s->Np + 5 + gb::diagnostics_scratch_doubles()));
+  if (rc) return rc;
+  cudaError_t ce = cudaMemcpyAsync(s->d_diag, s->ref.wq.data(), sizeof(double) * s->Np, cudaMemcpyHostToDevice, s->stream);
+  return ce == cudaSuccess ? GB_OK : cuda_fail(s, ce, "diagnostics weights");
+}
+
+// after a step: the recorded diagnostics, when enabled
+static int record_diagnostics(gb_solver *s, void *stream) {
+  if (s->diag_every <= 0) return GB_OK;
+  const bool mixed = s->precision == GB_MIXED;
+  const int64_t stride = mixed ? gb::mixed_stride(s->N) : 6 * s->Np;
+  int lr = gb::launch_diagnostics_record(s->N, s->d_qn, mixed, mixed, stride, mixed ? s->d_mesh_int : s->d_mesh, s->d_xn,
+                                         s->period[0], s->period[1], s->d_diag, s->c, s->K, s->d_diag + s->Np + 5,
+                                         s->d_clock, s->d_hctl, s->diag_every, s->d_hist, s->diag_cap, stream);
+  return lr ? cuda_fail(s, (cudaError_t)lr, "diagnostics record launch") : GB_OK;
 }
 
 static int ensure_tmp(gb_solver *s, size_t bytes) {
@@ -652,6 +686,7 @@ static int step_impl(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms)
       }
       if (kernel_ms) cudaEventRecord(ev[(size_t)k * 10 + 2 * st + 1], s->stream);
     }
+    if (rc == GB_OK) rc = record_diagnostics(s, s->stream);
   }
   if (kernel_ms) {
     cudaError_t ce = cudaStreamSynchronize(s->stream);
@@ -754,6 +789,8 @@ int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int 
     ga.args = g->d_args + 3 * (size_t)g->capacity;
     int rc = gb::launch_group_vertex_update(ga, g->stream);
     if (rc) return gfail(GB_ECUDA, std::string("gb_group_step launch: ") + cudaGetErrorString((cudaError_t)rc));
+    for (int r = 0; r < n; ++r)
+      if (record_diagnostics(solvers[r], g->stream)) return gfail(GB_ECUDA, "gb_group_step: " + solvers[r]->err);
   }
   return GB_OK;
 }
@@ -773,13 +810,66 @@ int gb_group_destroy(gb_group *g) {
 
 const char *gb_group_last_error(gb_group *g) { return g ? g->err.c_str() : g_create_error.c_str(); }
 
+int gb_set_diagnostics(gb_solver *s, int every, int64_t capacity) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (every < 0 || (every > 0 && (capacity < 1 || capacity > ((int64_t)1 << 32))))
+    return fail(s, GB_EINVAL, "every must be >= 0 and capacity in 1 .. 2^32");
+  cudaError_t ce = s->stream ? cudaStreamSynchronize(s->stream) : cudaDeviceSynchronize();
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_diagnostics");
+  drop_graph(s);
+  dev_free(s, (void **)&s->d_hist, sizeof(double) * 6 * (size_t)s->diag_cap);
+  dev_free(s, (void **)&s->d_hctl, 2 * sizeof(int64_t));
+  s->diag_every = 0;
+  s->diag_cap = 0;
+  if (every == 0) return GB_OK;
+  int rc = ensure_diag(s);
+  if (!rc) rc = dev_alloc(s, (void **)&s->d_hist, sizeof(double) * 6 * (size_t)capacity);
+  if (!rc) rc = dev_alloc(s, (void **)&s->d_hctl, 2 * sizeof(int64_t));
+  if (rc) {
+    dev_free(s, (void **)&s->d_hist, sizeof(double) * 6 * (size_t)capacity);
+    return rc;
+  }
+  ce = cudaMemsetAsync(s->d_hctl, 0, 2 * sizeof(int64_t), s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_diagnostics");
+  s->diag_every = every;
+  s->diag_cap = capacity;
+  return GB_OK;
+}
+
+int gb_diagnostics_history(gb_solver *s, double *out, int64_t max, int64_t *count, int64_t *total) {
+  if (!s || !count || (max > 0 && !out) || max < 0) return fail(s, GB_EINVAL, "NULL argument or max < 0");
+  *count = 0;
+  if (total) *total = 0;
+  if (s->diag_every <= 0) return GB_OK;
+  int64_t ctl[2] = {0, 0};
+  cudaError_t ce = cudaMemcpyAsync(ctl, s->d_hctl, sizeof(ctl), cudaMemcpyDeviceToHost, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_diagnostics_history");
+  const int64_t kept = ctl[1] < s->diag_cap ? ctl[1] : s->diag_cap;
+  const int64_t n = kept < max ? kept : max;
+  // the n most recent records, oldest first: record j sits in slot j mod cap, so at
+  // most two contiguous pieces of the ring
+  if (n > 0) {
+    const int64_t a = (ctl[1] - n) % s->diag_cap;
+    const int64_t first = n < s->diag_cap - a ? n : s->diag_cap - a;
+    ce = cudaMemcpyAsync(out, s->d_hist + 6 * a, 6 * sizeof(double) * (size_t)first, cudaMemcpyDeviceToHost, s->stream);
+    if (ce == cudaSuccess && first < n)
+      ce = cudaMemcpyAsync(out + 6 * first, s->d_hist, 6 * sizeof(double) * (size_t)(n - first), cudaMemcpyDeviceToHost,
+                           s->stream);
+    if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_diagnostics_history");
+  }
+  ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_diagnostics_history");
+  *count = n;
+  if (total) *total = ctl[1];
+  return GB_OK;
+}
+
 int gb_diagnostics(gb_solver *s, double *out) {
   if (!s || !out) return fail(s, GB_EINVAL, "NULL argument");
-  if (!s->d_diag) {
-    int rc = dev_alloc(s, (void **)&s->d_diag, sizeof(double) * (s->Np + 5 + gb::diagnostics_scratch_doubles()));
+  {
+    int rc = ensure_diag(s);
     if (rc) return rc;
-    cudaError_t ce = cudaMemcpyAsync(s->d_diag, s->ref.wq.data(), sizeof(double) * s->Np, cudaMemcpyHostToDevice, s->stream);
-    if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_diagnostics");
   }
   const bool mixed = s->precision == GB_MIXED;
   const int64_t stride = mixed ? gb::mixed_stride(s->N) : 6 * s->Np;

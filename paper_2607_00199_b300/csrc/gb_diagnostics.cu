@@ -30,11 +30,18 @@ __device__ __forceinline__ void block_sum5(double (&acc)[5], double *part) {
   }
 }
 
+// ctl (recording mode, else NULL): ctl[0] steps since recording was enabled, ctl[1]
+// records written; only every `every`-th step is integrated.
+__device__ __forceinline__ bool diag_skip(const int64_t *ctl, int every) {
+  return ctl != nullptr && (ctl[0] + 1) % every != 0;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kDiagThreads) diagnostics_kernel(const T *q, bool pert, int64_t stride, int Np,
                                                                   const MeshRec *mesh, const double *xn, double px,
                                                                   double py, const double *wq, double c, int64_t K,
-                                                                  double *part) {
+                                                                  double *part, const int64_t *ctl, int every) {
+  if (diag_skip(ctl, every)) return;   // uniform over the grid
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < K; e += (int64_t)gridDim.x * blockDim.x) {
     const MeshRec rec = mesh[e];
@@ -70,23 +77,73 @@ __global__ void __launch_bounds__(kDiagThreads) diagnostics_reduce_kernel(const 
   block_sum5(acc, out);
 }
 
+// Recording mode: one record (t, mass, E_K, momentum x, y, area) into slot
+// ctl[1] mod cap of the ring hist, then the counters advance.
+__global__ void __launch_bounds__(kDiagThreads) diagnostics_record_kernel(const double *part, int nblocks,
+                                                                         const double *clock, int64_t *ctl, int every,
+                                                                         double *hist, int64_t cap) {
+  const bool skip = diag_skip(ctl, every);
+  __shared__ double tot[5];
+  if (!skip) {
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+      for (int k = 0; k < 5; ++k) acc[k] += part[5 * b + k];
+    block_sum5(acc, tot);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (!skip) {
+      double *r = hist + 6 * (ctl[1] % cap);
+      r[0] = clock[0];
+      r[1] = tot[0];
+      r[2] = tot[1] / tot[4];
+      r[3] = tot[2];
+      r[4] = tot[3];
+      r[5] = tot[4];
+      ctl[1] += 1;
+    }
+    ctl[0] += 1;
+  }
+}
+
 int diagnostics_scratch_doubles() { return 5 * kDiagBlocks; }
+
+static int64_t diag_blocks(int64_t K) {
+  int64_t blocks = (K + kDiagThreads - 1) / kDiagThreads;
+  if (blocks > kDiagBlocks) blocks = kDiagBlocks;
+  return blocks < 1 ? 1 : blocks;
+}
+
+static void launch_partials(int N, const void *q, bool is_float, bool perturbation, int64_t stride, const MeshRec *mesh,
+                            const double *xn, double px, double py, const double *wq, double c, int64_t K, double *part,
+                            const int64_t *ctl, int every, cudaStream_t st) {
+  const int Np = (N + 1) * (N + 2) / 2;
+  const unsigned blocks = (unsigned)diag_blocks(K);
+  if (is_float)
+    diagnostics_kernel<float><<<blocks, kDiagThreads, 0, st>>>((const float *)q, perturbation, stride, Np, mesh, xn, px,
+                                                                 py, wq, c, K, part, ctl, every);
+  else
+    diagnostics_kernel<double><<<blocks, kDiagThreads, 0, st>>>((const double *)q, perturbation, stride, Np, mesh, xn,
+                                                                  px, py, wq, c, K, part, ctl, every);
+}
 
 int launch_diagnostics(int N, const void *q, bool is_float, bool perturbation, int64_t stride, const MeshRec *mesh,
                        const double *xn, double px, double py, const double *wq, double c, int64_t K, double *part,
                        double *out, void *stream) {
   cudaStream_t st = (cudaStream_t)stream;
-  const int Np = (N + 1) * (N + 2) / 2;
-  int64_t blocks = (K + kDiagThreads - 1) / kDiagThreads;
-  if (blocks > kDiagBlocks) blocks = kDiagBlocks;
-  if (blocks < 1) blocks = 1;
-  if (is_float)
-    diagnostics_kernel<float><<<(unsigned)blocks, kDiagThreads, 0, st>>>((const float *)q, perturbation, stride, Np, mesh,
-                                                                           xn, px, py, wq, c, K, part);
-  else
-    diagnostics_kernel<double><<<(unsigned)blocks, kDiagThreads, 0, st>>>((const double *)q, perturbation, stride, Np,
-                                                                            mesh, xn, px, py, wq, c, K, part);
-  diagnostics_reduce_kernel<<<1, kDiagThreads, 0, st>>>(part, (int)blocks, out);
+  launch_partials(N, q, is_float, perturbation, stride, mesh, xn, px, py, wq, c, K, part, nullptr, 1, st);
+  diagnostics_reduce_kernel<<<1, kDiagThreads, 0, st>>>(part, (int)diag_blocks(K), out);
+  return (int)cudaGetLastError();
+}
+
+int launch_diagnostics_record(int N, const void *q, bool is_float, bool perturbation, int64_t stride,
+                              const MeshRec *mesh, const double *xn, double px, double py, const double *wq, double c,
+                              int64_t K, double *part, const double *clock, int64_t *ctl, int every, double *hist,
+                              int64_t cap, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  launch_partials(N, q, is_float, perturbation, stride, mesh, xn, px, py, wq, c, K, part, ctl, every, st);
+  diagnostics_record_kernel<<<1, kDiagThreads, 0, st>>>(part, (int)diag_blocks(K), clock, ctl, every, hist, cap);
   return (int)cudaGetLastError();
 }
 

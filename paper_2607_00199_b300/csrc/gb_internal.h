@@ -110,6 +110,12 @@ int launch_diagnostics(int N, const void *q, bool is_float, bool perturbation, i
                        const double *xn, double px, double py, const double *wq, double c, int64_t K, double *part,
                        double *out, void *stream);
 int diagnostics_scratch_doubles();
+// the same integrals recorded on the device every `every` steps (ctl: int64 step and
+// record counters; hist: cap records of 6 doubles t, mass, E_K, momentum x, y, area)
+int launch_diagnostics_record(int N, const void *q, bool is_float, bool perturbation, int64_t stride,
+                              const MeshRec *mesh, const double *xn, double px, double py, const double *wq, double c,
+                              int64_t K, double *part, const double *clock, int64_t *ctl, int every, double *hist,
+                              int64_t cap, void *stream);
 int launch_group_mixed(int N, int stage, const GroupArgs &g, void *stream, int num_sms);
 int launch_group_vertex_update(const GroupArgs &g, void *stream);
 int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, int *N, int64_t *K, int *Np,

@@ -62,6 +62,9 @@ def _load():
         'gb_set_stream': ([vp, vp], c_int),
         'gb_set_graph': ([vp, c_int], c_int),
         'gb_diagnostics': ([vp, _dp], c_int),
+        'gb_set_diagnostics': ([vp, c_int, ctypes.c_int64], c_int),
+        'gb_diagnostics_history': ([vp, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_int64)], c_int),
         'gb_launch_config': ([vp, ctypes.POINTER(c_int)], c_int),
         'gb_set_launch_config': ([vp, c_int], c_int),
         'gb_info': ([vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
@@ -125,6 +128,16 @@ def sark_coefficients(gamma):
     E, A, B = np.zeros(5), np.zeros(16), np.zeros(4)
     _check(lib.gb_sark_coefficients(float(gamma), _ptr(E), _ptr(A), _ptr(B)))
     return E, A.reshape(4, 4), B
+
+
+def dissipation_rate(t, kinetic_energy):
+    """epsilon = -dE_K/dt (Sec. 7.2) from a recorded series, by second-order finite
+    differences (central inside, one-sided at the ends; uneven spacing allowed)."""
+    t = np.asarray(t, dtype=np.float64)
+    e = np.asarray(kinetic_energy, dtype=np.float64)
+    if t.size < 3:
+        raise ValueError('need at least 3 records')
+    return -np.gradient(e, t, edge_order=2)
 
 
 class Solver:
@@ -210,6 +223,24 @@ class Solver:
         out = np.zeros(5)
         self._c(lib.gb_diagnostics(self.h, _ptr(out)))
         return {'mass': out[0], 'kinetic_energy': out[1], 'momentum_x': out[2], 'momentum_y': out[3], 'area': out[4]}
+
+    def set_diagnostics(self, every, capacity=4096):
+        """Record the diagnostics on the device after every `every`-th step (0: off)."""
+        self._c(lib.gb_set_diagnostics(self.h, int(every), int(capacity)))
+        self._diag_cap = int(capacity) if every else 0
+
+    def diagnostics_history(self):
+        """Recorded diagnostics, oldest first: dict of arrays t, mass, kinetic_energy,
+        momentum_x, momentum_y, area, plus 'total' (records written since enabled)."""
+        cap = getattr(self, '_diag_cap', 0)
+        out = np.zeros((max(cap, 1), 6))
+        n, tot = ctypes.c_int64(), ctypes.c_int64()
+        self._c(lib.gb_diagnostics_history(self.h, _ptr(out), cap, ctypes.byref(n), ctypes.byref(tot)))
+        r = out[:n.value]
+        keys = ('t', 'mass', 'kinetic_energy', 'momentum_x', 'momentum_y', 'area')
+        d = {k: r[:, i].copy() for i, k in enumerate(keys)}
+        d['total'] = tot.value
+        return d
 
     def launch_config(self):
         """Warps per CTA of the GB_MIXED kernel (tuned at the first step; 0 for GB_FP64)."""

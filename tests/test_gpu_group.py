@@ -55,6 +55,26 @@ def test_group_step_is_bitwise_equal_to_alone(N):
     g.close()
 
 
+def test_group_records_diagnostics_like_alone():
+    specs = [(5, 0.05, 1.0, 100.0), (8, 0.03, 0.7, 500.0)]
+    grouped = [_solver(n, 3, A, T, Re) for (n, A, T, Re) in specs]
+    grouped[0][0].set_diagnostics(1, 32)
+    grouped[1][0].set_diagnostics(2, 32)
+    g = gb.Group(4, _stream())
+    g.step([s for s, _, _ in grouped], [dt for _, _, dt in grouped], 6)
+    for (n, A, T, Re), (sg, _, dt), every in zip(specs, grouped, (1, 2)):
+        sa, _, _ = _solver(n, 3, A, T, Re)
+        sa.set_diagnostics(every, 32)
+        sa.step(dt, 6)
+        hg, ha = sg.diagnostics_history(), sa.diagnostics_history()
+        assert hg['total'] == ha['total'] == 6 // every
+        for key in ('t', 'mass', 'kinetic_energy', 'momentum_x', 'momentum_y', 'area'):
+            assert np.array_equal(hg[key], ha[key]), key
+        sa.close()
+        sg.close()
+    g.close()
+
+
 def test_group_rejects_mismatched_members():
     a, _, dta = _solver(4, 2, 0.05, 1.0, 100.0)
     b, _, dtb = _solver(4, 3, 0.05, 1.0, 100.0)

@@ -253,6 +253,63 @@ def test_diagnostics_full_size_cfg2():
         s.close()
 
 
+@pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
+def test_diagnostics_history_equals_on_demand(precision):
+    # records taken inside the step (and its CUDA graph) equal gb_diagnostics after
+    # each step taken one by one, bit for bit
+    mesh, o, a = make_pair(6, 3, 0.1, 200.0, 0.05, 1.0, jitter=0.1, precision=precision)
+    b = gb.Solver(mesh, 3, 0.1, 200.0, precision=precision, stream=torch.cuda.current_stream().cuda_stream)
+    b.set_motion(0.05, 1.0)
+    q0 = oracle_state(o, o.X, lambda x, y: inputs.random_flow(x, y, 21))
+    a.set_fields(q0, 0.0)
+    b.set_fields(q0, 0.0)
+    dt = inputs.cfl_dt(mesh, 3, o.c, 0.5)
+    a.set_diagnostics(1, 64)
+    a.step(dt, 10)
+    h = a.diagnostics_history()
+    assert h['total'] == 10 and len(h['t']) == 10
+    for k in range(10):
+        b.step(dt, 1)
+        d = b.diagnostics()
+        assert h['t'][k] == b.fields()[1]
+        for key in d:
+            assert h[key][k] == d[key], (k, key)
+    # every 3rd step into a ring of 2: the records of steps 3, 6, 9 were written, 6 and 9 kept
+    a.set_diagnostics(3, 2)
+    t0 = a.fields()[1]
+    a.step(dt, 10)
+    h = a.diagnostics_history()
+    assert h['total'] == 3 and len(h['t']) == 2
+    assert np.allclose(h['t'], [t0 + 6 * dt, t0 + 9 * dt], rtol=0, atol=1e-12)
+    a.set_diagnostics(0)
+    assert len(a.diagnostics_history()['t']) == 0
+    with pytest.raises(gb.GBError):
+        a.set_diagnostics(-1)
+    with pytest.raises(gb.GBError):
+        a.set_diagnostics(1, 0)
+
+
+def test_recorded_kinetic_energy_follows_oracle():
+    # Sec. 7.2 E_K(t) of a moving Taylor-Green vortex, recorded every step on the GPU
+    # (FP64 path), against the oracle's integrals of the oracle's own run
+    mesh, o, s = make_pair(5, 3, 0.1, 50.0, 0.05, 1.0, jitter=0.1)
+    q = oracle_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1))
+    s.set_fields(q, 0.0)
+    dt = inputs.cfl_dt(mesh, 3, o.c, 0.5)
+    s.set_diagnostics(1, 16)
+    s.step(dt, 8)
+    h = s.diagnostics_history()
+    xv, t = o.X.copy(), 0.0
+    for k in range(8):
+        q, xv = o.step(q, xv, t, dt)
+        t += dt
+        d = o.diagnostics(q, xv)
+        assert abs(h['t'][k] - t) <= 1e-14 * max(1.0, t)
+        for key in ('mass', 'kinetic_energy', 'momentum_x', 'momentum_y', 'area'):
+            assert abs(h[key][k] - d[key]) <= 1e-12 * max(1.0, abs(d[key])), (k, key)
+    assert h['kinetic_energy'][-1] < h['kinetic_energy'][0]     # viscous decay
+
+
 def test_mixed_rhs_matches_fp64_rhs():
     mesh, o, s = make_pair(8, 4, 0.1, 100.0, 0.05, 1.0, jitter=0.1, precision=gb.GB_MIXED)
     xv = o.X + o.motion.displacement(o.X, 0.1)
