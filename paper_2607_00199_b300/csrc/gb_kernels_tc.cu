@@ -95,6 +95,11 @@ __device__ __forceinline__ void mma3(float (&c)[4], const unsigned (&ahi)[4], co
   mma_tf32(c, ahi, __float_as_uint(b.z), __float_as_uint(b.w));
 }
 
+// packed FP32x2 arithmetic (two lanes of independent values per instruction)
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float a, float2 x, float2 y) { return __ffma2_rn(bc2(a), x, y); }
+__device__ __forceinline__ float2 mul2(float a, float2 x) { return __fmul2_rn(bc2(a), x); }
+
 __device__ __forceinline__ void tc_cp_async16(float *dst, const float *src) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
@@ -338,24 +343,29 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
           mma_tf32(ds[nt], ahi, __float_as_uint(bs[nt].z), __float_as_uint(bs[nt].w));
         }
       }
-      // pointwise: chain rule, v_G . grad q_f and the Atilde couplings (Sec. 2)
+      // pointwise: chain rule, v_G . grad q_f and the Atilde couplings (Sec. 2), on the
+      // two columns of a fragment row at once
 #pragma unroll
       for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int h = j >> 1, col = j & 1;
-          const float qx = rxr[h] * dr[nt][j] + sxr[h] * ds[nt][j];
-          const float qy = ryr[h] * dr[nt][j] + syr[h] * ds[nt][j];
-          const float ale = vgxp[h][nt][col] * qx + vgyp[h][nt][col] * qy;
+        for (int h = 0; h < 2; ++h) {
+          const int j0 = 2 * h;
+          const float2 d_r = make_float2(dr[nt][j0], dr[nt][j0 + 1]), d_s = make_float2(ds[nt][j0], ds[nt][j0 + 1]);
+          const float2 qx = fma2(sxr[h], d_s, mul2(rxr[h], d_r));
+          const float2 qy = fma2(syr[h], d_s, mul2(ryr[h], d_r));
+          const float2 ale = __ffma2_rn(make_float2(vgyp[h][nt][0], vgyp[h][nt][1]), qy,
+                                        __fmul2_rn(make_float2(vgxp[h][nt][0], vgxp[h][nt][1]), qx));
+          auto A = [&](int ff) { return make_float2(acc[ff][nt][j0], acc[ff][nt][j0 + 1]); };
+          auto P = [&](int ff, float2 v) { acc[ff][nt][j0] = v.x; acc[ff][nt][j0 + 1] = v.y; };
           switch (f) {
-            case 0: acc[0][nt][j] += ale; acc[1][nt][j] = fmaf(mc, qx, acc[1][nt][j]); acc[2][nt][j] = fmaf(mc, qy, acc[2][nt][j]); break;
-            case 1: acc[1][nt][j] += ale; acc[0][nt][j] = fmaf(mc, qx, acc[0][nt][j]); acc[3][nt][j] = fmaf(mc, qy, acc[3][nt][j]);
-                    acc[4][nt][j] = fmaf(mcs, qx, acc[4][nt][j]); break;
-            case 2: acc[2][nt][j] += ale; acc[0][nt][j] = fmaf(mc, qy, acc[0][nt][j]); acc[3][nt][j] = fmaf(mc, qx, acc[3][nt][j]);
-                    acc[5][nt][j] = fmaf(mcs, qy, acc[5][nt][j]); break;
-            case 3: acc[3][nt][j] += ale; acc[2][nt][j] = fmaf(mc, qx, acc[2][nt][j]); acc[1][nt][j] = fmaf(mc, qy, acc[1][nt][j]); break;
-            case 4: acc[4][nt][j] += ale; acc[1][nt][j] = fmaf(mcs, qx, acc[1][nt][j]); break;
-            default: acc[5][nt][j] += ale; acc[2][nt][j] = fmaf(mcs, qy, acc[2][nt][j]); break;
+            case 0: P(0, __fadd2_rn(A(0), ale)); P(1, fma2(mc, qx, A(1))); P(2, fma2(mc, qy, A(2))); break;
+            case 1: P(1, __fadd2_rn(A(1), ale)); P(0, fma2(mc, qx, A(0))); P(3, fma2(mc, qy, A(3)));
+                    P(4, fma2(mcs, qx, A(4))); break;
+            case 2: P(2, __fadd2_rn(A(2), ale)); P(0, fma2(mc, qy, A(0))); P(3, fma2(mc, qx, A(3)));
+                    P(5, fma2(mcs, qy, A(5))); break;
+            case 3: P(3, __fadd2_rn(A(3), ale)); P(2, fma2(mc, qx, A(2))); P(1, fma2(mc, qy, A(1))); break;
+            case 4: P(4, __fadd2_rn(A(4), ale)); P(1, fma2(mcs, qx, A(1))); break;
+            default: P(5, __fadd2_rn(A(5), ale)); P(2, fma2(mcs, qy, A(2))); break;
           }
         }
     }
@@ -395,27 +405,41 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
       const float N11 = h * (al * o11 + be * (o11 * o11 + o12 * o12));
       const float N12 = h * (al * o12 + be * (o11 * o12 + o12 * o22));
       const float N22 = h * (al * o22 + be * (o12 * o12 + o22 * o22));
-      const float hnx = h * nx, hny = h * ny, hsx = h * SQ2 * nx, hsy = h * SQ2 * ny;
+      const float nhx = -h * nx, nhy = -h * ny, nsx = -h * SQ2 * nx, nsy = -h * SQ2 * ny;
       const float vx0 = gm[5], vx1 = gm[6], vx2 = gm[7], vy0 = gm[8], vy1 = gm[9], vy2 = gm[10];
       const float *bary = reinterpret_cast<const float *>(a.ops) + D::NSETS * 128;
+      // face nodes in pairs (k, k + 1); an odd last node is paired with itself
 #pragma unroll
-      for (int k = 0; k < Nfp; ++k) {
-        const int vol = tc_fmask<N>(f, k);
-        const int j = f * Nfp + k;
-        float *tr = trc + el * ST + j;
-        const float *qm = own + el * S + vol;
-        float w[6];
+      for (int k = 0; k < Nfp; k += 2) {
+        const int k1 = k + 1 < Nfp ? k + 1 : k;
+        const int vol0 = tc_fmask<N>(f, k), vol1 = tc_fmask<N>(f, k1);
+        float *tr0 = trc + el * ST + f * Nfp + k, *tr1 = trc + el * ST + f * Nfp + k1;
+        const float *qm0 = own + el * S + vol0, *qm1 = own + el * S + vol1;
+        float2 w[6];
 #pragma unroll
-        for (int fld = 0; fld < 6; ++fld) w[fld] = tr[fld * FJ] - qm[fld * Np];
-        const float b0 = __ldg(bary + 4 * vol), b1 = __ldg(bary + 4 * vol + 1), b2 = __ldg(bary + 4 * vol + 2);
-        const float vn = (b0 * vx0 + b1 * vx1 + b2 * vx2) * nx + (b0 * vy0 + b1 * vy1 + b2 * vy2) * ny;
-        const float ale = vn > 0.0f ? vn * fs : 0.0f;
-        tr[0 * FJ] = M00 * w[0] + M03 * w[3] + M04 * w[4] + M05 * w[5] - hnx * w[1] - hny * w[2] + ale * w[0];
-        tr[3 * FJ] = M03 * w[0] + M33 * w[3] + M34 * w[4] + M35 * w[5] - hnx * w[2] - hny * w[1] + ale * w[3];
-        tr[4 * FJ] = M04 * w[0] + M34 * w[3] + M44 * w[4] + M45 * w[5] - hsx * w[1] + ale * w[4];
-        tr[5 * FJ] = M05 * w[0] + M35 * w[3] + M45 * w[4] + M55 * w[5] - hsy * w[2] + ale * w[5];
-        tr[1 * FJ] = N11 * w[1] + N12 * w[2] - hnx * w[0] - hsx * w[4] - hny * w[3] + ale * w[1];
-        tr[2 * FJ] = N12 * w[1] + N22 * w[2] - hny * w[0] - hsy * w[5] - hnx * w[3] + ale * w[2];
+        for (int fld = 0; fld < 6; ++fld)
+          w[fld] = make_float2(tr0[fld * FJ] - qm0[fld * Np], tr1[fld * FJ] - qm1[fld * Np]);
+        float2 ale;
+        {
+          const float *b = bary + 4 * vol0, *c1 = bary + 4 * vol1;
+          const float vn0 = (__ldg(b) * vx0 + __ldg(b + 1) * vx1 + __ldg(b + 2) * vx2) * nx +
+                            (__ldg(b) * vy0 + __ldg(b + 1) * vy1 + __ldg(b + 2) * vy2) * ny;
+          const float vn1 = (__ldg(c1) * vx0 + __ldg(c1 + 1) * vx1 + __ldg(c1 + 2) * vx2) * nx +
+                            (__ldg(c1) * vy0 + __ldg(c1 + 1) * vy1 + __ldg(c1 + 2) * vy2) * ny;
+          ale = make_float2(vn0 > 0.0f ? vn0 * fs : 0.0f, vn1 > 0.0f ? vn1 * fs : 0.0f);
+        }
+        float2 o[6];
+        o[0] = __ffma2_rn(ale, w[0], fma2(M00, w[0], fma2(M03, w[3], fma2(M04, w[4], fma2(M05, w[5], fma2(nhx, w[1], mul2(nhy, w[2])))))));
+        o[3] = __ffma2_rn(ale, w[3], fma2(M03, w[0], fma2(M33, w[3], fma2(M34, w[4], fma2(M35, w[5], fma2(nhx, w[2], mul2(nhy, w[1])))))));
+        o[4] = __ffma2_rn(ale, w[4], fma2(M04, w[0], fma2(M34, w[3], fma2(M44, w[4], fma2(M45, w[5], mul2(nsx, w[1]))))));
+        o[5] = __ffma2_rn(ale, w[5], fma2(M05, w[0], fma2(M35, w[3], fma2(M45, w[4], fma2(M55, w[5], mul2(nsy, w[2]))))));
+        o[1] = __ffma2_rn(ale, w[1], fma2(N11, w[1], fma2(N12, w[2], fma2(nhx, w[0], fma2(nsx, w[4], mul2(nhy, w[3]))))));
+        o[2] = __ffma2_rn(ale, w[2], fma2(N12, w[1], fma2(N22, w[2], fma2(nhy, w[0], fma2(nsy, w[5], mul2(nhx, w[3]))))));
+#pragma unroll
+        for (int fld = 0; fld < 6; ++fld) {
+          tr0[fld * FJ] = o[fld].x;
+          if (k1 != k) tr1[fld * FJ] = o[fld].y;
+        }
       }
     }
     __syncwarp();
@@ -502,29 +526,43 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
               if (STAGE >= 2) x2[rr][sl] = ac[gi];
             }
           }
+        // rows in pairs (rr, rr + 1): one packed instruction for both
 #pragma unroll
-        for (int rr = 0; rr < RB; ++rr)
+        for (int rr = 0; rr < RB; rr += 2)
 #pragma unroll
           for (int sl = 0; sl < NSL; ++sl) {
             const int r = r0 + rr, w = lane + 32 * sl;
-            if (!(r < nel && w < 6 * Np)) continue;
-            const int64_t gi = (e0 + r) * S + w;
-            const float r_ = rv[rr][sl], qv = x0[rr][sl], f0 = x1[rr][sl], av = x2[rr][sl];
+            if (!(w < 6 * Np) || r >= nel) continue;
+            const bool ok1 = r + 1 < nel;
+            const int64_t gi = (e0 + r) * S + w, gi1 = gi + S;
+            const float2 r_ = make_float2(rv[rr][sl], rv[rr + 1][sl]), qv = make_float2(x0[rr][sl], x0[rr + 1][sl]);
+            const float2 f0 = make_float2(x1[rr][sl], x1[rr + 1][sl]), av = make_float2(x2[rr][sl], x2[rr + 1][sl]);
+            float2 o = make_float2(0.0f, 0.0f), o2 = make_float2(0.0f, 0.0f);
             if (STAGE < 0) {
-              Fo[gi] = r_;
+              o = r_;
             } else if (STAGE == 0) {
-              F0[gi] = r_;
-              qo[gi] = E1[sl] * qv + dt * (A0[sl] * r_);
+              o2 = r_;
+              o = fma2(dt, mul2(A0[sl], r_), mul2(E1[sl], qv));
             } else if (STAGE == 1) {
-              qo[gi] = E1[sl] * qv + dt * (A0[sl] * f0 + A1[sl] * r_);
-              ac[gi] = Bc[sl] * f0 + B1[sl] * r_;
+              o = fma2(dt, fma2(A1[sl], r_, mul2(A0[sl], f0)), mul2(E1[sl], qv));
+              o2 = fma2(B1[sl], r_, mul2(Bc[sl], f0));
             } else if (STAGE == 2) {
-              qo[gi] = E1[sl] * qv + dt * (A0[sl] * f0 + A1[sl] * r_);
-              ac[gi] = av + Bc[sl] * r_;
+              o = fma2(dt, fma2(A1[sl], r_, mul2(A0[sl], f0)), mul2(E1[sl], qv));
+              o2 = fma2(Bc[sl], r_, av);
             } else {
-              const float o = E1[sl] * qv + dt * (av + Bc[sl] * r_);
-              qo[gi] = o;
-              bad |= (__float_as_int(o) & 0x7f800000) == 0x7f800000;
+              o = fma2(dt, fma2(Bc[sl], r_, av), mul2(E1[sl], qv));
+              bad |= (__float_as_int(o.x) & 0x7f800000) == 0x7f800000;
+              bad |= ok1 && (__float_as_int(o.y) & 0x7f800000) == 0x7f800000;
+            }
+            float *dst = STAGE < 0 ? Fo : qo;
+            dst[gi] = o.x;
+            if (ok1) dst[gi1] = o.y;
+            if (STAGE == 0) {
+              F0[gi] = o2.x;
+              if (ok1) F0[gi1] = o2.y;
+            } else if (STAGE == 1 || STAGE == 2) {
+              ac[gi] = o2.x;
+              if (ok1) ac[gi1] = o2.y;
             }
           }
       }
