@@ -76,9 +76,13 @@ __device__ __forceinline__ unsigned to_tf32(float x) {
   return r;
 }
 
-__device__ __forceinline__ void split_tf32(float x, unsigned &hi, unsigned &lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
+// two splits with one packed subtraction
+__device__ __forceinline__ void split_tf32x2(float2 x, unsigned &h0, unsigned &l0, unsigned &h1, unsigned &l1) {
+  h0 = to_tf32(x.x);
+  h1 = to_tf32(x.y);
+  const float2 r = __fadd2_rn(x, make_float2(-__uint_as_float(h0), -__uint_as_float(h1)));
+  l0 = to_tf32(r.x);
+  l1 = to_tf32(r.y);
 }
 
 // not volatile: the compiler may interleave products into independent accumulators
@@ -124,10 +128,8 @@ __device__ __forceinline__ void load_a(const float *tile, int col0, int ncol, in
   const float x1 = c0 < ncol ? tile[(g + 8) * STRIDE + c0] : 0.0f;
   const float x2 = c1 < ncol ? tile[g * STRIDE + c1] : 0.0f;
   const float x3 = c1 < ncol ? tile[(g + 8) * STRIDE + c1] : 0.0f;
-  split_tf32(x0, hi[0], lo[0]);
-  split_tf32(x1, hi[1], lo[1]);
-  split_tf32(x2, hi[2], lo[2]);
-  split_tf32(x3, hi[3], lo[3]);
+  split_tf32x2(make_float2(x0, x1), hi[0], lo[0], hi[1], lo[1]);
+  split_tf32x2(make_float2(x2, x3), hi[2], lo[2], hi[3], lo[3]);
 }
 
 // One 16-element tile of one request: staging, geometry, volume, surface, cubature and the SARK
@@ -257,16 +259,17 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
         // Ntilde at the 4 (element, point) positions; the accumulator order (c0, c2, c1, c3)
         // is the A-fragment order of the permuted chunk
         unsigned nh[3][4], nl[3][4];
-        const int perm[4] = {0, 2, 1, 3};
+        // fragment slots (j, j + 1) take accumulator entries (jp, jp + 2), jp = j / 2
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int src = perm[j];
-          const float q1 = 1.0f + qc[0][src], q2 = qc[1][src], q3 = qc[2][src];
-          const float r1 = itau * __frcp_rn(q1);
-          const float rs = r1 * ISQ2;
-          split_tf32(q2 * q3 * r1, nh[0][j], nl[0][j]);
-          split_tf32(q2 * q2 * rs, nh[1][j], nl[1][j]);
-          split_tf32(q3 * q3 * rs, nh[2][j], nl[2][j]);
+        for (int j = 0; j < 4; j += 2) {
+          const int jp = j >> 1;
+          const float2 q1 = __fadd2_rn(bc2(1.0f), make_float2(qc[0][jp], qc[0][jp + 2]));
+          const float2 q2 = make_float2(qc[1][jp], qc[1][jp + 2]), q3 = make_float2(qc[2][jp], qc[2][jp + 2]);
+          const float2 r1 = mul2(itau, make_float2(__frcp_rn(q1.x), __frcp_rn(q1.y)));
+          const float2 rs = mul2(ISQ2, r1);
+          split_tf32x2(__fmul2_rn(__fmul2_rn(q2, q3), r1), nh[0][j], nl[0][j], nh[0][j + 1], nl[0][j + 1]);
+          split_tf32x2(__fmul2_rn(__fmul2_rn(q2, q2), rs), nh[1][j], nl[1][j], nh[1][j + 1], nl[1][j + 1]);
+          split_tf32x2(__fmul2_rn(__fmul2_rn(q3, q3), rs), nh[2][j], nl[2][j], nh[2][j + 1], nl[2][j + 1]);
         }
         float4 bp[NT];
 #pragma unroll
