@@ -126,3 +126,98 @@ def serving_requests(n=256, rate=50.0, seed=1):
                     'A': 0.01 + 0.07 * float(u[3][r]), 'T': 0.5 + 1.5 * float(u[4][r]),
                     'Re': 100.0 + 1900.0 * float(u[5][r]), 'Ma': 0.1})
     return out
+
+
+# ---- three dimensions: periodic box of tetrahedra ------------------------------------
+
+# Kuhn (Freudenthal) subdivision of the unit cube: one tetrahedron per ordering of the
+# three axes, walking from corner (0,0,0) to (1,1,1) along unit steps.  The same split
+# in every cell makes the faces of neighbouring cells (and of periodic copies) match.
+_KUHN_ORDERS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
+
+
+def periodic_box_tet_mesh(nx, ny, nz, L=(8.0, 2.0, 2.0), jitter=0.0, seed=DEFAULT_SEED):
+    """Periodic box [0, Lx] x [0, Ly] x [0, Lz] with nx x ny x nz hexahedral cells,
+    each split into 6 tetrahedra (Kuhn subdivision); K = 6 nx ny nz.
+
+    Unique vertices are the nx ny nz grid points, id = i + nx (j + ny k).  Every
+    tetrahedron is listed with positive orientation (det[v1-v0, v2-v0, v3-v0] > 0).
+    jitter > 0 moves every unique vertex by independent U[-jitter h_d, jitter h_d]
+    offsets per direction d (h_d = L_d / n_d), splitmix64 counter 3 id + d.
+
+    Returns a dict: X (n_vert, 3), EToV (K, 4) int32, shift (K, 4, 3) periodic unwrap
+    offsets (vertex k of element e sits at X[EToV[e, k]] + shift[e, k]), L (3,), dims.
+    """
+    if min(nx, ny, nz) < 3:
+        raise ValueError('at least 3 cells per direction are needed so that faces have unique vertex triples')
+    L = np.asarray(L, dtype=np.float64)
+    n = np.array([nx, ny, nz])
+    h = L / n
+    i, j, k = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing='ij')
+    vid = (i + nx * (j + ny * k)).ravel()
+    X = np.zeros((nx * ny * nz, 3))
+    X[vid, 0] = (i * h[0]).ravel()
+    X[vid, 1] = (j * h[1]).ravel()
+    X[vid, 2] = (k * h[2]).ravel()
+    if jitter > 0.0:
+        ids = np.arange(nx * ny * nz, dtype=np.uint64)
+        for d in range(3):
+            X[:, d] += uniform(3 * ids + d, seed, -jitter * h[d], jitter * h[d])
+    # cells in order (k outer, j, i inner), six tetrahedra per cell
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing='ij')
+    cell = np.stack([ii.ravel(), jj.ravel(), kk.ravel()], axis=1)          # (ncell, 3)
+    corners = []
+    for order in _KUHN_ORDERS:
+        c = [np.zeros(3, dtype=np.int64)]
+        for ax in order:
+            nxt = c[-1].copy()
+            nxt[ax] += 1
+            c.append(nxt)
+        # det[e_o0, e_o1, e_o2] is the sign of the axis permutation; fix odd ones
+        sign = np.linalg.det(np.eye(3)[list(order)])
+        if sign < 0:
+            c[2], c[3] = c[3], c[2]
+        corners.append(np.stack(c))
+    corners = np.stack(corners)                                              # (6, 4, 3)
+    g = cell[:, None, None, :] + corners[None, :, :, :]                      # (ncell, 6, 4, 3)
+    wrap = g // n
+    gm = g % n
+    EToV = (gm[..., 0] + nx * (gm[..., 1] + ny * gm[..., 2])).reshape(-1, 4).astype(np.int32)
+    shift = (wrap * L).reshape(-1, 4, 3).astype(np.float64)
+    return {'X': X, 'EToV': EToV, 'shift': shift, 'L': L.copy(), 'dims': (nx, ny, nz)}
+
+
+def min_altitude_3d(mesh):
+    """Smallest tetrahedron altitude (3 volume / largest face area) at the Lagrangian positions."""
+    P = mesh['X'][mesh['EToV']] + mesh['shift']
+    vol = np.abs(np.einsum('ei,ei->e', P[:, 1] - P[:, 0], np.cross(P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]))) / 6.0
+    faces = ((0, 1, 2), (0, 1, 3), (1, 2, 3), (0, 2, 3))
+    area = np.stack([0.5 * np.linalg.norm(np.cross(P[:, b] - P[:, a], P[:, c] - P[:, a]), axis=1) for a, b, c in faces])
+    return float(np.min(3.0 * vol / area.max(axis=0)))
+
+
+def cfl_dt_3d(mesh, N, c, cfl):
+    """dt = cfl * h_min / (sqrt(3) c (N+1)^2) on a tetrahedral mesh (the 2D rule of cfl_dt)."""
+    return cfl * min_altitude_3d(mesh) / (math.sqrt(3.0) * c * (N + 1) ** 2)
+
+
+def random_flow_3d(x, y, z, seed, amp=0.05, L=(8.0, 2.0, 2.0)):
+    """Smooth seeded periodic perturbation of the rest state on the box (rho, u, v, w)."""
+    k = uniform(np.arange(16), seed)
+    ax, ay, az = (2.0 * math.pi / Ld for Ld in L)
+    rho = 1.0 + amp * (np.sin(ax * x + 6 * k[0]) * np.cos(ay * y + 6 * k[1]) + 0.5 * np.sin(az * z + 6 * k[2]))
+    u = 0.5 * np.sin(ay * y + 6 * k[3]) + 0.3 * np.cos(ax * x + az * z + 6 * k[4])
+    v = 0.5 * np.cos(az * z + 6 * k[5]) - 0.3 * np.sin(ax * x - ay * y + 6 * k[6])
+    w = 0.4 * np.sin(ax * x + 6 * k[7]) + 0.2 * np.cos(ay * y + az * z + 6 * k[8])
+    return rho, u, v, w
+
+
+def channel_flow_3d(x, y, z, Ma, L=(8.0, 2.0, 2.0), eps=0.05):
+    """Uniform stream u = 1 along x with a small smooth transverse disturbance (the
+    deforming-channel workload's initial state): v, w of amplitude eps, rho from p' = c^2 rho'."""
+    ax, ay, az = (2.0 * math.pi / Ld for Ld in L)
+    u = np.ones_like(x)
+    v = eps * np.sin(ax * x) * np.cos(az * z)
+    w = eps * np.cos(ax * x) * np.sin(ay * y)
+    rho = 1.0 + Ma * Ma * eps * np.cos(ax * x) * np.cos(ay * y)
+    return rho, u, v, w
