@@ -1,8 +1,10 @@
 /*
  * gb.h -- C ABI of libgb, the B300 (sm_103a) solver for the arbitrary
- * Lagrangian-Eulerian (ALE) nodal discontinuous Galerkin form of the 2D
- * Galerkin-Boltzmann equations with semi-analytic Runge-Kutta (SARK) time
- * stepping (arXiv 2607.00199, Secs. 2-6).
+ * Lagrangian-Eulerian (ALE) nodal discontinuous Galerkin form of the
+ * Galerkin-Boltzmann equations (2D triangles, 6 fields; 3D tetrahedra, 10
+ * fields) with semi-analytic Runge-Kutta (SARK) time stepping (arXiv
+ * 2607.00199, Secs. 2-6).  Everything below describes the 2D solver; the
+ * section "three dimensions" near the end lists what changes for dim = 3.
  *
  * Conventions (every entry point):
  *  - Returns GB_OK (0) or a negative GB_E* code; gb_last_error() gives a
@@ -49,9 +51,10 @@ extern "C" {
 
 typedef struct gb_solver gb_solver;   /* opaque */
 
-/* Straight-sided periodic triangle mesh (Sec. 3: affine simplices, fixed topology). */
+/* Straight-sided periodic simplex mesh (Sec. 3: affine simplices, fixed topology).
+ * The 2D layout is given here; for dim = 3 see "three dimensions" below. */
 typedef struct {
-  int32_t dim;               /* must be 2 */
+  int32_t dim;               /* 2 (triangles) or 3 (tetrahedra) */
   int64_t n_vert;            /* number of unique vertices (periodic images share one id) */
   const double *X;           /* n_vert x 2, Lagrangian (initial) vertex coordinates, host */
   int64_t n_elem;            /* K */
@@ -236,6 +239,58 @@ int gb_reference_operators(int N, double *r, double *s, double *Dr, double *Ds, 
  * E[5] = exp(c_i gamma) (i = 0..3) and exp(gamma); A[16] row-major atilde (strictly
  * lower); B[4] btilde.  Evaluated through phi-functions (series for |gamma| < 1). */
 int gb_sark_coefficients(double gamma, double *E, double *A, double *B);
+
+/* ---- three dimensions (tetrahedra, 10 fields) --------------------------------
+ * The paper runs the same scheme on tetrahedra (Sec. 3: simplices in two and
+ * three dimensions; Sec. 2: n = 10 Hermite coefficients in 3D).  gb_create with
+ * mesh->dim == 3 builds a 3D solver; then:
+ *  - mesh: X is n_vert x 3, EToV n_elem x 4 with det[v1-v0, v2-v0, v3-v0] > 0,
+ *    elem_shift n_elem x 4 x 3 (integer multiples |m| <= 7 of one period per
+ *    direction); n_elem < 2^26; every face (vertex-id triple) shared by exactly
+ *    two elements (periodic meshes).  N in 1..4.
+ *  - reference tetrahedron (-1,-1,-1), (1,-1,-1), (-1,1,-1), (-1,-1,1); canonical
+ *    field layout q[k][f][i] with f < 10 fields and i < Np = (N+1)(N+2)(N+3)/6
+ *    Warp & Blend nodes (Warburton 2006, tetrahedral alpha), ordered by the
+ *    equidistant lattice indices (i, j, k) = N (l1, l2, l3) before warping,
+ *    i fastest, k slowest (l1 = (1+r)/2, l2 = (1+s)/2, l3 = (1+t)/2).
+ *  - fields: moments of multi-index (0,0,0); (1,0,0), (0,1,0), (0,0,1); (1,1,0),
+ *    (1,0,1), (0,1,1); (2,0,0), (0,2,0), (0,0,2): q1 = rho, q2..q4 = rho u / c,
+ *    q5..q10 the second-order coefficients (equilibrium q_{i+j} = q_i q_j / q1,
+ *    q_{2i} = q_i^2 / (sqrt2 q1)); fields 1..4 step with RK4, 5..10 with the
+ *    exponential SARK coefficients.
+ *  - motion: gb_set_wave_motion (below); gb_set_motion accepts GB_MOTION_STATIC.
+ *  - gb_nodes writes n_elem x Np x 3; gb_vertices / gb_set_vertices n_vert x 3.
+ *  - GB_MIXED: FP32 perturbations around the rest state in the canonical layout
+ *    (gb_rhs takes and returns that layout; gb_state_ptr points at it), FP64
+ *    geometry, motion and SARK coefficients; no tensor-core contractions.
+ *  - gb_step, gb_step_timed (kernel_ms[0..4] as in 2D), gb_rhs, gb_sync, gb_info,
+ *    gb_set_graph, gb_set_stream, gb_state_ptr, gb_destroy and gb_last_error
+ *    work as in 2D.  Groups, gb_rhs_noalloc, diagnostics and launch
+ *    configuration return GB_EINVAL for dim = 3 solvers. */
+
+/* Travelling-wave lateral motion of a deforming channel (dim = 3): the vertex with
+ * Lagrangian position (X, Y, Z) moves in y by
+ *   A(X) sin(2 pi X / wavelength - omega t) exp(-r^2 / r0sq),
+ *   A(X) = A0 + A1 X / Lx,  r^2 = (Y - yc)^2 + (Z - zc)^2,
+ * with the velocity of that Lagrangian point (Sec. 5). */
+typedef struct {
+  double A0, A1, Lx, wavelength, omega, r0sq, yc, zc;
+} gb_wave_motion;
+
+/* gb_set_wave_motion: set the motion of a dim = 3 solver (copied; takes effect at
+ * the next step).  A0 = A1 = 0 or omega = 0 is a static mesh.  GB_EINVAL for a
+ * 2D solver, non-finite parameters, Lx = 0, wavelength = 0 or r0sq <= 0. */
+int gb_set_wave_motion(gb_solver *s, const gb_wave_motion *m);
+
+/* gb_reference_operators3d: the library's order-N tetrahedral operators (Sec. 3),
+ * row-major FP64, host only: r, s, t [Np]; Dr, Ds, Dt [Np x Np]; LIFT [Np x 4 Nfp]
+ * (faces (v0,v1,v2), (v0,v1,v3), (v1,v2,v3), (v0,v2,v3), face nodes in increasing
+ * volume index, face measure of area 2 per face); Icub [Nc x Np]; Pcub [Np x Nc];
+ * cr, cs, ct, cw [Nc] (conical-product rule exact for degree 3N, Nc = q^3,
+ * q = ceil((3N+1)/2)).  Any output may be NULL.  N in 1..4. */
+int gb_reference_operators3d(int N, double *r, double *s, double *t, double *Dr, double *Ds, double *Dt,
+                             double *LIFT, double *Icub, double *Pcub, double *cr, double *cs, double *ct,
+                             double *cw, int *Nc_out);
 
 #ifdef __cplusplus
 }

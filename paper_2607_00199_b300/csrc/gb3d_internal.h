@@ -1,0 +1,59 @@
+// Internal declarations of the 3D (tetrahedral, 10-field) solver: shared by its host
+// side (gb3d.cpp) and its kernels (gb_kernels3d.cu).
+#ifndef GB3D_INTERNAL_H
+#define GB3D_INTERNAL_H
+
+#include <stdint.h>
+
+#include "gb_internal.h"
+
+namespace gb {
+
+// Per-element record, 48 bytes: vertex ids; per face the neighbour packed as
+// (element << 5 | permutation code << 2 | face) (permutation codes of kPerm3); the
+// periodic shift of each vertex as signed multiples of the periods (x, y, z per vertex).
+struct __attribute__((aligned(16))) MeshRec3 {
+  int32_t v[4];
+  int32_t nbr[4];
+  int8_t shift[12];
+  int8_t pad[4];
+};
+static_assert(sizeof(MeshRec3) == 48, "MeshRec3 must be 48 bytes");
+
+// travelling-wave lateral motion of the deforming channel (y displacement only)
+struct Wave3 {
+  double A0, A1, Lx, wavelength, omega, r0sq, yc, zc;
+};
+
+struct Stage3Args {
+  const void *qin, *qn;
+  void *qout, *F0, *acc, *Fout;
+  const double *xn;      // n_vert x 3 current vertex positions
+  const double *shape;   // n_vert x 2: S1, S2 of the y-velocity
+  const MeshRec3 *mesh;
+  const void *ops;       // operator block (T), layout in gb_kernels3d.cu
+  const int *tab;        // neighbour face-node table [4][4][6][Nfp], then fmask [4][Nfp]
+  double *clock;         // t_n, then the final vertex-update factors f1, f2
+  int *status;
+  int64_t K;
+  double period[3];
+  double c, inv_tau, dt;
+  int moving;            // 0: static mesh
+  double omega;
+  int stage;             // -1: rhs only, 0..3 SARK stage
+  double rhs_time;
+  SarkCoef co;
+};
+
+int launch_stage3(int N, bool fp64, const Stage3Args &a, void *stream, int num_sms);
+int launch_vertex_update3(double *xn, const double *shape, int64_t nv, double *clock, double dt, void *stream);
+int launch_shape3(const double *X, double *shape, int64_t nv, const Wave3 &m, void *stream);
+int launch_nodes3(const double *bary, int Np, const double *xn, const MeshRec3 *mesh, const double period[3], int64_t K,
+                  double *out, void *stream);
+int launch_cast3(double *d, float *f, int64_t K, int Np, bool to_float, void *stream);
+int upload_ops3(int N, bool fp64, const RefOps3 &R, void **dev_ops, int **dev_tab, double **dev_bary, size_t *bytes,
+                void *stream);
+
+}  // namespace gb
+
+#endif

@@ -12,6 +12,7 @@
 
 #include "gb.h"
 #include "gb_internal.h"
+#include "gb3d.h"
 
 #include <algorithm>
 #include <map>
@@ -20,6 +21,7 @@
 using gb::MeshRec;
 
 struct gb_solver {
+  gb::Solver3 *s3 = nullptr;   // set for dim = 3 solvers: every call routes to gb3d.cpp
   int N = 0, Np = 0, Nfp = 0, Nc = 0, precision = GB_FP64;
   int64_t K = 0, nv = 0;
   double c = 0, tau = 0, period[2] = {0, 0};
@@ -278,7 +280,7 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   if (!out) return fail(nullptr, GB_EINVAL, "out is NULL");
   *out = nullptr;
   if (!mesh || !mesh->X || !mesh->EToV) return fail(nullptr, GB_EINVAL, "mesh, X or EToV is NULL");
-  if (mesh->dim != 2) return fail(nullptr, GB_EINVAL, "only dim = 2 is supported");
+  if (mesh->dim != 2 && mesh->dim != 3) return fail(nullptr, GB_EINVAL, "dim must be 2 or 3");
   if (mesh->n_vert <= 0 || mesh->n_elem <= 0) return fail(nullptr, GB_EINVAL, "empty mesh");
   if (mesh->n_elem >= (int64_t(1) << 29)) return fail(nullptr, GB_EINVAL, "n_elem must be < 2^29");
   if (mesh->n_vert >= (int64_t(1) << 31)) return fail(nullptr, GB_EINVAL, "n_vert must be < 2^31");
@@ -286,6 +288,20 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   if (!(Ma > 0.0) || !(Re > 0.0) || !std::isfinite(Ma) || !std::isfinite(Re))
     return fail(nullptr, GB_EINVAL, "Ma and Re must be positive and finite");
   if (precision != GB_FP64 && precision != GB_MIXED) return fail(nullptr, GB_EINVAL, "precision must be GB_FP64 or GB_MIXED");
+  if (mesh->dim == 3) {
+    gb::Solver3 *s3 = nullptr;
+    std::string err;
+    int rc = gb::s3_create(mesh, N, Ma, Re, precision, cuda_stream, &s3, err);
+    if (rc != GB_OK) return fail(nullptr, rc, err);
+    gb_solver *s = new gb_solver();
+    s->s3 = s3;
+    s->N = N;
+    s->precision = precision;
+    s->K = mesh->n_elem;
+    s->nv = mesh->n_vert;
+    *out = s;
+    return GB_OK;
+  }
 
   const int64_t K = mesh->n_elem, nv = mesh->n_vert;
   for (int64_t i = 0; i < 3 * K; ++i)
@@ -463,6 +479,10 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
 
 int gb_set_motion(gb_solver *s, const gb_motion *m) {
   if (!s || !m) return fail(s, GB_EINVAL, "NULL argument");
+  if (s->s3) {
+    if (m->kind != GB_MOTION_STATIC) return fail(s, GB_EINVAL, "dim = 3 solvers take gb_set_wave_motion (gb_set_motion accepts GB_MOTION_STATIC only)");
+    return gb::s3_set_static(s->s3);
+  }
   if (m->kind != GB_MOTION_STATIC && m->kind != GB_MOTION_SINXY) return fail(s, GB_EINVAL, "unknown motion kind");
   if (m->kind == GB_MOTION_SINXY) {
     if (!(m->T > 0.0) || !(m->Lx != 0.0) || !(m->Ly != 0.0) || !std::isfinite(m->A) || !std::isfinite(m->T))
@@ -478,6 +498,7 @@ int gb_set_motion(gb_solver *s, const gb_motion *m) {
 int gb_set_fields(gb_solver *s, const double *q_host, double t) {
   if (!s || !q_host) return fail(s, GB_EINVAL, "NULL argument");
   if (!std::isfinite(t)) return fail(s, GB_EINVAL, "t must be finite");
+  if (s->s3) return gb::s3_set_fields(s->s3, q_host, t);
   const size_t n = (size_t)s->K * 6 * s->Np;
   cudaError_t ce;
   if (s->precision == GB_FP64) {
@@ -500,6 +521,7 @@ int gb_set_fields(gb_solver *s, const double *q_host, double t) {
 
 int gb_sync(gb_solver *s) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->s3) return gb::s3_sync(s->s3);
   int status = 0, zero = 0;
   cudaError_t ce = cudaMemcpyAsync(&status, s->d_status, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream);
@@ -512,6 +534,7 @@ int gb_sync(gb_solver *s) {
 
 int gb_fields(gb_solver *s, double *q_host_out, double *t_out) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->s3) return gb::s3_fields(s->s3, q_host_out, t_out);
   int st = gb_sync(s);
   const size_t n = (size_t)s->K * 6 * s->Np;
   cudaError_t ce = cudaSuccess;
@@ -536,6 +559,7 @@ int gb_fields(gb_solver *s, double *q_host_out, double *t_out) {
 
 int gb_set_vertices(gb_solver *s, const double *x_host) {
   if (!s || !x_host) return fail(s, GB_EINVAL, "NULL argument");
+  if (s->s3) return gb::s3_set_vertices(s->s3, x_host);
   cudaError_t ce = cudaMemcpyAsync(s->d_xn, x_host, sizeof(double) * 2 * s->nv, cudaMemcpyHostToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
   if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_vertices");
@@ -544,6 +568,7 @@ int gb_set_vertices(gb_solver *s, const double *x_host) {
 
 int gb_vertices(gb_solver *s, double *x_host_out) {
   if (!s || !x_host_out) return fail(s, GB_EINVAL, "NULL argument");
+  if (s->s3) return gb::s3_vertices(s->s3, x_host_out);
   cudaError_t ce = cudaMemcpyAsync(x_host_out, s->d_xn, sizeof(double) * 2 * s->nv, cudaMemcpyDeviceToHost, s->stream);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
   if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_vertices");
@@ -552,6 +577,7 @@ int gb_vertices(gb_solver *s, double *x_host_out) {
 
 int gb_nodes(gb_solver *s, double *xy_out) {
   if (!s || !xy_out) return fail(s, GB_EINVAL, "NULL argument");
+  if (s->s3) return gb::s3_nodes(s->s3, xy_out);
   const size_t n = (size_t)s->K * s->Np * 2;
   int rc = ensure_tmp(s, n * sizeof(double));
   if (rc) return rc;
@@ -565,6 +591,7 @@ int gb_nodes(gb_solver *s, double *xy_out) {
 int gb_rhs(gb_solver *s, double t, const void *q_dev, void *F_dev) {
   if (!s || !q_dev || !F_dev) return fail(s, GB_EINVAL, "NULL argument");
   if (!std::isfinite(t)) return fail(s, GB_EINVAL, "t must be finite");
+  if (s->s3) return gb::s3_rhs(s->s3, t, q_dev, F_dev);
   gb::StageArgs a = base_args(s);
   a.stage = -1;
   a.rhs_time = t;
@@ -593,6 +620,7 @@ static int step_impl(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms)
 
 int gb_step(gb_solver *s, double dt, int64_t nsteps) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->s3) return gb::s3_step(s->s3, dt, nsteps);
   if (nsteps > 0) {
     int trc = tune_launch(s);
     if (trc) return trc;
@@ -634,6 +662,7 @@ int gb_step(gb_solver *s, double dt, int64_t nsteps) {
 
 int gb_step_timed(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms) {
   if (!kernel_ms) return fail(s, GB_EINVAL, "kernel_ms is NULL");
+  if (s && s->s3) return gb::s3_step_timed(s->s3, dt, nsteps, kernel_ms);
   if (s && nsteps > 0) {
     int trc = tune_launch(s);
     if (trc) return trc;
@@ -738,6 +767,7 @@ int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int 
   for (int r = 0; r < n; ++r) {
     gb_solver *s = solvers[r];
     if (!s) return gfail(GB_EINVAL, "gb_group_step: NULL solver");
+    if (s->s3) return gfail(GB_EINVAL, "gb_group_step: dim = 3 solvers cannot be grouped");
     if (s->precision != GB_MIXED) return gfail(GB_EINVAL, "gb_group_step: only GB_MIXED solvers can be grouped");
     if (s->N != N) return gfail(GB_EINVAL, "gb_group_step: all solvers of a group must have the same N");
     if (s->stream != g->stream) return gfail(GB_EINVAL, "gb_group_step: solvers must use the group's stream");
@@ -812,6 +842,7 @@ const char *gb_group_last_error(gb_group *g) { return g ? g->err.c_str() : g_cre
 
 int gb_set_diagnostics(gb_solver *s, int every, int64_t capacity) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->s3) return fail(s, GB_EINVAL, "not available for dim = 3 solvers");
   if (every < 0 || (every > 0 && (capacity < 1 || capacity > ((int64_t)1 << 32))))
     return fail(s, GB_EINVAL, "every must be >= 0 and capacity in 1 .. 2^32");
   cudaError_t ce = s->stream ? cudaStreamSynchronize(s->stream) : cudaDeviceSynchronize();
@@ -838,6 +869,7 @@ int gb_set_diagnostics(gb_solver *s, int every, int64_t capacity) {
 
 int gb_diagnostics_history(gb_solver *s, double *out, int64_t max, int64_t *count, int64_t *total) {
   if (!s || !count || (max > 0 && !out) || max < 0) return fail(s, GB_EINVAL, "NULL argument or max < 0");
+  if (s->s3) return fail(s, GB_EINVAL, "not available for dim = 3 solvers");
   *count = 0;
   if (total) *total = 0;
   if (s->diag_every <= 0) return GB_OK;
@@ -867,6 +899,7 @@ int gb_diagnostics_history(gb_solver *s, double *out, int64_t max, int64_t *coun
 
 int gb_diagnostics(gb_solver *s, double *out) {
   if (!s || !out) return fail(s, GB_EINVAL, "NULL argument");
+  if (s->s3) return fail(s, GB_EINVAL, "not available for dim = 3 solvers");
   {
     int rc = ensure_diag(s);
     if (rc) return rc;
@@ -891,12 +924,17 @@ int gb_diagnostics(gb_solver *s, double *out) {
 
 int gb_launch_config(gb_solver *s, int *warps_per_cta) {
   if (!s || !warps_per_cta) return fail(s, GB_EINVAL, "NULL argument");
+  if (s->s3) {
+    *warps_per_cta = 0;
+    return GB_OK;
+  }
   *warps_per_cta = s->precision == GB_MIXED ? (s->warps ? s->warps : 4) : 0;
   return GB_OK;
 }
 
 int gb_set_launch_config(gb_solver *s, int warps_per_cta) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->s3) return fail(s, GB_EINVAL, "not available for dim = 3 solvers");
   if (s->precision != GB_MIXED) return fail(s, GB_EINVAL, "launch shapes apply to GB_MIXED solvers");
   if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4)
     return fail(s, GB_EINVAL, "warps_per_cta must be 1, 2 or 4");
@@ -907,6 +945,7 @@ int gb_set_launch_config(gb_solver *s, int warps_per_cta) {
 
 int gb_set_graph(gb_solver *s, int enable) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->s3) return gb::s3_set_graph(s->s3, enable);
   s->use_graph = enable != 0;
   drop_graph(s);
   return GB_OK;
@@ -914,6 +953,7 @@ int gb_set_graph(gb_solver *s, int enable) {
 
 int gb_set_stream(gb_solver *s, void *cuda_stream) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->s3) return gb::s3_set_stream(s->s3, cuda_stream);
   cudaError_t ce = s->stream ? cudaStreamSynchronize(s->stream) : cudaDeviceSynchronize();
   if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_stream");
   drop_graph(s);
@@ -924,6 +964,7 @@ int gb_set_stream(gb_solver *s, void *cuda_stream) {
 int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *n_vert, double *c, double *tau,
             int64_t *device_bytes) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->s3) return gb::s3_info(s->s3, Np, Nfp, Nc, n_elem, n_vert, c, tau, device_bytes);
   if (Np) *Np = s->Np;
   if (Nfp) *Nfp = s->Nfp;
   if (Nc) *Nc = s->Nc;
@@ -937,12 +978,18 @@ int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *
 
 int gb_state_ptr(gb_solver *s, void **q_dev) {
   if (!s || !q_dev) return fail(s, GB_EINVAL, "NULL argument");
+  if (s->s3) return gb::s3_state_ptr(s->s3, q_dev);
   *q_dev = s->d_qn;
   return GB_OK;
 }
 
 int gb_destroy(gb_solver *s) {
   if (!s) return GB_OK;
+  if (s->s3) {
+    gb::s3_destroy(s->s3);
+    delete s;
+    return GB_OK;
+  }
   if (s->stream) cudaStreamSynchronize(s->stream); else cudaDeviceSynchronize();
   drop_graph(s);
   free_all(s);
@@ -950,7 +997,16 @@ int gb_destroy(gb_solver *s) {
   return GB_OK;
 }
 
-const char *gb_last_error(gb_solver *s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+const char *gb_last_error(gb_solver *s) {
+  if (s && s->s3 && s->err.empty()) return gb::s3_error(s->s3);
+  return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+int gb_set_wave_motion(gb_solver *s, const gb_wave_motion *m) {
+  if (!s || !m) return fail(s, GB_EINVAL, "NULL argument");
+  if (!s->s3) return fail(s, GB_EINVAL, "gb_set_wave_motion applies to dim = 3 solvers");
+  return gb::s3_set_wave_motion(s->s3, m);
+}
 
 int gb_reference_operators(int N, double *r, double *s_, double *Dr, double *Ds, double *LIFT, double *Icub,
                            double *Pcub, double *cr, double *cs, double *cw, int *Nc_out) {
@@ -981,7 +1037,7 @@ namespace gb {
 // the sizes.  Returns GB_EINVAL for a NULL solver.
 int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, int *N, int64_t *K, int *Np,
                     int *precision, void **stream, int *num_sms) {
-  if (!s) return GB_EINVAL;
+  if (!s || s->s3) return GB_EINVAL;
   *a = base_args(s);
   a->stage = -1;
   a->rhs_time = t;

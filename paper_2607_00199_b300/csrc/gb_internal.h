@@ -30,6 +30,25 @@ struct RefOps {
 };
 
 bool build_reference(int N, RefOps &R);
+
+// Reference operators of the tetrahedron (3D, 10 fields), FP64, row-major.
+#define GB3_MAX_N 4
+struct RefOps3 {
+  int N = 0, Np = 0, Nfp = 0, Nc = 0;
+  std::vector<double> r, s, t;        // Np
+  std::vector<double> Dr, Ds, Dt;     // Np x Np
+  std::vector<double> LIFT;           // Np x 4 Nfp (parameter measure: every face has area 2)
+  std::vector<double> I, P;           // Nc x Np, Np x Nc
+  std::vector<double> cr, cs, ct, cw; // Nc
+  std::vector<double> wq;             // Np: 1^T Mhat
+  std::vector<double> bary;           // Np x 4
+  std::vector<int> fmask;             // 4 x Nfp, increasing volume index
+  std::vector<int> nbr_node;          // [f][f2][perm][k]: neighbour volume node of my face node k
+};
+// the six permutations of a face's three vertices, in a fixed order: code p maps my
+// face vertex i to the neighbour's face vertex kPerm3[p][i]
+static const int kPerm3[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+bool build_reference3d(int N, RefOps3 &R);
 void sark_coefficients(double gamma, double E[5], double A[16], double B[4]);
 
 // Per-element mesh record, 32 bytes: vertex ids, face neighbours packed as

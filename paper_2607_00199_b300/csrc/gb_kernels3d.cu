@@ -1,0 +1,604 @@
+// CUDA kernels of the 3D (tetrahedral, 10-field) ALE-DG Galerkin-Boltzmann solver.
+//
+// One fused kernel per SARK stage (Sec. 4) computes, for a tile of E elements per CTA:
+//   geometry  : stage vertex positions y_i = y_n + xfac1 S1(X) + xfac2 S2(X) and
+//               velocities v_y = gfac1 S1(X) + gfac2 S2(X) of the travelling-wave motion
+//               (Sec. 5), then G = dx/d(r,s,t), J, G^-1, the four outward normals and
+//               Fscale = face area / (2 J), all in FP64 from the four vertices (GCL);
+//   volume    : Dr, Ds, Dt of the 10 fields, chain rule, (A + v_G) . grad q;
+//   surface   : neighbour traces through the face-node permutation table, the upwind
+//               fluxes c/2 (|At_n| - At_n) dq (|At_n| = alpha At_n^2 + beta At_n^4,
+//               applied as repeated products with the sparse At_n) and max(v_G.n, 0) dq,
+//               scaled by Fscale and lifted with LIFT;
+//   cubature  : q1..q4 at the degree-3N points, Ntilde there, projected onto fields 5..10;
+//   update    : the SARK stage / final combination (fields 1..4 RK4, 5..10 exponential).
+// One thread per (element, node) for the volume, lift and update phases; the surface
+// and cubature phases loop over (element, face node) and (element, point) items.
+// T = double (GB_FP64) or float (GB_MIXED: FP32 perturbations of the rest state, FP64
+// geometry, motion and SARK coefficients).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "gb3d_internal.h"
+
+namespace gb {
+
+template <int N>
+struct Dim3 {
+  static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  static constexpr int Nfp = (N + 1) * (N + 2) / 2;
+  static constexpr int NFN = 4 * Nfp;
+  static constexpr int qc = (3 * N + 2) / 2;
+  static constexpr int Nc = qc * qc * qc;
+  static constexpr int NQ = 10 * Np;
+};
+
+// elements per CTA: (T, N)
+template <typename T, int N> struct Tile3 { static constexpr int E = sizeof(T) == 8 ? (N <= 2 ? 16 : (N == 3 ? 8 : 4)) : (N <= 2 ? 32 : (N == 3 ? 16 : 8)); };
+
+// operator block (in T): the small operators live in shared memory, I and P stay in
+// global memory (read through the L1 cache); then the integer tables.
+template <int N>
+struct Op3 {
+  typedef Dim3<N> D;
+  static constexpr int DrT = 0;                           // [m][n] = Dr[n][m]
+  static constexpr int DsT = DrT + D::Np * D::Np;
+  static constexpr int DtT = DsT + D::Np * D::Np;
+  static constexpr int LiftT = DtT + D::Np * D::Np;       // [j][n] = LIFT[n][j]
+  static constexpr int Bary = LiftT + D::NFN * D::Np;     // [n][4]
+  static constexpr int SmemSize = Bary + 4 * D::Np;       // staged in shared memory
+  static constexpr int IT = SmemSize;                     // [m][c] = I[c][m]
+  static constexpr int PT = IT + D::Np * D::Nc;           // [c][n] = P[n][c]
+  static constexpr int Size = PT + D::Nc * D::Np;
+  static constexpr int TabInts = 4 * 4 * 6 * D::Nfp + 4 * D::Nfp;   // neighbour node table, fmask
+};
+
+// geometry block per element (in T): G^-1 (9, row-major r_x r_y r_z s_x ... t_z),
+// vertex y-velocities (4), per face nx ny nz Fscale (16)
+constexpr int GEO3 = 32;
+
+__constant__ int c_face_verts[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+// orientation of (P_b - P_a) x (P_c - P_a) relative to the outward normal, per face
+__constant__ double c_face_sign[4] = {-1.0, 1.0, 1.0, -1.0};
+
+template <typename T> __device__ __forceinline__ T fma3(T a, T b, T c);
+template <> __device__ __forceinline__ double fma3<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
+template <> __device__ __forceinline__ float fma3<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+__device__ __forceinline__ bool bad3(double v) { return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000; }
+__device__ __forceinline__ bool bad3(float v) { return (__float_as_int(v) & 0x7f800000) == 0x7f800000; }
+
+// y = At_n w for the 10-moment Hermite system (Sec. 2 structure, 3D)
+template <typename T>
+__device__ __forceinline__ void apply_An(T nx, T ny, T nz, const T (&w)[10], T (&y)[10]) {
+  const T s2 = (T)1.41421356237309504880;
+  y[0] = nx * w[1] + ny * w[2] + nz * w[3];
+  y[1] = nx * fma3(s2, w[7], w[0]) + ny * w[4] + nz * w[5];
+  y[2] = nx * w[4] + ny * fma3(s2, w[8], w[0]) + nz * w[6];
+  y[3] = nx * w[5] + ny * w[6] + nz * fma3(s2, w[9], w[0]);
+  y[4] = nx * w[2] + ny * w[1];
+  y[5] = nx * w[3] + nz * w[1];
+  y[6] = ny * w[3] + nz * w[2];
+  y[7] = s2 * nx * w[1];
+  y[8] = s2 * ny * w[2];
+  y[9] = s2 * nz * w[3];
+}
+
+// stage motion factors from the device clock: v_y = g1 S1 + g2 S2, y_i = y_n + x1 S1 + x2 S2
+struct Motion3 { double g1, g2, x1, x2; };
+
+__device__ __forceinline__ Motion3 stage_motion3(const Stage3Args &a, int stage) {
+  Motion3 m{0.0, 0.0, 0.0, 0.0};
+  if (!a.moving) return m;
+  const double w = a.omega;
+  if (stage < 0) {
+    m.g1 = cos(w * a.rhs_time);
+    m.g2 = sin(w * a.rhs_time);
+    return m;
+  }
+  const double t = a.clock[0], dt = a.dt;
+  const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+  const double ti = t + cst[stage] * dt;
+  m.g1 = cos(w * ti);
+  m.g2 = sin(w * ti);
+  if (stage > 0) {
+    const double tp = t + cst[stage - 1] * dt, ap = cst[stage == 3 ? 3 : 1];   // a_{i,i-1} = 1/2, 1/2, 1
+    m.x1 = dt * ap * cos(w * tp);
+    m.x2 = dt * ap * sin(w * tp);
+  }
+  return m;
+}
+
+template <typename T, int N, int STAGE>
+__global__ void __launch_bounds__(((Tile3<T, N>::E * Dim3<N>::Np + 31) / 32) * 32)
+stage3_kernel(const Stage3Args a) {
+  typedef Dim3<N> D;
+  typedef Op3<N> L;
+  constexpr int E = Tile3<T, N>::E;
+  constexpr int Np = D::Np, Nfp = D::Nfp, NFN = D::NFN, Nc = D::Nc, NQ = D::NQ;
+  constexpr bool PERTURB = sizeof(T) == 4;
+  const T ISQ2 = (T)0.70710678118654752440;
+
+  extern __shared__ __align__(16) unsigned char smem3[];
+  T *sops = reinterpret_cast<T *>(smem3);
+  int *stab = reinterpret_cast<int *>(sops + L::SmemSize);   // nbr_node [f][f2][p][k], then fmask [f][k]
+  T *sq = reinterpret_cast<T *>(stab + ((L::TabInts + 3) & ~3));
+  T *sflux = sq + E * NQ;          // [E][10][NFN]
+  T *snt = sflux + E * 10 * NFN;   // [E][6][Nc]
+  T *sgeo = snt + E * 6 * Nc;      // [E][GEO3]
+  __shared__ double s_motion[4];
+
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const T *gops = reinterpret_cast<const T *>(a.ops);
+  for (int i = tid; i < L::SmemSize; i += nthr) sops[i] = gops[i];
+  for (int i = tid; i < L::TabInts; i += nthr) stab[i] = a.tab[i];
+  if (tid == 0) {
+    const Motion3 m = stage_motion3(a, STAGE);
+    s_motion[0] = m.g1; s_motion[1] = m.g2; s_motion[2] = m.x1; s_motion[3] = m.x2;
+    if (STAGE == 3 && blockIdx.x == 0) {
+      // final vertex update factors dt sum_j b_j (cos, sin)(omega t_j)
+      double f1 = 0.0, f2 = 0.0;
+      if (a.moving) {
+        const double t = a.clock[0], dt = a.dt, w = a.omega;
+        f1 = dt * (cos(w * t) / 6.0 + cos(w * (t + 0.5 * dt)) * (2.0 / 3.0) + cos(w * (t + dt)) / 6.0);
+        f2 = dt * (sin(w * t) / 6.0 + sin(w * (t + 0.5 * dt)) * (2.0 / 3.0) + sin(w * (t + dt)) / 6.0);
+      }
+      const_cast<double *>(a.clock)[1] = f1;
+      const_cast<double *>(a.clock)[2] = f2;
+    }
+  }
+  __syncthreads();
+  const double g1 = s_motion[0], g2 = s_motion[1], x1 = s_motion[2], x2 = s_motion[3];
+  const int *snbr = stab;
+  const int *sfmask = stab + 4 * 4 * 6 * Nfp;
+  const T *gIT = gops + L::IT;
+  const T *gPT = gops + L::PT;
+
+  const T *qin = reinterpret_cast<const T *>(a.qin);
+  const int e_loc = tid / Np, n_loc = tid - (tid / Np) * Np;
+  const bool node_thread = e_loc < E;
+  const T c = (T)a.c;
+
+  const int64_t ntiles = (a.K + E - 1) / E;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t elem0 = tile * E;
+    const int nel = (int)((a.K - elem0) < E ? (a.K - elem0) : E);
+    {
+      const T *src = qin + elem0 * NQ;
+      const int cnt = nel * NQ;
+      for (int i = tid; i < cnt; i += nthr) sq[i] = src[i];
+    }
+    // ---- geometry, one thread per element, FP64 ----
+    for (int e = tid; e < nel; e += nthr) {
+      const MeshRec3 rec = a.mesh[elem0 + e];
+      double P[4][3], vy[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int64_t v = rec.v[k];
+        const double2 sv = reinterpret_cast<const double2 *>(a.shape)[v];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) P[k][d] = a.xn[3 * v + d] + rec.shift[3 * k + d] * a.period[d];
+        P[k][1] += x1 * sv.x + x2 * sv.y;
+        vy[k] = g1 * sv.x + g2 * sv.y;
+      }
+      double G[3][3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) G[d][q] = 0.5 * (P[q + 1][d] - P[0][d]);
+      const double C00 = G[1][1] * G[2][2] - G[1][2] * G[2][1];
+      const double C01 = G[1][2] * G[2][0] - G[1][0] * G[2][2];
+      const double C02 = G[1][0] * G[2][1] - G[1][1] * G[2][0];
+      const double J = G[0][0] * C00 + G[0][1] * C01 + G[0][2] * C02;
+      if (!(J > 0.0)) atomicOr(a.status, GB_STATUS_MESH);
+      const double iJ = 1.0 / J;
+      // G^-1 = adj(G) / J; row a of G^-1 is the gradient of reference coordinate a
+      double Gi[3][3];
+      Gi[0][0] = C00 * iJ; Gi[1][0] = C01 * iJ; Gi[2][0] = C02 * iJ;
+      Gi[0][1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) * iJ;
+      Gi[1][1] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) * iJ;
+      Gi[2][1] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) * iJ;
+      Gi[0][2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) * iJ;
+      Gi[1][2] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) * iJ;
+      Gi[2][2] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) * iJ;
+      T *g = sgeo + e * GEO3;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) g[3 * i + j] = (T)Gi[i][j];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) g[9 + k] = (T)vy[k];
+#pragma unroll
+      for (int f = 0; f < 4; ++f) {
+        const int va = c_face_verts[f][0], vb = c_face_verts[f][1], vc = c_face_verts[f][2];
+        const double ux = P[vb][0] - P[va][0], uy = P[vb][1] - P[va][1], uz = P[vb][2] - P[va][2];
+        const double wx = P[vc][0] - P[va][0], wy = P[vc][1] - P[va][1], wz = P[vc][2] - P[va][2];
+        double nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
+        const double len = sqrt(nx * nx + ny * ny + nz * nz);
+        const double sg = c_face_sign[f] / len;
+        nx *= sg; ny *= sg; nz *= sg;
+        g[13 + 4 * f] = (T)nx;
+        g[14 + 4 * f] = (T)ny;
+        g[15 + 4 * f] = (T)nz;
+        g[16 + 4 * f] = (T)(0.25 * len * iJ);   // face area / (2 J)
+      }
+    }
+    __syncthreads();
+
+    // ---- volume term, one thread per node ----
+    T rhs[10];
+    if (node_thread && e_loc < nel) {
+      const T *q = sq + e_loc * NQ;
+      T qr[10], qs[10], qt[10];
+#pragma unroll
+      for (int f = 0; f < 10; ++f) { qr[f] = 0; qs[f] = 0; qt[f] = 0; }
+#pragma unroll 4
+      for (int m = 0; m < Np; ++m) {
+        const T dr = sops[L::DrT + m * Np + n_loc], ds = sops[L::DsT + m * Np + n_loc], dt = sops[L::DtT + m * Np + n_loc];
+#pragma unroll
+        for (int f = 0; f < 10; ++f) {
+          const T v = q[f * Np + m];
+          qr[f] = fma3(dr, v, qr[f]);
+          qs[f] = fma3(ds, v, qs[f]);
+          qt[f] = fma3(dt, v, qt[f]);
+        }
+      }
+      const T *g = sgeo + e_loc * GEO3;
+      const T *bl = sops + L::Bary + 4 * n_loc;
+      const T vgy = bl[0] * g[9] + bl[1] * g[10] + bl[2] * g[11] + bl[3] * g[12];
+      T qx[10], qy[10], qz[10];
+#pragma unroll
+      for (int f = 0; f < 10; ++f) {
+        qx[f] = fma3(g[0], qr[f], fma3(g[3], qs[f], g[6] * qt[f]));
+        qy[f] = fma3(g[1], qr[f], fma3(g[4], qs[f], g[7] * qt[f]));
+        qz[f] = fma3(g[2], qr[f], fma3(g[5], qs[f], g[8] * qt[f]));
+      }
+      // -c (At_x q_x + At_y q_y + At_z q_z) + v_G . grad q, with v_G = (0, vgy, 0)
+      T ax[10], ay[10], az[10];
+      apply_An<T>((T)1, (T)0, (T)0, qx, ax);
+      apply_An<T>((T)0, (T)1, (T)0, qy, ay);
+      apply_An<T>((T)0, (T)0, (T)1, qz, az);
+#pragma unroll
+      for (int f = 0; f < 10; ++f) rhs[f] = fma3(vgy, qy[f], -c * (ax[f] + ay[f] + az[f]));
+    }
+
+    // ---- surface fluxes at the face nodes ----
+    const T al = (T)((9.0 - 1.7320508075688772935) / 6.0), be = (T)((1.7320508075688772935 - 3.0) / 6.0);
+    for (int item = tid; item < E * NFN; item += nthr) {
+      const int e = item / NFN, j = item - NFN * (item / NFN);
+      if (e >= nel) continue;
+      const int f = j / Nfp, k = j - Nfp * (j / Nfp);
+      const int vol = sfmask[f * Nfp + k];
+      const int nb = a.mesh[elem0 + e].nbr[f];
+      const int64_t e2 = nb >> 5;
+      const int p = (nb >> 2) & 7, f2 = nb & 3;
+      const int vol2 = snbr[((f * 4 + f2) * 6 + p) * Nfp + k];
+      const T *qp = qin + e2 * NQ + vol2;
+      const T *qm = sq + e * NQ + vol;
+      T w[10];
+#pragma unroll
+      for (int fld = 0; fld < 10; ++fld) w[fld] = qp[fld * Np] - qm[fld * Np];
+      const T *g = sgeo + e * GEO3;
+      const T nx = g[13 + 4 * f], ny = g[14 + 4 * f], nz = g[15 + 4 * f], fs = g[16 + 4 * f];
+      const T *bl = sops + L::Bary + 4 * vol;
+      const T vn = (bl[0] * g[9] + bl[1] * g[10] + bl[2] * g[11] + bl[3] * g[12]) * ny;
+      const T ale = vn > (T)0 ? vn : (T)0;
+      T y1[10], y2[10], y3[10], y4[10];
+      apply_An<T>(nx, ny, nz, w, y1);
+      apply_An<T>(nx, ny, nz, y1, y2);
+      apply_An<T>(nx, ny, nz, y2, y3);
+      apply_An<T>(nx, ny, nz, y3, y4);
+      const T h = (T)0.5 * c;
+      T *fl = sflux + e * 10 * NFN + j;
+#pragma unroll
+      for (int fld = 0; fld < 10; ++fld)
+        fl[fld * NFN] = fs * fma3(ale, w[fld], h * (fma3(al, y2[fld], be * y4[fld]) - y1[fld]));
+    }
+    // ---- cubature: q1..q4 at the points, Ntilde there ----
+    const T itau = (T)a.inv_tau;
+    for (int item = tid; item < E * Nc; item += nthr) {
+      const int e = item / Nc, cpt = item - Nc * (item / Nc);
+      if (e >= nel) continue;
+      const T *q = sq + e * NQ;
+      T q1 = 0, q2 = 0, q3 = 0, q4 = 0;
+#pragma unroll 4
+      for (int m = 0; m < Np; ++m) {
+        const T im = __ldg(gIT + m * Nc + cpt);
+        q1 = fma3(im, q[m], q1);
+        q2 = fma3(im, q[Np + m], q2);
+        q3 = fma3(im, q[2 * Np + m], q3);
+        q4 = fma3(im, q[3 * Np + m], q4);
+      }
+      if (PERTURB) q1 += (T)1;
+      const T r1 = itau / q1, rs = r1 * ISQ2;
+      T *nt = snt + e * 6 * Nc + cpt;
+      nt[0] = q2 * q3 * r1;
+      nt[Nc] = q2 * q4 * r1;
+      nt[2 * Nc] = q3 * q4 * r1;
+      nt[3 * Nc] = q2 * q2 * rs;
+      nt[4 * Nc] = q3 * q3 * rs;
+      nt[5 * Nc] = q4 * q4 * rs;
+    }
+    __syncthreads();
+
+    // ---- lift, projection, SARK update ----
+    if (node_thread && e_loc < nel) {
+      const T *fl = sflux + e_loc * 10 * NFN;
+#pragma unroll 4
+      for (int j = 0; j < NFN; ++j) {
+        const T lj = sops[L::LiftT + j * Np + n_loc];
+#pragma unroll
+        for (int f = 0; f < 10; ++f) rhs[f] = fma3(lj, fl[f * NFN + j], rhs[f]);
+      }
+      const T *nt = snt + e_loc * 6 * Nc;
+#pragma unroll 5
+      for (int cpt = 0; cpt < Nc; ++cpt) {
+        const T pc = __ldg(gPT + cpt * Np + n_loc);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) rhs[4 + f] = fma3(pc, nt[f * Nc + cpt], rhs[4 + f]);
+      }
+      const int64_t base = (elem0 + e_loc) * NQ + n_loc;
+      const T dt = (T)a.dt;
+      if (STAGE < 0) {
+        T *F = reinterpret_cast<T *>(a.Fout);
+#pragma unroll
+        for (int f = 0; f < 10; ++f) F[base + f * Np] = rhs[f];
+      } else {
+        const T *qn = reinterpret_cast<const T *>(a.qn);
+        T *qout = reinterpret_cast<T *>(a.qout);
+        T *F0 = reinterpret_cast<T *>(a.F0);
+        T *acc = reinterpret_cast<T *>(a.acc);
+        bool bad = false;
+#pragma unroll
+        for (int f = 0; f < 10; ++f) {
+          const int cl = f < 4 ? 0 : 1;
+          const int64_t idx = base + f * Np;
+          const T r = rhs[f];
+          if (STAGE == 0) {
+            const T qv = sq[e_loc * NQ + f * Np + n_loc];
+            F0[idx] = r;
+            qout[idx] = (T)a.co.E[cl][1] * qv + dt * ((T)a.co.A[cl][4] * r);
+          } else if (STAGE == 1) {
+            const T qv = qn[idx], f0 = F0[idx];
+            qout[idx] = (T)a.co.E[cl][2] * qv + dt * ((T)a.co.A[cl][8] * f0 + (T)a.co.A[cl][9] * r);
+            acc[idx] = (T)a.co.B[cl][0] * f0 + (T)a.co.B[cl][1] * r;
+          } else if (STAGE == 2) {
+            const T qv = qn[idx], f0 = F0[idx], ac = acc[idx];
+            qout[idx] = (T)a.co.E[cl][3] * qv + dt * ((T)a.co.A[cl][12] * f0 + (T)a.co.A[cl][14] * r);
+            acc[idx] = ac + (T)a.co.B[cl][2] * r;
+          } else {
+            const T qv = qn[idx], ac = acc[idx];
+            const T out = (T)a.co.E[cl][4] * qv + dt * (ac + (T)a.co.B[cl][3] * r);
+            qout[idx] = out;
+            bad |= bad3(out);
+          }
+        }
+        if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <typename T, int N>
+static size_t stage3_smem() {
+  typedef Dim3<N> D;
+  typedef Op3<N> L;
+  constexpr int E = Tile3<T, N>::E;
+  return sizeof(T) * (size_t)L::SmemSize + sizeof(int) * (size_t)((L::TabInts + 3) & ~3) +
+         sizeof(T) * (size_t)E * (D::NQ + 10 * D::NFN + 6 * D::Nc + GEO3);
+}
+
+template <typename T, int N, int STAGE>
+static int launch3_one(const Stage3Args &a, cudaStream_t st, int num_sms) {
+  constexpr int E = Tile3<T, N>::E;
+  const int threads = ((E * Dim3<N>::Np + 31) / 32) * 32;
+  const size_t smem = stage3_smem<T, N>();
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t err = cudaFuncSetAttribute(stage3_kernel<T, N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    attr_set = true;
+  }
+  static int per_sm = 0;   // cached: no runtime queries while a graph is being captured
+  if (per_sm == 0) {
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage3_kernel<T, N, STAGE>, threads, smem);
+    if (err != cudaSuccess) return (int)err;
+    if (per_sm < 1) per_sm = 1;
+  }
+  const int64_t ntiles = (a.K + E - 1) / E;
+  int64_t grid = (int64_t)num_sms * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  if (grid < 1) grid = 1;
+  stage3_kernel<T, N, STAGE><<<(unsigned)grid, threads, smem, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <typename T, int N>
+static int launch3_n(const Stage3Args &a, cudaStream_t st, int num_sms) {
+  switch (a.stage) {
+    case -1: return launch3_one<T, N, -1>(a, st, num_sms);
+    case 0: return launch3_one<T, N, 0>(a, st, num_sms);
+    case 1: return launch3_one<T, N, 1>(a, st, num_sms);
+    case 2: return launch3_one<T, N, 2>(a, st, num_sms);
+    case 3: return launch3_one<T, N, 3>(a, st, num_sms);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int launch_stage3(int N, bool fp64, const Stage3Args &a, void *stream, int num_sms) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (fp64) {
+    switch (N) {
+      case 1: return launch3_n<double, 1>(a, st, num_sms);
+      case 2: return launch3_n<double, 2>(a, st, num_sms);
+      case 3: return launch3_n<double, 3>(a, st, num_sms);
+      case 4: return launch3_n<double, 4>(a, st, num_sms);
+    }
+  } else {
+    switch (N) {
+      case 1: return launch3_n<float, 1>(a, st, num_sms);
+      case 2: return launch3_n<float, 2>(a, st, num_sms);
+      case 3: return launch3_n<float, 3>(a, st, num_sms);
+      case 4: return launch3_n<float, 4>(a, st, num_sms);
+    }
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+// ---- vertex update, motion shapes, node coordinates, precision conversion ----------
+
+// y_{n+1} = y_n + fin1 S1(X) + fin2 S2(X); t_{n+1} = t_n + dt
+__global__ void vertex_update3_kernel(double *xn, const double *shape, int64_t nv, double *clock, double dt) {
+  const double f1 = clock[1], f2 = clock[2];
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
+    xn[3 * i + 1] += f1 * shape[2 * i] + f2 * shape[2 * i + 1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) clock[0] += dt;
+}
+
+int launch_vertex_update3(double *xn, const double *shape, int64_t nv, double *clock, double dt, void *stream) {
+  int64_t blocks = (nv + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  vertex_update3_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(xn, shape, nv, clock, dt);
+  return (int)cudaGetLastError();
+}
+
+// travelling-wave shapes at the Lagrangian positions:
+// v_y = -omega A(X) e^{-r^2/r0sq} cos(k X - omega t) = S1 cos(omega t) + S2 sin(omega t)
+__global__ void shape3_kernel(const double *X, double *shape, int64_t nv, Wave3 m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
+    const double r2 = (y - m.yc) * (y - m.yc) + (z - m.zc) * (z - m.zc);
+    const double amp = -m.omega * (m.A0 + m.A1 * x / m.Lx) * exp(-r2 / m.r0sq);
+    const double kx = 2.0 * 3.14159265358979323846 / m.wavelength * x;
+    shape[2 * i] = amp * cos(kx);
+    shape[2 * i + 1] = amp * sin(kx);
+  }
+}
+
+int launch_shape3(const double *X, double *shape, int64_t nv, const Wave3 &m, void *stream) {
+  int64_t blocks = (nv + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  shape3_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(X, shape, nv, m);
+  return (int)cudaGetLastError();
+}
+
+// physical node coordinates: x = sum_v l_v(node) (X_v + shift_v)
+__global__ void nodes3_kernel(const double *bary, int Np, const double *xn, const MeshRec3 *mesh, double px, double py,
+                              double pz, int64_t K, double *out) {
+  const double per[3] = {px, py, pz};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * Np; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = i / Np;
+    const int n = (int)(i - e * Np);
+    const MeshRec3 rec = mesh[e];
+    double x[3] = {0, 0, 0};
+    for (int k = 0; k < 4; ++k)
+      for (int d = 0; d < 3; ++d) x[d] += bary[4 * n + k] * (xn[3 * (int64_t)rec.v[k] + d] + rec.shift[3 * k + d] * per[d]);
+    for (int d = 0; d < 3; ++d) out[3 * i + d] = x[d];
+  }
+}
+
+int launch_nodes3(const double *bary, int Np, const double *xn, const MeshRec3 *mesh, const double period[3], int64_t K,
+                  double *out, void *stream) {
+  nodes3_kernel<<<1024, 256, 0, (cudaStream_t)stream>>>(bary, Np, xn, mesh, period[0], period[1], period[2], K, out);
+  return (int)cudaGetLastError();
+}
+
+// canonical FP64 <-> FP32 perturbation (field 1 minus the rest density 1)
+__global__ void cast3_kernel(double *d, float *f, int64_t K, int Np, bool to_float) {
+  const int NQ = 10 * Np;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < K * NQ; i += (int64_t)gridDim.x * blockDim.x) {
+    const int fn = (int)(i % NQ);
+    const double rest = fn < Np ? 1.0 : 0.0;
+    if (to_float) f[i] = (float)(d[i] - rest);
+    else d[i] = (double)f[i] + rest;
+  }
+}
+
+int launch_cast3(double *d, float *f, int64_t K, int Np, bool to_float, void *stream) {
+  cast3_kernel<<<2048, 256, 0, (cudaStream_t)stream>>>(d, f, K, Np, to_float);
+  return (int)cudaGetLastError();
+}
+
+// ---- operator block ----
+template <typename T, int N>
+static void fill3(const RefOps3 &R, std::vector<T> &h) {
+  typedef Dim3<N> D;
+  typedef Op3<N> L;
+  const int Np = D::Np, NFN = D::NFN, Nc = D::Nc;
+  h.assign(L::Size, (T)0);
+  for (int n = 0; n < Np; ++n)
+    for (int m = 0; m < Np; ++m) {
+      h[L::DrT + m * Np + n] = (T)R.Dr[n * Np + m];
+      h[L::DsT + m * Np + n] = (T)R.Ds[n * Np + m];
+      h[L::DtT + m * Np + n] = (T)R.Dt[n * Np + m];
+    }
+  for (int n = 0; n < Np; ++n)
+    for (int j = 0; j < NFN; ++j) h[L::LiftT + j * Np + n] = (T)R.LIFT[n * NFN + j];
+  for (int n = 0; n < Np; ++n)
+    for (int v = 0; v < 4; ++v) h[L::Bary + 4 * n + v] = (T)R.bary[n * 4 + v];
+  for (int q = 0; q < Nc; ++q)
+    for (int m = 0; m < Np; ++m) h[L::IT + m * Nc + q] = (T)R.I[q * Np + m];
+  for (int n = 0; n < Np; ++n)
+    for (int q = 0; q < Nc; ++q) h[L::PT + q * Np + n] = (T)R.P[n * Nc + q];
+}
+
+template <typename T>
+static int upload_vec(const std::vector<T> &h, void **dev, void *stream) {
+  cudaError_t err = cudaMalloc(dev, h.size() * sizeof(T));
+  if (err != cudaSuccess) return (int)err;
+  err = cudaMemcpyAsync(*dev, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize((cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    cudaFree(*dev);
+    *dev = nullptr;
+  }
+  return (int)err;
+}
+
+int upload_ops3(int N, bool fp64, const RefOps3 &R, void **dev_ops, int **dev_tab, double **dev_bary, size_t *bytes,
+                void *stream) {
+  size_t total = 0;
+  int rc = 0;
+  if (fp64) {
+    std::vector<double> h;
+    switch (N) {
+      case 1: fill3<double, 1>(R, h); break;
+      case 2: fill3<double, 2>(R, h); break;
+      case 3: fill3<double, 3>(R, h); break;
+      case 4: fill3<double, 4>(R, h); break;
+      default: return (int)cudaErrorInvalidValue;
+    }
+    rc = upload_vec(h, dev_ops, stream);
+    total += h.size() * sizeof(double);
+  } else {
+    std::vector<float> h;
+    switch (N) {
+      case 1: fill3<float, 1>(R, h); break;
+      case 2: fill3<float, 2>(R, h); break;
+      case 3: fill3<float, 3>(R, h); break;
+      case 4: fill3<float, 4>(R, h); break;
+      default: return (int)cudaErrorInvalidValue;
+    }
+    rc = upload_vec(h, dev_ops, stream);
+    total += h.size() * sizeof(float);
+  }
+  if (rc) return rc;
+  std::vector<int> tab(R.nbr_node);
+  tab.insert(tab.end(), R.fmask.begin(), R.fmask.end());
+  rc = upload_vec(tab, (void **)dev_tab, stream);
+  if (rc) return rc;
+  total += tab.size() * sizeof(int);
+  rc = upload_vec(R.bary, (void **)dev_bary, stream);
+  total += R.bary.size() * sizeof(double);
+  *bytes = total;
+  return rc;
+}
+
+}  // namespace gb

@@ -37,7 +37,8 @@ extern "C" int gb_rhs_noalloc(gb_solver *s, double t, const void *q_dev, void *F
   int N = 0, Np = 0, precision = 0, num_sms = 1;
   int64_t K = 0;
   void *stream = nullptr;
-  gb::rhs_launch_view(s, t, &a, &perm, &N, &K, &Np, &precision, &stream, &num_sms);
+  if (gb::rhs_launch_view(s, t, &a, &perm, &N, &K, &Np, &precision, &stream, &num_sms) != GB_OK)
+    return gb::set_solver_error(s, GB_EINVAL, "gb_rhs_noalloc: not available for dim = 3 solvers");
   if (precision != GB_MIXED)
     return gb::set_solver_error(s, GB_EINVAL, "gb_rhs_noalloc: only GB_MIXED solvers use scratch; call gb_rhs");
   const int S = gb::mixed_stride(N);

@@ -11,6 +11,7 @@
 //    Gauss-Jacobi(1,0), both by Golub-Welsch) with I = Vc V^-1 and
 //    P = V V^T I^T W (the projection of Sec. 3);
 //  * the SARK-4 coefficients of Sec. 4 written through phi-functions.
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -334,6 +335,247 @@ bool build_reference(int N, RefOps &R) {
   };
   cp(r, R.r); cp(s, R.s); cp(Dr, R.Dr); cp(Ds, R.Ds); cp(LIFT, R.LIFT);
   cp(I, R.I); cp(P, R.P); cp(cr, R.cr); cp(cs, R.cs); cp(cw, R.cw); cp(wq, R.wq);
+  return true;
+}
+
+
+// ---- the reference tetrahedron (3D, 10 fields) -------------------------------------
+//
+// Reference tetrahedron v0 = (-1,-1,-1), v1 = (1,-1,-1), v2 = (-1,1,-1), v3 = (-1,-1,1);
+// barycentric l0 = -(1+r+s+t)/2, l1 = (1+r)/2, l2 = (1+s)/2, l3 = (1+t)/2.  Faces
+// (local vertex triples) 0 = (0,1,2), 1 = (0,1,3), 2 = (1,2,3), 3 = (0,2,3).  Node
+// order: lattice (i, j, k) = N (l1, l2, l3) before warping, i fastest, k slowest.
+
+static const int kFaceVerts[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+
+static ld alpha_tet(int N) {
+  static const ld tab[15] = {0.0L, 0.0L, 0.0L, 0.1002L, 1.1332L, 1.5608L, 1.3413L, 1.2577L,
+                             1.1603L, 1.10153L, 0.6080L, 0.4523L, 0.8856L, 0.8717L, 0.9655L};
+  return N <= 15 ? tab[N - 1] : 1.0L;
+}
+
+// Warp & Blend nodes on the tetrahedron (Warburton 2006): the equidistant nodes of the
+// regular tetrahedron with edge 2 are moved by each face's warp (per face edge: the 1D
+// warp along the edge direction, times 4 la lb (1 + (alpha lc)^2)), blended into the
+// volume by lb lc ld (1 + (alpha la)^2) / ((lb + la/2)(lc + la/2)(ld + la/2)) with la the
+// coordinate of the opposite vertex; edge nodes of a face take that face's warp.
+// Output: barycentric coordinates lam[Np][4].
+static void warp_blend_tet(int N, std::vector<std::array<ld, 4>> &lam) {
+  const ld s3 = sqrtl(3.0L), s6 = sqrtl(6.0L);
+  const ld V[4][3] = {{-1.0L, -1.0L / s3, -1.0L / s6}, {1.0L, -1.0L / s3, -1.0L / s6},
+                      {0.0L, 2.0L / s3, -1.0L / s6}, {0.0L, 0.0L, 3.0L / s6}};
+  const ld alpha = alpha_tet(N), tol = 1e-10L;
+  std::vector<ld> gll = gauss_lobatto(N);
+  lam.clear();
+  for (int k = 0; k <= N; ++k)
+    for (int j = 0; j <= N - k; ++j)
+      for (int i = 0; i <= N - j - k; ++i) {
+        ld L[4] = {1.0L - (ld)(i + j + k) / N, (ld)i / N, (ld)j / N, (ld)k / N};
+        ld X[3] = {0, 0, 0}, sh[3] = {0, 0, 0};
+        for (int v = 0; v < 4; ++v)
+          for (int d = 0; d < 3; ++d) X[d] += L[v] * V[v][d];
+        for (int f = 0; f < 4; ++f) {
+          const int *fv = kFaceVerts[f];
+          const int opp = 6 - fv[0] - fv[1] - fv[2];
+          const ld La = L[opp];
+          ld fw[3] = {0, 0, 0};
+          for (int e = 0; e < 3; ++e) {
+            const int a = fv[e], b = fv[(e + 1) % 3], c = fv[(e + 2) % 3];
+            ld d[3], len = 0;
+            for (int q = 0; q < 3; ++q) { d[q] = V[b][q] - V[a][q]; len += d[q] * d[q]; }
+            len = sqrtl(len);
+            const ld amt = 4.0L * L[a] * L[b] * warp_over_blend(N, L[b] - L[a], gll) * (1.0L + alpha * alpha * L[c] * L[c]);
+            for (int q = 0; q < 3; ++q) fw[q] += amt * d[q] / len;
+          }
+          const ld Lb = L[fv[0]], Lc = L[fv[1]], Ld = L[fv[2]];
+          ld blend = Lb * Lc * Ld;
+          const ld den = (Lb + 0.5L * La) * (Lc + 0.5L * La) * (Ld + 0.5L * La);
+          if (den > tol) blend = (1.0L + alpha * alpha * La * La) * blend / den;
+          const int inside = (Lb > tol) + (Lc > tol) + (Ld > tol);
+          if (La < tol && inside < 3) {
+            for (int q = 0; q < 3; ++q) sh[q] = fw[q];
+          } else {
+            for (int q = 0; q < 3; ++q) sh[q] += blend * fw[q];
+          }
+        }
+        for (int d = 0; d < 3; ++d) X[d] += sh[d];
+        // barycentric coordinates of X in the regular tetrahedron: solve [V^T; 1] l = [X; 1]
+        std::vector<ld> A(16), Ai;
+        for (int v = 0; v < 4; ++v) {
+          for (int d = 0; d < 3; ++d) A[(size_t)d * 4 + v] = V[v][d];
+          A[12 + v] = 1.0L;
+        }
+        invert(A, 4, Ai);
+        const ld rhs[4] = {X[0], X[1], X[2], 1.0L};
+        std::array<ld, 4> l;
+        for (int v = 0; v < 4; ++v) {
+          l[v] = 0;
+          for (int q = 0; q < 4; ++q) l[v] += Ai[(size_t)v * 4 + q] * rhs[q];
+        }
+        lam.push_back(l);
+      }
+}
+
+// Homogeneous form of the orthonormal Jacobi polynomials: T_n(x, y) = y^n p_n(x / y),
+// with its partial derivatives, from the three-term recurrence multiplied through by
+// y^{n+1} (no division by y, so it is regular where the collapsed map is singular).
+static void jacobi_homog(ld x, ld y, ld a, ld b, int n, ld *T, ld *Tx, ld *Ty) {
+  ld t0 = 1.0L / sqrtl(jac_mass(a, b)), x0 = 0, y0 = 0;
+  if (n == 0) { *T = t0; *Tx = 0; *Ty = 0; return; }
+  const ld A1 = jac_A(1, a, b), B0 = jac_B(0, a, b);
+  ld t1 = (x - B0 * y) * t0 / A1, x1 = t0 / A1, y1 = -B0 * t0 / A1;
+  for (int k = 1; k < n; ++k) {
+    const ld Ak = jac_A(k, a, b), Bk = jac_B(k, a, b), Ak1 = jac_A(k + 1, a, b);
+    const ld t2 = ((x - Bk * y) * t1 - Ak * y * y * t0) / Ak1;
+    const ld x2 = (t1 + (x - Bk * y) * x1 - Ak * y * y * x0) / Ak1;
+    const ld y2 = (-Bk * t1 + (x - Bk * y) * y1 - 2.0L * Ak * y * t0 - Ak * y * y * y0) / Ak1;
+    t0 = t1; x0 = x1; y0 = y1;
+    t1 = t2; x1 = x2; y1 = y2;
+  }
+  *T = t1; *Tx = x1; *Ty = y1;
+}
+
+// Orthonormal tetrahedral mode psi_ijk = 2 sqrt2 p_i(a) p_j^{(2i+1,0)}(b) (1-b)^i
+// p_k^{(2i+2j+2,0)}(c) (1-c)^{i+j} (collapsed a, b, c), written as
+// 2 sqrt2 2^i T_i(2(1+r) - S, S) T_j(2(1+s) - (1-t), 1-t) p_k(t) with S = -s-t, so that
+// value and gradient are polynomial evaluations everywhere on the element.
+static void mode3_eval(ld r, ld s, ld t, int i, int j, int k, ld *val, ld *g) {
+  const ld S = -s - t, w = 1.0L - t;
+  ld A, Ax, Ay, B, Bx, By;
+  jacobi_homog(2.0L * (1.0L + r) - S, S, 0, 0, i, &A, &Ax, &Ay);
+  jacobi_homog(2.0L * (1.0L + s) - w, w, 2.0L * i + 1.0L, 0, j, &B, &Bx, &By);
+  const ld ac = 2.0L * i + 2.0L * j + 2.0L;
+  const ld C = jacobi(t, ac, 0, k), Ct = jacobi_deriv(t, ac, 0, k);
+  const ld f = 2.0L * sqrtl(2.0L) * powl(2.0L, (ld)i);
+  // dA/dr = 2 Ax; dA/ds = dA/dt = Ax - Ay (x = 2(1+r) + s + t, y = -s - t)
+  // dB/ds = 2 Bx; dB/dt = Bx - By (x = 2(1+s) - 1 + t, y = 1 - t)
+  if (val) *val = f * A * B * C;
+  if (g) {
+    g[0] = f * 2.0L * Ax * B * C;
+    g[1] = f * ((Ax - Ay) * B * C + A * 2.0L * Bx * C);
+    g[2] = f * ((Ax - Ay) * B * C + A * (Bx - By) * C + A * B * Ct);
+  }
+}
+
+bool build_reference3d(int N, RefOps3 &R) {
+  if (N < 1 || N > GB3_MAX_N) return false;
+  const int Np = (N + 1) * (N + 2) * (N + 3) / 6, Nfp = (N + 1) * (N + 2) / 2, NFN = 4 * Nfp;
+  const int qc = (3 * N + 2) / 2;   // ceil((3N+1)/2): conical rule exact for degree 3N
+  const int Nc = qc * qc * qc;
+  R.N = N; R.Np = Np; R.Nfp = Nfp; R.Nc = Nc;
+  std::vector<std::array<ld, 4>> lam;
+  warp_blend_tet(N, lam);
+  std::vector<ld> r(Np), s(Np), t(Np);
+  for (int n = 0; n < Np; ++n) {
+    r[n] = 2.0L * lam[n][1] - 1.0L;
+    s[n] = 2.0L * lam[n][2] - 1.0L;
+    t[n] = 2.0L * lam[n][3] - 1.0L;
+  }
+  struct M3 { int i, j, k; };
+  std::vector<M3> md;
+  for (int i = 0; i <= N; ++i)
+    for (int j = 0; j <= N - i; ++j)
+      for (int k = 0; k <= N - i - j; ++k) md.push_back({i, j, k});
+  std::vector<ld> V((size_t)Np * Np), Vd[3];
+  for (auto &v : Vd) v.resize((size_t)Np * Np);
+  for (int n = 0; n < Np; ++n)
+    for (int m = 0; m < Np; ++m) {
+      ld g[3];
+      mode3_eval(r[n], s[n], t[n], md[m].i, md[m].j, md[m].k, &V[(size_t)n * Np + m], g);
+      for (int d = 0; d < 3; ++d) Vd[d][(size_t)n * Np + m] = g[d];
+    }
+  std::vector<ld> Vinv;
+  if (!invert(V, Np, Vinv)) return false;
+  std::vector<ld> D[3];
+  for (int d = 0; d < 3; ++d) D[d] = matmul(Vd[d], Vinv, Np, Np, Np);
+  std::vector<ld> Minv = matmul(V, transpose(V, Np, Np), Np, Np, Np);
+  // face nodes: nodes with zero coordinate of the opposite vertex, increasing index
+  R.fmask.assign(NFN, 0);
+  for (int f = 0; f < 4; ++f) {
+    const int opp = 6 - kFaceVerts[f][0] - kFaceVerts[f][1] - kFaceVerts[f][2];
+    int c = 0;
+    for (int n = 0; n < Np; ++n)
+      if (fabsl(lam[n][opp]) < 1e-10L) {
+        if (c >= Nfp) return false;
+        R.fmask[f * Nfp + c++] = n;
+      }
+    if (c != Nfp) return false;
+  }
+  // face mass in the parameter measure of each face (its own reference triangle):
+  // (V2 V2^T)^-1 with the orthonormal triangle modes at the face nodes
+  std::vector<Mode> md2 = modes(N);
+  std::vector<ld> E((size_t)Np * NFN, 0.0L);
+  for (int f = 0; f < 4; ++f) {
+    std::vector<ld> V2((size_t)Nfp * Nfp), M2;
+    for (int k = 0; k < Nfp; ++k) {
+      const int n = R.fmask[f * Nfp + k];
+      const ld r2 = 2.0L * lam[n][kFaceVerts[f][1]] - 1.0L, s2 = 2.0L * lam[n][kFaceVerts[f][2]] - 1.0L;
+      for (int m = 0; m < Nfp; ++m) mode_eval(r2, s2, md2[m].i, md2[m].j, &V2[(size_t)k * Nfp + m], nullptr, nullptr);
+    }
+    if (!invert(matmul(V2, transpose(V2, Nfp, Nfp), Nfp, Nfp, Nfp), Nfp, M2)) return false;
+    for (int k = 0; k < Nfp; ++k)
+      for (int l = 0; l < Nfp; ++l) E[(size_t)R.fmask[f * Nfp + k] * NFN + f * Nfp + l] = M2[(size_t)k * Nfp + l];
+  }
+  std::vector<ld> LIFT = matmul(Minv, E, Np, Np, NFN);
+  // conical-product cubature: Gauss-Legendre (a) x Gauss-Jacobi(1,0) (b) x Gauss-Jacobi(2,0) (c)
+  std::vector<ld> ga, wa, gbv, wbv, gc, wc;
+  gauss_jacobi(qc, 0.0L, 0.0L, ga, wa);
+  gauss_jacobi(qc, 1.0L, 0.0L, gbv, wbv);
+  gauss_jacobi(qc, 2.0L, 0.0L, gc, wc);
+  std::vector<ld> cr(Nc), cs(Nc), ct(Nc), cw(Nc);
+  for (int kc = 0; kc < qc; ++kc)
+    for (int jb = 0; jb < qc; ++jb)
+      for (int ia = 0; ia < qc; ++ia) {
+        const int q = (kc * qc + jb) * qc + ia;
+        ct[q] = gc[kc];
+        cs[q] = (1.0L + gbv[jb]) * (1.0L - gc[kc]) / 2.0L - 1.0L;
+        cr[q] = (1.0L + ga[ia]) * (1.0L - gbv[jb]) * (1.0L - gc[kc]) / 4.0L - 1.0L;
+        cw[q] = wa[ia] * wbv[jb] * wc[kc] / 8.0L;
+      }
+  std::vector<ld> Vc((size_t)Nc * Np);
+  for (int q = 0; q < Nc; ++q)
+    for (int m = 0; m < Np; ++m) mode3_eval(cr[q], cs[q], ct[q], md[m].i, md[m].j, md[m].k, &Vc[(size_t)q * Np + m], nullptr);
+  std::vector<ld> I = matmul(Vc, Vinv, Nc, Np, Np);
+  std::vector<ld> ITW = transpose(I, Nc, Np);
+  for (int i = 0; i < Np; ++i)
+    for (int q = 0; q < Nc; ++q) ITW[(size_t)i * Nc + q] *= cw[q];
+  std::vector<ld> P = matmul(Minv, ITW, Np, Np, Nc);
+  std::vector<ld> Mhat;
+  if (!invert(Minv, Np, Mhat)) return false;
+  std::vector<ld> wq(Np, 0.0L);
+  for (int i = 0; i < Np; ++i)
+    for (int j = 0; j < Np; ++j) wq[j] += Mhat[(size_t)i * Np + j];
+  // neighbour face-node table: my face f (vertex ids in kFaceVerts order), neighbour face
+  // f2, permutation code p (my face vertex i is the neighbour's face vertex kPerm3[p][i]):
+  // the neighbour's volume node holding the same point as my face node k
+  R.nbr_node.assign((size_t)4 * 4 * 6 * Nfp, -1);
+  for (int f = 0; f < 4; ++f)
+    for (int f2 = 0; f2 < 4; ++f2)
+      for (int p = 0; p < 6; ++p)
+        for (int k = 0; k < Nfp; ++k) {
+          const int n = R.fmask[f * Nfp + k];
+          ld nu[3];
+          for (int i = 0; i < 3; ++i) nu[kPerm3[p][i]] = lam[n][kFaceVerts[f][i]];
+          int best = -1;
+          ld bd = 1e30L;
+          for (int k2 = 0; k2 < Nfp; ++k2) {
+            const int n2 = R.fmask[f2 * Nfp + k2];
+            ld d = 0;
+            for (int i = 0; i < 3; ++i) d += fabsl(lam[n2][kFaceVerts[f2][i]] - nu[i]);
+            if (d < bd) { bd = d; best = n2; }
+          }
+          if (bd > 1e-10L) return false;
+          R.nbr_node[((size_t)(f * 4 + f2) * 6 + p) * Nfp + k] = best;
+        }
+  auto cp = [](const std::vector<ld> &a, std::vector<double> &b) {
+    b.resize(a.size());
+    for (size_t i = 0; i < a.size(); ++i) b[i] = (double)a[i];
+  };
+  cp(r, R.r); cp(s, R.s); cp(t, R.t); cp(D[0], R.Dr); cp(D[1], R.Ds); cp(D[2], R.Dt); cp(LIFT, R.LIFT);
+  cp(I, R.I); cp(P, R.P); cp(cr, R.cr); cp(cs, R.cs); cp(ct, R.ct); cp(cw, R.cw); cp(wq, R.wq);
+  R.bary.resize((size_t)Np * 4);
+  for (int n = 0; n < Np; ++n)
+    for (int v = 0; v < 4; ++v) R.bary[(size_t)n * 4 + v] = (double)lam[n][v];
   return true;
 }
 

@@ -35,6 +35,10 @@ class GbMotion(ctypes.Structure):
                 ('Lx', ctypes.c_double), ('Ly', ctypes.c_double)]
 
 
+class GbWaveMotion(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ('A0', 'A1', 'Lx', 'wavelength', 'omega', 'r0sq', 'yc', 'zc')]
+
+
 class GBError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__('%s: %s' % (_NAMES.get(code, str(code)), msg))
@@ -74,6 +78,8 @@ def _load():
         'gb_last_error': ([vp], ctypes.c_char_p),
         'gb_reference_operators': ([c_int] + [_dp] * 10 + [ctypes.POINTER(c_int)], c_int),
         'gb_sark_coefficients': ([c_double, _dp, _dp, _dp], c_int),
+        'gb_set_wave_motion': ([vp, ctypes.POINTER(GbWaveMotion)], c_int),
+        'gb_reference_operators3d': ([c_int] + [_dp] * 13 + [ctypes.POINTER(c_int)], c_int),
         'gb_group_create': ([c_int, vp, ctypes.POINTER(vp)], c_int),
         'gb_group_step': ([vp, ctypes.POINTER(vp), _dp, c_int, i64], c_int),
         'gb_group_destroy': ([vp], c_int),
@@ -123,6 +129,22 @@ def reference_operators(N):
     return out
 
 
+def reference_operators3d(N):
+    """The library's order-N tetrahedral reference operators (host computation, no GPU)."""
+    Np, Nfp = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2
+    nc = ctypes.c_int(0)
+    _check(lib.gb_reference_operators3d(N, *([None] * 13), ctypes.byref(nc)))
+    Nc = nc.value
+    out = {'r': np.zeros(Np), 's': np.zeros(Np), 't': np.zeros(Np), 'Dr': np.zeros((Np, Np)),
+           'Ds': np.zeros((Np, Np)), 'Dt': np.zeros((Np, Np)), 'LIFT': np.zeros((Np, 4 * Nfp)),
+           'I': np.zeros((Nc, Np)), 'P': np.zeros((Np, Nc)), 'cr': np.zeros(Nc), 'cs': np.zeros(Nc),
+           'ct': np.zeros(Nc), 'cw': np.zeros(Nc)}
+    keys = ['r', 's', 't', 'Dr', 'Ds', 'Dt', 'LIFT', 'I', 'P', 'cr', 'cs', 'ct', 'cw']
+    _check(lib.gb_reference_operators3d(N, *[_ptr(out[k]) for k in keys], ctypes.byref(nc)))
+    out['Nc'] = Nc
+    return out
+
+
 def sark_coefficients(gamma):
     """(E[5], A[4,4], B[4]) from the library (host computation, no GPU)."""
     E, A, B = np.zeros(5), np.zeros(16), np.zeros(4)
@@ -141,14 +163,18 @@ def dissipation_rate(t, kinetic_energy):
 
 
 class Solver:
-    """Owns one gb_solver.  mesh is a dict with X, EToV, shift (see inputs.py)."""
+    """Owns one gb_solver.  mesh is a dict with X, EToV, shift (see inputs.py); the
+    dimension follows from X: (n_vert, 2) triangles with 6 fields, (n_vert, 3)
+    tetrahedra with 10 fields."""
 
     def __init__(self, mesh, N, Ma, Re, precision=GB_FP64, stream=None):
         self._X = np.ascontiguousarray(mesh['X'], dtype=np.float64)
         self._EToV = np.ascontiguousarray(mesh['EToV'], dtype=np.int32)
         shift = mesh.get('shift')
         self._shift = None if shift is None else np.ascontiguousarray(shift, dtype=np.float64)
-        m = GbMesh(2, self._X.shape[0], _ptr(self._X), self._EToV.shape[0],
+        self.dim = int(self._X.shape[1])
+        self.nfields = 6 if self.dim == 2 else 10
+        m = GbMesh(self.dim, self._X.shape[0], _ptr(self._X), self._EToV.shape[0],
                    self._EToV.ctypes.data_as(_ip), None if self._shift is None else _ptr(self._shift))
         h = ctypes.c_void_p(None)
         st = None if stream is None else ctypes.c_void_p(int(stream))
@@ -173,31 +199,37 @@ class Solver:
         m = GbMotion(kind, float(A), float(T), float(Lx), float(Ly))
         self._c(lib.gb_set_motion(self.h, ctypes.byref(m)))
 
+    def set_wave_motion(self, A0, A1=0.0, Lx=8.0, wavelength=1.0, omega=2 * np.pi, r0sq=0.25, yc=1.0, zc=1.0):
+        """Travelling-wave lateral motion of a dim = 3 solver (gb_set_wave_motion)."""
+        m = GbWaveMotion(float(A0), float(A1), float(Lx), float(wavelength), float(omega), float(r0sq),
+                         float(yc), float(zc))
+        self._c(lib.gb_set_wave_motion(self.h, ctypes.byref(m)))
+
     def set_fields(self, q, t=0.0):
         q = np.ascontiguousarray(q, dtype=np.float64)
-        if q.size != self.K * 6 * self.Np:
-            raise ValueError('q must hold K*6*Np values')
+        if q.size != self.K * self.nfields * self.Np:
+            raise ValueError('q must hold K*nfields*Np values')
         self._c(lib.gb_set_fields(self.h, _ptr(q), float(t)))
 
     def fields(self, out=None):
-        q = out if out is not None else np.empty((self.K, 6, self.Np))
+        q = out if out is not None else np.empty((self.K, self.nfields, self.Np))
         t = ctypes.c_double()
         self._c(lib.gb_fields(self.h, _ptr(q), ctypes.byref(t)))
         return q, t.value
 
     def set_vertices(self, x):
         x = np.ascontiguousarray(x, dtype=np.float64)
-        if x.size != 2 * self.nv:
-            raise ValueError('x must hold n_vert*2 values')
+        if x.size != self.dim * self.nv:
+            raise ValueError('x must hold n_vert*dim values')
         self._c(lib.gb_set_vertices(self.h, _ptr(x)))
 
     def vertices(self):
-        x = np.empty((self.nv, 2))
+        x = np.empty((self.nv, self.dim))
         self._c(lib.gb_vertices(self.h, _ptr(x)))
         return x
 
     def nodes(self):
-        xy = np.empty((self.K, self.Np, 2))
+        xy = np.empty((self.K, self.Np, self.dim))
         self._c(lib.gb_nodes(self.h, _ptr(xy)))
         return xy
 

@@ -122,3 +122,19 @@ def test_dissipation_rate_of_an_exponential_decay():
         assert np.max(np.abs(eps - 4 * nu * e) / (4 * nu * e)) < 1e-4
     with pytest.raises(ValueError):
         gb.dissipation_rate([0.0, 1.0], [1.0, 0.5])
+
+
+@pytest.mark.parametrize('N', [1, 2, 3, 4])
+def test_library_tet_operators_match_oracle(N):
+    """The library's long-double tetrahedral builder (orthonormal modes through homogeneous
+    Jacobi recurrences) against the oracle's (monomial route)."""
+    from oracle import tet
+    from paper_2607_00199_b300 import gb
+    L = gb.reference_operators3d(N)
+    R = tet.ReferenceTet(N)
+    assert L['Nc'] == R.Nc
+    for k in ('r', 's', 't', 'cr', 'cs', 'ct', 'cw'):
+        np.testing.assert_allclose(L[k], getattr(R, k), atol=1e-15)
+    for k in ('Dr', 'Ds', 'Dt', 'I', 'P'):
+        np.testing.assert_allclose(L[k], getattr(R, k), atol=1e-13)
+    np.testing.assert_allclose(L['LIFT'], R.LIFT, atol=2e-12)
