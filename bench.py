@@ -88,6 +88,101 @@ def run_serving(torch, n_req=256, steps=500, rate=50.0, budget_gib=16.0):
                     'completion (includes set-up of each request and idle time before arrivals)'}
 
 
+WORKLOAD3 = dict(dims=(64, 16, 16), L=(8.0, 2.0, 2.0), N=3, Ma=0.1, Re=500.0, cfl=0.5,
+                 wave=dict(A0=0.02, A1=0.08, Lx=8.0, wavelength=1.0, omega=2 * math.pi, r0sq=0.25, yc=1.0, zc=1.0))
+WORKLOAD3_NAME = ('3D deforming channel: periodic box [0,8]x[0,2]x[0,2], 64x16x16 hexes -> K=98304 tetrahedra '
+                  '(6 per hex), N=3 (Np=20), 10 fields, Ma=0.1, Re=500, y += (0.02+0.08x/8) sin(2 pi x - 2 pi t) '
+                  'exp(-r^2/0.25), CFL 0.5, uniform stream u=1 with a small transverse disturbance')
+
+
+def sizes3(N):
+    Np, Nfp = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2
+    qc = (3 * N + 2) // 2
+    return Np, Nfp, qc ** 3
+
+
+def flops3_per_element_stage(N):
+    """Algorithmic flops (FMA = 2) of one tetrahedron-stage of the fused 3D RHS + update."""
+    Np, Nfp, Nc = sizes3(N)
+    macs = 3 * 10 * Np * Np + 10 * Np * 4 * Nfp + 4 * Nc * Np + 6 * Np * Nc   # Dr Ds Dt, LIFT, I, P
+    volume = Np * 250         # chain rule 180, v_G interpolation 8, At_x/y/z products 42, sums 20
+    surface = 4 * Nfp * 190   # jump 10, four At_n products 120, upwind/ALE combination 60
+    cubature = Nc * 24        # Ntilde with one division
+    update = 10 * Np * 4
+    return 2 * macs + volume + surface + cubature + update
+
+
+def bytes3_per_step(K, N, nv, elem_bytes):
+    """Algorithmic HBM bytes of the 4 stage launches of one 3D step: 18 field arrays,
+    plus per launch the 48-byte mesh record of every element and x_n (24 B) and
+    S1, S2 (16 B) of every unique vertex."""
+    Np, _, _ = sizes3(N)
+    return 18 * K * 10 * Np * elem_bytes + 4 * (48 * K + 40 * nv)
+
+
+def run_3d(torch, steps_fp64=10, steps_mixed=50, warmup=3):
+    """The 3D deforming-channel workload, FP64 and GB_MIXED (FP32 SIMT, no tensor cores),
+    timed like the 2D headline (CUDA-graph step replay between CUDA events), with the
+    mixed path's error against the FP64 path after the same steps."""
+    from paper_2607_00199_b300 import gb, inputs, state
+    W = WORKLOAD3
+    mesh = inputs.periodic_box_tet_mesh(*W['dims'], L=W['L'])
+    tstream = torch.cuda.Stream()
+    N = W['N']
+    Np, Nfp, Nc = sizes3(N)
+    hbm, sm_max, peak_kind = load_peaks()
+    res = {}
+    qend = {}
+    for name, prec, steps in (('fp64', gb.GB_FP64, steps_fp64), ('mixed', gb.GB_MIXED, steps_mixed)):
+        s = gb.Solver(mesh, N, W['Ma'], W['Re'], precision=prec, stream=tstream.cuda_stream)
+        s.set_wave_motion(**W['wave'])
+        xyz = s.nodes()
+        rho, u, v, w = inputs.channel_flow_3d(xyz[..., 0], xyz[..., 1], xyz[..., 2], W['Ma'])
+        q0 = state.equilibrium_fields3(rho, u, v, w, s.c)
+        dt = inputs.cfl_dt_3d(mesh, N, s.c, W['cfl'])
+        ms, kms = time_path(torch, s, q0, dt, steps, warmup, lambda: None, tstream)
+        # same state and steps for the error comparison
+        s.set_vertices(mesh['X'])
+        s.set_fields(q0, 0.0)
+        s.step(dt, 10)
+        qend[name], _ = s.fields()
+        stage_ms = float(sum(kms[:4]))
+        dof = s.K * Np * 10
+        ebytes = 8 if prec == gb.GB_FP64 else 4
+        alg = bytes3_per_step(s.K, N, s.nv, ebytes)
+        fl = flops3_per_element_stage(N) * s.K * 4
+        gbs = alg * steps / (stage_ms / 1e3) / 1e9
+        tfl = fl * steps / (stage_ms / 1e3) / 1e12
+        r = {'value': dof * 4 * steps / (ms / 1e3), 'ms_per_step': ms / steps, 'steps': steps, 'warmup': warmup,
+             'kernel_ms_per_step': [x / steps for x in kms], 'mean_launch_ms': stage_ms / (4 * steps),
+             'hbm': {'achieved_gbs': gbs, 'peak_gbs': hbm, 'frac': gbs / hbm, 'algorithmic_bytes_per_step': alg},
+             'algorithmic_flops_per_element_stage': flops3_per_element_stage(N)}
+        if prec == gb.GB_FP64:
+            peak = 148 * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
+            r['roofline'] = {'bound': 'alu', 'achieved': tfl, 'peak': peak, 'unit': 'TFLOP/s', 'frac': tfl / peak,
+                             'kernel': 'stage3_kernel<double,3,*>',
+                             'peak_source': 'FP64 pipe: 148 SMs x 2 FMA/clk x 2 flop x %.0f MHz' % sm_max}
+        else:
+            peak = 148 * 256.0 * sm_max * 1e6 / 1e12
+            r['roofline'] = {'bound': 'alu', 'achieved': tfl, 'peak': peak, 'unit': 'TFLOP/s', 'frac': tfl / peak,
+                             'kernel': 'stage3_kernel<float,3,*>',
+                             'peak_source': 'FP32 pipe: 148 SMs x 128 FMA/clk x 2 flop x %.0f MHz' % sm_max}
+        res[name] = r
+        K, nv = s.K, s.nv
+        s.close()
+    rest = np.zeros_like(qend['fp64'])
+    rest[:, 0, :] = 1.0
+    dq = qend['mixed'] - qend['fp64']
+    return {'workload': WORKLOAD3_NAME, 'K': K, 'n_vert': nv, 'N': N, 'Np': Np, 'fields': 10, 'dof': K * Np * 10,
+            'metric': 'DOF-stage updates/s', 'fp64': res['fp64'], 'mixed': res['mixed'],
+            'mixed_speedup_vs_fp64': res['mixed']['value'] / res['fp64']['value'],
+            'mixed_error': {'rel_l2_fields': float(np.linalg.norm(dq) / np.linalg.norm(qend['fp64'])),
+                            'rel_l2_perturbation': float(np.linalg.norm(dq) / np.linalg.norm(qend['fp64'] - rest)),
+                            'steps': 10, 'against': 'GB_FP64 3D path (oracle-parity-tested) from the same state'},
+            'timing': 'ms_per_step: gb_step (CUDA graph replay) between CUDA events; inputs larger than L2 '
+                      '(FP64 state 157 MB per array, FP32 79 MB)'}
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument('--gpus', type=int, default=1)
@@ -97,6 +192,7 @@ def parse():
     p.add_argument('--no-cpu-baseline', action='store_true')
     p.add_argument('--no-serve', action='store_true', help='skip the serving-stream measurement')
     p.add_argument('--serve-only', action='store_true', help='only the serving-stream measurement')
+    p.add_argument('--no-3d', action='store_true', help='skip the 3D deforming-channel measurement')
     p.add_argument('--serve-requests', type=int, default=256)
     p.add_argument('--serve-steps', type=int, default=500)
     return p.parse_args()
@@ -425,6 +521,8 @@ def run_ours(args):
         'mixed_speedup_vs_fp64': out['mixed']['value'] / out['fp64']['value'],
         'mixed_error': err,
     }
+    if ws == 1 and not args.no_3d:
+        line['d3'] = run_3d(torch)
     if ws == 1 and not args.no_serve:
         line['serving'] = run_serving(torch, args.serve_requests, args.serve_steps)
     if ws == 1 and not args.no_cpu_baseline:

@@ -21,6 +21,11 @@ physics    the 2D Galerkin-Boltzmann flux matrices, the collision term and the
 sark       semi-analytic Runge-Kutta coefficients (Sec. 4).
 solver     the ALE right-hand side and the SARK step on a moving periodic
            triangle mesh (Secs. 2-5).
+tet        Warp & Blend nodes and the reference operators of the tetrahedron
+           (Sec. 3 in three dimensions; monomial route, exact rules).
+physics3d  the 10-moment 3D Galerkin-Boltzmann system (Sec. 2 construction).
+solver3d   the ALE right-hand side and SARK step on a moving periodic
+           tetrahedral mesh.
 
 Parity status of each function is stated in its docstring; functions with no
 independent pin say "parity unpinned".
