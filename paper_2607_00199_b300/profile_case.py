@@ -3,6 +3,10 @@ workload (K = 131072 jittered triangles, N = 4): set-up, `--warmup` steps, then
 `--steps` steps, with as few other launches as possible.
 
     python -m paper_2607_00199_b300.profile_case --precision mixed|fp64 [--steps 2] [--warmup 2] [--n 256] [--warps 4]
+    python -m paper_2607_00199_b300.profile_case --dim 3 --precision mixed|fp64 [--nx 64 --ny 16 --nz 16] [--N 3]
+
+With --dim 3 the case is the deforming-channel workload (periodic box [0,8]x[0,2]x[0,2]
+of nx x ny x nz hexes, 6 tetrahedra each, travelling-wave motion).
 
 The mixed kernel's launch shape is fixed by --warps (no tuning launches) so that
 launch indices in a capture are the same from run to run: set-up launches, then
@@ -21,10 +25,18 @@ def main():
     p.add_argument('--steps', type=int, default=2)
     p.add_argument('--warmup', type=int, default=2)
     p.add_argument('--n', type=int, default=256)
-    p.add_argument('--N', type=int, default=4)
+    p.add_argument('--N', type=int, default=None, help='order (default 4 in 2D, 3 in 3D)')
     p.add_argument('--warps', type=int, default=4, choices=[1, 2, 4])
+    p.add_argument('--dim', type=int, default=2, choices=[2, 3])
+    p.add_argument('--nx', type=int, default=64)
+    p.add_argument('--ny', type=int, default=16)
+    p.add_argument('--nz', type=int, default=16)
     a = p.parse_args()
     prec = gb.GB_MIXED if a.precision == 'mixed' else gb.GB_FP64
+    if a.N is None:
+        a.N = 4 if a.dim == 2 else 3
+    if a.dim == 3:
+        return main3(a, prec)
     mesh = inputs.periodic_square_mesh(a.n, jitter=0.1)
     s = gb.Solver(mesh, a.N, 0.1, 1000.0, precision=prec, stream=torch.cuda.current_stream().cuda_stream)
     s.set_motion(0.05, 1.0)
@@ -35,6 +47,22 @@ def main():
     rho, u, v = inputs.taylor_green(xy[..., 0], xy[..., 1], 0.1)
     s.set_fields(state.equilibrium_fields(rho, u, v, s.c), 0.0)
     dt = inputs.cfl_dt(mesh, a.N, s.c, 0.5)
+    s.step(dt, a.warmup)
+    s.sync()
+    ms = s.step_timed(dt, a.steps)
+    print('kernel ms per step:', [round(x / a.steps, 4) for x in ms])
+
+
+def main3(a, prec):
+    import math
+    mesh = inputs.periodic_box_tet_mesh(a.nx, a.ny, a.nz, L=(8.0, 2.0, 2.0))
+    s = gb.Solver(mesh, a.N, 0.1, 500.0, precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_wave_motion(0.02, 0.08, 8.0, 1.0, 2 * math.pi, 0.25, 1.0, 1.0)
+    s.set_graph(False)
+    xyz = s.nodes()
+    rho, u, v, w = inputs.channel_flow_3d(xyz[..., 0], xyz[..., 1], xyz[..., 2], 0.1)
+    s.set_fields(state.equilibrium_fields3(rho, u, v, w, s.c), 0.0)
+    dt = inputs.cfl_dt_3d(mesh, a.N, s.c, 0.5)
     s.step(dt, a.warmup)
     s.sync()
     ms = s.step_timed(dt, a.steps)
