@@ -3,8 +3,9 @@
 // One fused kernel per SARK stage (Sec. 4) computes, for a tile of E elements per CTA:
 //   geometry  : stage vertex positions y_i = y_n + xfac1 S1(X) + xfac2 S2(X) and
 //               velocities v_y = gfac1 S1(X) + gfac2 S2(X) of the travelling-wave motion
-//               (Sec. 5), then G = dx/d(r,s,t), J, G^-1, the four outward normals and
-//               Fscale = face area / (2 J), all in FP64 from the four vertices (GCL);
+//               (Sec. 5) in FP64, then the edge vectors (FP64 differences) and from them
+//               G = dx/d(r,s,t), J, G^-1, the four outward normals and Fscale = face
+//               area / (2 J) in the field precision (FP64 in GB_FP64) (GCL);
 //   volume    : Dr, Ds, Dt of the 10 fields, chain rule, (A + v_G) . grad q;
 //   surface   : neighbour traces through the face-node permutation table, the upwind
 //               fluxes c/2 (|At_n| - At_n) dq (|At_n| = alpha At_n^2 + beta At_n^4,
@@ -37,22 +38,25 @@ struct Dim3 {
 };
 
 // elements per CTA: (T, N)
-template <typename T, int N> struct Tile3 { static constexpr int E = sizeof(T) == 8 ? (N <= 2 ? 16 : (N == 3 ? 8 : 4)) : (N <= 2 ? 32 : (N == 3 ? 16 : 8)); };
+template <typename T, int N> struct Tile3 { static constexpr int E = sizeof(T) == 8 ? (N <= 2 ? 16 : (N == 3 ? 8 : 4)) : (N <= 2 ? 32 : (N == 3 ? 12 : 8)); };
 
-// operator block (in T): the small operators live in shared memory, I and P stay in
-// global memory (read through the L1 cache); then the integer tables.
-template <int N>
+// operator block (in T): Dr, Ds, Dt, LIFT and the barycentric table, then I and P, then
+// (in int) the neighbour node table and the face masks.  The first part always lives in
+// shared memory; I and P too in FP32 up to N = 3 (IP_SMEM), otherwise they are read
+// through the L1 cache.
+template <typename T, int N>
 struct Op3 {
   typedef Dim3<N> D;
+  static constexpr bool IP_SMEM = sizeof(T) == 4 && N <= 3;
   static constexpr int DrT = 0;                           // [m][n] = Dr[n][m]
   static constexpr int DsT = DrT + D::Np * D::Np;
   static constexpr int DtT = DsT + D::Np * D::Np;
   static constexpr int LiftT = DtT + D::Np * D::Np;       // [j][n] = LIFT[n][j]
   static constexpr int Bary = LiftT + D::NFN * D::Np;     // [n][4]
-  static constexpr int SmemSize = Bary + 4 * D::Np;       // staged in shared memory
-  static constexpr int IT = SmemSize;                     // [m][c] = I[c][m]
+  static constexpr int IT = Bary + 4 * D::Np;             // [m][c] = I[c][m]
   static constexpr int PT = IT + D::Np * D::Nc;           // [c][n] = P[n][c]
   static constexpr int Size = PT + D::Nc * D::Np;
+  static constexpr int SmemSize = IP_SMEM ? Size : IT;    // staged in shared memory
   static constexpr int TabInts = 4 * 4 * 6 * D::Nfp + 4 * D::Nfp;   // neighbour node table, fmask
 };
 
@@ -60,9 +64,6 @@ struct Op3 {
 // vertex y-velocities (4), per face nx ny nz Fscale (16)
 constexpr int GEO3 = 32;
 
-__constant__ int c_face_verts[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
-// orientation of (P_b - P_a) x (P_c - P_a) relative to the outward normal, per face
-__constant__ double c_face_sign[4] = {-1.0, 1.0, 1.0, -1.0};
 
 template <typename T> __device__ __forceinline__ T fma3(T a, T b, T c);
 template <> __device__ __forceinline__ double fma3<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -116,7 +117,7 @@ template <typename T, int N, int STAGE>
 __global__ void __launch_bounds__(((Tile3<T, N>::E * Dim3<N>::Np + 31) / 32) * 32)
 stage3_kernel(const Stage3Args a) {
   typedef Dim3<N> D;
-  typedef Op3<N> L;
+  typedef Op3<T, N> L;
   constexpr int E = Tile3<T, N>::E;
   constexpr int Np = D::Np, Nfp = D::Nfp, NFN = D::NFN, Nc = D::Nc, NQ = D::NQ;
   constexpr bool PERTURB = sizeof(T) == 4;
@@ -154,8 +155,8 @@ stage3_kernel(const Stage3Args a) {
   const double g1 = s_motion[0], g2 = s_motion[1], x1 = s_motion[2], x2 = s_motion[3];
   const int *snbr = stab;
   const int *sfmask = stab + 4 * 4 * 6 * Nfp;
-  const T *gIT = gops + L::IT;
-  const T *gPT = gops + L::PT;
+  const T *gIT = (L::IP_SMEM ? sops : gops) + L::IT;
+  const T *gPT = (L::IP_SMEM ? sops : gops) + L::PT;
 
   const T *qin = reinterpret_cast<const T *>(a.qin);
   const int e_loc = tid / Np, n_loc = tid - (tid / Np) * Np;
@@ -171,59 +172,65 @@ stage3_kernel(const Stage3Args a) {
       const int cnt = nel * NQ;
       for (int i = tid; i < cnt; i += nthr) sq[i] = src[i];
     }
-    // ---- geometry, one thread per element, FP64 ----
+    // ---- geometry, one thread per element: vertex positions in FP64, edge vectors as FP64
+    //      differences, everything after them in T (FP64 in GB_FP64) ----
     for (int e = tid; e < nel; e += nthr) {
       const MeshRec3 rec = a.mesh[elem0 + e];
-      double P[4][3], vy[4];
+      double P0[3];
+      T dv[4][3], vy[4];   // dv[k] = P_k - P_0 (dv[0] = 0)
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int64_t v = rec.v[k];
         const double2 sv = reinterpret_cast<const double2 *>(a.shape)[v];
+        double Pk[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) P[k][d] = a.xn[3 * v + d] + rec.shift[3 * k + d] * a.period[d];
-        P[k][1] += x1 * sv.x + x2 * sv.y;
-        vy[k] = g1 * sv.x + g2 * sv.y;
+        for (int d = 0; d < 3; ++d) Pk[d] = a.xn[3 * v + d] + rec.shift[3 * k + d] * a.period[d];
+        Pk[1] += x1 * sv.x + x2 * sv.y;
+        vy[k] = (T)(g1 * sv.x + g2 * sv.y);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          if (k == 0) P0[d] = Pk[d];
+          dv[k][d] = k == 0 ? (T)0 : (T)(Pk[d] - P0[d]);
+        }
       }
-      double G[3][3];
+      T G[3][3];
 #pragma unroll
       for (int d = 0; d < 3; ++d)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) G[d][q] = 0.5 * (P[q + 1][d] - P[0][d]);
-      const double C00 = G[1][1] * G[2][2] - G[1][2] * G[2][1];
-      const double C01 = G[1][2] * G[2][0] - G[1][0] * G[2][2];
-      const double C02 = G[1][0] * G[2][1] - G[1][1] * G[2][0];
-      const double J = G[0][0] * C00 + G[0][1] * C01 + G[0][2] * C02;
-      if (!(J > 0.0)) atomicOr(a.status, GB_STATUS_MESH);
-      const double iJ = 1.0 / J;
+        for (int q = 0; q < 3; ++q) G[d][q] = (T)0.5 * dv[q + 1][d];
+      const T C00 = G[1][1] * G[2][2] - G[1][2] * G[2][1];
+      const T C01 = G[1][2] * G[2][0] - G[1][0] * G[2][2];
+      const T C02 = G[1][0] * G[2][1] - G[1][1] * G[2][0];
+      const T J = G[0][0] * C00 + G[0][1] * C01 + G[0][2] * C02;
+      if (!(J > (T)0)) atomicOr(a.status, GB_STATUS_MESH);
+      const T iJ = (T)1 / J;
       // G^-1 = adj(G) / J; row a of G^-1 is the gradient of reference coordinate a
-      double Gi[3][3];
-      Gi[0][0] = C00 * iJ; Gi[1][0] = C01 * iJ; Gi[2][0] = C02 * iJ;
-      Gi[0][1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) * iJ;
-      Gi[1][1] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) * iJ;
-      Gi[2][1] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) * iJ;
-      Gi[0][2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) * iJ;
-      Gi[1][2] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) * iJ;
-      Gi[2][2] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) * iJ;
       T *g = sgeo + e * GEO3;
+      g[0] = C00 * iJ; g[3] = C01 * iJ; g[6] = C02 * iJ;
+      g[1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) * iJ;
+      g[4] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) * iJ;
+      g[7] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) * iJ;
+      g[2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) * iJ;
+      g[5] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) * iJ;
+      g[8] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) * iJ;
 #pragma unroll
-      for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) g[3 * i + j] = (T)Gi[i][j];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) g[9 + k] = (T)vy[k];
+      for (int k = 0; k < 4; ++k) g[9 + k] = vy[k];
+      // faces (local vertex triples) and the orientation of (P_b - P_a) x (P_c - P_a)
+      // relative to the outward normal; compile-time so that dv stays in registers
+      constexpr int fvt[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+      constexpr float fsign[4] = {-1.0f, 1.0f, 1.0f, -1.0f};
 #pragma unroll
       for (int f = 0; f < 4; ++f) {
-        const int va = c_face_verts[f][0], vb = c_face_verts[f][1], vc = c_face_verts[f][2];
-        const double ux = P[vb][0] - P[va][0], uy = P[vb][1] - P[va][1], uz = P[vb][2] - P[va][2];
-        const double wx = P[vc][0] - P[va][0], wy = P[vc][1] - P[va][1], wz = P[vc][2] - P[va][2];
-        double nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
-        const double len = sqrt(nx * nx + ny * ny + nz * nz);
-        const double sg = c_face_sign[f] / len;
-        nx *= sg; ny *= sg; nz *= sg;
-        g[13 + 4 * f] = (T)nx;
-        g[14 + 4 * f] = (T)ny;
-        g[15 + 4 * f] = (T)nz;
-        g[16 + 4 * f] = (T)(0.25 * len * iJ);   // face area / (2 J)
+        const int va = fvt[f][0], vb = fvt[f][1], vc = fvt[f][2];
+        const T ux = dv[vb][0] - dv[va][0], uy = dv[vb][1] - dv[va][1], uz = dv[vb][2] - dv[va][2];
+        const T wx = dv[vc][0] - dv[va][0], wy = dv[vc][1] - dv[va][1], wz = dv[vc][2] - dv[va][2];
+        const T nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
+        const T len = sqrt(nx * nx + ny * ny + nz * nz);
+        const T sg = (T)fsign[f] / len;
+        g[13 + 4 * f] = nx * sg;
+        g[14 + 4 * f] = ny * sg;
+        g[15 + 4 * f] = nz * sg;
+        g[16 + 4 * f] = (T)0.25 * len * iJ;   // face area / (2 J)
       }
     }
     __syncthreads();
@@ -306,7 +313,7 @@ stage3_kernel(const Stage3Args a) {
       T q1 = 0, q2 = 0, q3 = 0, q4 = 0;
 #pragma unroll 4
       for (int m = 0; m < Np; ++m) {
-        const T im = __ldg(gIT + m * Nc + cpt);
+        const T im = L::IP_SMEM ? gIT[m * Nc + cpt] : __ldg(gIT + m * Nc + cpt);
         q1 = fma3(im, q[m], q1);
         q2 = fma3(im, q[Np + m], q2);
         q3 = fma3(im, q[2 * Np + m], q3);
@@ -336,7 +343,7 @@ stage3_kernel(const Stage3Args a) {
       const T *nt = snt + e_loc * 6 * Nc;
 #pragma unroll 5
       for (int cpt = 0; cpt < Nc; ++cpt) {
-        const T pc = __ldg(gPT + cpt * Np + n_loc);
+        const T pc = L::IP_SMEM ? gPT[cpt * Np + n_loc] : __ldg(gPT + cpt * Np + n_loc);
 #pragma unroll
         for (int f = 0; f < 6; ++f) rhs[4 + f] = fma3(pc, nt[f * Nc + cpt], rhs[4 + f]);
       }
@@ -387,7 +394,7 @@ stage3_kernel(const Stage3Args a) {
 template <typename T, int N>
 static size_t stage3_smem() {
   typedef Dim3<N> D;
-  typedef Op3<N> L;
+  typedef Op3<T, N> L;
   constexpr int E = Tile3<T, N>::E;
   return sizeof(T) * (size_t)L::SmemSize + sizeof(int) * (size_t)((L::TabInts + 3) & ~3) +
          sizeof(T) * (size_t)E * (D::NQ + 10 * D::NFN + 6 * D::Nc + GEO3);
@@ -530,7 +537,7 @@ int launch_cast3(double *d, float *f, int64_t K, int Np, bool to_float, void *st
 template <typename T, int N>
 static void fill3(const RefOps3 &R, std::vector<T> &h) {
   typedef Dim3<N> D;
-  typedef Op3<N> L;
+  typedef Op3<T, N> L;
   const int Np = D::Np, NFN = D::NFN, Nc = D::Nc;
   h.assign(L::Size, (T)0);
   for (int n = 0; n < Np; ++n)
