@@ -229,6 +229,23 @@ def bytes_per_step(K, N, nv, elem_bytes):
 # ---------------------------------------------------------------------------
 # environment helpers
 # ---------------------------------------------------------------------------
+def max_over_ranks(dist, x, device='cuda'):
+    """The largest value of x over the ranks (the job's timed region ends when the
+    slowest replica ends); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world_size, units_per_rank, seconds):
+    """Whole-job throughput of independent replicas: every rank processes the same
+    units (weak scaling), divided by the max-over-ranks time."""
+    return world_size * units_per_rank / seconds
+
+
 def dist_env():
     ws = int(os.environ.get('WORLD_SIZE', '1'))
     rank = int(os.environ.get('RANK', '0'))
@@ -432,14 +449,6 @@ def run_ours(args):
                                  warps=s.launch_config())
     clocks = sampler.summary()
 
-    # max over ranks of the timed region
-    def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device='cuda')
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     K = results['mixed']['solver'].K
     nv = results['mixed']['solver'].nv
     dof = K * Np * 6
@@ -447,9 +456,9 @@ def run_ours(args):
     out = {}
     for name in ('mixed', 'fp64'):
         r = results[name]
-        ms = max_over_ranks(r['ms'])
+        ms = max_over_ranks(dist, r['ms'])
         stage_ms = float(sum(r['kernel_ms'][:4]))
-        v = ws * dof * 4 * args.steps / (ms / 1e3)
+        v = aggregate_rate(ws, dof * 4 * args.steps, ms / 1e3)
         ebytes = 4 if name == 'mixed' else 8
         if name == 'mixed':
             alg = bytes_per_step(K, W['N'], nv, ebytes) * args.steps
@@ -495,9 +504,9 @@ def run_ours(args):
     s.set_fields(pin_in, 0.0)
     s.step(results['mixed']['dt'], args.steps)
     s.fields(out=pin_out)
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(dist, time.perf_counter() - t0)
     nbytes = q0.nbytes
-    e2e = {'value': ws * dof * 4 * args.steps / e2e_s, 'unit': 'DOF-stage updates/s',
+    e2e = {'value': aggregate_rate(ws, dof * 4 * args.steps, e2e_s), 'unit': 'DOF-stage updates/s',
            'h2d_bytes_per_step': nbytes / args.steps, 'd2h_bytes_per_step': nbytes / args.steps,
            'note': 'gb_set_fields (pinned host FP64 state) + gb_step x K + gb_fields (pinned host), wall clock'}
 
