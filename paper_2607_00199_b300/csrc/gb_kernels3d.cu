@@ -53,11 +53,15 @@ struct Op3 {
   static constexpr int DtT = DsT + D::Np * D::Np;
   static constexpr int LiftT = DtT + D::Np * D::Np;       // [j][n] = LIFT[n][j]
   static constexpr int Bary = LiftT + D::NFN * D::Np;     // [n][4]
-  static constexpr int IT = Bary + 4 * D::Np;             // [m][c] = I[c][m]
+  static constexpr int IT = Bary + 4 * D::Np;             // [m][c] = I[c][m]; row-major I[c][m] when IP_SMEM
   static constexpr int PT = IT + D::Np * D::Nc;           // [c][n] = P[n][c]
   static constexpr int Size = PT + D::Nc * D::Np;
   static constexpr int SmemSize = IP_SMEM ? Size : IT;    // staged in shared memory
   static constexpr int TabInts = 4 * 4 * 6 * D::Nfp + 4 * D::Nfp;   // neighbour node table, fmask
+  // shared-memory path: cubature points per work item, nodes per projection item, vector widths
+  static constexpr int CPI = N == 3 ? 5 : (N == 2 ? 4 : 2);
+  static constexpr int NG = D::Np % 4 == 0 ? 4 : (D::Np % 2 == 0 ? 2 : 1);
+  static_assert(!IP_SMEM || D::Nc % CPI == 0, "cubature points must split evenly into work items");
 };
 
 // geometry block per element (in T): G^-1 (9, row-major r_x r_y r_z s_x ... t_z),
@@ -158,6 +162,16 @@ stage3_kernel(const Stage3Args a) {
   const T *gIT = (L::IP_SMEM ? sops : gops) + L::IT;
   const T *gPT = (L::IP_SMEM ? sops : gops) + L::PT;
 
+  // this stage's SARK coefficients of the two field classes, converted once per thread
+  T kE[2], kA0[2], kA1[2], kB0[2], kB1[2];
+#pragma unroll
+  for (int cl = 0; cl < 2; ++cl) {
+    kE[cl] = (T)a.co.E[cl][STAGE < 0 ? 0 : (STAGE < 3 ? STAGE + 1 : 4)];
+    kA0[cl] = (T)(STAGE == 0 ? a.co.A[cl][4] : STAGE == 1 ? a.co.A[cl][8] : STAGE == 2 ? a.co.A[cl][12] : 0.0);
+    kA1[cl] = (T)(STAGE == 1 ? a.co.A[cl][9] : STAGE == 2 ? a.co.A[cl][14] : 0.0);
+    kB0[cl] = (T)(STAGE == 1 ? a.co.B[cl][0] : STAGE == 2 ? a.co.B[cl][2] : STAGE == 3 ? a.co.B[cl][3] : 0.0);
+    kB1[cl] = (T)a.co.B[cl][1];
+  }
   const T *qin = reinterpret_cast<const T *>(a.qin);
   const int e_loc = tid / Np, n_loc = tid - (tid / Np) * Np;
   const bool node_thread = e_loc < E;
@@ -306,6 +320,54 @@ stage3_kernel(const Stage3Args a) {
     }
     // ---- cubature: q1..q4 at the points, Ntilde there ----
     const T itau = (T)a.inv_tau;
+    if constexpr (L::IP_SMEM) {
+      // item = (element, group of CPI points): q1..q4 of the element in registers, one row of
+      // I per point, so every operator load feeds four FMAs
+      constexpr int CPI = L::CPI, NPG = Nc / CPI;
+      for (int item = tid; item < E * NPG; item += nthr) {
+        const int e = item / NPG, c0 = (item - NPG * (item / NPG)) * CPI;
+        if (e >= nel) continue;
+        const T *q = sq + e * NQ;
+        T qr4[4][Np];
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+          for (int m = 0; m < Np; ++m) qr4[f][m] = q[f * Np + m];
+#pragma unroll 1
+        for (int k = 0; k < CPI; ++k) {
+          const int cpt = c0 + k;
+          const T *irow = sops + L::IT + cpt * Np;
+          T im[Np];
+          if constexpr (Np % 4 == 0) {   // 16-byte rows: conflict-free vector loads
+#pragma unroll
+            for (int m = 0; m < Np; m += 4) {
+              const float4 v = *reinterpret_cast<const float4 *>(irow + m);
+              im[m] = v.x; im[m + 1] = v.y; im[m + 2] = v.z; im[m + 3] = v.w;
+            }
+          } else {
+#pragma unroll
+            for (int m = 0; m < Np; ++m) im[m] = irow[m];
+          }
+          T q1 = 0, q2 = 0, q3 = 0, q4 = 0;
+#pragma unroll
+          for (int m = 0; m < Np; ++m) {
+            q1 = fma3(im[m], qr4[0][m], q1);
+            q2 = fma3(im[m], qr4[1][m], q2);
+            q3 = fma3(im[m], qr4[2][m], q3);
+            q4 = fma3(im[m], qr4[3][m], q4);
+          }
+          q1 += (T)1;
+          const T r1 = itau / q1, rs = r1 * ISQ2;
+          T *nt = snt + e * 6 * Nc + cpt;
+          nt[0] = q2 * q3 * r1;
+          nt[Nc] = q2 * q4 * r1;
+          nt[2 * Nc] = q3 * q4 * r1;
+          nt[3 * Nc] = q2 * q2 * rs;
+          nt[4 * Nc] = q3 * q3 * rs;
+          nt[5 * Nc] = q4 * q4 * rs;
+        }
+      }
+    } else
     for (int item = tid; item < E * Nc; item += nthr) {
       const int e = item / Nc, cpt = item - Nc * (item / Nc);
       if (e >= nel) continue;
@@ -313,7 +375,7 @@ stage3_kernel(const Stage3Args a) {
       T q1 = 0, q2 = 0, q3 = 0, q4 = 0;
 #pragma unroll 4
       for (int m = 0; m < Np; ++m) {
-        const T im = L::IP_SMEM ? gIT[m * Nc + cpt] : __ldg(gIT + m * Nc + cpt);
+        const T im = __ldg(gIT + m * Nc + cpt);
         q1 = fma3(im, q[m], q1);
         q2 = fma3(im, q[Np + m], q2);
         q3 = fma3(im, q[2 * Np + m], q3);
@@ -331,6 +393,40 @@ stage3_kernel(const Stage3Args a) {
     }
     __syncthreads();
 
+    // ---- projection P Ntilde (shared-memory path): item = (element, group of NG nodes,
+    //      field), written over the element's field tile (no longer needed) ----
+    T *sproj = sq;   // [E][6][Np]
+    if constexpr (L::IP_SMEM) {
+      constexpr int NG = L::NG, NGR = Np / NG;
+      for (int item = tid; item < E * NGR * 6; item += nthr) {
+        const int f = item % 6, rest = item / 6, gq = rest % NGR, e = rest / NGR;
+        if (e >= nel) continue;
+        const T *nt = snt + e * 6 * Nc + f * Nc;
+        const T *pc = sops + L::PT + gq * NG;
+        T acc[NG];
+#pragma unroll
+        for (int i = 0; i < NG; ++i) acc[i] = 0;
+#pragma unroll 5
+        for (int cpt = 0; cpt < Nc; ++cpt) {
+          const T nv = nt[cpt];
+          if constexpr (NG == 4) {
+            const float4 pv = *reinterpret_cast<const float4 *>(pc + cpt * Np);
+            acc[0] = fma3(pv.x, nv, acc[0]);
+            acc[1] = fma3(pv.y, nv, acc[1]);
+            acc[2] = fma3(pv.z, nv, acc[2]);
+            acc[3] = fma3(pv.w, nv, acc[3]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < NG; ++i) acc[i] = fma3(pc[cpt * Np + i], nv, acc[i]);
+          }
+        }
+        T *o = sproj + e * 6 * Np + f * Np + gq * NG;
+#pragma unroll
+        for (int i = 0; i < NG; ++i) o[i] = acc[i];
+      }
+      __syncthreads();
+    }
+
     // ---- lift, projection, SARK update ----
     if (node_thread && e_loc < nel) {
       const T *fl = sflux + e_loc * 10 * NFN;
@@ -340,12 +436,17 @@ stage3_kernel(const Stage3Args a) {
 #pragma unroll
         for (int f = 0; f < 10; ++f) rhs[f] = fma3(lj, fl[f * NFN + j], rhs[f]);
       }
-      const T *nt = snt + e_loc * 6 * Nc;
-#pragma unroll 5
-      for (int cpt = 0; cpt < Nc; ++cpt) {
-        const T pc = L::IP_SMEM ? gPT[cpt * Np + n_loc] : __ldg(gPT + cpt * Np + n_loc);
+      if constexpr (L::IP_SMEM) {
 #pragma unroll
-        for (int f = 0; f < 6; ++f) rhs[4 + f] = fma3(pc, nt[f * Nc + cpt], rhs[4 + f]);
+        for (int f = 0; f < 6; ++f) rhs[4 + f] += sproj[e_loc * 6 * Np + f * Np + n_loc];
+      } else {
+        const T *nt = snt + e_loc * 6 * Nc;
+#pragma unroll 5
+        for (int cpt = 0; cpt < Nc; ++cpt) {
+          const T pc = __ldg(gPT + cpt * Np + n_loc);
+#pragma unroll
+          for (int f = 0; f < 6; ++f) rhs[4 + f] = fma3(pc, nt[f * Nc + cpt], rhs[4 + f]);
+        }
       }
       const int64_t base = (elem0 + e_loc) * NQ + n_loc;
       const T dt = (T)a.dt;
@@ -365,20 +466,20 @@ stage3_kernel(const Stage3Args a) {
           const int64_t idx = base + f * Np;
           const T r = rhs[f];
           if (STAGE == 0) {
-            const T qv = sq[e_loc * NQ + f * Np + n_loc];
+            const T qv = L::IP_SMEM ? qin[idx] : sq[e_loc * NQ + f * Np + n_loc];   // stage 0: qin is q_n
             F0[idx] = r;
-            qout[idx] = (T)a.co.E[cl][1] * qv + dt * ((T)a.co.A[cl][4] * r);
+            qout[idx] = kE[cl] * qv + dt * (kA0[cl] * r);
           } else if (STAGE == 1) {
             const T qv = qn[idx], f0 = F0[idx];
-            qout[idx] = (T)a.co.E[cl][2] * qv + dt * ((T)a.co.A[cl][8] * f0 + (T)a.co.A[cl][9] * r);
-            acc[idx] = (T)a.co.B[cl][0] * f0 + (T)a.co.B[cl][1] * r;
+            qout[idx] = kE[cl] * qv + dt * (kA0[cl] * f0 + kA1[cl] * r);
+            acc[idx] = kB0[cl] * f0 + kB1[cl] * r;
           } else if (STAGE == 2) {
             const T qv = qn[idx], f0 = F0[idx], ac = acc[idx];
-            qout[idx] = (T)a.co.E[cl][3] * qv + dt * ((T)a.co.A[cl][12] * f0 + (T)a.co.A[cl][14] * r);
-            acc[idx] = ac + (T)a.co.B[cl][2] * r;
+            qout[idx] = kE[cl] * qv + dt * (kA0[cl] * f0 + kA1[cl] * r);
+            acc[idx] = ac + kB0[cl] * r;
           } else {
             const T qv = qn[idx], ac = acc[idx];
-            const T out = (T)a.co.E[cl][4] * qv + dt * (ac + (T)a.co.B[cl][3] * r);
+            const T out = kE[cl] * qv + dt * (ac + kB0[cl] * r);
             qout[idx] = out;
             bad |= bad3(out);
           }
@@ -551,7 +652,7 @@ static void fill3(const RefOps3 &R, std::vector<T> &h) {
   for (int n = 0; n < Np; ++n)
     for (int v = 0; v < 4; ++v) h[L::Bary + 4 * n + v] = (T)R.bary[n * 4 + v];
   for (int q = 0; q < Nc; ++q)
-    for (int m = 0; m < Np; ++m) h[L::IT + m * Nc + q] = (T)R.I[q * Np + m];
+    for (int m = 0; m < Np; ++m) h[L::IT + (L::IP_SMEM ? q * Np + m : m * Nc + q)] = (T)R.I[q * Np + m];
   for (int n = 0; n < Np; ++n)
     for (int q = 0; q < Nc; ++q) h[L::PT + q * Np + n] = (T)R.P[n * Nc + q];
 }
