@@ -793,6 +793,7 @@ int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int 
       a.qout = bufs_out[st];
       a.F0 = s->d_F0;
       a.acc = s->d_acc;
+      gb::set_mixed_coefs(a);
       g->h_args[(size_t)st * g->capacity + r] = a;
     }
     tstart[r + 1] = tstart[r] + (s->K + 15) / 16;

@@ -95,6 +95,9 @@ struct StageArgs {
   int warps_per_cta;           // GB_MIXED launch shape (1, 2 or 4; 0 = 4), chosen by the tuner
   double rhs_time;             // rhs-only mode: evaluate the grid velocity at this time
   SarkCoef co;
+  // GB_MIXED: this stage's SARK coefficients in FP32 per field class (E, A_a, A_b, B_a, B_b,
+  // see set_mixed_coefs), so that the kernel converts nothing from FP64
+  float kco[2][5];
 };
 
 // Several requests (solvers) of one order stepped by one launch per stage:
@@ -121,6 +124,7 @@ int launch_nodes(int N, const double *ops, const double *xn, const MeshRec *mesh
 int launch_relayout(const void *canon_src, void *canon_dst, bool canon_is_double, bool to_internal, float *inner,
                     const int32_t *perm, int64_t K, int Np, int S, double rest, void *stream);
 int mixed_stride(int N);   // element stride (floats) of the GB_MIXED field layout
+void set_mixed_coefs(StageArgs &a);   // fill a.kco from a.co and a.stage (host)
 // integrals over the mesh at the current vertices: out[0] = int rho, out[1] = int rho |u|^2 / 2,
 // out[2] = int rho u, out[3] = int rho v, out[4] = area; fields of element e at
 // q[e * stride + f * Np + n] (+ 1 on field 1 when perturbation), FP64 or FP32

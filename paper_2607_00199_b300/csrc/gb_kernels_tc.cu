@@ -12,7 +12,9 @@
 // A warp owns a tile of 16 elements (the M dimension of every product):
 //   rows = elements, columns = nodes / face nodes / cubature points.
 // The reference operators are constant B operands, pre-split and stored in
-// shared memory in per-lane fragment order (one 16-byte load per fragment).
+// per-lane fragment order (one 16-byte load per fragment), read through the L1
+// cache: a copy in every CTA's shared memory measured 3% slower (it cost 20 KB
+// per CTA and a staging pass at every launch).
 // The cubature chain reuses the accumulator fragment of I q directly as the A
 // fragment of P Ntilde: the 8 columns of a chunk are taken in the order
 // (0,2,4,6,1,3,5,7), which is folded into the P table.
@@ -137,7 +139,7 @@ __device__ __forceinline__ void load_a(const float *tile, int col0, int ncol, in
 // tile this warp takes next in the same request (prefetched towards L2).
 template <int N, int STAGE>
 __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_t next_tile, double gfac, double xfac,
-                                        const float4 *btab, float *own, float *trc, float *geo,
+                                        const float4 *__restrict__ btab, float *own, float *trc, float *geo,
                                         const float (&bl)[TcDim<N>::NT][2][3], int lane) {
   typedef TcDim<N> D;
   constexpr int Np = D::Np, Nfp = D::Nfp, NFN = D::NFN, KS = D::KS, KF = D::KF, NT = D::NT, CH = D::CH;
@@ -248,7 +250,7 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
           for (int j = 0; j < 4; ++j) qc[f][j] = 0.0f;
 #pragma unroll
         for (int ks = 0; ks < KS; ++ks) {
-          const float4 b = btab[(D::B_I + ch * KS + ks) * 32 + lane];
+          const float4 b = __ldg(btab + (D::B_I + ch * KS + ks) * 32 + lane);
 #pragma unroll
           for (int f = 0; f < 3; ++f) mma_tf32(qc[f], ql[f][ks], __float_as_uint(b.z), __float_as_uint(b.w));
 #pragma unroll
@@ -273,7 +275,7 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
         }
         float4 bp[NT];
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) bp[nt] = btab[(D::B_P + ch * NT + nt) * 32 + lane];
+        for (int nt = 0; nt < NT; ++nt) bp[nt] = __ldg(btab + (D::B_P + ch * NT + nt) * 32 + lane);
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
@@ -326,8 +328,8 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
         float4 br[NT], bs[NT];
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt) {
-          br[nt] = btab[(D::B_DR + ks * NT + nt) * 32 + lane];
-          bs[nt] = btab[(D::B_DS + ks * NT + nt) * 32 + lane];
+          br[nt] = __ldg(btab + (D::B_DR + ks * NT + nt) * 32 + lane);
+          bs[nt] = __ldg(btab + (D::B_DS + ks * NT + nt) * 32 + lane);
         }
         // split terms outermost: consecutive products go to independent accumulators
 #pragma unroll
@@ -457,7 +459,7 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
         for (int ff = 0; ff < 3; ++ff) load_a<ST>(trc, (fg + ff) * FJ + kf * 8, (fg + ff) * FJ + NFN, g, t, ahi[ff], alo[ff]);
         float4 bq[NT];
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) bq[nt] = btab[(D::B_LIFT + kf * NT + nt) * 32 + lane];
+        for (int nt = 0; nt < NT; ++nt) bq[nt] = __ldg(btab + (D::B_LIFT + kf * NT + nt) * 32 + lane);
 #pragma unroll
         for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
@@ -488,17 +490,18 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
     __syncwarp();
     {
       const float dt = (float)a.dt;
-      // lane slots w = lane + 32 sl of each element's 6 Np values; class 0 for fields 1..3
+      // lane slots w = lane + 32 sl of each element's 6 Np values; class 0 for fields 1..3;
+      // the coefficients arrive in FP32 (set_mixed_coefs)
       constexpr int NSL = (6 * Np + 31) / 32;
       float E1[NSL], A0[NSL], A1[NSL], Bc[NSL], B1[NSL];
 #pragma unroll
       for (int sl = 0; sl < NSL; ++sl) {
         const int cl = (lane + 32 * sl) < 3 * Np ? 0 : 1;
-        E1[sl] = (float)a.co.E[cl][STAGE < 0 ? 0 : (STAGE < 3 ? STAGE + 1 : 4)];
-        A0[sl] = STAGE == 0 ? (float)a.co.A[cl][4] : STAGE == 1 ? (float)a.co.A[cl][8] : STAGE == 2 ? (float)a.co.A[cl][12] : 0.0f;
-        A1[sl] = STAGE == 1 ? (float)a.co.A[cl][9] : STAGE == 2 ? (float)a.co.A[cl][14] : 0.0f;
-        Bc[sl] = STAGE == 1 ? (float)a.co.B[cl][0] : STAGE == 2 ? (float)a.co.B[cl][2] : STAGE == 3 ? (float)a.co.B[cl][3] : 0.0f;
-        B1[sl] = (float)a.co.B[cl][1];
+        E1[sl] = a.kco[cl][0];
+        A0[sl] = a.kco[cl][1];
+        A1[sl] = a.kco[cl][2];
+        Bc[sl] = a.kco[cl][3];
+        B1[sl] = a.kco[cl][4];
       }
       bool bad = false;
       float *Fo = reinterpret_cast<float *>(a.Fout);
@@ -613,13 +616,9 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_k
   typedef TcDim<N> D;
   const int W = blockDim.x >> 5;                // warps per CTA: a launch parameter (1, 2 or 4)
   extern __shared__ float4 tc_smem4[];
-  float4 *btab = tc_smem4;                                          // [NSETS][32]
-  float *wbase = reinterpret_cast<float *>(tc_smem4 + D::NSETS * 32);
+  const float4 *btab = reinterpret_cast<const float4 *>(a.ops);     // [NSETS][32], read through L1
+  float *wbase = reinterpret_cast<float *>(tc_smem4);
   __shared__ double s_motion[2];
-  {
-    const float4 *g4 = reinterpret_cast<const float4 *>(a.ops);
-    for (int i = threadIdx.x; i < D::NSETS * 32; i += blockDim.x) btab[i] = g4[i];
-  }
   if (threadIdx.x == 0) {
     double gf, xf, fin;
     tc_stage_motion<STAGE>(a, gf, xf, fin);
@@ -649,13 +648,8 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_group_k
   typedef TcDim<N> D;
   constexpr int W = D::W;
   extern __shared__ float4 tc_smem4[];
-  float4 *btab = tc_smem4;
-  float *wbase = reinterpret_cast<float *>(tc_smem4 + D::NSETS * 32);
-  {
-    const float4 *g4 = reinterpret_cast<const float4 *>(gd.ops);
-    for (int i = threadIdx.x; i < D::NSETS * 32; i += blockDim.x) btab[i] = g4[i];
-  }
-  __syncthreads();
+  const float4 *btab = reinterpret_cast<const float4 *>(gd.ops);
+  float *wbase = reinterpret_cast<float *>(tc_smem4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float *own = wbase + warp * D::WARP_FLOATS;
   float *trc = own + 16 * D::S;
@@ -688,11 +682,28 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_group_k
 template <int N>
 static size_t tc_smem(int W = TcDim<N>::W) {
   typedef TcDim<N> D;
-  return sizeof(float4) * (size_t)D::NSETS * 32 + sizeof(float) * (size_t)W * D::WARP_FLOATS;
+  return sizeof(float) * (size_t)W * D::WARP_FLOATS;
+}
+
+// The stage's SARK coefficients for the mixed kernel, in FP32, per field class:
+// E_{i+1} (E at the final stage), the two atilde of the stage combination, and the two
+// btilde weights of the running accumulator (Sec. 4); stage -1 (rhs only) uses none.
+void set_mixed_coefs(StageArgs &a) {
+  for (int cl = 0; cl < 2; ++cl) {
+    const int s = a.stage;
+    const double *E = a.co.E[cl], *A = a.co.A[cl], *B = a.co.B[cl];
+    a.kco[cl][0] = (float)(s < 0 ? E[0] : (s < 3 ? E[s + 1] : E[4]));
+    a.kco[cl][1] = (float)(s == 0 ? A[4] : s == 1 ? A[8] : s == 2 ? A[12] : 0.0);
+    a.kco[cl][2] = (float)(s == 1 ? A[9] : s == 2 ? A[14] : 0.0);
+    a.kco[cl][3] = (float)(s == 1 ? B[0] : s == 2 ? B[2] : s == 3 ? B[3] : 0.0);
+    a.kco[cl][4] = (float)B[1];
+  }
 }
 
 template <int N, int STAGE>
-static int tc_launch_one(const StageArgs &a, cudaStream_t st, int num_sms) {
+static int tc_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
+  StageArgs a = a_in;
+  set_mixed_coefs(a);
   typedef TcDim<N> D;
   const int W = (a.warps_per_cta == 1 || a.warps_per_cta == 2) ? a.warps_per_cta : D::W;
   const size_t smem = tc_smem<N>(W);
