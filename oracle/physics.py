@@ -12,6 +12,10 @@ Reading of (Ma, Re) (the paper only states nu = tau RT): lengths and the
 reference velocity are 1 and rho0 = 1, so c = sqrt(RT) = 1/Ma, nu = 1/Re and
 tau = nu / RT = Ma^2 / Re.
 
+Reading of the wall condition (paper silent): bounce-back of the particle velocities about
+the wall velocity, `wall_ghost`.  Far field (the paper's PML equations are not given):
+the free-stream equilibrium as the exterior state of the upwind flux.
+
 Reading of the initial non-equilibrium moments (not stated in the paper): q4..q6
 start at their equilibrium values q2 q3/q1, q2^2/(sqrt2 q1), q3^2/(sqrt2 q1).
 """
@@ -94,3 +98,24 @@ def equilibrium_state(rho, u, v, c):
 def macroscopic(q, c):
     """(rho, rho u, rho v) from q (fields on the last axis)."""
     return q[..., 0], c * q[..., 1], c * q[..., 2]
+
+
+def wall_ghost(q, wx, wy):
+    """Ghost state of a wall moving with velocity (wx, wy) c (reading; the paper gives no wall
+    condition): the particle velocities are reflected about the wall velocity, xi -> 2 u_w - xi
+    (bounce-back).  With zeta = xi / c the Hermite moments (Sec. 2 definitions:
+    q2 = E[zeta_x], q4 = E[zeta_x zeta_y], q5 = (E[zeta_x^2] - rho)/sqrt2, ...) of the reflected
+    density follow in closed form:
+      q1+ = q1,  q2+ = 2 wx q1 - q2,  q3+ = 2 wy q1 - q3,
+      q4+ = q4 + 4 wx wy q1 - 2 wx q3 - 2 wy q2,
+      q5+ = q5 + 2 sqrt2 (wx^2 q1 - wx q2),  q6+ = q6 + 2 sqrt2 (wy^2 q1 - wy q3).
+    Fields on the last axis; wx, wy broadcast against q[..., 0]."""
+    q1, q2, q3, q4, q5, q6 = (q[..., k] for k in range(6))
+    out = np.empty_like(q)
+    out[..., 0] = q1
+    out[..., 1] = 2.0 * wx * q1 - q2
+    out[..., 2] = 2.0 * wy * q1 - q3
+    out[..., 3] = q4 + 4.0 * wx * wy * q1 - 2.0 * wx * q3 - 2.0 * wy * q2
+    out[..., 4] = q5 + 2.0 * SQ2 * (wx * wx * q1 - wx * q2)
+    out[..., 5] = q6 + 2.0 * SQ2 * (wy * wy * q1 - wy * q3)
+    return out

@@ -49,23 +49,27 @@ _DLAM_DS = np.array([-0.5, 0.0, 0.5])
 
 
 class Motion:
-    """Prescribed vertex displacement d(X, t) = A sin(2 pi t/T) sin(2 pi X/Lx) sin(2 pi Y/Ly),
-    the same for x and y (free-stream test of Sec. 7.1); A = 0 is a static mesh."""
+    """Prescribed vertex displacement d(X, t) = A sin(2 pi t/T) S(X).  kind 'sinxy': S(X) =
+    sin(2 pi X/Lx) sin(2 pi Y/Ly) for both x and y (free-stream test of Sec. 7.1); kind
+    'plunge': S = (0, 1), the rigid plunge h(t) = A sin(2 pi t/T) of the airfoil case (Sec. 7).
+    A = 0 is a static mesh."""
 
-    def __init__(self, A=0.0, T=1.0, Lx=2.0 * math.pi, Ly=2.0 * math.pi):
+    def __init__(self, A=0.0, T=1.0, Lx=2.0 * math.pi, Ly=2.0 * math.pi, kind='sinxy'):
         self.A, self.T, self.Lx, self.Ly = float(A), float(T), float(Lx), float(Ly)
+        self.kind = kind
+
+    def shape(self, X):
+        if self.kind == 'plunge':
+            return np.stack([np.zeros(X.shape[0]), np.ones(X.shape[0])], axis=1)
+        sxy = np.sin(2.0 * math.pi * X[:, 0] / self.Lx) * np.sin(2.0 * math.pi * X[:, 1] / self.Ly)
+        return np.stack([sxy, sxy], axis=1)
 
     def velocity(self, X, t):
         w = 2.0 * math.pi / self.T
-        amp = self.A * w * math.cos(w * t)
-        shape = np.sin(2.0 * math.pi * X[:, 0] / self.Lx) * np.sin(2.0 * math.pi * X[:, 1] / self.Ly)
-        v = (amp * shape)[:, None]
-        return np.concatenate([v, v], axis=1)
+        return self.A * w * math.cos(w * t) * self.shape(X)
 
     def displacement(self, X, t):
-        shape = np.sin(2.0 * math.pi * X[:, 0] / self.Lx) * np.sin(2.0 * math.pi * X[:, 1] / self.Ly)
-        d = (self.A * math.sin(2.0 * math.pi * t / self.T) * shape)[:, None]
-        return np.concatenate([d, d], axis=1)
+        return self.A * math.sin(2.0 * math.pi * t / self.T) * self.shape(X)
 
 
 class OracleSolver:
@@ -76,7 +80,7 @@ class OracleSolver:
     off (a test-only knob that makes the system linear).
     """
 
-    def __init__(self, mesh, N, Ma=None, Re=None, c=None, tau=None, motion=None):
+    def __init__(self, mesh, N, Ma=None, Re=None, c=None, tau=None, motion=None, far_state=(1.0, 1.0, 0.0)):
         self.ref = ReferenceElement(N)
         self.N = N
         if c is None:
@@ -89,6 +93,10 @@ class OracleSolver:
         self.L = np.asarray(mesh['L'], dtype=np.float64)
         self.K = self.EToV.shape[0]
         self.motion = motion if motion is not None else Motion(0.0)
+        # boundary faces (reading, see physics.wall_ghost): per face 0 interior or periodic,
+        # 1 wall, 2 far field with the free-stream equilibrium of far_state = (rho, u, v)
+        self.bc = np.asarray(mesh.get('bc', np.zeros((self.K, 3))), dtype=np.int64)
+        self.q_far = physics.equilibrium_state(*far_state, self.c)
         self._connect()
 
     # ---- mesh -----------------------------------------------------------
@@ -108,9 +116,11 @@ class OracleSolver:
         faces = {}
         for e in range(K):
             for f in range(3):
+                if self.bc[e, f]:
+                    continue
                 key = tuple(sorted((int(self.EToV[e, f]), int(self.EToV[e, (f + 1) % 3]))))
                 faces.setdefault(key, []).append((e, f))
-        self.nbr_elem = np.zeros((K, 3), dtype=np.int64)
+        self.nbr_elem = np.full((K, 3), -1, dtype=np.int64)
         self.nbr_face = np.zeros((K, 3), dtype=np.int64)
         for key, lst in faces.items():
             if len(lst) != 2:
@@ -120,16 +130,21 @@ class OracleSolver:
             self.nbr_elem[e2, f2], self.nbr_face[e2, f2] = e1, f1
         xn = self.node_coords(self.X)
         self.nbr_node = np.zeros((K, 3, Nfp), dtype=np.int64)
+        per = np.where(self.L > 0, self.L, 1.0)
+        scale = max(float(np.max(self.L)), float(np.ptp(self.X)))
         for e in range(K):
             for f in range(3):
                 e2, f2 = self.nbr_elem[e, f], self.nbr_face[e, f]
+                if e2 < 0:
+                    self.nbr_node[e, f] = ref.fmask[f]   # unused: the exterior state comes from the boundary condition
+                    continue
                 mine = xn[e, ref.fmask[f]]              # (Nfp, 2)
                 theirs = xn[e2, ref.fmask[f2]]
                 d = mine[:, None, :] - theirs[None, :, :]
-                d = d - self.L * np.round(d / self.L)
+                d = d - np.where(self.L > 0, self.L * np.round(d / per), 0.0)
                 dist = np.sqrt((d ** 2).sum(-1))
                 k2 = np.argmin(dist, axis=1)
-                if dist[np.arange(Nfp), k2].max() > 1e-8 * max(self.L):
+                if dist[np.arange(Nfp), k2].max() > 1e-8 * scale:
                     raise ValueError('face nodes of element %d face %d do not match' % (e, f))
                 self.nbr_node[e, f] = ref.fmask[f2][k2]
 
@@ -175,13 +190,20 @@ class OracleSolver:
         # surface term: LIFT of the upwind flux jump
         fm = np.concatenate(ref.fmask)                                      # (3 Nfp,)
         qM = q[:, :, fm].reshape(K, 6, 3, Nfp)
-        qP = q[self.nbr_elem[:, :, None], :, self.nbr_node]                 # (K, 3, Nfp, 6)
+        qP = q[np.maximum(self.nbr_elem, 0)[:, :, None], :, self.nbr_node]  # (K, 3, Nfp, 6)
+        vgf = vg[:, fm, :].reshape(K, 3, Nfp, 2)
+        wall = self.bc == 1
+        if wall.any():
+            qm_w = np.transpose(qM, (0, 2, 3, 1))[wall]                      # (nw, Nfp, 6)
+            qP[wall] = physics.wall_ghost(qm_w, vgf[wall][..., 0] / self.c, vgf[wall][..., 1] / self.c)
+        far = self.bc == 2
+        if far.any():
+            qP[far] = self.q_far
         qP = np.transpose(qP, (0, 3, 1, 2))
         dq = qP - qM
         An = (normals[..., 0, None, None] * physics.ATX + normals[..., 1, None, None] * physics.ATY)
         absAn = physics.abs_normal_matrix(normals[..., 0], normals[..., 1])  # (K, 3, 6, 6)
         fluxS = 0.5 * self.c * np.einsum('efgh,ehfk->egfk', absAn - An, dq)
-        vgf = vg[:, fm, :].reshape(K, 3, Nfp, 2)
         vn = vgf[..., 0] * normals[:, :, None, 0] + vgf[..., 1] * normals[:, :, None, 1]
         fluxA = np.maximum(vn, 0.0)[:, None, :, :] * dq
         flux = (fscale[:, None, :, None] * (fluxS + fluxA)).reshape(K, 6, 3 * Nfp)

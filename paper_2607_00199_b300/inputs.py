@@ -221,3 +221,84 @@ def channel_flow_3d(x, y, z, Ma, L=(8.0, 2.0, 2.0), eps=0.05):
     w = eps * np.cos(ax * x) * np.sin(ay * y)
     rho = 1.0 + Ma * Ma * eps * np.cos(ax * x) * np.cos(ay * y)
     return rho, u, v, w
+
+
+# ---- two dimensions with boundaries: O-grid around a symmetric airfoil ------------------
+
+BC_INTERIOR, BC_WALL, BC_FARFIELD = 0, 1, 2
+
+
+def naca4_thickness(x, t=0.12):
+    """Half-thickness of the symmetric NACA 4-digit section with the closed trailing edge
+    (x in [0, 1], chord 1): 5 t (0.2969 sqrt x - 0.1260 x - 0.3516 x^2 + 0.2843 x^3 - 0.1036 x^4)."""
+    x = np.asarray(x, dtype=np.float64)
+    return 5.0 * t * (0.2969 * np.sqrt(x) - 0.1260 * x - 0.3516 * x ** 2 + 0.2843 * x ** 3 - 0.1036 * x ** 4)
+
+
+def naca_ogrid_mesh(ni=256, nj=192, R=20.0, t=0.12, growth=1.02):
+    """O-grid of ni wrap-around x nj radial quads around the NACA 00xx section (chord 1,
+    leading edge at the origin), out to the circle of radius R about the mid-chord,
+    each quad split into two counter-clockwise triangles; K = 2 ni nj.
+
+    Surface point i sits at x = (1 + cos phi_i)/2, y = +-thickness (upper for
+    sin phi > 0), phi_i = 2 pi i / ni; radial line i runs straight to the circle point at
+    the same angle with geometric spacing (cell lengths grow by `growth` per cell).  Vertex id = i + ni j (i wraps around).  Returns the periodic-
+    mesh dict of periodic_square_mesh plus bc (K, 3): per face (face f from local vertex f
+    to f + 1) BC_WALL on the airfoil, BC_FARFIELD on the circle, BC_INTERIOR otherwise.
+    """
+    phi = 2.0 * math.pi * np.arange(ni) / ni
+    xs = (1.0 + np.cos(phi)) / 2.0
+    ys = np.sign(np.sin(phi)) * naca4_thickness(xs, t)
+    cx = 0.5 + R * np.cos(phi)
+    cy = R * np.sin(phi)
+    q = float(growth)
+    s = (q ** np.arange(nj + 1) - 1.0) / (q ** nj - 1.0) if q != 1.0 else np.linspace(0.0, 1.0, nj + 1)
+    X = np.zeros((ni * (nj + 1), 2))
+    for j in range(nj + 1):
+        X[j * ni:(j + 1) * ni, 0] = xs + (cx - xs) * s[j]
+        X[j * ni:(j + 1) * ni, 1] = ys + (cy - ys) * s[j]
+    vid = lambda i, j: (i % ni) + ni * j
+    tris, bcs = [], []
+    for j in range(nj):
+        for i in range(ni):
+            a, b, c, d = vid(i, j), vid(i + 1, j), vid(i + 1, j + 1), vid(i, j + 1)
+            for tri, fbc in (((a, b, c), (BC_WALL if j == 0 else 0, 0, 0)),
+                             ((a, c, d), (0, BC_FARFIELD if j == nj - 1 else 0, 0))):
+                P = X[list(tri)]
+                area2 = (P[1, 0] - P[0, 0]) * (P[2, 1] - P[0, 1]) - (P[2, 0] - P[0, 0]) * (P[1, 1] - P[0, 1])
+                if area2 < 0:   # reverse to counter-clockwise; face f runs from vertex f to f + 1
+                    tri = (tri[0], tri[2], tri[1])
+                    fbc = (fbc[2], fbc[1], fbc[0])
+                tris.append(tri)
+                bcs.append(fbc)
+    EToV = np.array(tris, dtype=np.int32)
+    return {'X': X, 'EToV': EToV, 'shift': np.zeros((EToV.shape[0], 3, 2)), 'L': np.array([0.0, 0.0]),
+            'bc': np.array(bcs, dtype=np.int8), 'dims': (ni, nj)}
+
+
+def wall_channel_mesh(nx, ny, Lx=1.0, Ly=1.0):
+    """Box [0, Lx] x [0, Ly] of nx x ny squares split along the (0,0)-(1,1) diagonal into
+    counter-clockwise triangles, walls at x = 0 and x = Lx, periodic in y; K = 2 nx ny.
+    Vertex id = i + (nx + 1) j, j wrapping.  Same dict as naca_ogrid_mesh (bc per face)."""
+    if ny < 3:
+        raise ValueError('ny >= 3 is needed for unique periodic vertex pairs')
+    hx, hy = Lx / nx, Ly / ny
+    X = np.zeros(((nx + 1) * ny, 2))
+    for j in range(ny):
+        for i in range(nx + 1):
+            X[i + (nx + 1) * j] = (i * hx, j * hy)
+    vid = lambda i, j: i + (nx + 1) * (j % ny)
+    tris, bcs, shifts = [], [], []
+    for j in range(ny):
+        for i in range(nx):
+            wrap = lambda jj: (jj // ny) * Ly
+            # (0,0),(1,0),(1,1): face 0 on y = const, face 1 on x = i + 1, face 2 the diagonal
+            tris.append((vid(i, j), vid(i + 1, j), vid(i + 1, j + 1)))
+            shifts.append(((0, wrap(j)), (0, wrap(j)), (0, wrap(j + 1))))
+            bcs.append((0, BC_WALL if i + 1 == nx else 0, 0))
+            # (0,0),(1,1),(0,1): face 0 the diagonal, face 1 on y = const, face 2 on x = i
+            tris.append((vid(i, j), vid(i + 1, j + 1), vid(i, j + 1)))
+            shifts.append(((0, wrap(j)), (0, wrap(j + 1)), (0, wrap(j + 1))))
+            bcs.append((0, 0, BC_WALL if i == 0 else 0))
+    return {'X': X, 'EToV': np.array(tris, dtype=np.int32), 'shift': np.array(shifts, dtype=np.float64),
+            'L': np.array([0.0, Ly]), 'bc': np.array(bcs, dtype=np.int8), 'dims': (nx, ny)}
