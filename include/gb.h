@@ -48,6 +48,11 @@ extern "C" {
 
 #define GB_MOTION_STATIC 0
 #define GB_MOTION_SINXY  1
+#define GB_MOTION_PLUNGE 2   /* rigid plunge: every vertex moves by (0, A sin(2 pi t / T)) */
+
+#define GB_BC_INTERIOR 0     /* face shared with another element (or its periodic copy) */
+#define GB_BC_WALL     1     /* wall moving with the mesh: bounce-back ghost state */
+#define GB_BC_FARFIELD 2     /* far field: the free-stream equilibrium as the exterior state */
 
 typedef struct gb_solver gb_solver;   /* opaque */
 
@@ -66,9 +71,11 @@ typedef struct {
 
 /* Prescribed grid motion (Sec. 5 and the free-stream test of Sec. 7.1):
  * GB_MOTION_SINXY displaces both coordinates of a vertex with Lagrangian
- * position X by A sin(2 pi t / T) sin(2 pi X / Lx) sin(2 pi Y / Ly). */
+ * position X by A sin(2 pi t / T) sin(2 pi X / Lx) sin(2 pi Y / Ly);
+ * GB_MOTION_PLUNGE moves every vertex by (0, A sin(2 pi t / T)) (the rigid plunge of
+ * the airfoil case of Sec. 7; Lx, Ly unused). */
 typedef struct {
-  int32_t kind;              /* GB_MOTION_STATIC or GB_MOTION_SINXY */
+  int32_t kind;              /* GB_MOTION_STATIC, GB_MOTION_SINXY or GB_MOTION_PLUNGE */
   double A, T, Lx, Ly;
 } gb_motion;
 
@@ -80,6 +87,21 @@ typedef struct {
  * at X, the time at 0, the motion static.  On success *out owns the solver. */
 int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision,
               void *cuda_stream, gb_solver **out);
+
+/* gb_create_bounded: gb_create for a 2D mesh with boundary faces (the plunging-airfoil
+ * O-grid of Sec. 7).  face_bc (host, n_elem x 3, face f running from local vertex f to
+ * f + 1) tags each face GB_BC_INTERIOR, GB_BC_WALL or GB_BC_FARFIELD; every interior face
+ * must be shared by exactly two elements (periodic copies allowed) and no boundary face
+ * may be.  far_state = (rho, u, v) of the free stream.  The paper gives neither condition;
+ * the library reads them as: at a wall the particle velocities are reflected about the
+ * wall velocity (the grid velocity at the face node), which maps the moments to
+ * q1+ = q1, q2+ = 2 wx q1 - q2, q3+ = 2 wy q1 - q3, q4+ = q4 + 4 wx wy q1 - 2 wx q3 - 2 wy q2,
+ * q5+ = q5 + 2 sqrt2 (wx^2 q1 - wx q2), q6+ = q6 + 2 sqrt2 (wy^2 q1 - wy q3) with
+ * (wx, wy) = v_G / c; at the far field the exterior state is the free-stream equilibrium
+ * (no perfectly matched layer).  Both enter the upwind flux as q+.  N in 1..4; groups
+ * reject such solvers; everything else as gb_create (dim = 2 only). */
+int gb_create_bounded(const gb_mesh *mesh, const int8_t *face_bc, const double *far_state, int N, double Ma,
+                      double Re, int precision, void *cuda_stream, gb_solver **out);
 
 /* gb_set_motion: prescribe the vertex velocity d/dt of the displacement above,
  * evaluated at the Lagrangian X (Sec. 5).  Copied; takes effect at the next step. */

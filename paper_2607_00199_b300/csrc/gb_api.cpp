@@ -57,6 +57,8 @@ struct gb_solver {
   int64_t *d_hctl = nullptr;   // steps since enabled, records written
   size_t tmp_bytes = 0;
   int64_t device_bytes = 0;
+  int has_bc = 0;              // the mesh has wall / far-field faces (gb_create_bounded)
+  double far[6] = {0, 0, 0, 0, 0, 0};   // far-field state in the kernels' representation
 };
 
 static std::string g_create_error;
@@ -144,8 +146,11 @@ static gb::StageArgs base_args(gb_solver *s) {
   a.period[1] = s->period[1];
   a.c = s->c;
   a.inv_tau = 1.0 / s->tau;
-  a.motion_A = (s->motion.kind == GB_MOTION_SINXY) ? s->motion.A : 0.0;
-  a.motion_w = (s->motion.kind == GB_MOTION_SINXY) ? 2.0 * M_PI / s->motion.T : 0.0;
+  const bool moving = s->motion.kind == GB_MOTION_SINXY || s->motion.kind == GB_MOTION_PLUNGE;
+  a.motion_A = moving ? s->motion.A : 0.0;
+  a.motion_w = moving ? 2.0 * M_PI / s->motion.T : 0.0;
+  a.bc = s->has_bc;
+  memcpy(a.far, s->far, sizeof(a.far));
   a.co = s->co;
   a.warps_per_cta = s->warps;
   return a;
@@ -274,7 +279,22 @@ static std::vector<int32_t> morton_order(const std::vector<double> &cx, const st
   return perm;
 }
 
+static int create2d(const gb_mesh *mesh, const int8_t *face_bc, const double *far_state, int N, double Ma, double Re,
+                    int precision, void *cuda_stream, gb_solver **out);
+
 extern "C" {
+
+int gb_create_bounded(const gb_mesh *mesh, const int8_t *face_bc, const double *far_state, int N, double Ma,
+                      double Re, int precision, void *cuda_stream, gb_solver **out) {
+  if (!out) return fail(nullptr, GB_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!mesh || !face_bc || !far_state) return fail(nullptr, GB_EINVAL, "mesh, face_bc or far_state is NULL");
+  if (mesh->dim != 2) return fail(nullptr, GB_EINVAL, "gb_create_bounded: dim must be 2");
+  if (N < 1 || N > 4) return fail(nullptr, GB_EINVAL, "gb_create_bounded: N must be in 1..4");
+  if (!(far_state[0] > 0.0) || !std::isfinite(far_state[0]) || !std::isfinite(far_state[1]) || !std::isfinite(far_state[2]))
+    return fail(nullptr, GB_EINVAL, "far_state must be finite with rho > 0");
+  return create2d(mesh, face_bc, far_state, N, Ma, Re, precision, cuda_stream, out);
+}
 
 int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, void *cuda_stream, gb_solver **out) {
   if (!out) return fail(nullptr, GB_EINVAL, "out is NULL");
@@ -302,7 +322,19 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
     *out = s;
     return GB_OK;
   }
+  return create2d(mesh, nullptr, nullptr, N, Ma, Re, precision, cuda_stream, out);
+}
 
+}  // extern "C"
+
+static int create2d(const gb_mesh *mesh, const int8_t *face_bc, const double *far_state, int N, double Ma, double Re,
+                    int precision, void *cuda_stream, gb_solver **out) {
+  if (!mesh->X || !mesh->EToV) return fail(nullptr, GB_EINVAL, "mesh, X or EToV is NULL");
+  if (mesh->n_vert <= 0 || mesh->n_elem <= 0) return fail(nullptr, GB_EINVAL, "empty mesh");
+  if (mesh->n_elem >= (int64_t(1) << 29)) return fail(nullptr, GB_EINVAL, "n_elem must be < 2^29");
+  if (!(Ma > 0.0) || !(Re > 0.0) || !std::isfinite(Ma) || !std::isfinite(Re))
+    return fail(nullptr, GB_EINVAL, "Ma and Re must be positive and finite");
+  if (precision != GB_FP64 && precision != GB_MIXED) return fail(nullptr, GB_EINVAL, "precision must be GB_FP64 or GB_MIXED");
   const int64_t K = mesh->n_elem, nv = mesh->n_vert;
   for (int64_t i = 0; i < 3 * K; ++i)
     if (mesh->EToV[i] < 0 || mesh->EToV[i] >= nv) return fail(nullptr, GB_EINVAL, "EToV entry out of range");
@@ -345,8 +377,16 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   // every unordered vertex pair must occur on exactly two faces
   std::unordered_map<uint64_t, int64_t> first;   // key -> 3 e + f of the first face, -1 once paired
   first.reserve((size_t)(3 * K));
+  int has_bc = 0;
   for (int64_t e = 0; e < K; ++e)
     for (int f = 0; f < 3; ++f) {
+      if (face_bc && face_bc[3 * e + f] != GB_BC_INTERIOR) {
+        const int b = face_bc[3 * e + f];
+        if (b != GB_BC_WALL && b != GB_BC_FARFIELD) return fail(nullptr, GB_EINVAL, "face_bc entries must be 0, 1 or 2");
+        rec[e].nbr[f] = -b;
+        has_bc = 1;
+        continue;
+      }
       uint64_t a = (uint32_t)rec[e].v[f], b = (uint32_t)rec[e].v[(f + 1) % 3];
       if (a == b) return fail(nullptr, GB_EMESH, "degenerate face (repeated vertex id)");
       uint64_t key = a < b ? (a << 32 | b) : (b << 32 | a);
@@ -372,7 +412,9 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
     }
   for (const auto &kv : first)
     if (kv.second >= 0)
-      return fail(nullptr, GB_EMESH, "the mesh is not closed: a face has no neighbour (only periodic meshes are supported)");
+      return fail(nullptr, GB_EMESH, face_bc ? "an interior face has no neighbour (tag boundary faces in face_bc)"
+                                             : "the mesh is not closed: a face has no neighbour (only periodic meshes are "
+                                               "supported by gb_create; see gb_create_bounded)");
 
   gb_solver *s = new gb_solver();
   s->N = N;
@@ -387,6 +429,14 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   s->period[1] = period[1];
   s->stream = (cudaStream_t)cuda_stream;
   s->elem_bytes = precision == GB_FP64 ? sizeof(double) : sizeof(float);
+  s->has_bc = has_bc;
+  if (far_state) {
+    // free-stream equilibrium (Sec. 2 maps; second moments at equilibrium), minus the rest
+    // state in the perturbation representation of GB_MIXED
+    const double rho = far_state[0], u2 = rho * far_state[1] / s->c, u3 = rho * far_state[2] / s->c;
+    const double q[6] = {rho, u2, u3, u2 * u3 / rho, u2 * u2 / (M_SQRT2 * rho), u3 * u3 / (M_SQRT2 * rho)};
+    for (int k = 0; k < 6; ++k) s->far[k] = q[k] - ((precision == GB_MIXED && k == 0) ? 1.0 : 0.0);
+  }
   if (!gb::build_reference(N, s->ref)) {
     delete s;
     return fail(nullptr, GB_EINVAL, "reference operator construction failed");
@@ -427,7 +477,7 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
       rec_int[i] = rec[perm[i]];
       for (int f = 0; f < 3; ++f) {
         const int32_t nb = rec_int[i].nbr[f];
-        rec_int[i].nbr[f] = (inv[nb >> 2] << 2) | (nb & 3);
+        if (nb >= 0) rec_int[i].nbr[f] = (inv[nb >> 2] << 2) | (nb & 3);
       }
     }
   }
@@ -477,13 +527,18 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   return GB_OK;
 }
 
+extern "C" {
+
 int gb_set_motion(gb_solver *s, const gb_motion *m) {
   if (!s || !m) return fail(s, GB_EINVAL, "NULL argument");
   if (s->s3) {
     if (m->kind != GB_MOTION_STATIC) return fail(s, GB_EINVAL, "dim = 3 solvers take gb_set_wave_motion (gb_set_motion accepts GB_MOTION_STATIC only)");
     return gb::s3_set_static(s->s3);
   }
-  if (m->kind != GB_MOTION_STATIC && m->kind != GB_MOTION_SINXY) return fail(s, GB_EINVAL, "unknown motion kind");
+  if (m->kind != GB_MOTION_STATIC && m->kind != GB_MOTION_SINXY && m->kind != GB_MOTION_PLUNGE)
+    return fail(s, GB_EINVAL, "unknown motion kind");
+  if (m->kind == GB_MOTION_PLUNGE && (!(m->T > 0.0) || !std::isfinite(m->A) || !std::isfinite(m->T)))
+    return fail(s, GB_EINVAL, "GB_MOTION_PLUNGE needs T > 0 and finite A");
   if (m->kind == GB_MOTION_SINXY) {
     if (!(m->T > 0.0) || !(m->Lx != 0.0) || !(m->Ly != 0.0) || !std::isfinite(m->A) || !std::isfinite(m->T))
       return fail(s, GB_EINVAL, "GB_MOTION_SINXY needs T > 0, Lx != 0, Ly != 0 and finite A");
@@ -768,6 +823,7 @@ int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int 
     gb_solver *s = solvers[r];
     if (!s) return gfail(GB_EINVAL, "gb_group_step: NULL solver");
     if (s->s3) return gfail(GB_EINVAL, "gb_group_step: dim = 3 solvers cannot be grouped");
+    if (s->has_bc) return gfail(GB_EINVAL, "gb_group_step: solvers with boundary faces cannot be grouped");
     if (s->precision != GB_MIXED) return gfail(GB_EINVAL, "gb_group_step: only GB_MIXED solvers can be grouped");
     if (s->N != N) return gfail(GB_EINVAL, "gb_group_step: all solvers of a group must have the same N");
     if (s->stream != g->stream) return gfail(GB_EINVAL, "gb_group_step: solvers must use the group's stream");

@@ -52,8 +52,9 @@ bool build_reference3d(int N, RefOps3 &R);
 void sark_coefficients(double gamma, double E[5], double A[16], double B[4]);
 
 // Per-element mesh record, 32 bytes: vertex ids, face neighbours packed as
-// (neighbour element << 2 | neighbour face), and periodic shifts of the three
-// vertices as signed multiples of the periods (x then y per vertex).
+// (neighbour element << 2 | neighbour face) or, for a boundary face, -1 (wall) or -2
+// (far field), and periodic shifts of the three vertices as signed multiples of the
+// periods (x then y per vertex).
 struct __attribute__((aligned(16))) MeshRec {
   int32_t v[3];
   int32_t nbr[3];
@@ -98,6 +99,11 @@ struct StageArgs {
   // GB_MIXED: this stage's SARK coefficients in FP32 per field class (E, A_a, A_b, B_a, B_b,
   // see set_mixed_coefs), so that the kernel converts nothing from FP64
   float kco[2][5];
+  // boundary faces (nbr < 0: -1 wall, -2 far field) present; far-field state q_inf in the
+  // field representation of the kernel (FP64 full state, or FP32 perturbation)
+  int bc;
+  double far[6];
+  float farf[6];
 };
 
 // Several requests (solvers) of one order stepped by one launch per stage:

@@ -111,7 +111,30 @@ __device__ __forceinline__ StageMotion stage_motion(const StageArgs &a) {
 // ---------------------------------------------------------------------------
 // the fused stage kernel
 // ---------------------------------------------------------------------------
-template <typename T, int N, int STAGE>
+// Exterior state of a boundary face node (reading; the paper states neither condition):
+// nb = -1 wall moving with the grid velocity (vgx, vgy) -- the particle velocities reflected
+// about it, in moments the affine map below with (wx, wy) = v_G / c; nb = -2 far field --
+// the free-stream equilibrium.  qm points at the node's field 1 value (stride Np); in the
+// perturbation representation q1 is 1 + qm[0] and the map is applied to the full state.
+template <typename T, int Np, bool PERTURB>
+__device__ __forceinline__ void boundary_state(int nb, const T *qm, T vgx, T vgy, T inv_c, const double *far, T (&qe)[6]) {
+  if (nb == -1) {
+    const T wx = vgx * inv_c, wy = vgy * inv_c;
+    const T q1 = qm[0] + (PERTURB ? (T)1 : (T)0), q2 = qm[Np], q3 = qm[2 * Np];
+    const T s2 = (T)2.8284271247461900976;   // 2 sqrt2
+    qe[0] = qm[0];
+    qe[1] = (T)2 * wx * q1 - q2;
+    qe[2] = (T)2 * wy * q1 - q3;
+    qe[3] = qm[3 * Np] + (T)4 * wx * wy * q1 - (T)2 * wx * q3 - (T)2 * wy * q2;
+    qe[4] = qm[4 * Np] + s2 * (wx * wx * q1 - wx * q2);
+    qe[5] = qm[5 * Np] + s2 * (wy * wy * q1 - wy * q3);
+  } else {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) qe[f] = (T)far[f];
+  }
+}
+
+template <typename T, int N, int STAGE, bool BC = false>
 __global__ void __launch_bounds__(((Tile<T, N>::E * Dim<N>::Np + 31) / 32) * 32)
 stage_kernel(const StageArgs a) {
   typedef Dim<N> D;
@@ -285,19 +308,26 @@ stage_kernel(const StageArgs a) {
       const int vol = fmask<N>(f, k);
       const MeshRec &rec = a.mesh[elem0 + e];
       const int nb = rec.nbr[f];
-      const int64_t e2 = nb >> 2;
-      const int f2 = nb & 3;
-      const int vol2 = fmask<N>(f2, Nfp - 1 - k);
-      const T *qp = qin + e2 * NQ + vol2;
       const T *qm = sq + e * NQ + vol;
-      T w[6];
-#pragma unroll
-      for (int fld = 0; fld < 6; ++fld) w[fld] = qp[fld * Np] - qm[fld * Np];
       const T *g = sgeo + e * GEO;
       const T *gf = g + 10 + 20 * f;
       const T l0 = sops[L::Bary + 3 * vol], l1 = sops[L::Bary + 3 * vol + 1], l2 = sops[L::Bary + 3 * vol + 2];
       const T vgx = l0 * g[4] + l1 * g[6] + l2 * g[8];
       const T vgy = l0 * g[5] + l1 * g[7] + l2 * g[9];
+      T w[6];
+      if (BC && nb < 0) {
+        T qe[6];
+        boundary_state<T, Np, PERTURB>(nb, qm, vgx, vgy, (T)(1.0 / a.c), a.far, qe);
+#pragma unroll
+        for (int fld = 0; fld < 6; ++fld) w[fld] = qe[fld] - qm[fld * Np];
+      } else {
+        const int64_t e2 = nb >> 2;
+        const int f2 = nb & 3;
+        const int vol2 = fmask<N>(f2, Nfp - 1 - k);
+        const T *qp = qin + e2 * NQ + vol2;
+#pragma unroll
+        for (int fld = 0; fld < 6; ++fld) w[fld] = qp[fld * Np] - qm[fld * Np];
+      }
       const T vn = vgx * gf[17] + vgy * gf[18];
       const T ale = vn > (T)0 ? vn * gf[19] : (T)0;
       const T M00 = gf[0], M03 = gf[1], M04 = gf[2], M05 = gf[3], M33 = gf[4], M34 = gf[5], M35 = gf[6];
@@ -408,20 +438,20 @@ static size_t stage_smem() {
   return sizeof(T) * (size_t)(OpLayout<N>::Size + E * (D::NQ + 6 * D::NFN + 3 * D::Nc + GEO));
 }
 
-template <typename T, int N, int STAGE>
+template <typename T, int N, int STAGE, bool BC>
 static int launch_one(const StageArgs &a, cudaStream_t st, int num_sms) {
   constexpr int E = Tile<T, N>::E;
   const int threads = ((E * Dim<N>::Np + 31) / 32) * 32;
   const size_t smem = stage_smem<T, N>();
   static bool attr_set = false;   // per template instance (one device per process assumed)
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(stage_kernel<T, N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(stage_kernel<T, N, STAGE, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     attr_set = true;
   }
   static int per_sm = 0;   // cached: no runtime queries while a graph is being captured
   if (per_sm == 0) {
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel<T, N, STAGE>, threads, smem);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel<T, N, STAGE, BC>, threads, smem);
     if (err != cudaSuccess) return (int)err;
   }
   if (per_sm < 1) per_sm = 1;
@@ -429,20 +459,30 @@ static int launch_one(const StageArgs &a, cudaStream_t st, int num_sms) {
   int64_t grid = (int64_t)num_sms * per_sm;
   if (grid > ntiles) grid = ntiles;
   if (grid < 1) grid = 1;
-  stage_kernel<T, N, STAGE><<<(unsigned)grid, threads, smem, st>>>(a);
+  stage_kernel<T, N, STAGE, BC><<<(unsigned)grid, threads, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
-template <typename T, int N>
-static int launch_stage_n(const StageArgs &a, cudaStream_t st, int num_sms) {
+template <typename T, int N, bool BC>
+static int launch_stage_nb(const StageArgs &a, cudaStream_t st, int num_sms) {
   switch (a.stage) {
-    case -1: return launch_one<T, N, -1>(a, st, num_sms);
-    case 0: return launch_one<T, N, 0>(a, st, num_sms);
-    case 1: return launch_one<T, N, 1>(a, st, num_sms);
-    case 2: return launch_one<T, N, 2>(a, st, num_sms);
-    case 3: return launch_one<T, N, 3>(a, st, num_sms);
+    case -1: return launch_one<T, N, -1, BC>(a, st, num_sms);
+    case 0: return launch_one<T, N, 0, BC>(a, st, num_sms);
+    case 1: return launch_one<T, N, 1, BC>(a, st, num_sms);
+    case 2: return launch_one<T, N, 2, BC>(a, st, num_sms);
+    case 3: return launch_one<T, N, 3, BC>(a, st, num_sms);
   }
   return (int)cudaErrorInvalidValue;
+}
+
+// meshes with boundary faces use the BC variant (orders 1..4)
+template <typename T, int N>
+static int launch_stage_n(const StageArgs &a, cudaStream_t st, int num_sms) {
+  if (a.bc) {
+    if constexpr (N <= 4) return launch_stage_nb<T, N, true>(a, st, num_sms);
+    return (int)cudaErrorInvalidValue;
+  }
+  return launch_stage_nb<T, N, false>(a, st, num_sms);
 }
 
 template <typename T>
@@ -488,8 +528,8 @@ __global__ void shape_kernel(const double *X, double *shape, int64_t nv, int kin
   for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < nv; v += (int64_t)gridDim.x * blockDim.x) {
     double s = 0.0;
     if (kind == GB_MOTION_SINXY) s = sin(two_pi * X[2 * v] / Lx) * sin(two_pi * X[2 * v + 1] / Ly);
-    shape[2 * v] = s;
-    shape[2 * v + 1] = s;
+    shape[2 * v] = kind == GB_MOTION_PLUNGE ? 0.0 : s;
+    shape[2 * v + 1] = kind == GB_MOTION_PLUNGE ? 1.0 : s;
   }
 }
 

@@ -134,10 +134,33 @@ __device__ __forceinline__ void load_a(const float *tile, int col0, int ncol, in
   split_tf32x2(make_float2(x2, x3), hi[2], lo[2], hi[3], lo[3]);
 }
 
+// Exterior state of a boundary face node, FP32 perturbation form (reading; see the FP64
+// kernel): nb = -1 wall moving with the grid velocity (vgx, vgy), the particle velocities
+// reflected about it (affine map of the moments with (wx, wy) = v_G / c, applied to the full
+// state q1 = 1 + qm[0]); nb = -2 far field, the free-stream equilibrium minus the rest state.
+template <int Np>
+__device__ __forceinline__ void tc_boundary_state(int nb, const float *qm, float vgx, float vgy, float inv_c,
+                                                  const float *farf, float (&qe)[6]) {
+  if (nb == -1) {
+    const float wx = vgx * inv_c, wy = vgy * inv_c;
+    const float q1 = 1.0f + qm[0], q2 = qm[Np], q3 = qm[2 * Np];
+    const float s2 = 2.8284271247461901f;   // 2 sqrt2
+    qe[0] = qm[0];
+    qe[1] = 2.0f * wx * q1 - q2;
+    qe[2] = 2.0f * wy * q1 - q3;
+    qe[3] = qm[3 * Np] + 4.0f * wx * wy * q1 - 2.0f * wx * q3 - 2.0f * wy * q2;
+    qe[4] = qm[4 * Np] + s2 * (wx * wx * q1 - wx * q2);
+    qe[5] = qm[5 * Np] + s2 * (wy * wy * q1 - wy * q3);
+  } else {
+#pragma unroll
+    for (int f = 0; f < 6; ++f) qe[f] = farf[f];
+  }
+}
+
 // One 16-element tile of one request: staging, geometry, volume, surface, cubature and the SARK
-// combination.  gfac / xfac are the stage's motion factors of the request; next_tile (or -1) is the
+// combination.  BC: the mesh has boundary faces (neighbour codes -1 wall, -2 far field).  gfac / xfac are the stage's motion factors of the request; next_tile (or -1) is the
 // tile this warp takes next in the same request (prefetched towards L2).
-template <int N, int STAGE>
+template <int N, int STAGE, bool BC>
 __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_t next_tile, double gfac, double xfac,
                                         const float4 *__restrict__ btab, float *own, float *trc, float *geo,
                                         const float (&bl)[TcDim<N>::NT][2][3], int lane) {
@@ -164,6 +187,7 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
       const int el = item % 16, f = item / 16;
       if (el < nel) {
         const int nb = a.mesh[e0 + el].nbr[f];
+        if (BC && nb < 0) continue;   // exterior state formed in the flux phase
         const int f2 = nb & 3;
         const float *qp = qin + (int64_t)(nb >> 2) * S;
 #pragma unroll
@@ -381,6 +405,7 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
     for (int item = lane; item < 48; item += 32) {
       const int el = item % 16, f = item / 16;
       if (el >= nel) continue;
+      const int nbf = BC ? a.mesh[e0 + el].nbr[f] : 0;
       const float *gm = geo + el * GEOS;
       const float dx = gm[11 + f], dy = gm[14 + f];
       const float len = sqrtf(dx * dx + dy * dy);
@@ -420,17 +445,26 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
         const int vol0 = tc_fmask<N>(f, k), vol1 = tc_fmask<N>(f, k1);
         float *tr0 = trc + el * ST + f * Nfp + k, *tr1 = trc + el * ST + f * Nfp + k1;
         const float *qm0 = own + el * S + vol0, *qm1 = own + el * S + vol1;
+        const float *b = bary + 4 * vol0, *c1 = bary + 4 * vol1;
+        const float gx0 = __ldg(b) * vx0 + __ldg(b + 1) * vx1 + __ldg(b + 2) * vx2;
+        const float gy0 = __ldg(b) * vy0 + __ldg(b + 1) * vy1 + __ldg(b + 2) * vy2;
+        const float gx1 = __ldg(c1) * vx0 + __ldg(c1 + 1) * vx1 + __ldg(c1 + 2) * vx2;
+        const float gy1 = __ldg(c1) * vy0 + __ldg(c1 + 1) * vy1 + __ldg(c1 + 2) * vy2;
         float2 w[6];
+        if (BC && nbf < 0) {
+          float qe0[6], qe1[6];
+          tc_boundary_state<Np>(nbf, qm0, gx0, gy0, 1.0f / c, a.farf, qe0);
+          tc_boundary_state<Np>(nbf, qm1, gx1, gy1, 1.0f / c, a.farf, qe1);
 #pragma unroll
-        for (int fld = 0; fld < 6; ++fld)
-          w[fld] = make_float2(tr0[fld * FJ] - qm0[fld * Np], tr1[fld * FJ] - qm1[fld * Np]);
+          for (int fld = 0; fld < 6; ++fld) w[fld] = make_float2(qe0[fld] - qm0[fld * Np], qe1[fld] - qm1[fld * Np]);
+        } else {
+#pragma unroll
+          for (int fld = 0; fld < 6; ++fld)
+            w[fld] = make_float2(tr0[fld * FJ] - qm0[fld * Np], tr1[fld * FJ] - qm1[fld * Np]);
+        }
         float2 ale;
         {
-          const float *b = bary + 4 * vol0, *c1 = bary + 4 * vol1;
-          const float vn0 = (__ldg(b) * vx0 + __ldg(b + 1) * vx1 + __ldg(b + 2) * vx2) * nx +
-                            (__ldg(b) * vy0 + __ldg(b + 1) * vy1 + __ldg(b + 2) * vy2) * ny;
-          const float vn1 = (__ldg(c1) * vx0 + __ldg(c1 + 1) * vx1 + __ldg(c1 + 2) * vx2) * nx +
-                            (__ldg(c1) * vy0 + __ldg(c1 + 1) * vy1 + __ldg(c1 + 2) * vy2) * ny;
+          const float vn0 = gx0 * nx + gy0 * ny, vn1 = gx1 * nx + gy1 * ny;
           ale = make_float2(vn0 > 0.0f ? vn0 * fs : 0.0f, vn1 > 0.0f ? vn1 * fs : 0.0f);
         }
         float2 o[6];
@@ -611,7 +645,7 @@ __device__ __forceinline__ void tc_load_bary(const void *ops, int lane, float (&
     }
 }
 
-template <int N, int STAGE>
+template <int N, int STAGE, bool BC>
 __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_kernel(const StageArgs a) {
   typedef TcDim<N> D;
   const int W = blockDim.x >> 5;                // warps per CTA: a launch parameter (1, 2 or 4)
@@ -637,7 +671,7 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_k
   const int64_t ntile = (a.K + 15) >> 4;
   const int64_t tstride = (int64_t)gridDim.x * W;
   for (int64_t tile = (int64_t)blockIdx.x * W + warp; tile < ntile; tile += tstride)
-    tc_tile<N, STAGE>(a, tile, tile + tstride < ntile ? tile + tstride : -1, gfac, xfac, btab, own, trc, geo, bl, lane);
+    tc_tile<N, STAGE, BC>(a, tile, tile + tstride < ntile ? tile + tstride : -1, gfac, xfac, btab, own, trc, geo, bl, lane);
 }
 
 // Many requests of the same order in one launch: tile T of the launch is tile
@@ -674,7 +708,7 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_group_k
     }
     gf = __shfl_sync(0xffffffffu, gf, 0);
     xf = __shfl_sync(0xffffffffu, xf, 0);
-    tc_tile<N, STAGE>(a, tile, tile + tstride < ntile ? tile + tstride : -1, gf, xf, btab, own, trc, geo, bl, lane);
+    tc_tile<N, STAGE, false>(a, tile, tile + tstride < ntile ? tile + tstride : -1, gf, xf, btab, own, trc, geo, bl, lane);
   }
 }
 
@@ -698,9 +732,10 @@ void set_mixed_coefs(StageArgs &a) {
     a.kco[cl][3] = (float)(s == 1 ? B[0] : s == 2 ? B[2] : s == 3 ? B[3] : 0.0);
     a.kco[cl][4] = (float)B[1];
   }
+  for (int f = 0; f < 6; ++f) a.farf[f] = (float)a.far[f];
 }
 
-template <int N, int STAGE>
+template <int N, int STAGE, bool BC>
 static int tc_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
   StageArgs a = a_in;
   set_mixed_coefs(a);
@@ -710,14 +745,14 @@ static int tc_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
   const int threads = 32 * W;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(tc_stage_kernel<N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<N>());
+    cudaError_t err = cudaFuncSetAttribute(tc_stage_kernel<N, STAGE, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<N>());
     if (err != cudaSuccess) return (int)err;
     attr_set = true;
   }
   static int per_sm_w[5] = {0, 0, 0, 0, 0};   // cached: no runtime queries while a graph is being captured
   int &per_sm = per_sm_w[W];
   if (per_sm == 0) {
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_stage_kernel<N, STAGE>, threads, smem);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_stage_kernel<N, STAGE, BC>, threads, smem);
     if (err != cudaSuccess) return (int)err;
     if (per_sm < 1) per_sm = 1;
   }
@@ -725,20 +760,30 @@ static int tc_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
   const int64_t need = ((a.K + 15) / 16 + W - 1) / W;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
-  tc_stage_kernel<N, STAGE><<<(unsigned)grid, threads, smem, st>>>(a);
+  tc_stage_kernel<N, STAGE, BC><<<(unsigned)grid, threads, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
-template <int N>
-static int tc_launch_n(const StageArgs &a, cudaStream_t st, int num_sms) {
+template <int N, bool BC>
+static int tc_launch_nb(const StageArgs &a, cudaStream_t st, int num_sms) {
   switch (a.stage) {
-    case -1: return tc_launch_one<N, -1>(a, st, num_sms);
-    case 0: return tc_launch_one<N, 0>(a, st, num_sms);
-    case 1: return tc_launch_one<N, 1>(a, st, num_sms);
-    case 2: return tc_launch_one<N, 2>(a, st, num_sms);
-    case 3: return tc_launch_one<N, 3>(a, st, num_sms);
+    case -1: return tc_launch_one<N, -1, BC>(a, st, num_sms);
+    case 0: return tc_launch_one<N, 0, BC>(a, st, num_sms);
+    case 1: return tc_launch_one<N, 1, BC>(a, st, num_sms);
+    case 2: return tc_launch_one<N, 2, BC>(a, st, num_sms);
+    case 3: return tc_launch_one<N, 3, BC>(a, st, num_sms);
   }
   return (int)cudaErrorInvalidValue;
+}
+
+// meshes with boundary faces use the BC variant (orders 1..4)
+template <int N>
+static int tc_launch_n(const StageArgs &a, cudaStream_t st, int num_sms) {
+  if (a.bc) {
+    if constexpr (N <= 4) return tc_launch_nb<N, true>(a, st, num_sms);
+    return (int)cudaErrorInvalidValue;
+  }
+  return tc_launch_nb<N, false>(a, st, num_sms);
 }
 
 int launch_stage_mixed(int N, const StageArgs &a, void *stream, int num_sms) {

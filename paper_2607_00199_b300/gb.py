@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(_HERE, 'libgb.so')
 
 GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_EMESH, GB_ENAN = 0, -1, -2, -3, -4, -5
 GB_FP64, GB_MIXED = 0, 1
-GB_MOTION_STATIC, GB_MOTION_SINXY = 0, 1
+GB_MOTION_STATIC, GB_MOTION_SINXY, GB_MOTION_PLUNGE = 0, 1, 2
+GB_BC_INTERIOR, GB_BC_WALL, GB_BC_FARFIELD = 0, 1, 2
 _NAMES = {GB_EINVAL: 'GB_EINVAL', GB_ENOMEM: 'GB_ENOMEM', GB_ECUDA: 'GB_ECUDA', GB_EMESH: 'GB_EMESH', GB_ENAN: 'GB_ENAN'}
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -52,6 +53,8 @@ def _load():
     vp, i64, c_int, c_double = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     sig = {
         'gb_create': ([ctypes.POINTER(GbMesh), c_int, c_double, c_double, c_int, vp, ctypes.POINTER(vp)], c_int),
+        'gb_create_bounded': ([ctypes.POINTER(GbMesh), ctypes.POINTER(ctypes.c_int8), _dp, c_int, c_double, c_double,
+                               c_int, vp, ctypes.POINTER(vp)], c_int),
         'gb_set_motion': ([vp, ctypes.POINTER(GbMotion)], c_int),
         'gb_set_fields': ([vp, _dp, c_double], c_int),
         'gb_fields': ([vp, _dp, _dp], c_int),
@@ -165,9 +168,10 @@ def dissipation_rate(t, kinetic_energy):
 class Solver:
     """Owns one gb_solver.  mesh is a dict with X, EToV, shift (see inputs.py); the
     dimension follows from X: (n_vert, 2) triangles with 6 fields, (n_vert, 3)
-    tetrahedra with 10 fields."""
+    tetrahedra with 10 fields.  A 2D mesh with a 'bc' array (n_elem x 3 face tags) is
+    created with gb_create_bounded and the free stream far_state = (rho, u, v)."""
 
-    def __init__(self, mesh, N, Ma, Re, precision=GB_FP64, stream=None):
+    def __init__(self, mesh, N, Ma, Re, precision=GB_FP64, stream=None, far_state=(1.0, 1.0, 0.0)):
         self._X = np.ascontiguousarray(mesh['X'], dtype=np.float64)
         self._EToV = np.ascontiguousarray(mesh['EToV'], dtype=np.int32)
         shift = mesh.get('shift')
@@ -178,7 +182,14 @@ class Solver:
                    self._EToV.ctypes.data_as(_ip), None if self._shift is None else _ptr(self._shift))
         h = ctypes.c_void_p(None)
         st = None if stream is None else ctypes.c_void_p(int(stream))
-        _check(lib.gb_create(ctypes.byref(m), int(N), float(Ma), float(Re), int(precision), st, ctypes.byref(h)))
+        if mesh.get('bc') is not None:
+            self._bc = np.ascontiguousarray(mesh['bc'], dtype=np.int8)
+            self._far = np.ascontiguousarray(far_state, dtype=np.float64)
+            _check(lib.gb_create_bounded(ctypes.byref(m), self._bc.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)),
+                                         _ptr(self._far), int(N), float(Ma), float(Re), int(precision), st,
+                                         ctypes.byref(h)))
+        else:
+            _check(lib.gb_create(ctypes.byref(m), int(N), float(Ma), float(Re), int(precision), st, ctypes.byref(h)))
         self.h = h
         self.N = int(N)
         self.precision = int(precision)
