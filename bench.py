@@ -183,6 +183,53 @@ def run_3d(torch, steps_fp64=10, steps_mixed=50, warmup=3):
                       '(FP64 state 157 MB per array, FP32 79 MB)'}
 
 
+WORKLOAD_AF = dict(ni=256, nj=192, R=20.0, N=4, Ma=0.1, Re=1000.0, A=0.25, T=2.0, far=(1.0, 1.0, 0.0), cfl=0.5)
+WORKLOAD_AF_NAME = ('2D plunging NACA 0012 airfoil: O-grid of 256 wrap-around x 192 radial quads (geometric growth 1.02, '
+                    'radius 20 chords) -> K=98304 triangles, N=4, 6 fields, Ma=0.1, Re=1000, rigid plunge '
+                    'h(t)=0.25 sin(2 pi 0.5 t), walls on the airfoil (bounce-back about the wall velocity), free-stream '
+                    'far field (no PML), whole SARK step captured as a CUDA graph')
+
+
+def run_airfoil(torch, steps=50, warmup=3):
+    """The plunging-airfoil workload (throughput; the paper's drag and lift comparisons need
+    its published curves): GB_MIXED and GB_FP64, timed like the headline."""
+    from paper_2607_00199_b300 import gb, inputs, state
+    W = WORKLOAD_AF
+    mesh = inputs.naca_ogrid_mesh(W['ni'], W['nj'], R=W['R'])
+    tstream = torch.cuda.Stream()
+    Np, _, _ = sizes(W['N'])
+    hbm, sm_max, _ = load_peaks()
+    out = {'workload': WORKLOAD_AF_NAME, 'K': int(mesh['EToV'].shape[0]), 'N': W['N'], 'Np': Np, 'fields': 6}
+    for name, prec, nst in (('mixed', gb.GB_MIXED, steps), ('fp64', gb.GB_FP64, max(4, steps // 10))):
+        s = gb.Solver(mesh, W['N'], W['Ma'], W['Re'], precision=prec, stream=tstream.cuda_stream, far_state=W['far'])
+        s.set_motion(W['A'], W['T'], kind=gb.GB_MOTION_PLUNGE)
+        xy = s.nodes()
+        rho, u, v = inputs.free_stream(xy[..., 0], xy[..., 1], W['far'][1], W['far'][2])
+        q0 = state.equilibrium_fields(rho, u, v, s.c)
+        dt = inputs.cfl_dt(mesh, W['N'], s.c, W['cfl'])
+        ms, kms = time_path(torch, s, q0, dt, nst, warmup, lambda: None, tstream)
+        dof = s.K * Np * 6
+        stage_ms = float(sum(kms[:4]))
+        r = {'value': dof * 4 * nst / (ms / 1e3), 'ms_per_step': ms / nst, 'steps': nst, 'warmup': warmup,
+             'kernel_ms_per_step': [x / nst for x in kms]}
+        if prec == gb.GB_MIXED:
+            alg = bytes_per_step(s.K, W['N'], s.nv, 4)
+            gbs = alg * nst / (stage_ms / 1e3) / 1e9
+            r['roofline'] = {'bound': 'hbm', 'achieved': gbs, 'peak': hbm, 'unit': 'GB/s', 'frac': gbs / hbm,
+                             'kernel': 'tc_stage_kernel<4,*,BC> (4 launches per step)'}
+        else:
+            fl = flops_per_element_stage(W['N']) * s.K * 4 * nst / (stage_ms / 1e3) / 1e12
+            peak = 148 * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
+            r['roofline'] = {'bound': 'alu', 'achieved': fl, 'peak': peak, 'unit': 'TFLOP/s', 'frac': fl / peak,
+                             'kernel': 'stage_kernel<double,4,*,BC>'}
+        out[name] = r
+        s.close()
+    out['mixed_speedup_vs_fp64'] = out['mixed']['value'] / out['fp64']['value']
+    out['note'] = ('throughput only; dt from CFL 0.5 on the thinnest O-grid cell, so a step covers little physical '
+                   'time; the per-step cost is what is measured')
+    return out
+
+
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument('--gpus', type=int, default=1)
@@ -193,6 +240,7 @@ def parse():
     p.add_argument('--no-serve', action='store_true', help='skip the serving-stream measurement')
     p.add_argument('--serve-only', action='store_true', help='only the serving-stream measurement')
     p.add_argument('--no-3d', action='store_true', help='skip the 3D deforming-channel measurement')
+    p.add_argument('--no-airfoil', action='store_true', help='skip the plunging-airfoil measurement')
     p.add_argument('--serve-requests', type=int, default=256)
     p.add_argument('--serve-steps', type=int, default=500)
     return p.parse_args()
@@ -532,6 +580,8 @@ def run_ours(args):
     }
     if ws == 1 and not args.no_3d:
         line['d3'] = run_3d(torch)
+    if ws == 1 and not args.no_airfoil:
+        line['airfoil'] = run_airfoil(torch)
     if ws == 1 and not args.no_serve:
         line['serving'] = run_serving(torch, args.serve_requests, args.serve_steps)
     if ws == 1 and not args.no_cpu_baseline:
