@@ -55,6 +55,7 @@ struct gb_solver {
   int64_t diag_cap = 0;
   double *d_hist = nullptr;
   int64_t *d_hctl = nullptr;   // steps since enabled, records written
+  unsigned *d_done = nullptr;  // CTA counter of the fused record (zero between launches)
   size_t tmp_bytes = 0;
   int64_t device_bytes = 0;
   int has_bc = 0;              // the mesh has wall / far-field faces (gb_create_bounded)
@@ -85,7 +86,7 @@ static int dev_alloc(gb_solver *s, void **p, size_t bytes) {
 static void free_all(gb_solver *s) {
   void *ptrs[] = {s->d_ops, s->d_ops_mixed, s->d_mesh, s->d_mesh_int, s->d_perm, s->d_X, s->d_xn, s->d_shape,
                   s->d_clock, s->d_status, s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp, s->d_diag,
-                  s->d_hist, s->d_hctl};
+                  s->d_hist, s->d_hctl, s->d_done};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -102,7 +103,10 @@ static void dev_free(gb_solver *s, void **p, size_t bytes) {
 static int ensure_diag(gb_solver *s) {
   if (s->d_diag) return GB_OK;
   int rc = dev_alloc(s, (void **)&s->d_diag, sizeof(double) * (s->Np + 5 + gb::diagnostics_scratch_doubles()));
+  if (!rc) rc = dev_alloc(s, (void **)&s->d_done, sizeof(unsigned));
   if (rc) return rc;
+  cudaError_t ze = cudaMemsetAsync(s->d_done, 0, sizeof(unsigned), s->stream);
+  if (ze != cudaSuccess) return cuda_fail(s, ze, "diagnostics counter");
   cudaError_t ce = cudaMemcpyAsync(s->d_diag, s->ref.wq.data(), sizeof(double) * s->Np, cudaMemcpyHostToDevice, s->stream);
   return ce == cudaSuccess ? GB_OK : cuda_fail(s, ce, "diagnostics weights");
 }
@@ -763,14 +767,25 @@ static int step_impl(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms)
         a.qout = bufs_out[st];
         a.F0 = s->d_F0;
         a.acc = s->d_acc;
+        if (st == 3 && s->diag_every > 0) {
+          // diagnostics fused into the last stage: integrals of q_{n+1} on x_{n+1}, recorded by the
+          // last CTA (partials in the diagnostics scratch, after the weights and result slots)
+          a.rec_every = s->diag_every;
+          a.rec_cap = s->diag_cap;
+          a.rec_wq = s->d_diag;
+          a.rec_part = s->d_diag + s->Np + 5;
+          a.rec_done = s->d_done;
+          a.rec_ctl = s->d_hctl;
+          a.rec_hist = s->d_hist;
+        }
         rc = launch_stage(s, a);
+        a.rec_every = 0;
       } else {
         int lr = gb::launch_vertex_update(a, s->nv, s->stream);
         if (lr) rc = cuda_fail(s, (cudaError_t)lr, "vertex update launch");
       }
       if (kernel_ms) cudaEventRecord(ev[(size_t)k * 10 + 2 * st + 1], s->stream);
     }
-    if (rc == GB_OK) rc = record_diagnostics(s, s->stream);
   }
   if (kernel_ms) {
     cudaError_t ce = cudaStreamSynchronize(s->stream);

@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kDiagThreads) diagnostics_record_kernel(const 
   }
 }
 
+static_assert(kDiagBlocks >= kRecMaxCtas, "the partials buffer also serves the fused record");
 int diagnostics_scratch_doubles() { return 5 * kDiagBlocks; }
 
 static int64_t diag_blocks(int64_t K) {

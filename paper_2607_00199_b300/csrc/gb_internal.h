@@ -104,7 +104,73 @@ struct StageArgs {
   int bc;
   double far[6];
   float farf[6];
+  // diagnostics fused into the last stage (rec_every > 0): on every rec_every-th step the
+  // stage-3 kernel integrates mass, E_K, momentum and area of q_{n+1} on x_{n+1} (weights
+  // rec_wq = 1^T Mhat), leaves per-CTA partials in rec_part and the last CTA to finish writes
+  // the record (t, mass, E_K, momentum x, y, area) into the ring rec_hist of rec_cap records;
+  // rec_ctl = (steps since enabled, records written), rec_done a CTA counter (zero between launches)
+  int rec_every;
+  int64_t rec_cap;
+  const double *rec_wq;
+  double *rec_part;
+  unsigned *rec_done;
+  int64_t *rec_ctl;
+  double *rec_hist;
 };
+
+// most CTAs of a launch with the fused record (the size of its partials buffer)
+constexpr int kRecMaxCtas = 1184;
+
+// Fused diagnostics: every CTA of a stage-3 launch calls this once at its end with its
+// threads' partial sums (mass, kinetic energy, momentum x, y, area); the last CTA to finish
+// sums the per-CTA partials in CTA order (so the result does not depend on scheduling),
+// writes the record and advances the step counter.  Requires blockDim.x <= 1024 and a
+// multiple of 32; all threads of the CTA must call it.
+#ifdef __CUDACC__
+__device__ __forceinline__ void fused_record(const StageArgs &a, bool record, double (&acc)[5], double t_next) {
+  __shared__ double red[32][5];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (record) {
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      double v = acc[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[warp][k] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (record)
+      for (int k = 0; k < 5; ++k) {
+        double v = 0.0;
+        for (int w = 0; w < nw; ++w) v += red[w][k];
+        a.rec_part[5 * blockIdx.x + k] = v;
+      }
+    __threadfence();
+    last = atomicAdd(a.rec_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    if (record) {
+      double tot[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+      for (unsigned b = 0; b < gridDim.x; ++b)
+        for (int k = 0; k < 5; ++k) tot[k] += ((volatile double *)a.rec_part)[5 * b + k];
+      double *r = a.rec_hist + 6 * (a.rec_ctl[1] % a.rec_cap);
+      r[0] = t_next;
+      r[1] = tot[0];
+      r[2] = tot[1] / tot[4];
+      r[3] = tot[2];
+      r[4] = tot[3];
+      r[5] = tot[4];
+      a.rec_ctl[1] += 1;
+    }
+    a.rec_ctl[0] += 1;
+    *a.rec_done = 0u;
+  }
+}
+#endif
 
 // Several requests (solvers) of one order stepped by one launch per stage:
 // args[r] are their stage arguments, tile_start the exclusive prefix of their

@@ -78,6 +78,7 @@ __device__ __forceinline__ int fmask(int f, int k) {
 //   10 + 20 f + (0..12): h|At_n| entries M00 M03 M04 M05 M33 M34 M35 M44 M45 M55 N11 N12 N22
 //   10 + 20 f + 13..16 : h nx, h ny, h sqrt2 nx, h sqrt2 ny   (h = c Fscale / 2)
 //   10 + 20 f + 17..19 : nx, ny, Fscale
+//   70                  : J at x_{n+1} (stage 3 with fused diagnostics)
 constexpr int GEO = 72;
 
 __device__ __forceinline__ bool bad_double(double v) {
@@ -134,7 +135,7 @@ __device__ __forceinline__ void boundary_state(int nb, const T *qm, T vgx, T vgy
   }
 }
 
-template <typename T, int N, int STAGE, bool BC = false>
+template <typename T, int N, int STAGE, bool BC = false, bool REC = false>
 __global__ void __launch_bounds__(((Tile<T, N>::E * Dim<N>::Np + 31) / 32) * 32)
 stage_kernel(const StageArgs a) {
   typedef Dim<N> D;
@@ -151,7 +152,11 @@ stage_kernel(const StageArgs a) {
   T *sflux = sq + E * NQ;              // [E][6][NFN]
   T *snt = sflux + E * 6 * NFN;        // [E][3][Nc]
   T *sgeo = snt + E * 3 * Nc;          // [E][GEO]
-  __shared__ double s_motion[2];
+  __shared__ double s_motion[3];
+  // REC: whether this step is recorded, read before any CTA can advance the counter
+  const bool record = REC && ((a.rec_ctl[0] + 1) % a.rec_every == 0);
+  const double t_now = a.clock[0];
+  double dacc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
 
   const int tid = threadIdx.x;
   const int nthr = blockDim.x;
@@ -163,18 +168,17 @@ stage_kernel(const StageArgs a) {
     StageMotion m = stage_motion(a);
     s_motion[0] = m.gfac;
     s_motion[1] = m.xfac;
-    if (STAGE == 3 && blockIdx.x == 0) {
-      // factor of the final vertex update x_{n+1} = x_n + dt sum_j b_j v_j (RK4 b)
-      double fin = 0.0;
-      if (a.motion_A != 0.0) {
-        const double t = a.clock[0], dt = a.dt, w = a.motion_w, Aw = a.motion_A * a.motion_w;
-        fin = dt * Aw * (cos(w * t) / 6.0 + cos(w * (t + 0.5 * dt)) * (2.0 / 3.0) + cos(w * (t + dt)) / 6.0);
-      }
-      const_cast<double *>(a.clock)[1] = fin;
+    // factor of the final vertex update x_{n+1} = x_n + dt sum_j b_j v_j (RK4 b)
+    double fin = 0.0;
+    if (STAGE == 3 && a.motion_A != 0.0) {
+      const double t = t_now, dt = a.dt, w = a.motion_w, Aw = a.motion_A * a.motion_w;
+      fin = dt * Aw * (cos(w * t) / 6.0 + cos(w * (t + 0.5 * dt)) * (2.0 / 3.0) + cos(w * (t + dt)) / 6.0);
     }
+    s_motion[2] = fin;
   }
   __syncthreads();
-  const double gfac = s_motion[0], xfac = s_motion[1];
+  if (STAGE == 3 && blockIdx.x == 0 && tid == 0) const_cast<double *>(a.clock)[1] = s_motion[2];
+  const double gfac = s_motion[0], xfac = s_motion[1], fin = s_motion[2];
 
   const T *qin = reinterpret_cast<const T *>(a.qin);
   const int e_loc = tid / Np, n_loc = tid - (tid / Np) * Np;
@@ -217,6 +221,15 @@ stage_kernel(const StageArgs a) {
         g[1] = (T)(-yr * iJ);
         g[2] = (T)(-xs * iJ);
         g[3] = (T)(xr * iJ);
+        if (REC && record) {   // J at x_{n+1}, where the recorded integrals are taken
+          double xn1[3], yn1[3];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            xn1[k] = px[k] + (fin - xfac) * sx_[k];
+            yn1[k] = py[k] + (fin - xfac) * sy_[k];
+          }
+          g[70] = (T)(0.25 * ((xn1[1] - xn1[0]) * (yn1[2] - yn1[0]) - (xn1[2] - xn1[0]) * (yn1[1] - yn1[0])));
+        }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           g[4 + 2 * k] = (T)(gfac * sx_[k]);
@@ -397,6 +410,7 @@ stage_kernel(const StageArgs a) {
         T *F0 = reinterpret_cast<T *>(a.F0);
         T *acc = reinterpret_cast<T *>(a.acc);
         bool bad = false;
+        T qrec[3] = {0, 0, 0};
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
           const int cl = f < 3 ? 0 : 1;
@@ -419,13 +433,24 @@ stage_kernel(const StageArgs a) {
             const T out = (T)a.co.E[cl][4] * qv + dt * (ac + (T)a.co.B[cl][3] * r);
             qout[idx] = out;
             bad |= bad_value(out);
+            if (REC && f < 3) qrec[f] = out;
           }
         }
         if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
+        if (REC && record) {   // fused diagnostics: this node's share of the integrals of q_{n+1} on x_{n+1}
+          const double jw = (double)sgeo[e_loc * GEO + 70] * a.rec_wq[n_loc], cc = a.c;
+          const double q1 = (double)qrec[0] + (PERTURB ? 1.0 : 0.0), q2 = (double)qrec[1], q3 = (double)qrec[2];
+          dacc[0] += jw * q1;
+          dacc[1] += jw * 0.5 * cc * cc * (q2 * q2 + q3 * q3) / q1;
+          dacc[2] += jw * cc * q2;
+          dacc[3] += jw * cc * q3;
+          dacc[4] += jw;
+        }
       }
     }
     __syncthreads();
   }
+  if constexpr (REC) fused_record(a, record, dacc, t_now + a.dt);
 }
 
 // ---------------------------------------------------------------------------
@@ -438,28 +463,29 @@ static size_t stage_smem() {
   return sizeof(T) * (size_t)(OpLayout<N>::Size + E * (D::NQ + 6 * D::NFN + 3 * D::Nc + GEO));
 }
 
-template <typename T, int N, int STAGE, bool BC>
+template <typename T, int N, int STAGE, bool BC, bool REC = false>
 static int launch_one(const StageArgs &a, cudaStream_t st, int num_sms) {
   constexpr int E = Tile<T, N>::E;
   const int threads = ((E * Dim<N>::Np + 31) / 32) * 32;
   const size_t smem = stage_smem<T, N>();
   static bool attr_set = false;   // per template instance (one device per process assumed)
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(stage_kernel<T, N, STAGE, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(stage_kernel<T, N, STAGE, BC, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     attr_set = true;
   }
   static int per_sm = 0;   // cached: no runtime queries while a graph is being captured
   if (per_sm == 0) {
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel<T, N, STAGE, BC>, threads, smem);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel<T, N, STAGE, BC, REC>, threads, smem);
     if (err != cudaSuccess) return (int)err;
   }
   if (per_sm < 1) per_sm = 1;
   const int64_t ntiles = (a.K + E - 1) / E;
   int64_t grid = (int64_t)num_sms * per_sm;
   if (grid > ntiles) grid = ntiles;
+  if (REC && grid > kRecMaxCtas) grid = kRecMaxCtas;
   if (grid < 1) grid = 1;
-  stage_kernel<T, N, STAGE, BC><<<(unsigned)grid, threads, smem, st>>>(a);
+  stage_kernel<T, N, STAGE, BC, REC><<<(unsigned)grid, threads, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
@@ -470,7 +496,8 @@ static int launch_stage_nb(const StageArgs &a, cudaStream_t st, int num_sms) {
     case 0: return launch_one<T, N, 0, BC>(a, st, num_sms);
     case 1: return launch_one<T, N, 1, BC>(a, st, num_sms);
     case 2: return launch_one<T, N, 2, BC>(a, st, num_sms);
-    case 3: return launch_one<T, N, 3, BC>(a, st, num_sms);
+    case 3:
+      return a.rec_every > 0 ? launch_one<T, N, 3, BC, true>(a, st, num_sms) : launch_one<T, N, 3, BC>(a, st, num_sms);
   }
   return (int)cudaErrorInvalidValue;
 }

@@ -160,10 +160,11 @@ __device__ __forceinline__ void tc_boundary_state(int nb, const float *qm, float
 // One 16-element tile of one request: staging, geometry, volume, surface, cubature and the SARK
 // combination.  BC: the mesh has boundary faces (neighbour codes -1 wall, -2 far field).  gfac / xfac are the stage's motion factors of the request; next_tile (or -1) is the
 // tile this warp takes next in the same request (prefetched towards L2).
-template <int N, int STAGE, bool BC>
+template <int N, int STAGE, bool BC, bool REC = false>
 __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_t next_tile, double gfac, double xfac,
                                         const float4 *__restrict__ btab, float *own, float *trc, float *geo,
-                                        const float (&bl)[TcDim<N>::NT][2][3], int lane) {
+                                        const float (&bl)[TcDim<N>::NT][2][3], int lane, bool record = false,
+                                        double fin = 0.0, double *dacc = nullptr) {
   typedef TcDim<N> D;
   constexpr int Np = D::Np, Nfp = D::Nfp, NFN = D::NFN, KS = D::KS, KF = D::KF, NT = D::NT, CH = D::CH;
   constexpr int S = D::S, ST = D::ST, FJ = D::FJ, GEOS = D::GEOS;
@@ -214,21 +215,27 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
     // ---- geometry of the tile's elements (lanes 0..15), while the copies fly ----
+    double Jn1 = 0.0;   // REC: J of element `lane` at x_{n+1}
     if (lane < 16) {
       float *gm = geo + lane * GEOS;
       float ex[3] = {1.f, 0.f, -1.f}, ey[3] = {0.f, 1.f, -1.f}, vx[3] = {0.f, 0.f, 0.f}, vy[3] = {0.f, 0.f, 0.f};
       if (lane < nel) {
         const MeshRec rec = a.mesh[e0 + lane];
-        double px[3], py[3];
+        double px[3], py[3], pxn[3], pyn[3];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const double2 xv = reinterpret_cast<const double2 *>(a.xn)[rec.v[k]];
           const double2 sv = reinterpret_cast<const double2 *>(a.shape)[rec.v[k]];
           px[k] = fma(xfac, sv.x, xv.x + rec.shift[2 * k] * a.period[0]);
           py[k] = fma(xfac, sv.y, xv.y + rec.shift[2 * k + 1] * a.period[1]);
+          if (REC && record) {   // x_{n+1}, where the recorded integrals are taken
+            pxn[k] = fma(fin, sv.x, xv.x + rec.shift[2 * k] * a.period[0]);
+            pyn[k] = fma(fin, sv.y, xv.y + rec.shift[2 * k + 1] * a.period[1]);
+          }
           vx[k] = (float)(gfac * sv.x);
           vy[k] = (float)(gfac * sv.y);
         }
+        if (REC && record) Jn1 = 0.25 * ((pxn[1] - pxn[0]) * (pyn[2] - pyn[0]) - (pxn[2] - pxn[0]) * (pyn[1] - pyn[0]));
         ex[0] = (float)(px[1] - px[0]); ey[0] = (float)(py[1] - py[0]);
         ex[1] = (float)(px[2] - px[1]); ey[1] = (float)(py[2] - py[1]);
         ex[2] = (float)(px[0] - px[2]); ey[2] = (float)(py[0] - py[2]);
@@ -593,6 +600,10 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
               o = fma2(dt, fma2(Bc[sl], r_, av), mul2(E1[sl], qv));
               bad |= (__float_as_int(o.x) & 0x7f800000) == 0x7f800000;
               bad |= ok1 && (__float_as_int(o.y) & 0x7f800000) == 0x7f800000;
+              if (REC && record && w < 3 * Np) {   // q_{n+1} of fields 1..3 over the (already read) rhs
+                out[r * S + w] = o.x;
+                if (ok1) out[(r + 1) * S + w] = o.y;
+              }
             }
             float *dst = STAGE < 0 ? Fo : qo;
             dst[gi] = o.x;
@@ -607,6 +618,27 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
           }
       }
       if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
+    }
+    // ---- fused diagnostics (REC, record steps): integrals of q_{n+1} over the tile on x_{n+1}:
+    //      J w_n q1, J w_n c^2 (q2^2 + q3^2) / (2 q1), J w_n c q2, J w_n c q3, J w_n ----
+    if (REC && record) {
+      __syncwarp();
+      const double cc = a.c;
+      constexpr int NIT = (16 * Np + 31) / 32;
+#pragma unroll 1
+      for (int it = 0; it < NIT; ++it) {
+        const int item = lane + 32 * it, r = item / Np, n = item - Np * (item / Np);
+        const double J = __shfl_sync(0xffffffffu, Jn1, r & 15);
+        if (item < 16 * Np && r < nel) {
+          const double q1 = 1.0 + (double)out[r * S + n], q2 = (double)out[r * S + Np + n];
+          const double q3 = (double)out[r * S + 2 * Np + n], jw = J * a.rec_wq[n];
+          dacc[0] += jw * q1;
+          dacc[1] += jw * 0.5 * cc * cc * (q2 * q2 + q3 * q3) / q1;
+          dacc[2] += jw * cc * q2;
+          dacc[3] += jw * cc * q3;
+          dacc[4] += jw;
+        }
+      }
     }
   }
 }
@@ -645,23 +677,28 @@ __device__ __forceinline__ void tc_load_bary(const void *ops, int lane, float (&
     }
 }
 
-template <int N, int STAGE, bool BC>
+template <int N, int STAGE, bool BC, bool REC = false>
 __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_kernel(const StageArgs a) {
   typedef TcDim<N> D;
   const int W = blockDim.x >> 5;                // warps per CTA: a launch parameter (1, 2 or 4)
   extern __shared__ float4 tc_smem4[];
   const float4 *btab = reinterpret_cast<const float4 *>(a.ops);     // [NSETS][32], read through L1
   float *wbase = reinterpret_cast<float *>(tc_smem4);
-  __shared__ double s_motion[2];
+  __shared__ double s_motion[3];
+  // REC: whether this step is recorded, read before any CTA can advance the counter
+  const bool record = REC && ((a.rec_ctl[0] + 1) % a.rec_every == 0);
+  const double t_now = a.clock[0];
   if (threadIdx.x == 0) {
     double gf, xf, fin;
     tc_stage_motion<STAGE>(a, gf, xf, fin);
     s_motion[0] = gf;
     s_motion[1] = xf;
-    if (STAGE == 3 && blockIdx.x == 0) const_cast<double *>(a.clock)[1] = fin;
+    s_motion[2] = fin;
   }
   __syncthreads();
-  const double gfac = s_motion[0], xfac = s_motion[1];
+  if (STAGE == 3 && blockIdx.x == 0 && threadIdx.x == 0) const_cast<double *>(a.clock)[1] = s_motion[2];
+  const double gfac = s_motion[0], xfac = s_motion[1], fin = s_motion[2];
+  double dacc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float *own = wbase + warp * D::WARP_FLOATS;   // [16][S]   fields of the tile
   float *trc = own + 16 * D::S;                 // [16][ST] traces -> fluxes, then [16][S] rhs (16 OUTS floats)
@@ -671,7 +708,9 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_k
   const int64_t ntile = (a.K + 15) >> 4;
   const int64_t tstride = (int64_t)gridDim.x * W;
   for (int64_t tile = (int64_t)blockIdx.x * W + warp; tile < ntile; tile += tstride)
-    tc_tile<N, STAGE, BC>(a, tile, tile + tstride < ntile ? tile + tstride : -1, gfac, xfac, btab, own, trc, geo, bl, lane);
+    tc_tile<N, STAGE, BC, REC>(a, tile, tile + tstride < ntile ? tile + tstride : -1, gfac, xfac, btab, own, trc, geo, bl,
+                               lane, record, fin, dacc);
+  if constexpr (REC) fused_record(a, record, dacc, t_now + a.dt);
 }
 
 // Many requests of the same order in one launch: tile T of the launch is tile
@@ -735,7 +774,7 @@ void set_mixed_coefs(StageArgs &a) {
   for (int f = 0; f < 6; ++f) a.farf[f] = (float)a.far[f];
 }
 
-template <int N, int STAGE, bool BC>
+template <int N, int STAGE, bool BC, bool REC = false>
 static int tc_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
   StageArgs a = a_in;
   set_mixed_coefs(a);
@@ -745,22 +784,23 @@ static int tc_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
   const int threads = 32 * W;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(tc_stage_kernel<N, STAGE, BC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<N>());
+    cudaError_t err = cudaFuncSetAttribute(tc_stage_kernel<N, STAGE, BC, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<N>());
     if (err != cudaSuccess) return (int)err;
     attr_set = true;
   }
   static int per_sm_w[5] = {0, 0, 0, 0, 0};   // cached: no runtime queries while a graph is being captured
   int &per_sm = per_sm_w[W];
   if (per_sm == 0) {
-    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_stage_kernel<N, STAGE, BC>, threads, smem);
+    cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_stage_kernel<N, STAGE, BC, REC>, threads, smem);
     if (err != cudaSuccess) return (int)err;
     if (per_sm < 1) per_sm = 1;
   }
   int64_t grid = (int64_t)num_sms * per_sm;
   const int64_t need = ((a.K + 15) / 16 + W - 1) / W;
   if (grid > need) grid = need;
+  if (REC && grid > kRecMaxCtas) grid = kRecMaxCtas;
   if (grid < 1) grid = 1;
-  tc_stage_kernel<N, STAGE, BC><<<(unsigned)grid, threads, smem, st>>>(a);
+  tc_stage_kernel<N, STAGE, BC, REC><<<(unsigned)grid, threads, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
@@ -771,7 +811,8 @@ static int tc_launch_nb(const StageArgs &a, cudaStream_t st, int num_sms) {
     case 0: return tc_launch_one<N, 0, BC>(a, st, num_sms);
     case 1: return tc_launch_one<N, 1, BC>(a, st, num_sms);
     case 2: return tc_launch_one<N, 2, BC>(a, st, num_sms);
-    case 3: return tc_launch_one<N, 3, BC>(a, st, num_sms);
+    case 3:
+      return a.rec_every > 0 ? tc_launch_one<N, 3, BC, true>(a, st, num_sms) : tc_launch_one<N, 3, BC>(a, st, num_sms);
   }
   return (int)cudaErrorInvalidValue;
 }

@@ -68,8 +68,14 @@ def test_group_records_diagnostics_like_alone():
         sa.step(dt, 6)
         hg, ha = sg.diagnostics_history(), sa.diagnostics_history()
         assert hg['total'] == ha['total'] == 6 // every
-        for key in ('t', 'mass', 'kinetic_energy', 'momentum_x', 'momentum_y', 'area'):
-            assert np.array_equal(hg[key], ha[key]), key
+        assert np.array_equal(hg['t'], ha['t'])
+        # alone, the record is fused into the last stage kernel; in a group it is a separate
+        # reduction: the same integrals of the same (bitwise equal) states, summed in another order
+        for key in ('mass', 'kinetic_energy', 'momentum_x', 'momentum_y', 'area'):
+            np.testing.assert_allclose(hg[key], ha[key], rtol=1e-13, atol=1e-13 * float(ha['mass'].max()), err_msg=key)
+        q_g, _ = sg.fields()
+        q_a, _ = sa.fields()
+        np.testing.assert_array_equal(q_g, q_a)
         sa.close()
         sg.close()
     g.close()

@@ -255,8 +255,9 @@ def test_diagnostics_full_size_cfg2():
 
 @pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
 def test_diagnostics_history_equals_on_demand(precision):
-    # records taken inside the step (and its CUDA graph) equal gb_diagnostics after
-    # each step taken one by one, bit for bit
+    # records taken inside the step (fused into the last stage kernel, and its CUDA graph) equal
+    # gb_diagnostics after each step taken one by one: the same times bit for bit, the same
+    # integrals up to the order of the FP64 summation (1e-13 relative)
     mesh, o, a = make_pair(6, 3, 0.1, 200.0, 0.05, 1.0, jitter=0.1, precision=precision)
     b = gb.Solver(mesh, 3, 0.1, 200.0, precision=precision, stream=torch.cuda.current_stream().cuda_stream)
     b.set_motion(0.05, 1.0)
@@ -273,7 +274,7 @@ def test_diagnostics_history_equals_on_demand(precision):
         d = b.diagnostics()
         assert h['t'][k] == b.fields()[1]
         for key in d:
-            assert h[key][k] == d[key], (k, key)
+            assert abs(h[key][k] - d[key]) <= 1e-13 * (abs(d[key]) + d['mass']), (k, key, h[key][k], d[key])
     # every 3rd step into a ring of 2: the records of steps 3, 6, 9 were written, 6 and 9 kept
     a.set_diagnostics(3, 2)
     t0 = a.fields()[1]
