@@ -15,7 +15,8 @@ scheme on tetrahedra):
 Layout: q has shape (K, 10, Np).  Vertex arrays (n_vert, 3); element vertex k of
 element e is at x[EToV[e, k]] + shift[e, k].
 
-Motion (the deforming-channel workload): the vertex with Lagrangian position X moves in
+Motions: TGVMotion3D, the deformation of the moving 3D Taylor-Green vortex (Sec. 7.2),
+and WaveMotion, the deforming-channel workload: the vertex with Lagrangian position X moves in
 y by d(X, t) = A(X) sin(2 pi X/lambda - omega t) exp(-r^2/r0sq), A(X) = A0 + A1 X/Lx,
 r^2 = (Y - yc)^2 + (Z - zc)^2; its velocity is the time derivative of d at the same X
 (Sec. 5: velocity of the Lagrangian point).
@@ -55,6 +56,27 @@ class WaveMotion:
         v = np.zeros_like(X)
         v[:, 1] = -self.omega * self._amp(X) * np.cos(self.k * X[:, 0] - self.omega * t)
         return v
+
+
+class TGVMotion3D:
+    """Deformation of the moving 3D Taylor-Green vortex (Sec. 7.2, Eq. TGV_deformation): each
+    coordinate of the vertex with Lagrangian position X moves by
+    A sin(2 pi t / T) S(a) S(b), (a, b) the other two Lagrangian coordinates,
+    S(s) = sin(2 pi (s + L/2) / L); L = 2 pi, A = pi / 6, T = 20 in the paper."""
+
+    def __init__(self, A=math.pi / 6.0, T=20.0, L=2.0 * math.pi):
+        self.A, self.T, self.L = float(A), float(T), float(L)
+
+    def _shape(self, X):
+        S = np.sin(2.0 * math.pi * (X + 0.5 * self.L) / self.L)
+        return np.stack([S[:, 1] * S[:, 2], S[:, 0] * S[:, 2], S[:, 0] * S[:, 1]], axis=1)
+
+    def displacement(self, X, t):
+        return self.A * math.sin(2.0 * math.pi * t / self.T) * self._shape(X)
+
+    def velocity(self, X, t):
+        w = 2.0 * math.pi / self.T
+        return self.A * w * math.cos(w * t) * self._shape(X)
 
 
 class OracleSolver3D:
@@ -193,3 +215,14 @@ class OracleSolver3D:
         """int f over the mesh for nodal f (K, Np): sum_e J_e 1^T Mhat f_e."""
         _, J, _, _ = self.geometry(xv)
         return float(np.einsum('e,ij,ej->', J, self.ref.M, f))
+
+    def diagnostics(self, q, xv):
+        """Integrals of the state (Sec. 7.2 kinetic energy with rho_inf = 1), each the exact
+        integral of the nodal interpolant of its integrand: mass int rho,
+        E_K = (1/|Omega|) int rho |u|^2 / 2, momentum int rho u, int rho v, int rho w and
+        the volume |Omega|.  q has shape (K, 10, Np)."""
+        rho, mu, mv, mw = physics3d.macroscopic(np.moveaxis(q, 1, -1), self.c)
+        vol = self.integral(np.ones_like(rho), xv)
+        ke = self.integral(0.5 * (mu * mu + mv * mv + mw * mw) / rho, xv)
+        return {'mass': self.integral(rho, xv), 'kinetic_energy': ke / vol, 'momentum_x': self.integral(mu, xv),
+                'momentum_y': self.integral(mv, xv), 'momentum_z': self.integral(mw, xv), 'volume': vol}

@@ -136,9 +136,9 @@ def serving_requests(n=256, rate=50.0, seed=1):
 _KUHN_ORDERS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
 
 
-def periodic_box_tet_mesh(nx, ny, nz, L=(8.0, 2.0, 2.0), jitter=0.0, seed=DEFAULT_SEED):
-    """Periodic box [0, Lx] x [0, Ly] x [0, Lz] with nx x ny x nz hexahedral cells,
-    each split into 6 tetrahedra (Kuhn subdivision); K = 6 nx ny nz.
+def periodic_box_tet_mesh(nx, ny, nz, L=(8.0, 2.0, 2.0), jitter=0.0, seed=DEFAULT_SEED, origin=(0.0, 0.0, 0.0)):
+    """Periodic box origin + [0, Lx] x [0, Ly] x [0, Lz] with nx x ny x nz hexahedral
+    cells, each split into 6 tetrahedra (Kuhn subdivision); K = 6 nx ny nz.
 
     Unique vertices are the nx ny nz grid points, id = i + nx (j + ny k).  Every
     tetrahedron is listed with positive orientation (det[v1-v0, v2-v0, v3-v0] > 0).
@@ -159,6 +159,7 @@ def periodic_box_tet_mesh(nx, ny, nz, L=(8.0, 2.0, 2.0), jitter=0.0, seed=DEFAUL
     X[vid, 0] = (i * h[0]).ravel()
     X[vid, 1] = (j * h[1]).ravel()
     X[vid, 2] = (k * h[2]).ravel()
+    X += np.asarray(origin, dtype=np.float64)[None, :]
     if jitter > 0.0:
         ids = np.arange(nx * ny * nz, dtype=np.uint64)
         for d in range(3):
@@ -221,6 +222,24 @@ def channel_flow_3d(x, y, z, Ma, L=(8.0, 2.0, 2.0), eps=0.05):
     w = eps * np.cos(ax * x) * np.sin(ay * y)
     rho = 1.0 + Ma * Ma * eps * np.cos(ax * x) * np.cos(ay * y)
     return rho, u, v, w
+
+
+def taylor_green_3d(x, y, z, Ma, U0=1.0):
+    """Initial state of the 3D Taylor-Green vortex (Sec. 7.2): u = U0 sin x cos y cos z,
+    v = -U0 cos x sin y cos z, w = 0 on [-pi, pi]^3 (length scale 1); the paper gives no
+    density, so rho carries the incompressible pressure of this field,
+    p' = U0^2 (cos 2x + cos 2y)(cos 2z + 2) / 16, through p' = c^2 rho' with c = U0 / Ma."""
+    u = U0 * np.sin(x) * np.cos(y) * np.cos(z)
+    v = -U0 * np.cos(x) * np.sin(y) * np.cos(z)
+    w = np.zeros_like(x)
+    rho = 1.0 + Ma * Ma / 16.0 * (np.cos(2.0 * x) + np.cos(2.0 * y)) * (np.cos(2.0 * z) + 2.0)
+    return rho, u, v, w
+
+
+def tgv_box_tet_mesh(n, jitter=0.0, seed=DEFAULT_SEED):
+    """The moving 3D Taylor-Green vortex mesh (Sec. 7.2): the periodic cube [-pi, pi]^3 of
+    n^3 hexahedra, 6 tetrahedra each (K = 6 n^3; n = 32 gives the paper's 196608)."""
+    return periodic_box_tet_mesh(n, n, n, L=(2 * math.pi,) * 3, jitter=jitter, seed=seed, origin=(-math.pi,) * 3)
 
 
 # ---- two dimensions with boundaries: O-grid around a symmetric airfoil ------------------

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import physics3d
-from oracle.solver3d import OracleSolver3D, WaveMotion
+from oracle.solver3d import OracleSolver3D, TGVMotion3D, WaveMotion
 from paper_2607_00199_b300 import inputs
 
 TWO_PI = 2.0 * math.pi
@@ -125,3 +125,84 @@ def test_shear_wave_decays_at_nu_k_squared():
     rate = -math.log(amp(q) / amp(q0)) / T
     print('shear-wave decay rate %.5f, nu k^2 = %.5f' % (rate, 1.0 / Re))
     assert abs(rate - 1.0 / Re) < 0.03 / Re, rate
+
+
+# ---- the moving 3D Taylor-Green vortex (Sec. 7.2) ----------------------------------------
+
+def test_tgv_deformation_closed_forms():
+    """Eq. TGV_deformation: the velocity is the time derivative of the displacement, the
+    displacement vanishes at t = 0 and T/2 and peaks (amplitude A) at T/4, it is periodic on
+    the cube [-L/2, L/2]^3, and each component is independent of its own coordinate."""
+    m = TGVMotion3D()
+    rng = np.random.default_rng(3)
+    X = rng.uniform(-math.pi, math.pi, size=(50, 3))
+    h = 1e-5
+    for t in (0.0, 1.3, 7.9):
+        fd = (m.displacement(X, t + h) - m.displacement(X, t - h)) / (2 * h)
+        np.testing.assert_allclose(m.velocity(X, t), fd, atol=1e-9)
+    assert np.abs(m.displacement(X, 0.0)).max() == 0.0
+    assert np.abs(m.displacement(X, 10.0)).max() < 1e-15
+    corner = np.array([[-math.pi / 2, -math.pi / 2, -math.pi / 2]])   # S = sin(pi/2) = 1 there
+    np.testing.assert_allclose(m.displacement(corner, 5.0), [[math.pi / 6] * 3], rtol=1e-15)
+    for d in range(3):
+        Xs = X.copy()
+        Xs[:, d] += 2 * math.pi
+        np.testing.assert_allclose(m.displacement(Xs, 3.0), m.displacement(X, 3.0), atol=1e-14)
+        Xm = X.copy()
+        Xm[:, d] = rng.uniform(-math.pi, math.pi, size=50)
+        np.testing.assert_array_equal(m.displacement(Xm, 3.0)[:, d], m.displacement(X, 3.0)[:, d])
+
+
+@pytest.mark.parametrize('vel', [(0.0, 0.0, 0.0), (1.0, 0.3, -0.2)])
+def test_free_stream_preserved_on_the_tgv_deforming_cube(vel):
+    """GCL with all three grid-velocity components non-zero: a uniform state stays uniform."""
+    mesh = inputs.tgv_box_tet_mesh(4, jitter=0.1)
+    motion = TGVMotion3D(T=2.0)      # a faster period so that the mesh moves visibly in 10 steps
+    o = OracleSolver3D(mesh, 2, Ma=0.1, Re=1600, motion=motion)
+    q0 = _state(o, o.X, lambda x, y, z: (np.ones_like(x), vel[0] + 0 * x, vel[1] + 0 * x, vel[2] + 0 * x))
+    dt = inputs.cfl_dt_3d(mesh, 2, o.c, 0.5)
+    q, xv, _ = o.run(q0, o.X.copy(), 0.0, dt, 10)
+    assert np.abs(q - q0).max() < 1e-13
+    assert min(np.abs(xv[:, d] - o.X[:, d]).max() for d in range(3)) > 1e-3
+
+
+def test_tgv_diagnostics_closed_forms():
+    """Sec. 7.2 E_K: for u = sin x cos y cos z, v = -cos x sin y cos z, w = 0 and rho = 1 the
+    mean of |u|^2 / 2 over the cube is 1/8 and every momentum integral vanishes.  On the
+    unjittered cube every element is a translate of one of 6 shapes, so the integral of an
+    interpolant is a translation-invariant rule over n cells per direction, exact for
+    e^{i k.x} with every |k_d| < n (here |k_d| <= 2 < n = 3).  A periodic deformation
+    keeps the volume (2 pi)^3, and a uniform density integrates to it on the deformed mesh."""
+    mesh = inputs.tgv_box_tet_mesh(3)
+    o = OracleSolver3D(mesh, 3, Ma=0.1, Re=1600, motion=TGVMotion3D())
+    flow = lambda x, y, z: (np.ones_like(x),) + inputs.taylor_green_3d(x, y, z, 0.1)[1:]
+    d = o.diagnostics(_state(o, o.X, flow), o.X)
+    assert abs(d['kinetic_energy'] - 0.125) < 1e-13
+    assert abs(d['volume'] - TWO_PI ** 3) < 1e-11
+    for k in ('momentum_x', 'momentum_y', 'momentum_z'):
+        assert abs(d[k]) < 1e-12
+    # the interpolant is not exact: a frequency-3 mode is aliased to the mean by the same rule
+    d3 = o.diagnostics(_state(o, o.X, lambda x, y, z: (np.ones_like(x), np.sin(3 * x), 0 * x, 0 * x)), o.X)
+    assert abs(d3['kinetic_energy'] - 0.25) > 1e-3
+    mesh = inputs.tgv_box_tet_mesh(4, jitter=0.1)
+    o = OracleSolver3D(mesh, 2, Ma=0.1, Re=1600, motion=TGVMotion3D())
+    xv = o.X + o.motion.displacement(o.X, 5.0)
+    d = o.diagnostics(_state(o, xv, lambda x, y, z: (np.ones_like(x), 0 * x, 0 * x, 0 * x)), xv)
+    assert abs(d['volume'] - TWO_PI ** 3) < 1e-10 and abs(d['mass'] - TWO_PI ** 3) < 1e-10
+    assert abs(d['kinetic_energy']) == 0.0
+
+
+def test_tgv_mass_and_energy():
+    """The TGV state on the static cube keeps its mass to round-off; on the deforming cube
+    the nodal (non-conservative) ALE form keeps it to truncation error only.  The kinetic
+    energy decays in both."""
+    mesh = inputs.tgv_box_tet_mesh(3)
+    for motion, tol in ((TGVMotion3D(A=0.0), 1e-13), (TGVMotion3D(T=2.0), 1e-7)):
+        o = OracleSolver3D(mesh, 2, Ma=0.1, Re=100, motion=motion)
+        q0 = _state(o, o.X, lambda x, y, z: inputs.taylor_green_3d(x, y, z, 0.1))
+        dt = inputs.cfl_dt_3d(mesh, 2, o.c, 0.5)
+        d0 = o.diagnostics(q0, o.X)
+        q, xv, _ = o.run(q0, o.X.copy(), 0.0, dt, 8)
+        d1 = o.diagnostics(q, xv)
+        assert abs(d1['mass'] - d0['mass']) < tol * d0['mass']
+        assert d1['kinetic_energy'] < d0['kinetic_energy']
