@@ -95,6 +95,16 @@ WORKLOAD3_NAME = ('3D deforming channel: periodic box [0,8]x[0,2]x[0,2], 64x16x1
                   'exp(-r^2/0.25), CFL 0.5, uniform stream u=1 with a small transverse disturbance')
 
 
+WORKLOAD_TGV = dict(n=24, N=3, Ma=0.1, Re=1600.0, cfl=0.5, A=math.pi / 6, T=20.0, L=2 * math.pi)
+WORKLOAD_TGV_NAME = ('3D moving Taylor-Green vortex at the paper\'s per-GPU load: periodic cube [-pi,pi]^3, 24^3 hexes '
+                     '-> K=82944 tetrahedra (6 per hex), N=3 (Np=20), 10 fields, Ma=0.1, Re=1600, deformation '
+                     'x_d += (pi/6) sin(2 pi t/20) S(X_a) S(X_b), S(s) = sin(2 pi (s + pi)/(2 pi)), CFL 0.5, '
+                     'Taylor-Green initial state')
+# the paper's only timing (Sec. 7.2 weak-scaling table): 82944 tetrahedra per GPU, N = 3, one node of
+# 4 NVIDIA H100 (MareNostrum 5), mean t_step over 1000 SARK steps; context, another machine
+PAPER_TGV_T_STEP_MS = 14.18
+
+
 def sizes3(N):
     Np, Nfp = (N + 1) * (N + 2) * (N + 3) // 6, (N + 1) * (N + 2) // 2
     qc = (3 * N + 2) // 2
@@ -114,19 +124,20 @@ def flops3_per_element_stage(N):
 
 def bytes3_per_step(K, N, nv, elem_bytes):
     """Algorithmic HBM bytes of the 4 stage launches of one 3D step: 18 field arrays,
-    plus per launch the 48-byte mesh record of every element and x_n (24 B) and
-    S1, S2 (16 B) of every unique vertex."""
+    plus per launch the 48-byte mesh record of every element and x_n (24 B) and the
+    velocity shapes S1, S2 (48 B) of every unique vertex."""
     Np, _, _ = sizes3(N)
-    return 18 * K * 10 * Np * elem_bytes + 4 * (48 * K + 40 * nv)
+    return 18 * K * 10 * Np * elem_bytes + 4 * (48 * K + 72 * nv)
 
 
-def run_3d(torch, steps_fp64=10, steps_mixed=50, warmup=3):
-    """The 3D deforming-channel workload, FP64 and GB_MIXED (FP32 SIMT, no tensor cores),
-    timed like the 2D headline (CUDA-graph step replay between CUDA events), with the
-    mixed path's error against the FP64 path after the same steps."""
+def run_3d(torch, steps_fp64=10, steps_mixed=50, warmup=3, tgv=False):
+    """A 3D workload, FP64 and GB_MIXED (FP32 SIMT, no tensor cores), timed like the 2D
+    headline (CUDA-graph step replay between CUDA events), with the mixed path's error
+    against the FP64 path after the same steps: the deforming channel, or (tgv) the moving
+    Taylor-Green vortex at the per-GPU load of the paper's timing."""
     from paper_2607_00199_b300 import gb, inputs, state
-    W = WORKLOAD3
-    mesh = inputs.periodic_box_tet_mesh(*W['dims'], L=W['L'])
+    W = WORKLOAD_TGV if tgv else WORKLOAD3
+    mesh = inputs.tgv_box_tet_mesh(W['n']) if tgv else inputs.periodic_box_tet_mesh(*W['dims'], L=W['L'])
     tstream = torch.cuda.Stream()
     N = W['N']
     Np, Nfp, Nc = sizes3(N)
@@ -135,9 +146,13 @@ def run_3d(torch, steps_fp64=10, steps_mixed=50, warmup=3):
     qend = {}
     for name, prec, steps in (('fp64', gb.GB_FP64, steps_fp64), ('mixed', gb.GB_MIXED, steps_mixed)):
         s = gb.Solver(mesh, N, W['Ma'], W['Re'], precision=prec, stream=tstream.cuda_stream)
-        s.set_wave_motion(**W['wave'])
         xyz = s.nodes()
-        rho, u, v, w = inputs.channel_flow_3d(xyz[..., 0], xyz[..., 1], xyz[..., 2], W['Ma'])
+        if tgv:
+            s.set_tgv_motion(W['A'], W['T'], W['L'])
+            rho, u, v, w = inputs.taylor_green_3d(xyz[..., 0], xyz[..., 1], xyz[..., 2], W['Ma'])
+        else:
+            s.set_wave_motion(**W['wave'])
+            rho, u, v, w = inputs.channel_flow_3d(xyz[..., 0], xyz[..., 1], xyz[..., 2], W['Ma'])
         q0 = state.equilibrium_fields3(rho, u, v, w, s.c)
         dt = inputs.cfl_dt_3d(mesh, N, s.c, W['cfl'])
         ms, kms = time_path(torch, s, q0, dt, steps, warmup, lambda: None, tstream)
@@ -173,14 +188,22 @@ def run_3d(torch, steps_fp64=10, steps_mixed=50, warmup=3):
     rest = np.zeros_like(qend['fp64'])
     rest[:, 0, :] = 1.0
     dq = qend['mixed'] - qend['fp64']
-    return {'workload': WORKLOAD3_NAME, 'K': K, 'n_vert': nv, 'N': N, 'Np': Np, 'fields': 10, 'dof': K * Np * 10,
+    out = {'workload': WORKLOAD_TGV_NAME if tgv else WORKLOAD3_NAME, 'K': K, 'n_vert': nv, 'N': N, 'Np': Np,
+           'fields': 10, 'dof': K * Np * 10}
+    if tgv:
+        out['paper_context'] = {
+            't_step_ms': PAPER_TGV_T_STEP_MS, 'hardware': '4x NVIDIA H100 (one MareNostrum 5 node), 82944 tets per GPU',
+            'precision': 'not stated', 'ratio_fp64': PAPER_TGV_T_STEP_MS / res['fp64']['ms_per_step'],
+            'ratio_mixed': PAPER_TGV_T_STEP_MS / res['mixed']['ms_per_step'],
+            'note': 'paper t_step / this t_step on one B300; another machine and a multi-GPU run: context, not a target'}
+    return dict(out, **{
             'metric': 'DOF-stage updates/s', 'fp64': res['fp64'], 'mixed': res['mixed'],
             'mixed_speedup_vs_fp64': res['mixed']['value'] / res['fp64']['value'],
             'mixed_error': {'rel_l2_fields': float(np.linalg.norm(dq) / np.linalg.norm(qend['fp64'])),
                             'rel_l2_perturbation': float(np.linalg.norm(dq) / np.linalg.norm(qend['fp64'] - rest)),
                             'steps': 10, 'against': 'GB_FP64 3D path (oracle-parity-tested) from the same state'},
             'timing': 'ms_per_step: gb_step (CUDA graph replay) between CUDA events; inputs larger than L2 '
-                      '(FP64 state 157 MB per array, FP32 79 MB)'}
+                      '(FP64 state %d MB per array, FP32 %d MB)' % (K * Np * 80 // 10 ** 6, K * Np * 40 // 10 ** 6)})
 
 
 WORKLOAD_AF = dict(ni=256, nj=192, R=20.0, N=4, Ma=0.1, Re=1000.0, A=0.25, T=2.0, far=(1.0, 1.0, 0.0), cfl=0.5)
@@ -239,7 +262,8 @@ def parse():
     p.add_argument('--no-cpu-baseline', action='store_true')
     p.add_argument('--no-serve', action='store_true', help='skip the serving-stream measurement')
     p.add_argument('--serve-only', action='store_true', help='only the serving-stream measurement')
-    p.add_argument('--no-3d', action='store_true', help='skip the 3D deforming-channel measurement')
+    p.add_argument('--no-3d', action='store_true',
+                   help='skip the 3D measurements (deforming channel, moving Taylor-Green vortex)')
     p.add_argument('--no-airfoil', action='store_true', help='skip the plunging-airfoil measurement')
     p.add_argument('--serve-requests', type=int, default=256)
     p.add_argument('--serve-steps', type=int, default=500)
@@ -580,6 +604,7 @@ def run_ours(args):
     }
     if ws == 1 and not args.no_3d:
         line['d3'] = run_3d(torch)
+        line['tgv3d'] = run_3d(torch, tgv=True)
     if ws == 1 and not args.no_airfoil:
         line['airfoil'] = run_airfoil(torch)
     if ws == 1 and not args.no_serve:

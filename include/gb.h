@@ -49,6 +49,7 @@ extern "C" {
 #define GB_MOTION_STATIC 0
 #define GB_MOTION_SINXY  1
 #define GB_MOTION_PLUNGE 2   /* rigid plunge: every vertex moves by (0, A sin(2 pi t / T)) */
+#define GB_MOTION_TGV3D  3   /* dim = 3: the deformation of the moving Taylor-Green vortex (below) */
 
 #define GB_BC_INTERIOR 0     /* face shared with another element (or its periodic copy) */
 #define GB_BC_WALL     1     /* wall moving with the mesh: bounce-back ghost state */
@@ -73,9 +74,13 @@ typedef struct {
  * GB_MOTION_SINXY displaces both coordinates of a vertex with Lagrangian
  * position X by A sin(2 pi t / T) sin(2 pi X / Lx) sin(2 pi Y / Ly);
  * GB_MOTION_PLUNGE moves every vertex by (0, A sin(2 pi t / T)) (the rigid plunge of
- * the airfoil case of Sec. 7; Lx, Ly unused). */
+ * the airfoil case of Sec. 7; Lx, Ly unused);
+ * GB_MOTION_TGV3D (dim = 3 only; Sec. 7.2, Eq. TGV_deformation) moves each coordinate of
+ * the vertex at (X, Y, Z) by A sin(2 pi t / T) S(a) S(b) over the other two coordinates
+ * a, b, with S(s) = sin(2 pi (s + L/2) / L), L = Lx (Ly unused); the paper's cube
+ * [-pi, pi]^3 takes A = pi/6, T = 20, L = 2 pi. */
 typedef struct {
-  int32_t kind;              /* GB_MOTION_STATIC, GB_MOTION_SINXY or GB_MOTION_PLUNGE */
+  int32_t kind;              /* GB_MOTION_STATIC, GB_MOTION_SINXY, GB_MOTION_PLUNGE or GB_MOTION_TGV3D */
   double A, T, Lx, Ly;
 } gb_motion;
 
@@ -280,15 +285,21 @@ int gb_sark_coefficients(double gamma, double *E, double *A, double *B);
  *    q5..q10 the second-order coefficients (equilibrium q_{i+j} = q_i q_j / q1,
  *    q_{2i} = q_i^2 / (sqrt2 q1)); fields 1..4 step with RK4, 5..10 with the
  *    exponential SARK coefficients.
- *  - motion: gb_set_wave_motion (below); gb_set_motion accepts GB_MOTION_STATIC.
+ *  - motion: gb_set_wave_motion (below), or gb_set_motion with GB_MOTION_STATIC or
+ *    GB_MOTION_TGV3D (GB_EINVAL for non-finite A, T <= 0 or Lx = 0).
  *  - gb_nodes writes n_elem x Np x 3; gb_vertices / gb_set_vertices n_vert x 3.
  *  - GB_MIXED: FP32 perturbations around the rest state in the canonical layout
  *    (gb_rhs takes and returns that layout; gb_state_ptr points at it), FP64
  *    geometry, motion and SARK coefficients; no tensor-core contractions.
  *  - gb_step, gb_step_timed (kernel_ms[0..4] as in 2D), gb_rhs, gb_sync, gb_info,
  *    gb_set_graph, gb_set_stream, gb_state_ptr, gb_destroy and gb_last_error
- *    work as in 2D.  Groups, gb_rhs_noalloc, diagnostics and launch
- *    configuration return GB_EINVAL for dim = 3 solvers. */
+ *    work as in 2D.
+ *  - diagnostics: gb_diagnostics gives out[4] = the volume |Omega| (the rest as in 2D);
+ *    gb_diagnostics3d (below) adds int rho w.  gb_set_diagnostics and
+ *    gb_diagnostics_history work as in 2D with the same 6-double records (t, int rho,
+ *    E_K, int rho u, int rho v, |Omega|), taken by separate reduction launches at the
+ *    end of the recorded steps (inside the step's CUDA graph).
+ *  - groups, gb_rhs_noalloc and launch configuration return GB_EINVAL. */
 
 /* Travelling-wave lateral motion of a deforming channel (dim = 3): the vertex with
  * Lagrangian position (X, Y, Z) moves in y by
@@ -303,6 +314,14 @@ typedef struct {
  * the next step).  A0 = A1 = 0 or omega = 0 is a static mesh.  GB_EINVAL for a
  * 2D solver, non-finite parameters, Lx = 0, wavelength = 0 or r0sq <= 0. */
 int gb_set_wave_motion(gb_solver *s, const gb_wave_motion *m);
+
+/* gb_diagnostics3d: integrals of the current state of a dim = 3 solver, each the exact
+ * integral of the degree-N nodal interpolant (J sum_i w_i f_i per tetrahedron,
+ * w = 1^T Mhat): out[0] = int rho, out[1] = E_K = (1/|Omega|) int rho |u|^2 / 2
+ * (rho_inf = 1; the kinetic energy of Sec. 7.2), out[2..4] = int rho u, rho v, rho w,
+ * out[5] = |Omega|.  Host array of 6 doubles; synchronises the stream; FP64 reductions
+ * in a fixed order in both precisions.  GB_EINVAL for a 2D solver. */
+int gb_diagnostics3d(gb_solver *s, double *out);
 
 /* gb_reference_operators3d: the library's order-N tetrahedral operators (Sec. 3),
  * row-major FP64, host only: r, s, t [Np]; Dr, Ds, Dt [Np x Np]; LIFT [Np x 4 Nfp]

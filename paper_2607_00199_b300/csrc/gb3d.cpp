@@ -29,6 +29,7 @@ struct Solver3 {
   RefOps3 ref;
   Wave3 wave{0, 0, 1, 1, 0, 1, 0, 0};
   int moving = 0;
+  double omega = 0.0;          // angular frequency of the motion's time factors cos, sin(omega t)
   double coef_dt = -1.0;
   SarkCoef co{};
   cudaGraphExec_t graph = nullptr;
@@ -44,6 +45,12 @@ struct Solver3 {
   void *d_qn = nullptr, *d_b1 = nullptr, *d_b2 = nullptr, *d_F0 = nullptr, *d_acc = nullptr;
   double *d_tmp = nullptr;
   size_t tmp_bytes = 0;
+  // diagnostics: 1^T Mhat (Np), 6 result slots, block partials; the record ring and its
+  // counters (steps since recording began, records written)
+  double *d_diag = nullptr, *d_hist = nullptr;
+  int64_t *d_hctl = nullptr;
+  int diag_every = 0;
+  int64_t diag_cap = 0;
   int64_t device_bytes = 0;
 };
 
@@ -69,7 +76,7 @@ static int alloc3(Solver3 *s, void **p, size_t bytes) {
 
 static void free3(Solver3 *s) {
   void *ptrs[] = {s->d_ops, s->d_tab, s->d_bary, s->d_mesh, s->d_X, s->d_xn, s->d_shape, s->d_clock, s->d_status,
-                  s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp};
+                  s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp, s->d_diag, s->d_hist, s->d_hctl};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   if (s->graph) cudaGraphExecDestroy(s->graph);
@@ -235,7 +242,7 @@ int s3_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   arc = arc ? arc : alloc3(s, (void **)&s->d_mesh, sizeof(MeshRec3) * K);
   arc = arc ? arc : alloc3(s, (void **)&s->d_X, sizeof(double) * 3 * nv);
   arc = arc ? arc : alloc3(s, (void **)&s->d_xn, sizeof(double) * 3 * nv);
-  arc = arc ? arc : alloc3(s, (void **)&s->d_shape, sizeof(double) * 2 * nv);
+  arc = arc ? arc : alloc3(s, (void **)&s->d_shape, sizeof(double) * 6 * nv);
   arc = arc ? arc : alloc3(s, (void **)&s->d_clock, sizeof(double) * 4);
   arc = arc ? arc : alloc3(s, (void **)&s->d_status, sizeof(int));
   for (void **p : fields) arc = arc ? arc : alloc3(s, p, fbytes);
@@ -250,7 +257,7 @@ int s3_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   ce = cudaMemcpyAsync(s->d_mesh, rec.data(), sizeof(MeshRec3) * K, cudaMemcpyHostToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_X, mesh->X, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_xn, mesh->X, sizeof(double) * 3 * nv, cudaMemcpyHostToDevice, s->stream);
-  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->d_shape, 0, sizeof(double) * 2 * nv, s->stream);
+  if (ce == cudaSuccess) ce = cudaMemsetAsync(s->d_shape, 0, sizeof(double) * 6 * nv, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_clock, clock0, sizeof(clock0), cudaMemcpyHostToDevice, s->stream);
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_status, &zero, sizeof(int), cudaMemcpyHostToDevice, s->stream);
   for (void **p : fields)
@@ -278,8 +285,9 @@ const char *s3_error(Solver3 *s) { return s->err.c_str(); }
 
 int s3_set_static(Solver3 *s) {
   s->moving = 0;
+  s->omega = 0.0;
   drop_graph3(s);
-  cudaError_t ce = cudaMemsetAsync(s->d_shape, 0, sizeof(double) * 2 * s->nv, s->stream);
+  cudaError_t ce = cudaMemsetAsync(s->d_shape, 0, sizeof(double) * 6 * s->nv, s->stream);
   return ce == cudaSuccess ? GB_OK : cuda_fail3(s, ce, "gb_set_motion (dim = 3)");
 }
 
@@ -291,8 +299,19 @@ int s3_set_wave_motion(Solver3 *s, const gb_wave_motion *m) {
     return fail3(s, nullptr, GB_EINVAL, "gb_wave_motion needs Lx != 0, wavelength != 0 and r0sq > 0");
   s->wave = Wave3{m->A0, m->A1, m->Lx, m->wavelength, m->omega, m->r0sq, m->yc, m->zc};
   s->moving = (m->A0 != 0.0 || m->A1 != 0.0) && m->omega != 0.0;
+  s->omega = m->omega;
   drop_graph3(s);
   int rc = launch_shape3(s->d_X, s->d_shape, s->nv, s->wave, s->stream);
+  return rc ? cuda_fail3(s, (cudaError_t)rc, "shape kernel (dim = 3)") : GB_OK;
+}
+
+int s3_set_tgv_motion(Solver3 *s, double A, double T, double L) {
+  if (!std::isfinite(A) || !std::isfinite(T) || !std::isfinite(L) || !(T > 0.0) || !(L != 0.0))
+    return fail3(s, nullptr, GB_EINVAL, "GB_MOTION_TGV3D needs finite A, T > 0 and L != 0");
+  s->omega = 2.0 * 3.14159265358979323846 / T;
+  s->moving = A != 0.0;
+  drop_graph3(s);
+  int rc = launch_shape3_tgv(s->d_X, s->d_shape, s->nv, A, s->omega, L, s->stream);
   return rc ? cuda_fail3(s, (cudaError_t)rc, "shape kernel (dim = 3)") : GB_OK;
 }
 
@@ -380,6 +399,97 @@ static void set_coef3(Solver3 *s, double dt) {
   s->coef_dt = dt;
 }
 
+static Diag3Args diag_args3(Solver3 *s) {
+  Diag3Args d;
+  d.q = s->d_qn;
+  d.is_float = s->precision != GB_FP64;
+  d.Np = s->Np;
+  d.mesh = s->d_mesh;
+  d.xn = s->d_xn;
+  for (int k = 0; k < 3; ++k) d.period[k] = s->period[k];
+  d.wq = s->d_diag;
+  d.c = s->c;
+  d.K = s->K;
+  d.part = s->d_diag + s->Np + 6;
+  return d;
+}
+
+static int ensure_diag3(Solver3 *s) {
+  if (s->d_diag) return GB_OK;
+  int rc = alloc3(s, (void **)&s->d_diag, sizeof(double) * (s->Np + 6 + 6 * (size_t)kDiag3MaxBlocks));
+  if (rc) return rc;
+  cudaError_t ce = cudaMemcpyAsync(s->d_diag, s->ref.wq.data(), sizeof(double) * s->Np, cudaMemcpyHostToDevice, s->stream);
+  return ce == cudaSuccess ? GB_OK : cuda_fail3(s, ce, "diagnostics set-up (dim = 3)");
+}
+
+int s3_diagnostics(Solver3 *s, double *out) {
+  int rc = ensure_diag3(s);
+  if (rc) return rc;
+  rc = launch_diagnostics3(diag_args3(s), s->d_diag + s->Np, s->stream);
+  if (rc) return cuda_fail3(s, (cudaError_t)rc, "gb_diagnostics (dim = 3)");
+  double r[6];
+  cudaError_t ce = cudaMemcpyAsync(r, s->d_diag + s->Np, sizeof(r), cudaMemcpyDeviceToHost, s->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  if (ce != cudaSuccess) return cuda_fail3(s, ce, "gb_diagnostics (dim = 3)");
+  out[0] = r[0];
+  out[1] = r[1] / r[5];
+  out[2] = r[2];
+  out[3] = r[3];
+  out[4] = r[4];
+  out[5] = r[5];
+  return GB_OK;
+}
+
+static void free_ring3(Solver3 *s) {
+  if (s->d_hist) {
+    cudaFree(s->d_hist);
+    s->device_bytes -= (int64_t)(sizeof(double) * 6 * (size_t)s->diag_cap);
+    s->d_hist = nullptr;
+  }
+  if (s->d_hctl) {
+    cudaFree(s->d_hctl);
+    s->device_bytes -= (int64_t)(2 * sizeof(int64_t));
+    s->d_hctl = nullptr;
+  }
+  s->diag_every = 0;
+  s->diag_cap = 0;
+}
+
+int s3_set_diagnostics(Solver3 *s, int every, int64_t capacity) {
+  cudaError_t ce = s->stream ? cudaStreamSynchronize(s->stream) : cudaDeviceSynchronize();
+  if (ce != cudaSuccess) return cuda_fail3(s, ce, "gb_set_diagnostics (dim = 3)");
+  drop_graph3(s);
+  free_ring3(s);
+  if (every == 0) return GB_OK;
+  int rc = ensure_diag3(s);
+  if (!rc) rc = alloc3(s, (void **)&s->d_hist, sizeof(double) * 6 * (size_t)capacity);
+  if (!rc) {
+    s->diag_cap = capacity;
+    rc = alloc3(s, (void **)&s->d_hctl, 2 * sizeof(int64_t));
+  }
+  if (rc) {
+    free_ring3(s);
+    return rc;
+  }
+  ce = cudaMemsetAsync(s->d_hctl, 0, 2 * sizeof(int64_t), s->stream);
+  if (ce != cudaSuccess) {
+    free_ring3(s);
+    return cuda_fail3(s, ce, "gb_set_diagnostics (dim = 3)");
+  }
+  s->diag_every = every;
+  return GB_OK;
+}
+
+void *s3_stream(Solver3 *s) { return (void *)s->stream; }
+
+int s3_diag_ring(Solver3 *s, const double **hist, const int64_t **ctl, int *every, int64_t *capacity) {
+  *hist = s->d_hist;
+  *ctl = s->d_hctl;
+  *every = s->diag_every;
+  *capacity = s->diag_cap;
+  return GB_OK;
+}
+
 static Stage3Args base3(Solver3 *s) {
   Stage3Args a;
   memset(&a, 0, sizeof(a));
@@ -395,7 +505,7 @@ static Stage3Args base3(Solver3 *s) {
   a.c = s->c;
   a.inv_tau = 1.0 / s->tau;
   a.moving = s->moving;
-  a.omega = s->wave.omega;
+  a.omega = s->omega;
   a.co = s->co;
   return a;
 }
@@ -434,6 +544,12 @@ static int step_once3(Solver3 *s, double dt, cudaEvent_t *ev) {
   int rc = launch_vertex_update3(s->d_xn, s->d_shape, s->nv, s->d_clock, dt, s->stream);
   if (rc) return cuda_fail3(s, (cudaError_t)rc, "vertex update launch (dim = 3)");
   if (ev) cudaEventRecord(ev[9], s->stream);
+  if (s->diag_every > 0) {
+    // integrals of q_{n+1} on x_{n+1} at t_{n+1} (the clock has advanced), every diag_every-th step
+    rc = launch_diagnostics3_record(diag_args3(s), s->d_clock, s->d_hctl, s->diag_every, s->d_hist, s->diag_cap,
+                                    s->stream);
+    if (rc) return cuda_fail3(s, (cudaError_t)rc, "diagnostics record launch (dim = 3)");
+  }
   return GB_OK;
 }
 

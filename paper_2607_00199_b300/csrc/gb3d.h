@@ -20,6 +20,12 @@ void s3_destroy(Solver3 *s);
 const char *s3_error(Solver3 *s);
 int s3_set_static(Solver3 *s);
 int s3_set_wave_motion(Solver3 *s, const gb_wave_motion *m);
+int s3_set_tgv_motion(Solver3 *s, double A, double T, double L);
+int s3_diagnostics(Solver3 *s, double *out6);
+int s3_set_diagnostics(Solver3 *s, int every, int64_t capacity);
+// the record ring of gb_set_diagnostics (device pointers; NULL and every = 0 when off)
+void *s3_stream(Solver3 *s);   // the solver's cudaStream_t (NULL = legacy default stream)
+int s3_diag_ring(Solver3 *s, const double **hist, const int64_t **ctl, int *every, int64_t *capacity);
 int s3_set_fields(Solver3 *s, const double *q, double t);
 int s3_fields(Solver3 *s, double *q, double *t);
 int s3_sync(Solver3 *s);

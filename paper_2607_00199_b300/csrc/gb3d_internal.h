@@ -29,7 +29,7 @@ struct Stage3Args {
   const void *qin, *qn;
   void *qout, *F0, *acc, *Fout;
   const double *xn;      // n_vert x 3 current vertex positions
-  const double *shape;   // n_vert x 2: S1, S2 of the y-velocity
+  const double *shape;   // n_vert x 6: velocity shapes S1 (xyz), S2 (xyz)
   const MeshRec3 *mesh;
   const void *ops;       // operator block (T), layout in gb_kernels3d.cu
   const int *tab;        // neighbour face-node table [4][4][6][Nfp], then fmask [4][Nfp]
@@ -45,9 +45,30 @@ struct Stage3Args {
   SarkCoef co;
 };
 
+// inputs of the diagnostics reductions: the canonical state (FP64, or FP32 perturbations
+// of the rest state), current vertices, 1^T Mhat, and scratch for 6 doubles per block
+struct Diag3Args {
+  const void *q;
+  bool is_float;
+  int Np;
+  const MeshRec3 *mesh;
+  const double *xn;
+  double period[3];
+  const double *wq;
+  double c;
+  int64_t K;
+  double *part;
+};
+constexpr int kDiag3MaxBlocks = 1184;
+
 int launch_stage3(int N, bool fp64, const Stage3Args &a, void *stream, int num_sms);
+int diagnostics3_blocks(int64_t K);
+int launch_diagnostics3(const Diag3Args &d, double *out, void *stream);
+int launch_diagnostics3_record(const Diag3Args &d, const double *clock, int64_t *ctl, int every, double *hist,
+                               int64_t cap, void *stream);
 int launch_vertex_update3(double *xn, const double *shape, int64_t nv, double *clock, double dt, void *stream);
 int launch_shape3(const double *X, double *shape, int64_t nv, const Wave3 &m, void *stream);
+int launch_shape3_tgv(const double *X, double *shape, int64_t nv, double A, double omega, double L, void *stream);
 int launch_nodes3(const double *bary, int Np, const double *xn, const MeshRec3 *mesh, const double period[3], int64_t K,
                   double *out, void *stream);
 int launch_cast3(double *d, float *f, int64_t K, int Np, bool to_float, void *stream);

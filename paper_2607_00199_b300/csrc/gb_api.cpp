@@ -536,9 +536,11 @@ extern "C" {
 int gb_set_motion(gb_solver *s, const gb_motion *m) {
   if (!s || !m) return fail(s, GB_EINVAL, "NULL argument");
   if (s->s3) {
-    if (m->kind != GB_MOTION_STATIC) return fail(s, GB_EINVAL, "dim = 3 solvers take gb_set_wave_motion (gb_set_motion accepts GB_MOTION_STATIC only)");
-    return gb::s3_set_static(s->s3);
+    if (m->kind == GB_MOTION_STATIC) return gb::s3_set_static(s->s3);
+    if (m->kind == GB_MOTION_TGV3D) return gb::s3_set_tgv_motion(s->s3, m->A, m->T, m->Lx);
+    return fail(s, GB_EINVAL, "dim = 3 solvers take GB_MOTION_STATIC, GB_MOTION_TGV3D or gb_set_wave_motion");
   }
+  if (m->kind == GB_MOTION_TGV3D) return fail(s, GB_EINVAL, "GB_MOTION_TGV3D applies to dim = 3 solvers");
   if (m->kind != GB_MOTION_STATIC && m->kind != GB_MOTION_SINXY && m->kind != GB_MOTION_PLUNGE)
     return fail(s, GB_EINVAL, "unknown motion kind");
   if (m->kind == GB_MOTION_PLUNGE && (!(m->T > 0.0) || !std::isfinite(m->A) || !std::isfinite(m->T)))
@@ -914,9 +916,9 @@ const char *gb_group_last_error(gb_group *g) { return g ? g->err.c_str() : g_cre
 
 int gb_set_diagnostics(gb_solver *s, int every, int64_t capacity) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
-  if (s->s3) return fail(s, GB_EINVAL, "not available for dim = 3 solvers");
   if (every < 0 || (every > 0 && (capacity < 1 || capacity > ((int64_t)1 << 32))))
     return fail(s, GB_EINVAL, "every must be >= 0 and capacity in 1 .. 2^32");
+  if (s->s3) return gb::s3_set_diagnostics(s->s3, every, capacity);
   cudaError_t ce = s->stream ? cudaStreamSynchronize(s->stream) : cudaDeviceSynchronize();
   if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_diagnostics");
   drop_graph(s);
@@ -941,37 +943,57 @@ int gb_set_diagnostics(gb_solver *s, int every, int64_t capacity) {
 
 int gb_diagnostics_history(gb_solver *s, double *out, int64_t max, int64_t *count, int64_t *total) {
   if (!s || !count || (max > 0 && !out) || max < 0) return fail(s, GB_EINVAL, "NULL argument or max < 0");
-  if (s->s3) return fail(s, GB_EINVAL, "not available for dim = 3 solvers");
   *count = 0;
   if (total) *total = 0;
-  if (s->diag_every <= 0) return GB_OK;
+  const double *hist = s->d_hist;
+  const int64_t *hctl = s->d_hctl;
+  int every = s->diag_every;
+  int64_t cap = s->diag_cap;
+  if (s->s3) gb::s3_diag_ring(s->s3, &hist, &hctl, &every, &cap);
+  if (every <= 0) return GB_OK;
+  cudaStream_t st = s->s3 ? (cudaStream_t)gb::s3_stream(s->s3) : s->stream;
   int64_t ctl[2] = {0, 0};
-  cudaError_t ce = cudaMemcpyAsync(ctl, s->d_hctl, sizeof(ctl), cudaMemcpyDeviceToHost, s->stream);
-  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
+  cudaError_t ce = cudaMemcpyAsync(ctl, hctl, sizeof(ctl), cudaMemcpyDeviceToHost, st);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_diagnostics_history");
-  const int64_t kept = ctl[1] < s->diag_cap ? ctl[1] : s->diag_cap;
+  const int64_t kept = ctl[1] < cap ? ctl[1] : cap;
   const int64_t n = kept < max ? kept : max;
   // the n most recent records, oldest first: record j sits in slot j mod cap, so at
   // most two contiguous pieces of the ring
   if (n > 0) {
-    const int64_t a = (ctl[1] - n) % s->diag_cap;
-    const int64_t first = n < s->diag_cap - a ? n : s->diag_cap - a;
-    ce = cudaMemcpyAsync(out, s->d_hist + 6 * a, 6 * sizeof(double) * (size_t)first, cudaMemcpyDeviceToHost, s->stream);
+    const int64_t a = (ctl[1] - n) % cap;
+    const int64_t first = n < cap - a ? n : cap - a;
+    ce = cudaMemcpyAsync(out, hist + 6 * a, 6 * sizeof(double) * (size_t)first, cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess && first < n)
-      ce = cudaMemcpyAsync(out + 6 * first, s->d_hist, 6 * sizeof(double) * (size_t)(n - first), cudaMemcpyDeviceToHost,
-                           s->stream);
+      ce = cudaMemcpyAsync(out + 6 * first, hist, 6 * sizeof(double) * (size_t)(n - first), cudaMemcpyDeviceToHost, st);
     if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_diagnostics_history");
   }
-  ce = cudaStreamSynchronize(s->stream);
+  ce = cudaStreamSynchronize(st);
   if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_diagnostics_history");
   *count = n;
   if (total) *total = ctl[1];
   return GB_OK;
 }
 
+int gb_diagnostics3d(gb_solver *s, double *out) {
+  if (!s || !out) return fail(s, GB_EINVAL, "NULL argument");
+  if (!s->s3) return fail(s, GB_EINVAL, "gb_diagnostics3d applies to dim = 3 solvers");
+  return gb::s3_diagnostics(s->s3, out);
+}
+
 int gb_diagnostics(gb_solver *s, double *out) {
   if (!s || !out) return fail(s, GB_EINVAL, "NULL argument");
-  if (s->s3) return fail(s, GB_EINVAL, "not available for dim = 3 solvers");
+  if (s->s3) {
+    double r[6];
+    int rc = gb::s3_diagnostics(s->s3, r);
+    if (rc) return rc;
+    out[0] = r[0];
+    out[1] = r[1];
+    out[2] = r[2];
+    out[3] = r[3];
+    out[4] = r[5];
+    return GB_OK;
+  }
   {
     int rc = ensure_diag(s);
     if (rc) return rc;

@@ -65,8 +65,8 @@ struct Op3 {
 };
 
 // geometry block per element (in T): G^-1 (9, row-major r_x r_y r_z s_x ... t_z),
-// vertex y-velocities (4), per face nx ny nz Fscale (16)
-constexpr int GEO3 = 32;
+// vertex grid velocities (4 x 3, vertex-major), per face nx ny nz Fscale (16), padding
+constexpr int GEO3 = 40, GEO3_V = 9, GEO3_F = 21;
 
 
 template <typename T> __device__ __forceinline__ T fma3(T a, T b, T c);
@@ -92,7 +92,8 @@ __device__ __forceinline__ void apply_An(T nx, T ny, T nz, const T (&w)[10], T (
   y[9] = s2 * nz * w[3];
 }
 
-// stage motion factors from the device clock: v_y = g1 S1 + g2 S2, y_i = y_n + x1 S1 + x2 S2
+// stage motion factors from the device clock: v = g1 S1 + g2 S2, x_i = x_n + x1 S1 + x2 S2
+// (S1, S2: the per-vertex velocity shapes of the motion, 3 components each)
 struct Motion3 { double g1, g2, x1, x2; };
 
 __device__ __forceinline__ Motion3 stage_motion3(const Stage3Args &a, int stage) {
@@ -191,16 +192,20 @@ stage3_kernel(const Stage3Args a) {
     for (int e = tid; e < nel; e += nthr) {
       const MeshRec3 rec = a.mesh[elem0 + e];
       double P0[3];
-      T dv[4][3], vy[4];   // dv[k] = P_k - P_0 (dv[0] = 0)
+      T dv[4][3], vv[4][3];   // dv[k] = P_k - P_0 (dv[0] = 0); vv[k] the grid velocity of vertex k
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int64_t v = rec.v[k];
-        const double2 sv = reinterpret_cast<const double2 *>(a.shape)[v];
+        const double2 *sh = reinterpret_cast<const double2 *>(a.shape) + 3 * v;
+        const double2 s01 = sh[0], s23 = sh[1], s45 = sh[2];
+        const double S1[3] = {s01.x, s01.y, s23.x}, S2[3] = {s23.y, s45.x, s45.y};
         double Pk[3];
 #pragma unroll
-        for (int d = 0; d < 3; ++d) Pk[d] = a.xn[3 * v + d] + rec.shift[3 * k + d] * a.period[d];
-        Pk[1] += x1 * sv.x + x2 * sv.y;
-        vy[k] = (T)(g1 * sv.x + g2 * sv.y);
+        for (int d = 0; d < 3; ++d) {
+          Pk[d] = a.xn[3 * v + d] + rec.shift[3 * k + d] * a.period[d];
+          Pk[d] += x1 * S1[d] + x2 * S2[d];
+          vv[k][d] = (T)(g1 * S1[d] + g2 * S2[d]);
+        }
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           if (k == 0) P0[d] = Pk[d];
@@ -228,7 +233,9 @@ stage3_kernel(const Stage3Args a) {
       g[5] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) * iJ;
       g[8] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) * iJ;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) g[9 + k] = vy[k];
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) g[GEO3_V + 3 * k + d] = vv[k][d];
       // faces (local vertex triples) and the orientation of (P_b - P_a) x (P_c - P_a)
       // relative to the outward normal; compile-time so that dv stays in registers
       constexpr int fvt[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
@@ -241,10 +248,10 @@ stage3_kernel(const Stage3Args a) {
         const T nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
         const T len = sqrt(nx * nx + ny * ny + nz * nz);
         const T sg = (T)fsign[f] / len;
-        g[13 + 4 * f] = nx * sg;
-        g[14 + 4 * f] = ny * sg;
-        g[15 + 4 * f] = nz * sg;
-        g[16 + 4 * f] = (T)0.25 * len * iJ;   // face area / (2 J)
+        g[GEO3_F + 4 * f] = nx * sg;
+        g[GEO3_F + 1 + 4 * f] = ny * sg;
+        g[GEO3_F + 2 + 4 * f] = nz * sg;
+        g[GEO3_F + 3 + 4 * f] = (T)0.25 * len * iJ;   // face area / (2 J)
       }
     }
     __syncthreads();
@@ -269,7 +276,10 @@ stage3_kernel(const Stage3Args a) {
       }
       const T *g = sgeo + e_loc * GEO3;
       const T *bl = sops + L::Bary + 4 * n_loc;
-      const T vgy = bl[0] * g[9] + bl[1] * g[10] + bl[2] * g[11] + bl[3] * g[12];
+      const T *gv = g + GEO3_V;
+      const T vgx = bl[0] * gv[0] + bl[1] * gv[3] + bl[2] * gv[6] + bl[3] * gv[9];
+      const T vgy = bl[0] * gv[1] + bl[1] * gv[4] + bl[2] * gv[7] + bl[3] * gv[10];
+      const T vgz = bl[0] * gv[2] + bl[1] * gv[5] + bl[2] * gv[8] + bl[3] * gv[11];
       T qx[10], qy[10], qz[10];
 #pragma unroll
       for (int f = 0; f < 10; ++f) {
@@ -277,13 +287,14 @@ stage3_kernel(const Stage3Args a) {
         qy[f] = fma3(g[1], qr[f], fma3(g[4], qs[f], g[7] * qt[f]));
         qz[f] = fma3(g[2], qr[f], fma3(g[5], qs[f], g[8] * qt[f]));
       }
-      // -c (At_x q_x + At_y q_y + At_z q_z) + v_G . grad q, with v_G = (0, vgy, 0)
+      // -c (At_x q_x + At_y q_y + At_z q_z) + v_G . grad q
       T ax[10], ay[10], az[10];
       apply_An<T>((T)1, (T)0, (T)0, qx, ax);
       apply_An<T>((T)0, (T)1, (T)0, qy, ay);
       apply_An<T>((T)0, (T)0, (T)1, qz, az);
 #pragma unroll
-      for (int f = 0; f < 10; ++f) rhs[f] = fma3(vgy, qy[f], -c * (ax[f] + ay[f] + az[f]));
+      for (int f = 0; f < 10; ++f)
+        rhs[f] = fma3(vgx, qx[f], fma3(vgy, qy[f], fma3(vgz, qz[f], -c * (ax[f] + ay[f] + az[f]))));
     }
 
     // ---- surface fluxes at the face nodes ----
@@ -303,9 +314,12 @@ stage3_kernel(const Stage3Args a) {
 #pragma unroll
       for (int fld = 0; fld < 10; ++fld) w[fld] = qp[fld * Np] - qm[fld * Np];
       const T *g = sgeo + e * GEO3;
-      const T nx = g[13 + 4 * f], ny = g[14 + 4 * f], nz = g[15 + 4 * f], fs = g[16 + 4 * f];
+      const T nx = g[GEO3_F + 4 * f], ny = g[GEO3_F + 1 + 4 * f], nz = g[GEO3_F + 2 + 4 * f], fs = g[GEO3_F + 3 + 4 * f];
       const T *bl = sops + L::Bary + 4 * vol;
-      const T vn = (bl[0] * g[9] + bl[1] * g[10] + bl[2] * g[11] + bl[3] * g[12]) * ny;
+      const T *gv = g + GEO3_V;
+      T vn = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) vn = fma3(bl[k], fma3(gv[3 * k], nx, fma3(gv[3 * k + 1], ny, gv[3 * k + 2] * nz)), vn);
       const T ale = vn > (T)0 ? vn : (T)0;
       T y1[10], y2[10], y3[10], y4[10];
       apply_An<T>(nx, ny, nz, w, y1);
@@ -560,11 +574,12 @@ int launch_stage3(int N, bool fp64, const Stage3Args &a, void *stream, int num_s
 
 // ---- vertex update, motion shapes, node coordinates, precision conversion ----------
 
-// y_{n+1} = y_n + fin1 S1(X) + fin2 S2(X); t_{n+1} = t_n + dt
+// x_{n+1} = x_n + fin1 S1(X) + fin2 S2(X); t_{n+1} = t_n + dt
 __global__ void vertex_update3_kernel(double *xn, const double *shape, int64_t nv, double *clock, double dt) {
   const double f1 = clock[1], f2 = clock[2];
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x)
-    xn[3 * i + 1] += f1 * shape[2 * i] + f2 * shape[2 * i + 1];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) xn[3 * i + d] += f1 * shape[6 * i + d] + f2 * shape[6 * i + 3 + d];
   if (blockIdx.x == 0 && threadIdx.x == 0) clock[0] += dt;
 }
 
@@ -576,24 +591,186 @@ int launch_vertex_update3(double *xn, const double *shape, int64_t nv, double *c
   return (int)cudaGetLastError();
 }
 
-// travelling-wave shapes at the Lagrangian positions:
-// v_y = -omega A(X) e^{-r^2/r0sq} cos(k X - omega t) = S1 cos(omega t) + S2 sin(omega t)
+// Velocity shapes at the Lagrangian positions, v(X, t) = S1(X) cos(omega t) + S2(X) sin(omega t),
+// stored per vertex as S1x S1y S1z S2x S2y S2z.
+// Travelling wave (y only): v_y = -omega A(X) e^{-r^2/r0sq} cos(k X - omega t).
 __global__ void shape3_kernel(const double *X, double *shape, int64_t nv, Wave3 m) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
     const double x = X[3 * i], y = X[3 * i + 1], z = X[3 * i + 2];
     const double r2 = (y - m.yc) * (y - m.yc) + (z - m.zc) * (z - m.zc);
     const double amp = -m.omega * (m.A0 + m.A1 * x / m.Lx) * exp(-r2 / m.r0sq);
     const double kx = 2.0 * 3.14159265358979323846 / m.wavelength * x;
-    shape[2 * i] = amp * cos(kx);
-    shape[2 * i + 1] = amp * sin(kx);
+    double *o = shape + 6 * i;
+    o[0] = 0.0; o[1] = amp * cos(kx); o[2] = 0.0;
+    o[3] = 0.0; o[4] = amp * sin(kx); o[5] = 0.0;
   }
 }
 
-int launch_shape3(const double *X, double *shape, int64_t nv, const Wave3 &m, void *stream) {
+// Taylor-Green deformation (Sec. 7.2): x_d = X_d + A sin(omega t) S(X_a) S(X_b) over the other
+// two coordinates a, b, S(s) = sin(2 pi (s + L/2) / L), omega = 2 pi / T: S1 = A omega (...), S2 = 0.
+__global__ void shape3_tgv_kernel(const double *X, double *shape, int64_t nv, double A, double omega, double L) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nv; i += (int64_t)gridDim.x * blockDim.x) {
+    double S[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) S[d] = sin(2.0 * 3.14159265358979323846 * (X[3 * i + d] + 0.5 * L) / L);
+    const double amp = A * omega;
+    double *o = shape + 6 * i;
+    o[0] = amp * S[1] * S[2]; o[1] = amp * S[0] * S[2]; o[2] = amp * S[0] * S[1];
+    o[3] = 0.0; o[4] = 0.0; o[5] = 0.0;
+  }
+}
+
+static unsigned vertex_blocks(int64_t nv) {
   int64_t blocks = (nv + 255) / 256;
   if (blocks > 4096) blocks = 4096;
-  if (blocks < 1) blocks = 1;
-  shape3_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(X, shape, nv, m);
+  return (unsigned)(blocks < 1 ? 1 : blocks);
+}
+
+int launch_shape3(const double *X, double *shape, int64_t nv, const Wave3 &m, void *stream) {
+  shape3_kernel<<<vertex_blocks(nv), 256, 0, (cudaStream_t)stream>>>(X, shape, nv, m);
+  return (int)cudaGetLastError();
+}
+
+int launch_shape3_tgv(const double *X, double *shape, int64_t nv, double A, double omega, double L, void *stream) {
+  shape3_tgv_kernel<<<vertex_blocks(nv), 256, 0, (cudaStream_t)stream>>>(X, shape, nv, A, omega, L);
+  return (int)cudaGetLastError();
+}
+
+// ---- diagnostics: integrals of the nodal interpolants over the moving tetrahedra ----------
+// int f = J sum_i wq_i f_i per element (wq = 1^T Mhat, J = det G, G = dx/d(r,s,t)), for
+// f = rho, rho |u|^2 / 2 = c^2 (q2^2 + q3^2 + q4^2) / (2 q1), rho u, rho v, rho w and 1.
+// One thread per element (grid-stride), block partials in a fixed order, one block sums
+// them: the result does not depend on scheduling.
+constexpr int kDiag3Threads = 256;
+
+__device__ __forceinline__ void block_sum6(double (&acc)[6], double *part) {
+  __shared__ double red[kDiag3Threads / 32][6];
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    double v = acc[k];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w][threadIdx.x];
+    part[threadIdx.x] = v;
+  }
+}
+
+// ctl (recording mode, else NULL): ctl[0] steps since recording began, ctl[1] records
+// written; only every `every`-th step is integrated (uniform over the grid).
+template <typename T>
+__global__ void __launch_bounds__(kDiag3Threads) diagnostics3_kernel(const T *q, bool pert, int Np, const MeshRec3 *mesh,
+                                                                    const double *xn, double px, double py, double pz,
+                                                                    const double *wq, double c, int64_t K, double *part,
+                                                                    const int64_t *ctl, int every) {
+  if (ctl != nullptr && (ctl[0] + 1) % every != 0) return;
+  const double per[3] = {px, py, pz};
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < K; e += (int64_t)gridDim.x * blockDim.x) {
+    const MeshRec3 rec = mesh[e];
+    double P[4][3];
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int d = 0; d < 3; ++d) P[k][d] = xn[3 * (int64_t)rec.v[k] + d] + rec.shift[3 * k + d] * per[d];
+    double G[3][3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) G[d][j] = 0.5 * (P[j + 1][d] - P[0][d]);
+    const double J = G[0][0] * (G[1][1] * G[2][2] - G[1][2] * G[2][1]) - G[0][1] * (G[1][0] * G[2][2] - G[1][2] * G[2][0]) +
+                     G[0][2] * (G[1][0] * G[2][1] - G[1][1] * G[2][0]);
+    const T *qe = q + e * 10 * Np;
+    double m = 0.0, ke = 0.0, mu = 0.0, mv = 0.0, mw = 0.0, w = 0.0;
+    for (int n = 0; n < Np; ++n) {
+      const double q1 = (double)qe[n] + (pert ? 1.0 : 0.0);
+      const double q2 = (double)qe[Np + n], q3 = (double)qe[2 * Np + n], q4 = (double)qe[3 * Np + n];
+      const double wn = wq[n];
+      m += wn * q1;
+      ke += wn * 0.5 * c * c * (q2 * q2 + q3 * q3 + q4 * q4) / q1;
+      mu += wn * c * q2;
+      mv += wn * c * q3;
+      mw += wn * c * q4;
+      w += wn;
+    }
+    acc[0] += J * m; acc[1] += J * ke; acc[2] += J * mu; acc[3] += J * mv; acc[4] += J * mw; acc[5] += J * w;
+  }
+  block_sum6(acc, part + 6 * blockIdx.x);
+}
+
+// out = (int rho, int rho |u|^2 / 2, int rho u, int rho v, int rho w, |Omega|)
+__global__ void __launch_bounds__(kDiag3Threads) diagnostics3_reduce_kernel(const double *part, int nblocks, double *out) {
+  double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+  for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] += part[6 * b + k];
+  block_sum6(acc, out);
+}
+
+// recording mode: one record (t, mass, E_K, int rho u, int rho v, |Omega|) into slot
+// ctl[1] mod cap of the ring, then the counters advance
+__global__ void __launch_bounds__(kDiag3Threads) diagnostics3_record_kernel(const double *part, int nblocks,
+                                                                           const double *clock, int64_t *ctl, int every,
+                                                                           double *hist, int64_t cap) {
+  const bool skip = (ctl[0] + 1) % every != 0;
+  __shared__ double tot[6];
+  if (!skip) {
+    double acc[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x)
+#pragma unroll
+      for (int k = 0; k < 6; ++k) acc[k] += part[6 * b + k];
+    block_sum6(acc, tot);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (!skip) {
+      double *r = hist + 6 * (ctl[1] % cap);
+      r[0] = clock[0];
+      r[1] = tot[0];
+      r[2] = tot[1] / tot[5];
+      r[3] = tot[2];
+      r[4] = tot[3];
+      r[5] = tot[5];
+      ctl[1] += 1;
+    }
+    ctl[0] += 1;
+  }
+}
+
+int diagnostics3_blocks(int64_t K) {
+  int64_t blocks = (K + kDiag3Threads - 1) / kDiag3Threads;
+  if (blocks > kDiag3MaxBlocks) blocks = kDiag3MaxBlocks;
+  return blocks < 1 ? 1 : (int)blocks;
+}
+
+static void diag3_partials(const Diag3Args &d, const int64_t *ctl, int every, cudaStream_t st) {
+  const unsigned blocks = (unsigned)diagnostics3_blocks(d.K);
+  if (d.is_float)
+    diagnostics3_kernel<float><<<blocks, kDiag3Threads, 0, st>>>((const float *)d.q, true, d.Np, d.mesh, d.xn,
+                                                                   d.period[0], d.period[1], d.period[2], d.wq, d.c, d.K,
+                                                                   d.part, ctl, every);
+  else
+    diagnostics3_kernel<double><<<blocks, kDiag3Threads, 0, st>>>((const double *)d.q, false, d.Np, d.mesh, d.xn,
+                                                                    d.period[0], d.period[1], d.period[2], d.wq, d.c,
+                                                                    d.K, d.part, ctl, every);
+}
+
+int launch_diagnostics3(const Diag3Args &d, double *out, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  diag3_partials(d, nullptr, 1, st);
+  diagnostics3_reduce_kernel<<<1, kDiag3Threads, 0, st>>>(d.part, diagnostics3_blocks(d.K), out);
+  return (int)cudaGetLastError();
+}
+
+int launch_diagnostics3_record(const Diag3Args &d, const double *clock, int64_t *ctl, int every, double *hist,
+                               int64_t cap, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  diag3_partials(d, ctl, every, st);
+  diagnostics3_record_kernel<<<1, kDiag3Threads, 0, st>>>(d.part, diagnostics3_blocks(d.K), clock, ctl, every, hist,
+                                                          cap);
   return (int)cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, 'libgb.so')
 
 GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_EMESH, GB_ENAN = 0, -1, -2, -3, -4, -5
 GB_FP64, GB_MIXED = 0, 1
-GB_MOTION_STATIC, GB_MOTION_SINXY, GB_MOTION_PLUNGE = 0, 1, 2
+GB_MOTION_STATIC, GB_MOTION_SINXY, GB_MOTION_PLUNGE, GB_MOTION_TGV3D = 0, 1, 2, 3
 GB_BC_INTERIOR, GB_BC_WALL, GB_BC_FARFIELD = 0, 1, 2
 _NAMES = {GB_EINVAL: 'GB_EINVAL', GB_ENOMEM: 'GB_ENOMEM', GB_ECUDA: 'GB_ECUDA', GB_EMESH: 'GB_EMESH', GB_ENAN: 'GB_ENAN'}
 
@@ -69,6 +69,7 @@ def _load():
         'gb_set_stream': ([vp, vp], c_int),
         'gb_set_graph': ([vp, c_int], c_int),
         'gb_diagnostics': ([vp, _dp], c_int),
+        'gb_diagnostics3d': ([vp, _dp], c_int),
         'gb_set_diagnostics': ([vp, c_int, ctypes.c_int64], c_int),
         'gb_diagnostics_history': ([vp, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)], c_int),
@@ -210,6 +211,10 @@ class Solver:
         m = GbMotion(kind, float(A), float(T), float(Lx), float(Ly))
         self._c(lib.gb_set_motion(self.h, ctypes.byref(m)))
 
+    def set_tgv_motion(self, A=np.pi / 6, T=20.0, L=2 * np.pi):
+        """Deformation of the moving 3D Taylor-Green vortex (GB_MOTION_TGV3D, dim = 3)."""
+        self.set_motion(A, T, L, 0.0, kind=GB_MOTION_TGV3D)
+
     def set_wave_motion(self, A0, A1=0.0, Lx=8.0, wavelength=1.0, omega=2 * np.pi, r0sq=0.25, yc=1.0, zc=1.0):
         """Travelling-wave lateral motion of a dim = 3 solver (gb_set_wave_motion)."""
         m = GbWaveMotion(float(A0), float(A1), float(Lx), float(wavelength), float(omega), float(r0sq),
@@ -262,7 +267,13 @@ class Solver:
         return ms
 
     def diagnostics(self):
-        """dict: mass, kinetic_energy (per unit area), momentum_x, momentum_y, area."""
+        """dict: mass, kinetic_energy (per unit area or volume), momentum_x, momentum_y and
+        area (2D) or momentum_z and volume (3D)."""
+        if self.dim == 3:
+            out = np.zeros(6)
+            self._c(lib.gb_diagnostics3d(self.h, _ptr(out)))
+            keys = ('mass', 'kinetic_energy', 'momentum_x', 'momentum_y', 'momentum_z', 'volume')
+            return {k: out[i] for i, k in enumerate(keys)}
         out = np.zeros(5)
         self._c(lib.gb_diagnostics(self.h, _ptr(out)))
         return {'mass': out[0], 'kinetic_energy': out[1], 'momentum_x': out[2], 'momentum_y': out[3], 'area': out[4]}
@@ -274,7 +285,8 @@ class Solver:
 
     def diagnostics_history(self):
         """Recorded diagnostics, oldest first: dict of arrays t, mass, kinetic_energy,
-        momentum_x, momentum_y, area, plus 'total' (records written since enabled)."""
+        momentum_x, momentum_y, area (the volume in 3D), plus 'total' (records written
+        since enabled)."""
         cap = getattr(self, '_diag_cap', 0)
         out = np.zeros((max(cap, 1), 6))
         n, tot = ctypes.c_int64(), ctypes.c_int64()

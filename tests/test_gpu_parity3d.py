@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 from oracle import physics3d
-from oracle.solver3d import OracleSolver3D, WaveMotion
+from oracle.solver3d import OracleSolver3D, TGVMotion3D, WaveMotion
 from paper_2607_00199_b300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -204,6 +204,131 @@ def test_create_rejects_bad_3d_meshes():
     assert ei.value.code == gb.GB_EINVAL
     s = gb.Solver(mesh, 2, 0.1, 100.0, precision=gb.GB_MIXED)
     with pytest.raises(gb.GBError):
-        s.diagnostics()
-    with pytest.raises(gb.GBError):
-        s.set_motion(0.05, 1.0)
+        s.set_motion(0.05, 1.0)                     # GB_MOTION_SINXY is 2D only
+    for bad in (dict(T=0.0), dict(T=float('nan')), dict(L=0.0)):
+        with pytest.raises(gb.GBError) as ei:
+            s.set_tgv_motion(**bad)
+        assert ei.value.code == gb.GB_EINVAL
+
+
+# ---- the moving 3D Taylor-Green vortex (Sec. 7.2): three grid-velocity components -------
+
+def make_tgv_pair(n, N, precision=gb.GB_FP64, jitter=0.1, Re=1600.0, T=2.0):
+    """Cube [-pi, pi]^3 of n^3 hexes (6 tets each), deformation of Eq. TGV_deformation with
+    A = pi/6, L = 2 pi and a short period T so that the mesh moves visibly in a few steps."""
+    mesh = inputs.tgv_box_tet_mesh(n, jitter=jitter)
+    o = OracleSolver3D(mesh, N, Ma=0.1, Re=Re, motion=TGVMotion3D(T=T))
+    s = gb.Solver(mesh, N, 0.1, Re, precision=precision, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_tgv_motion(T=T)
+    return mesh, o, s
+
+
+def tgv_flow(x, y, z):
+    return inputs.taylor_green_3d(x, y, z, 0.1)
+
+
+@pytest.mark.parametrize('N', [1, 2, 3, 4])
+def test_tgv_rhs_parity(N):
+    mesh, o, s = make_tgv_pair(4, N)          # K = 384: ragged against every tile size
+    t = 0.7
+    xv = o.X + o.motion.displacement(o.X, t)
+    s.set_vertices(xv)
+    q = oracle_state(o, xv, tgv_flow)
+    F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
+    F = gpu_rhs(s, q, t)
+    assert rel_l2(F, F_or) <= 1e-12
+    # per field, against max(|F_f|, 1e-4 |F|): the relaxation of the stress moments dominates
+    # this near-equilibrium state, fields 1..4 are 2e-5..1e-4 of |F|, and their rounding error
+    # scales with the advection terms summed into them, not with their small sum
+    total = np.linalg.norm(F_or)
+    for f in range(10):
+        ref = max(np.linalg.norm(F_or[:, f]), 1e-4 * total)
+        assert np.linalg.norm(F[:, f] - F_or[:, f]) <= 1e-11 * ref, f
+
+
+@pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
+def test_tgv_steps_follow_oracle(precision):
+    mesh, o, s = make_tgv_pair(4, 3, precision)
+    q0 = oracle_state(o, o.X, tgv_flow)
+    dt = inputs.cfl_dt_3d(mesh, 3, o.c, 0.5)
+    s.set_fields(q0, 0.0)
+    s.step(dt, 8)
+    q_gpu, t_gpu = s.fields()
+    q_or, x_or, t_or = o.run(q0, o.X.copy(), 0.0, dt, 8)
+    assert abs(t_gpu - t_or) < 1e-14
+    np.testing.assert_allclose(s.vertices(), x_or, atol=1e-14)
+    assert min(np.abs(x_or[:, d] - o.X[:, d]).max() for d in range(3)) > 1e-3
+    assert rel_l2(q_gpu, q_or) <= (1e-10 if precision == gb.GB_FP64 else 1e-5)
+
+
+def test_tgv_free_stream_gcl_gpu():
+    mesh, o, s = make_tgv_pair(4, 3)
+    q0 = oracle_state(o, o.X, lambda x, y, z: (np.ones_like(x), 1.0 + 0 * x, 0.3 + 0 * x, -0.2 + 0 * x))
+    s.set_fields(q0, 0.0)
+    s.step(inputs.cfl_dt_3d(mesh, 3, o.c, 0.5), 25)
+    q, _ = s.fields()
+    assert np.abs(q - q0).max() < 1e-13
+
+
+@pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
+def test_diagnostics3d_parity(precision):
+    """Sec. 7.2 integrals of the GPU state against the oracle's on the same fields and
+    vertices (both reduce in FP64), at t = 0 (closed forms of the unjittered cube: E_K = 1/8
+    at rho = 1, volume (2 pi)^3) and after steps on the deforming mesh."""
+    mesh, o, s = make_tgv_pair(3, 3, precision, jitter=0.0)
+    flow1 = lambda x, y, z: (np.ones_like(x),) + tgv_flow(x, y, z)[1:]
+    s.set_fields(oracle_state(o, o.X, flow1), 0.0)
+    d = s.diagnostics()
+    tol = 1e-13 if precision == gb.GB_FP64 else 1e-7
+    assert abs(d['kinetic_energy'] - 0.125) <= tol and abs(d['volume'] - (2 * math.pi) ** 3) <= 1e-11
+    s2 = s.diagnostics()
+    assert s2 == d                               # fixed reduction order
+    lib_d = np.zeros(5)
+    s._c(gb.lib.gb_diagnostics(s.h, gb._ptr(lib_d)))
+    np.testing.assert_array_equal(lib_d, [d['mass'], d['kinetic_energy'], d['momentum_x'], d['momentum_y'],
+                                          d['volume']])
+    mesh, o, s = make_tgv_pair(4, 3, precision)
+    s.set_fields(oracle_state(o, o.X, tgv_flow), 0.0)
+    s.step(inputs.cfl_dt_3d(mesh, 3, o.c, 0.5), 6)
+    d = s.diagnostics()
+    want = o.diagnostics(s.fields()[0], s.vertices())
+    for k in want:
+        assert abs(d[k] - want[k]) <= 1e-12 * max(1.0, abs(want[k])), (k, d[k], want[k])
+
+
+@pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
+def test_diagnostics3d_history(precision):
+    """Records taken at the end of the recorded steps (inside the step's CUDA graph) equal
+    gb_diagnostics of a twin stepped one step at a time, and the oracle's run in FP64."""
+    mesh, o, a = make_tgv_pair(3, 2, precision)
+    _, _, b = make_tgv_pair(3, 2, precision)
+    q0 = oracle_state(o, o.X, tgv_flow)
+    dt = inputs.cfl_dt_3d(mesh, 2, o.c, 0.5)
+    a.set_fields(q0, 0.0)
+    b.set_fields(q0, 0.0)
+    a.set_diagnostics(1, 16)
+    a.step(dt, 6)
+    h = a.diagnostics_history()
+    assert h['total'] == 6 and len(h['t']) == 6
+    q, xv, t = q0, o.X.copy(), 0.0
+    for k in range(6):
+        b.step(dt, 1)
+        d = b.diagnostics()
+        assert h['t'][k] == b.fields()[1]
+        for key, hk in (('mass', 'mass'), ('kinetic_energy', 'kinetic_energy'), ('momentum_x', 'momentum_x'),
+                        ('momentum_y', 'momentum_y'), ('volume', 'area')):
+            assert abs(h[hk][k] - d[key]) <= 1e-13 * (abs(d[key]) + d['mass']), (k, key)
+        q, xv = o.step(q, xv, t, dt)
+        t += dt
+        if precision == gb.GB_FP64:
+            want = o.diagnostics(q, xv)
+            assert abs(h['kinetic_energy'][k] - want['kinetic_energy']) <= 1e-11 * want['kinetic_energy']
+    assert h['kinetic_energy'][-1] < h['kinetic_energy'][0]
+    # every 4th step into a ring of 2
+    a.set_diagnostics(4, 2)
+    t0 = a.fields()[1]
+    a.step(dt, 9)
+    h = a.diagnostics_history()
+    assert h['total'] == 2 and np.allclose(h['t'], [t0 + 4 * dt, t0 + 8 * dt], rtol=0, atol=1e-12)
+    a.set_diagnostics(0)
+    assert len(a.diagnostics_history()['t']) == 0
