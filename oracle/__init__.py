@@ -26,6 +26,8 @@ tet        Warp & Blend nodes and the reference operators of the tetrahedron
 physics3d  the 10-moment 3D Galerkin-Boltzmann system (Sec. 2 construction).
 solver3d   the ALE right-hand side and SARK step on a moving periodic
            tetrahedral mesh.
+pml        the perfectly matched layer of the airfoil case (a reading: complex
+           stretching along the layer's direction with auxiliary fields).
 
 Parity status of each function is stated in its docstring; functions with no
 independent pin say "parity unpinned".

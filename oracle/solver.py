@@ -80,7 +80,8 @@ class OracleSolver:
     off (a test-only knob that makes the system linear).
     """
 
-    def __init__(self, mesh, N, Ma=None, Re=None, c=None, tau=None, motion=None, far_state=(1.0, 1.0, 0.0)):
+    def __init__(self, mesh, N, Ma=None, Re=None, c=None, tau=None, motion=None, far_state=(1.0, 1.0, 0.0),
+                 pml=None):
         self.ref = ReferenceElement(N)
         self.N = N
         if c is None:
@@ -98,6 +99,11 @@ class OracleSolver:
         self.bc = np.asarray(mesh.get('bc', np.zeros((self.K, 3))), dtype=np.int64)
         self.q_far = physics.equilibrium_state(*far_state, self.c)
         self._connect()
+        # perfectly matched layer (oracle.pml): sigma and direction at the Lagrangian nodes
+        self.pml = pml
+        if pml is not None:
+            self.pml_sigma, self.pml_dir = pml.fields(self.node_coords(self.X))
+            self.pml_layer = (self.pml_sigma > 0).any(axis=1)
 
     # ---- mesh -----------------------------------------------------------
     def element_vertices(self, xv):
@@ -169,9 +175,11 @@ class OracleSolver:
         return Ginv, J, normals, fscale
 
     # ---- right-hand side F = L(q) + Ntilde(q) (Secs. 3-4) -----------------
-    def rhs(self, q, xv, vv):
+    def rhs(self, q, xv, vv, along_pml=False):
         """F(q) = volume + surface + P Ntilde(I q) at vertex positions xv and vertex
-        velocities vv; the stiff -Lambda q part is not included (Sec. 4)."""
+        velocities vv; the stiff -Lambda q part is not included (Sec. 4).  along_pml:
+        also return R_e, the part of the advective terms along the layer direction e
+        (oracle.pml)."""
         ref = self.ref
         K, Np, Nfp = self.K, ref.Np, ref.Nfp
         Ax, Ay = physics.flux_matrices(self.c)
@@ -208,12 +216,28 @@ class OracleSolver:
         fluxA = np.maximum(vn, 0.0)[:, None, :, :] * dq
         flux = (fscale[:, None, :, None] * (fluxS + fluxA)).reshape(K, 6, 3 * Nfp)
         F = F + np.einsum('im,egm->egi', ref.LIFT, flux)
+        if along_pml:
+            ex, ey = self.pml_dir[..., 0][:, None, :], self.pml_dir[..., 1][:, None, :]    # (K, 1, Np)
+            qe = ex * qx + ey * qy                                                       # e . grad q
+            vge = (vg[..., 0] * self.pml_dir[..., 0] + vg[..., 1] * self.pml_dir[..., 1])[:, None, :]
+            R = (ex * np.einsum('gf,efi->egi', Ax, qe) + ey * np.einsum('gf,efi->egi', Ay, qe) + vge * qe)
+            # face terms: the flux is 1/2 (A_n + v_n) dq (central) + 1/2 (c |At_n| + |v_n|) dq
+            # (upwind dissipation); A_n + v_n = (n.e)(A_e + v_e) + (n.t)(A_t + v_t) gives the
+            # central part along e exactly, the dissipation is shared with weights (n.e)^2
+            ef = self.pml_dir[:, fm, :].reshape(K, 3, Nfp, 2)                            # e at the face nodes
+            ne = np.einsum('efkd,efd->efk', ef, normals)                                 # n . e
+            Ae = (ef[..., 0, None, None] * Ax + ef[..., 1, None, None] * Ay)              # (K, 3, Nfp, 6, 6)
+            ve = (vgf * ef).sum(-1)                                                      # v_G . e
+            cen = 0.5 * ne[:, None] * (np.einsum('efkgh,ehfk->egfk', Ae, dq) + ve[:, None] * dq)
+            dis = 0.5 * (self.c * np.einsum('efgh,ehfk->egfk', absAn, dq) + np.abs(vn)[:, None] * dq)
+            fe = (fscale[:, None, :, None] * (cen + (ne ** 2)[:, None] * dis)).reshape(K, 6, 3 * Nfp)
+            R = R + np.einsum('im,egm->egi', ref.LIFT, fe)
         # collision term through the cubature: fields 4..6 get P Ntilde(I q)
         if np.isfinite(self.tau):
             qc = np.einsum('cj,efj->efc', ref.I, q[:, 0:3])
             n4, n5, n6 = physics.ntilde(qc[:, 0], qc[:, 1], qc[:, 2], self.tau)
             F[:, 3:6] += np.einsum('jc,efc->efj', ref.P, np.stack([n4, n5, n6], axis=1))
-        return F
+        return (F, R) if along_pml else F
 
     # ---- SARK step (Sec. 4) with RK4 vertex motion (Sec. 5) ----------------
     def field_coefficients(self, dt):
@@ -249,6 +273,37 @@ class OracleSolver:
             q, xv = self.step(q, xv, t, dt)
             t = t + dt
         return q, xv, t
+
+    def step_pml(self, q, phi, xv, t, dt):
+        """One SARK step with the perfectly matched layer (oracle.pml): F_i gets -sigma Phi_i
+        in every field, Phi advances by the RK4 stages with dPhi/dt = R_e - (alpha + sigma) Phi
+        on the layer's elements (zero elsewhere).  Returns (q_{n+1}, Phi_{n+1}, x_{n+1})."""
+        E, A, B = self.field_coefficients(dt)
+        sig = self.pml_sigma[:, None, :]
+        lay = self.pml_layer[:, None, None]
+        Fs, Gs, vs = [], [], []
+        qi, phii = q, phi
+        for i in range(4):
+            ti = t + RK4_C[i] * dt
+            xi = xv + dt * sum(RK4_A[i][j] * vs[j] for j in range(i)) if i else xv
+            vs.append(self.motion.velocity(self.X, ti))
+            F, R = self.rhs(qi, xi, vs[i], along_pml=True)
+            Fs.append(F - sig * phii)
+            Gs.append(np.where(lay, R - (self.pml.alpha + sig) * phii, 0.0))
+            if i < 3:
+                qi = E[i + 1][None, :, None] * q + dt * sum(
+                    A[i + 1, j][None, :, None] * Fs[j] for j in range(i + 1))
+                phii = phi + dt * sum(RK4_A[i + 1][j] * Gs[j] for j in range(i + 1))
+        qn = E[4][None, :, None] * q + dt * sum(B[j][None, :, None] * Fs[j] for j in range(4))
+        phin = phi + dt * sum(RK4_B[j] * Gs[j] for j in range(4))
+        xn = xv + dt * sum(RK4_B[j] * vs[j] for j in range(4))
+        return qn, phin, xn
+
+    def run_pml(self, q, phi, xv, t, dt, nsteps):
+        for _ in range(nsteps):
+            q, phi, xv = self.step_pml(q, phi, xv, t, dt)
+            t = t + dt
+        return q, phi, xv, t
 
     # ---- diagnostics ------------------------------------------------------
     def integral(self, f, xv):
