@@ -108,6 +108,48 @@ int gb_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision,
 int gb_create_bounded(const gb_mesh *mesh, const int8_t *face_bc, const double *far_state, int N, double Ma,
                       double Re, int precision, void *cuda_stream, gb_solver **out);
 
+/* Perfectly matched layer (dim = 2; the airfoil case's outer boundary, Sec. 7).  The paper
+ * uses a PML with auxiliary fields but prints no equations.  Reading implemented here:
+ * complex stretching of one direction e (planar approximation) with frequency shift alpha,
+ *   dq/dt   = L(q) + Ntilde(q) - sigma Phi,
+ *   dPhi/dt = R_e(q) - (alpha + sigma) Phi,
+ * L = R_e + R_t the advective terms split into their part along e and the rest: in the
+ * volume (A_e + v_G . e) e . grad q with A_e = -c (e_x Atilde_x + e_y Atilde_y); on the faces
+ * 1/2 (n.e)(A_e + v_G . e) dq (the central part of the upwind flux along e) plus
+ * (n.e)^2 times its dissipation 1/2 (c |Atilde_n| + |v_G . n|) dq, lifted.  Phi (6 fields
+ * per node) lives on the layer's elements and advances by the RK4 stages; -sigma Phi joins
+ * every field's SARK combinations.  sigma(r) = sigma_max ((r - r0)/d)^power for r > r0, else
+ * 0, with r and e at each node's Lagrangian position X:
+ *   GB_PML_RADIAL   r = |X - (cx, cy)|, e = (X - (cx, cy)) / r   (an outer ring);
+ *   GB_PML_SLAB     r = |(X - (cx, cy)) . u|, e = sign((X - (cx, cy)) . u) u,
+ *                   u = (ex, ey) normalised (two layers facing away from a centre line);
+ *   GB_PML_UNIFORM  sigma = sigma_max and e = u everywhere (r0, d, power unused).
+ * The layer = the elements with a node where sigma > 0. */
+#define GB_PML_RADIAL  0
+#define GB_PML_SLAB    1
+#define GB_PML_UNIFORM 2
+typedef struct {
+  int32_t kind;              /* GB_PML_RADIAL, GB_PML_SLAB or GB_PML_UNIFORM */
+  double cx, cy;             /* centre (radial) or a point on the centre line (slab) */
+  double ex, ey;             /* direction u (slab, uniform) */
+  double r0, d;              /* the layer starts at r = r0 and grades over depth d > 0 */
+  double sigma_max, power;   /* sigma_max >= 0, power >= 0 */
+  double alpha;              /* frequency shift >= 0 */
+} gb_pml;
+
+/* gb_set_pml: install the layer (copied; NULL removes it) and set Phi = 0.  N <= 4.
+ * Synchronises the stream.  gb_set_fields also zeroes Phi.  gb_rhs and gb_rhs_noalloc
+ * leave the layer out (they take no Phi); with a layer, gb_set_diagnostics records through
+ * separate reduction launches after each step.  Groups reject solvers with a layer.
+ * GB_EINVAL for a 3D solver, non-finite or out-of-range parameters. */
+int gb_set_pml(gb_solver *s, const gb_pml *p);
+
+/* gb_pml_fields: *n_layer = the number of layer elements; if phi_out (host, n_layer x 6 x Np
+ * doubles; FP32 values widened in GB_MIXED) and/or elem_out (host, n_layer) are non-NULL,
+ * copy Phi_n and the canonical element ids (ascending, the order of phi_out).
+ * Synchronises the stream. */
+int gb_pml_fields(gb_solver *s, double *phi_out, int64_t *elem_out, int64_t *n_layer);
+
 /* gb_set_motion: prescribe the vertex velocity d/dt of the displacement above,
  * evaluated at the Lagrangian X (Sec. 5).  Copied; takes effect at the next step. */
 int gb_set_motion(gb_solver *s, const gb_motion *m);

@@ -60,6 +60,12 @@ struct gb_solver {
   int64_t device_bytes = 0;
   int has_bc = 0;              // the mesh has wall / far-field faces (gb_create_bounded)
   double far[6] = {0, 0, 0, 0, 0, 0};   // far-field state in the kernels' representation
+  // perfectly matched layer (gb_set_pml): layer elements in ascending canonical order
+  int64_t n_layer = 0;
+  double pml_alpha = 0.0;
+  void *d_pml_ops = nullptr, *d_pml_node = nullptr, *d_phi = nullptr;   // d_phi: Phi_n, stage, RK4 sum
+  int32_t *d_pml_elem = nullptr;
+  size_t pml_bytes = 0;
 };
 
 static std::string g_create_error;
@@ -86,7 +92,7 @@ static int dev_alloc(gb_solver *s, void **p, size_t bytes) {
 static void free_all(gb_solver *s) {
   void *ptrs[] = {s->d_ops, s->d_ops_mixed, s->d_mesh, s->d_mesh_int, s->d_perm, s->d_X, s->d_xn, s->d_shape,
                   s->d_clock, s->d_status, s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp, s->d_diag,
-                  s->d_hist, s->d_hctl, s->d_done};
+                  s->d_hist, s->d_hctl, s->d_done, s->d_pml_ops, s->d_pml_node, s->d_phi, s->d_pml_elem};
   for (void *p : ptrs)
     if (p) cudaFree(p);
 }
@@ -165,6 +171,37 @@ static int launch_stage(gb_solver *s, const gb::StageArgs &a) {
                                    : gb::launch_stage_mixed(s->N, a, s->stream, s->num_sms);
   if (rc != 0) return cuda_fail(s, (cudaError_t)rc, "stage kernel launch");
   return GB_OK;
+}
+
+// the layer's terms of SARK stage a.stage (after the stage kernel, before the next one)
+static int launch_pml(gb_solver *s, const gb::StageArgs &a) {
+  if (s->n_layer <= 0) return GB_OK;
+  const bool fp64 = s->precision == GB_FP64;
+  const size_t eb = fp64 ? sizeof(double) : sizeof(float);
+  const size_t phi_elems = (size_t)s->n_layer * 6 * s->Np;
+  gb::PmlArgs p;
+  memset(&p, 0, sizeof(p));
+  p.ops = s->d_pml_ops;
+  p.elem = s->d_pml_elem;
+  p.node = s->d_pml_node;
+  p.phin = s->d_phi;
+  p.phis = (char *)s->d_phi + eb * phi_elems;
+  p.phiacc = (char *)s->d_phi + 2 * eb * phi_elems;
+  p.n_layer = s->n_layer;
+  p.stride = fp64 ? 6 * s->Np : gb::mixed_stride(s->N);
+  p.alpha = s->pml_alpha;
+  // coefficients of F_i in stage i's combinations (as the stage kernels form them)
+  for (int cl = 0; cl < 2; ++cl) {
+    const double *A = s->co.A[cl], *B = s->co.B[cl];
+    switch (a.stage) {
+      case 0: p.cq[cl] = A[4]; p.cs[cl] = 1.0; break;
+      case 1: p.cq[cl] = A[9]; p.cs[cl] = B[1]; break;
+      case 2: p.cq[cl] = A[14]; p.cs[cl] = B[2]; break;
+      default: p.cq[cl] = B[3]; p.cs[cl] = 0.0; break;
+    }
+  }
+  int rc = gb::launch_pml_stage(s->N, fp64, a, p, s->stream, s->num_sms);
+  return rc ? cuda_fail(s, (cudaError_t)rc, "layer kernel launch") : GB_OK;
 }
 
 struct gb_group {
@@ -531,6 +568,24 @@ static int create2d(const gb_mesh *mesh, const int8_t *face_bc, const double *fa
   return GB_OK;
 }
 
+static void free_pml(gb_solver *s) {
+  const size_t eb = s->precision == GB_FP64 ? sizeof(double) : sizeof(float);
+  dev_free(s, &s->d_phi, s->pml_bytes);
+  dev_free(s, &s->d_pml_node, eb * 3 * s->Np * (size_t)s->n_layer);
+  dev_free(s, (void **)&s->d_pml_elem, sizeof(int32_t) * (size_t)s->n_layer);
+  dev_free(s, &s->d_pml_ops, eb * (size_t)gb::pml_ops_size(s->N));
+  s->n_layer = 0;
+  s->pml_bytes = 0;
+}
+
+template <typename T>
+static std::vector<unsigned char> as_bytes(const std::vector<double> &v) {
+  std::vector<unsigned char> out(v.size() * sizeof(T));
+  T *o = reinterpret_cast<T *>(out.data());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = (T)v[i];
+  return out;
+}
+
 extern "C" {
 
 int gb_set_motion(gb_solver *s, const gb_motion *m) {
@@ -575,6 +630,7 @@ int gb_set_fields(gb_solver *s, const double *q_host, double t) {
     }
   }
   if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->d_clock, &t, sizeof(double), cudaMemcpyHostToDevice, s->stream);
+  if (ce == cudaSuccess && s->d_phi) ce = cudaMemsetAsync(s->d_phi, 0, s->pml_bytes, s->stream);   // Phi = 0
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s->stream);
   if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_fields");
   return GB_OK;
@@ -769,7 +825,7 @@ static int step_impl(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms)
         a.qout = bufs_out[st];
         a.F0 = s->d_F0;
         a.acc = s->d_acc;
-        if (st == 3 && s->diag_every > 0) {
+        if (st == 3 && s->diag_every > 0 && s->n_layer == 0) {
           // diagnostics fused into the last stage: integrals of q_{n+1} on x_{n+1}, recorded by the
           // last CTA (partials in the diagnostics scratch, after the weights and result slots)
           a.rec_every = s->diag_every;
@@ -782,9 +838,12 @@ static int step_impl(gb_solver *s, double dt, int64_t nsteps, double *kernel_ms)
         }
         rc = launch_stage(s, a);
         a.rec_every = 0;
+        if (rc == GB_OK) rc = launch_pml(s, a);
       } else {
         int lr = gb::launch_vertex_update(a, s->nv, s->stream);
         if (lr) rc = cuda_fail(s, (cudaError_t)lr, "vertex update launch");
+        // with a layer the record follows its last correction: separate reduction launches
+        if (rc == GB_OK && s->n_layer > 0) rc = record_diagnostics(s, s->stream);
       }
       if (kernel_ms) cudaEventRecord(ev[(size_t)k * 10 + 2 * st + 1], s->stream);
     }
@@ -841,6 +900,7 @@ int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int 
     if (!s) return gfail(GB_EINVAL, "gb_group_step: NULL solver");
     if (s->s3) return gfail(GB_EINVAL, "gb_group_step: dim = 3 solvers cannot be grouped");
     if (s->has_bc) return gfail(GB_EINVAL, "gb_group_step: solvers with boundary faces cannot be grouped");
+    if (s->n_layer > 0) return gfail(GB_EINVAL, "gb_group_step: solvers with a perfectly matched layer cannot be grouped");
     if (s->precision != GB_MIXED) return gfail(GB_EINVAL, "gb_group_step: only GB_MIXED solvers can be grouped");
     if (s->N != N) return gfail(GB_EINVAL, "gb_group_step: all solvers of a group must have the same N");
     if (s->stream != g->stream) return gfail(GB_EINVAL, "gb_group_step: solvers must use the group's stream");
@@ -1094,6 +1154,162 @@ int gb_destroy(gb_solver *s) {
 const char *gb_last_error(gb_solver *s) {
   if (s && s->s3 && s->err.empty()) return gb::s3_error(s->s3);
   return s ? s->err.c_str() : g_create_error.c_str();
+}
+
+int gb_set_pml(gb_solver *s, const gb_pml *p) {
+  if (!s) return fail(s, GB_EINVAL, "NULL solver");
+  if (s->s3) return fail(s, GB_EINVAL, "gb_set_pml applies to dim = 2 solvers");
+  cudaError_t ce = s->stream ? cudaStreamSynchronize(s->stream) : cudaDeviceSynchronize();
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_pml");
+  if (p) {
+    const double vals[10] = {p->cx, p->cy, p->ex, p->ey, p->r0, p->d, p->sigma_max, p->power, p->alpha, 0.0};
+    for (double v : vals)
+      if (!std::isfinite(v)) return fail(s, GB_EINVAL, "gb_pml: non-finite parameter");
+    if (p->kind != GB_PML_RADIAL && p->kind != GB_PML_SLAB && p->kind != GB_PML_UNIFORM)
+      return fail(s, GB_EINVAL, "gb_pml: unknown kind");
+    if (p->sigma_max < 0.0 || p->power < 0.0 || p->alpha < 0.0)
+      return fail(s, GB_EINVAL, "gb_pml: sigma_max, power and alpha must be >= 0");
+    if (p->kind != GB_PML_RADIAL && !(p->ex * p->ex + p->ey * p->ey > 0.0))
+      return fail(s, GB_EINVAL, "gb_pml: the direction (ex, ey) must be non-zero");
+    if (p->kind != GB_PML_UNIFORM && !(p->d > 0.0)) return fail(s, GB_EINVAL, "gb_pml: d must be > 0");
+    if (s->N > 4) return fail(s, GB_EINVAL, "gb_pml: N must be <= 4");
+  }
+  drop_graph(s);
+  free_pml(s);
+  if (!p) return GB_OK;
+  // sigma and the direction at every node, from the Lagrangian vertex positions
+  const int Np = s->Np;
+  std::vector<double> X((size_t)2 * s->nv);
+  std::vector<MeshRec> mesh((size_t)s->K);
+  std::vector<int32_t> perm;
+  ce = cudaMemcpy(X.data(), s->d_X, sizeof(double) * X.size(), cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess) ce = cudaMemcpy(mesh.data(), s->d_mesh, sizeof(MeshRec) * mesh.size(), cudaMemcpyDeviceToHost);
+  if (ce == cudaSuccess && s->precision == GB_MIXED) {
+    perm.resize((size_t)s->K);
+    ce = cudaMemcpy(perm.data(), s->d_perm, sizeof(int32_t) * perm.size(), cudaMemcpyDeviceToHost);
+  }
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_set_pml");
+  double ux = p->ex, uy = p->ey;
+  const double un = std::sqrt(ux * ux + uy * uy);
+  if (un > 0.0) { ux /= un; uy /= un; }
+  std::vector<double> node;                  // per layer element: sigma[Np], e_x[Np], e_y[Np]
+  std::vector<int64_t> layer;                // canonical ids, ascending
+  std::vector<double> sg(Np), exv(Np), eyv(Np);
+  for (int64_t e = 0; e < s->K; ++e) {
+    const MeshRec &rec = mesh[(size_t)e];
+    bool any = false;
+    for (int n = 0; n < Np; ++n) {
+      const double l[3] = {-0.5 * (s->ref.r[n] + s->ref.s[n]), 0.5 * (1.0 + s->ref.r[n]), 0.5 * (1.0 + s->ref.s[n])};
+      double x = 0.0, y = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        x += l[k] * (X[2 * (size_t)rec.v[k]] + rec.shift[2 * k] * s->period[0]);
+        y += l[k] * (X[2 * (size_t)rec.v[k] + 1] + rec.shift[2 * k + 1] * s->period[1]);
+      }
+      double r = 0.0, dx = ux, dy = uy;
+      if (p->kind == GB_PML_RADIAL) {
+        const double rx = x - p->cx, ry = y - p->cy;
+        r = std::sqrt(rx * rx + ry * ry);
+        dx = r > 0.0 ? rx / r : 0.0;
+        dy = r > 0.0 ? ry / r : 0.0;
+      } else if (p->kind == GB_PML_SLAB) {
+        const double sp = (x - p->cx) * ux + (y - p->cy) * uy;
+        r = std::fabs(sp);
+        if (sp < 0.0) { dx = -ux; dy = -uy; }
+      }
+      double sigma = p->sigma_max;
+      if (p->kind != GB_PML_UNIFORM) {
+        const double depth = (r - p->r0) / p->d;
+        sigma = depth > 0.0 ? p->sigma_max * std::pow(depth, p->power) : 0.0;
+      }
+      sg[n] = sigma; exv[n] = dx; eyv[n] = dy;
+      any = any || sigma > 0.0;
+    }
+    if (!any) continue;
+    layer.push_back(e);
+    node.insert(node.end(), sg.begin(), sg.end());
+    node.insert(node.end(), exv.begin(), exv.end());
+    node.insert(node.end(), eyv.begin(), eyv.end());
+  }
+  s->pml_alpha = p->alpha;
+  if (layer.empty()) return GB_OK;
+  // element indices in the kernels' numbering
+  std::vector<int32_t> elem(layer.size());
+  if (s->precision == GB_MIXED) {
+    std::vector<int32_t> inv((size_t)s->K);
+    for (int64_t i = 0; i < s->K; ++i) inv[(size_t)perm[(size_t)i]] = (int32_t)i;
+    for (size_t i = 0; i < layer.size(); ++i) elem[i] = inv[(size_t)layer[i]];
+  } else {
+    for (size_t i = 0; i < layer.size(); ++i) elem[i] = (int32_t)layer[i];
+  }
+  // operator block: Dr^T, Ds^T, LIFT^T, node barycentrics
+  const int NFN = 3 * s->Nfp;
+  std::vector<double> ops((size_t)gb::pml_ops_size(s->N));
+  for (int m = 0; m < Np; ++m)
+    for (int n = 0; n < Np; ++n) {
+      ops[(size_t)m * Np + n] = s->ref.Dr[(size_t)n * Np + m];
+      ops[(size_t)Np * Np + m * Np + n] = s->ref.Ds[(size_t)n * Np + m];
+    }
+  for (int j = 0; j < NFN; ++j)
+    for (int n = 0; n < Np; ++n) ops[(size_t)2 * Np * Np + j * Np + n] = s->ref.LIFT[(size_t)n * NFN + j];
+  for (int n = 0; n < Np; ++n) {
+    const size_t b = (size_t)2 * Np * Np + (size_t)NFN * Np + 3 * n;
+    ops[b] = -0.5 * (s->ref.r[n] + s->ref.s[n]);
+    ops[b + 1] = 0.5 * (1.0 + s->ref.r[n]);
+    ops[b + 2] = 0.5 * (1.0 + s->ref.s[n]);
+  }
+  const bool fp64 = s->precision == GB_FP64;
+  const size_t eb = fp64 ? sizeof(double) : sizeof(float);
+  std::vector<unsigned char> ops_b = fp64 ? as_bytes<double>(ops) : as_bytes<float>(ops);
+  std::vector<unsigned char> node_b = fp64 ? as_bytes<double>(node) : as_bytes<float>(node);
+  s->n_layer = (int64_t)layer.size();
+  s->pml_bytes = 3 * eb * 6 * Np * layer.size();
+  int rc = dev_alloc(s, &s->d_pml_ops, ops_b.size());
+  if (!rc) rc = dev_alloc(s, (void **)&s->d_pml_elem, sizeof(int32_t) * elem.size());
+  if (!rc) rc = dev_alloc(s, &s->d_pml_node, node_b.size());
+  if (!rc) rc = dev_alloc(s, &s->d_phi, s->pml_bytes);
+  if (rc) {
+    free_pml(s);
+    return rc;
+  }
+  ce = cudaMemcpy(s->d_pml_ops, ops_b.data(), ops_b.size(), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(s->d_pml_elem, elem.data(), sizeof(int32_t) * elem.size(), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemcpy(s->d_pml_node, node_b.data(), node_b.size(), cudaMemcpyHostToDevice);
+  if (ce == cudaSuccess) ce = cudaMemset(s->d_phi, 0, s->pml_bytes);
+  if (ce != cudaSuccess) {
+    free_pml(s);
+    return cuda_fail(s, ce, "gb_set_pml upload");
+  }
+  return GB_OK;
+}
+
+int gb_pml_fields(gb_solver *s, double *phi_out, int64_t *elem_out, int64_t *n_layer) {
+  if (!s || !n_layer) return fail(s, GB_EINVAL, "NULL argument");
+  if (s->s3) return fail(s, GB_EINVAL, "gb_pml_fields applies to dim = 2 solvers");
+  *n_layer = s->n_layer;
+  if (s->n_layer == 0 || (!phi_out && !elem_out)) return GB_OK;
+  const size_t n = (size_t)s->n_layer * 6 * s->Np;
+  cudaError_t ce = cudaStreamSynchronize(s->stream);
+  if (ce == cudaSuccess && phi_out) {
+    if (s->precision == GB_FP64) {
+      ce = cudaMemcpy(phi_out, s->d_phi, n * sizeof(double), cudaMemcpyDeviceToHost);
+    } else {
+      std::vector<float> f(n);
+      ce = cudaMemcpy(f.data(), s->d_phi, n * sizeof(float), cudaMemcpyDeviceToHost);
+      for (size_t i = 0; i < n; ++i) phi_out[i] = (double)f[i];
+    }
+  }
+  if (ce == cudaSuccess && elem_out) {
+    std::vector<int32_t> e((size_t)s->n_layer), perm;
+    ce = cudaMemcpy(e.data(), s->d_pml_elem, sizeof(int32_t) * e.size(), cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess && s->precision == GB_MIXED) {
+      perm.resize((size_t)s->K);
+      ce = cudaMemcpy(perm.data(), s->d_perm, sizeof(int32_t) * perm.size(), cudaMemcpyDeviceToHost);
+    }
+    for (size_t i = 0; ce == cudaSuccess && i < e.size(); ++i)
+      elem_out[i] = s->precision == GB_MIXED ? perm[(size_t)e[i]] : e[i];
+  }
+  if (ce != cudaSuccess) return cuda_fail(s, ce, "gb_pml_fields");
+  return GB_OK;
 }
 
 int gb_set_wave_motion(gb_solver *s, const gb_wave_motion *m) {

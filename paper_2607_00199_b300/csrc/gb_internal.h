@@ -118,6 +118,22 @@ struct StageArgs {
   double *rec_hist;
 };
 
+// Perfectly matched layer (gb_pml.cu): the layer's elements and auxiliary fields, in the
+// representation of the stage kernels (T = double for GB_FP64, float for GB_MIXED)
+struct PmlArgs {
+  const void *ops;              // Dr^T, Ds^T, LIFT^T, node barycentrics (T; layout in gb_pml.cu)
+  const int32_t *elem;          // n_layer element indices in the kernels' numbering
+  const void *node;             // n_layer x 3 x Np (T): sigma, e_x, e_y at every node
+  void *phin, *phis, *phiacc;   // n_layer x 6 x Np (T): Phi_n, the stage value, the RK4 sum
+  int64_t n_layer;
+  int64_t stride;               // element stride of the field arrays
+  double alpha;                 // frequency shift
+  double cq[2], cs[2];          // per field class: the coefficient of F_i in q_{i+1} (times dt)
+                                // and in the stored F_0 / accumulator, for this stage
+};
+int launch_pml_stage(int N, bool fp64, const StageArgs &a, const PmlArgs &p, void *stream, int num_sms);
+int pml_ops_size(int N);
+
 // most CTAs of a launch with the fused record (the size of its partials buffer)
 constexpr int kRecMaxCtas = 1184;
 

@@ -20,6 +20,7 @@ GB_OK, GB_EINVAL, GB_ENOMEM, GB_ECUDA, GB_EMESH, GB_ENAN = 0, -1, -2, -3, -4, -5
 GB_FP64, GB_MIXED = 0, 1
 GB_MOTION_STATIC, GB_MOTION_SINXY, GB_MOTION_PLUNGE, GB_MOTION_TGV3D = 0, 1, 2, 3
 GB_BC_INTERIOR, GB_BC_WALL, GB_BC_FARFIELD = 0, 1, 2
+GB_PML_RADIAL, GB_PML_SLAB, GB_PML_UNIFORM = 0, 1, 2
 _NAMES = {GB_EINVAL: 'GB_EINVAL', GB_ENOMEM: 'GB_ENOMEM', GB_ECUDA: 'GB_ECUDA', GB_EMESH: 'GB_EMESH', GB_ENAN: 'GB_ENAN'}
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -38,6 +39,11 @@ class GbMotion(ctypes.Structure):
 
 class GbWaveMotion(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ('A0', 'A1', 'Lx', 'wavelength', 'omega', 'r0sq', 'yc', 'zc')]
+
+
+class GbPml(ctypes.Structure):
+    _fields_ = [('kind', ctypes.c_int32)] + [(k, ctypes.c_double) for k in
+                                             ('cx', 'cy', 'ex', 'ey', 'r0', 'd', 'sigma_max', 'power', 'alpha')]
 
 
 class GBError(RuntimeError):
@@ -70,6 +76,8 @@ def _load():
         'gb_set_graph': ([vp, c_int], c_int),
         'gb_diagnostics': ([vp, _dp], c_int),
         'gb_diagnostics3d': ([vp, _dp], c_int),
+        'gb_set_pml': ([vp, ctypes.POINTER(GbPml)], c_int),
+        'gb_pml_fields': ([vp, _dp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], c_int),
         'gb_set_diagnostics': ([vp, c_int, ctypes.c_int64], c_int),
         'gb_diagnostics_history': ([vp, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)], c_int),
@@ -220,6 +228,27 @@ class Solver:
         m = GbWaveMotion(float(A0), float(A1), float(Lx), float(wavelength), float(omega), float(r0sq),
                          float(yc), float(zc))
         self._c(lib.gb_set_wave_motion(self.h, ctypes.byref(m)))
+
+    def set_pml(self, kind=GB_PML_RADIAL, centre=(0.5, 0.0), r0=17.0, d=3.0, sigma_max=1.0, power=2.0,
+                alpha=0.0, direction=(1.0, 0.0)):
+        """Perfectly matched layer (gb_set_pml, dim = 2); kind None removes it."""
+        if kind is None:
+            self._c(lib.gb_set_pml(self.h, None))
+            return
+        p = GbPml(int(kind), float(centre[0]), float(centre[1]), float(direction[0]), float(direction[1]),
+                  float(r0), float(d), float(sigma_max), float(power), float(alpha))
+        self._c(lib.gb_set_pml(self.h, ctypes.byref(p)))
+
+    def pml_fields(self):
+        """(Phi_n of the layer's elements (n_layer, 6, Np), their canonical ids ascending)."""
+        n = ctypes.c_int64()
+        self._c(lib.gb_pml_fields(self.h, None, None, ctypes.byref(n)))
+        phi = np.zeros((n.value, 6, self.Np))
+        ids = np.zeros(n.value, dtype=np.int64)
+        if n.value:
+            self._c(lib.gb_pml_fields(self.h, _ptr(phi), ids.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      ctypes.byref(n)))
+        return phi, ids
 
     def set_fields(self, q, t=0.0):
         q = np.ascontiguousarray(q, dtype=np.float64)
