@@ -206,11 +206,13 @@ def run_3d(torch, steps_fp64=10, steps_mixed=50, warmup=3, tgv=False):
                       '(FP64 state %d MB per array, FP32 %d MB)' % (K * Np * 80 // 10 ** 6, K * Np * 40 // 10 ** 6)})
 
 
-WORKLOAD_AF = dict(ni=256, nj=192, R=20.0, N=4, Ma=0.1, Re=1000.0, A=0.25, T=2.0, far=(1.0, 1.0, 0.0), cfl=0.5)
+WORKLOAD_AF = dict(ni=256, nj=192, R=20.0, N=4, Ma=0.1, Re=1000.0, A=0.25, T=2.0, far=(1.0, 1.0, 0.0), cfl=0.5,
+                   pml=dict(r0=17.0, d=3.0, power=2.0, alpha=1.0, reflection=1e-6))
 WORKLOAD_AF_NAME = ('2D plunging NACA 0012 airfoil: O-grid of 256 wrap-around x 192 radial quads (geometric growth 1.02, '
                     'radius 20 chords) -> K=98304 triangles, N=4, 6 fields, Ma=0.1, Re=1000, rigid plunge '
-                    'h(t)=0.25 sin(2 pi 0.5 t), walls on the airfoil (bounce-back about the wall velocity), free-stream '
-                    'far field (no PML), whole SARK step captured as a CUDA graph')
+                    'h(t)=0.25 sin(2 pi 0.5 t), walls on the airfoil (bounce-back about the wall velocity), outer 3-chord '
+                    'perfectly matched layer (radial, r = 17..20 about mid-chord, sigma ~ ((r-17)/3)^2, auxiliary fields '
+                    'on the layer elements) in front of the free-stream far field, whole SARK step captured as a CUDA graph')
 
 
 def run_airfoil(torch, steps=50, warmup=3):
@@ -223,9 +225,20 @@ def run_airfoil(torch, steps=50, warmup=3):
     Np, _, _ = sizes(W['N'])
     hbm, sm_max, _ = load_peaks()
     out = {'workload': WORKLOAD_AF_NAME, 'K': int(mesh['EToV'].shape[0]), 'N': W['N'], 'Np': Np, 'fields': 6}
-    for name, prec, nst in (('mixed', gb.GB_MIXED, steps), ('fp64', gb.GB_FP64, max(4, steps // 10))):
+    P = W['pml']
+    c = 1.0 / W['Ma']
+    # sigma_max for the continuous layer's normal-incidence round trip exp(-2 int sigma / (sqrt3 c)) = R
+    sigma_max = (P['power'] + 1.0) * math.sqrt(3.0) * c * math.log(1.0 / P['reflection']) / (2.0 * P['d'])
+    out['pml'] = dict(P, sigma_max=sigma_max, centre=(0.5, 0.0))
+    legs = (('mixed', gb.GB_MIXED, steps, True), ('mixed_no_pml', gb.GB_MIXED, steps, False),
+            ('fp64', gb.GB_FP64, max(4, steps // 10), True))
+    for name, prec, nst, layer in legs:
         s = gb.Solver(mesh, W['N'], W['Ma'], W['Re'], precision=prec, stream=tstream.cuda_stream, far_state=W['far'])
         s.set_motion(W['A'], W['T'], kind=gb.GB_MOTION_PLUNGE)
+        if layer:
+            s.set_pml(gb.GB_PML_RADIAL, centre=(0.5, 0.0), r0=P['r0'], d=P['d'], sigma_max=sigma_max,
+                      power=P['power'], alpha=P['alpha'])
+            out['pml']['n_layer_elements'] = int(s.pml_fields()[1].shape[0])
         xy = s.nodes()
         rho, u, v = inputs.free_stream(xy[..., 0], xy[..., 1], W['far'][1], W['far'][2])
         q0 = state.equilibrium_fields(rho, u, v, s.c)
@@ -234,12 +247,16 @@ def run_airfoil(torch, steps=50, warmup=3):
         dof = s.K * Np * 6
         stage_ms = float(sum(kms[:4]))
         r = {'value': dof * 4 * nst / (ms / 1e3), 'ms_per_step': ms / nst, 'steps': nst, 'warmup': warmup,
-             'kernel_ms_per_step': [x / nst for x in kms]}
+             'kernel_ms_per_step': [x / nst for x in kms], 'pml': layer}
+        if name == 'mixed_no_pml':
+            out[name] = {'ms_per_step': ms / nst, 'value': r['value']}
+            s.close()
+            continue
         if prec == gb.GB_MIXED:
             alg = bytes_per_step(s.K, W['N'], s.nv, 4)
             gbs = alg * nst / (stage_ms / 1e3) / 1e9
             r['roofline'] = {'bound': 'hbm', 'achieved': gbs, 'peak': hbm, 'unit': 'GB/s', 'frac': gbs / hbm,
-                             'kernel': 'tc_stage_kernel<4,*,BC> (4 launches per step)'}
+                             'kernel': 'tc_stage_kernel<4,*,BC> + pml_stage_kernel (4 + 4 launches per step)'}
         else:
             fl = flops_per_element_stage(W['N']) * s.K * 4 * nst / (stage_ms / 1e3) / 1e12
             peak = 148 * FP64_FLOP_PER_CLK_SM * sm_max * 1e6 / 1e12
@@ -248,6 +265,7 @@ def run_airfoil(torch, steps=50, warmup=3):
         out[name] = r
         s.close()
     out['mixed_speedup_vs_fp64'] = out['mixed']['value'] / out['fp64']['value']
+    out['pml_overhead_mixed'] = out['mixed']['ms_per_step'] / out['mixed_no_pml']['ms_per_step'] - 1.0
     out['note'] = ('throughput only; dt from CFL 0.5 on the thinnest O-grid cell, so a step covers little physical '
                    'time; the per-step cost is what is measured')
     return out

@@ -66,14 +66,16 @@ pml_stage_kernel(const StageArgs a, const PmlArgs p) {
   constexpr bool PERTURB = sizeof(T) == 4;
   __shared__ T sops[D::OpSize];
   __shared__ T sq[E][6 * Np];
-  __shared__ T sfl[E][6 * NFN];
-  __shared__ T sgeo[E][20];   // rx sx ry sy, vertex velocities (6), per face nx ny Fscale (9), J
+  __shared__ T strc[E][6 * NFN];   // neighbour traces q+, then the face terms along e
+  __shared__ T sgeo[E][20];        // rx sx ry sy, vertex velocities (6), per face nx ny Fscale (9), J
+  __shared__ MeshRec srec[E];
+  __shared__ int32_t selem[E];
   __shared__ double s_motion[2];
 
   const int tid = threadIdx.x, nthr = blockDim.x;
   const T *gops = reinterpret_cast<const T *>(p.ops);
   for (int i = tid; i < D::OpSize; i += nthr) sops[i] = gops[i];
-  if (tid == 0) {
+  if (tid == nthr - 1) {
     // the stage's motion factors, as the stage kernels form them: v_i = gfac S(X),
     // x_i = x_n + xfac S(X) (RK4 nodes and a_{i,i-1})
     double gfac = 0.0, xfac = 0.0;
@@ -86,22 +88,65 @@ pml_stage_kernel(const StageArgs a, const PmlArgs p) {
     s_motion[0] = gfac;
     s_motion[1] = xfac;
   }
-  __syncthreads();
-  const double gfac = s_motion[0], xfac = s_motion[1];
   const T *qin = reinterpret_cast<const T *>(a.qin);
   const T c = (T)a.c, half = (T)0.5;
   const T al = (T)((9.0 - 1.7320508075688772935) / 6.0), be = (T)((1.7320508075688772935 - 3.0) / 6.0);
   const int e_loc = tid / Np, n_loc = tid - Np * (tid / Np);
+  T *phin = reinterpret_cast<T *>(p.phin), *phis = reinterpret_cast<T *>(p.phis);
+  T *phia = reinterpret_cast<T *>(p.phiacc);
+  T *qo = reinterpret_cast<T *>(a.qout);
+  T *sto = reinterpret_cast<T *>(STAGE == 0 ? a.F0 : a.acc);
 
   for (int64_t l0 = (int64_t)blockIdx.x * E; l0 < p.n_layer; l0 += (int64_t)gridDim.x * E) {
     const int nel = (int)((p.n_layer - l0) < E ? (p.n_layer - l0) : E);
+    // phase 0: this tile's element indices; every node's own layer data straight into
+    // registers (independent of everything else, so their latency overlaps the rest)
+    if (tid < nel) selem[tid] = p.elem[l0 + tid];
+    const bool node = e_loc < nel;
+    T ph[6], pn[6], pa[6], sig = 0, ex = 0, ey = 0;   // Phi_i, Phi_n, the RK4 sum
+    if (node) {
+      const T *pe = reinterpret_cast<const T *>(p.node) + ((l0 + e_loc) * 3) * Np;
+      sig = pe[n_loc]; ex = pe[Np + n_loc]; ey = pe[2 * Np + n_loc];
+      const int64_t base = (l0 + e_loc) * 6 * Np + n_loc;
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        ph[f] = STAGE == 0 ? phin[base + f * Np] : phis[base + f * Np];
+        pn[f] = STAGE == 0 ? ph[f] : phin[base + f * Np];
+        pa[f] = STAGE == 0 ? (T)0 : phia[base + f * Np];
+      }
+    }
+    __syncthreads();
+    // phase 1: own fields and mesh records; the node's q_{i+1} and stored F values
+    T qv[6], sv[6];
+    const int64_t qbase = node ? (int64_t)selem[e_loc] * p.stride + n_loc : 0;
+    if (node) {
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        qv[f] = qo[qbase + f * Np];
+        sv[f] = STAGE < 3 ? sto[qbase + f * Np] : (T)0;
+      }
+    }
     for (int i = tid; i < nel * 6 * Np; i += nthr) {
       const int el = i / (6 * Np), j = i - 6 * Np * (i / (6 * Np));
-      sq[el][j] = qin[(int64_t)p.elem[l0 + el] * p.stride + j];
+      sq[el][j] = qin[(int64_t)selem[el] * p.stride + j];
     }
-    // geometry of the stage (FP64 vertex positions, T afterwards), one thread per element
+    if (tid < nel) srec[tid] = a.mesh[selem[tid]];
+    __syncthreads();
+    // phase 2: neighbour traces (all face nodes) and, for one thread per element, the
+    // stage geometry (FP64 vertex positions, T afterwards)
+    for (int item = tid; item < nel * NFN; item += nthr) {
+      const int el = item / NFN, j = item - NFN * (item / NFN);
+      const int f = j / Nfp, k = j - Nfp * (j / Nfp);
+      const int nb = srec[el].nbr[f];
+      if (nb >= 0) {
+        const T *qp = qin + (int64_t)(nb >> 2) * p.stride + pml_fmask<N>(nb & 3, Nfp - 1 - k);
+#pragma unroll
+        for (int fld = 0; fld < 6; ++fld) strc[el][fld * NFN + j] = qp[fld * Np];
+      }
+    }
+    const double gfac = s_motion[0], xfac = s_motion[1];
     for (int el = tid; el < nel; el += nthr) {
-      const MeshRec rec = a.mesh[p.elem[l0 + el]];
+      const MeshRec &rec = srec[el];
       double px[3], py[3];
       T vx[3], vy[3];
 #pragma unroll
@@ -124,21 +169,21 @@ pml_stage_kernel(const StageArgs a, const PmlArgs p) {
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
         const int f1 = (f + 1) % 3;
-        const T ex = (T)(px[f1] - px[f]), ey = (T)(py[f1] - py[f]);
-        const T len = sqrt(ex * ex + ey * ey);
-        g[10 + 3 * f] = ey / len;
-        g[11 + 3 * f] = -ex / len;
+        const T dx = (T)(px[f1] - px[f]), dy = (T)(py[f1] - py[f]);
+        const T len = sqrt(dx * dx + dy * dy);
+        g[10 + 3 * f] = dy / len;
+        g[11 + 3 * f] = -dx / len;
         g[12 + 3 * f] = (T)0.5 * len * iJ;   // sJ / J with sJ = len / 2
       }
       g[19] = J;
     }
     __syncthreads();
-    // face terms along e at every face node: item = (element, face node)
+    // phase 3: face terms along e at every face node, over the traces in place
     for (int item = tid; item < nel * NFN; item += nthr) {
       const int el = item / NFN, j = item - NFN * (item / NFN);
       const int f = j / Nfp, k = j - Nfp * (j / Nfp);
       const int vol = pml_fmask<N>(f, k);
-      const int nb = a.mesh[p.elem[l0 + el]].nbr[f];
+      const int nb = srec[el].nbr[f];
       const T *qm = sq[el] + vol;
       const T *g = sgeo[el];
       const T *bl = sops + D::Bary + 3 * vol;
@@ -164,31 +209,30 @@ pml_stage_kernel(const StageArgs a, const PmlArgs p) {
 #pragma unroll
         for (int fld = 0; fld < 6; ++fld) w[fld] = qe[fld] - qm[fld * Np];
       } else {
-        const T *qp = qin + (int64_t)(nb >> 2) * p.stride + pml_fmask<N>(nb & 3, Nfp - 1 - k);
 #pragma unroll
-        for (int fld = 0; fld < 6; ++fld) w[fld] = qp[fld * Np] - qm[fld * Np];
+        for (int fld = 0; fld < 6; ++fld) w[fld] = strc[el][fld * NFN + j] - qm[fld * Np];
       }
       const T nx = g[10 + 3 * f], ny = g[11 + 3 * f], fs = g[12 + 3 * f];
       const T *pe = reinterpret_cast<const T *>(p.node) + ((l0 + el) * 3) * Np;
-      const T ex = pe[Np + vol], ey = pe[2 * Np + vol];
-      const T ne = nx * ex + ny * ey, vn = vgx * nx + vgy * ny, ve = vgx * ex + vgy * ey;
+      const T fex = pe[Np + vol], fey = pe[2 * Np + vol];
+      const T ne = nx * fex + ny * fey, vn = vgx * nx + vgy * ny, ve = vgx * fex + vgy * fey;
       T y1[6], y2[6], y3[6], y4[6], ye[6];
       pml_apply_An<T>(nx, ny, w, y1);
       pml_apply_An<T>(nx, ny, y1, y2);
       pml_apply_An<T>(nx, ny, y2, y3);
       pml_apply_An<T>(nx, ny, y3, y4);
-      pml_apply_An<T>(ex, ey, w, ye);
+      pml_apply_An<T>(fex, fey, w, ye);
       const T avn = vn < (T)0 ? -vn : vn;
 #pragma unroll
       for (int fld = 0; fld < 6; ++fld) {
         const T cen = half * ne * (ve * w[fld] - c * ye[fld]);
         const T dis = half * (c * (al * y2[fld] + be * y4[fld]) + avn * w[fld]);
-        sfl[el][fld * NFN + j] = fs * (cen + ne * ne * dis);
+        strc[el][fld * NFN + j] = fs * (cen + ne * ne * dis);
       }
     }
     __syncthreads();
-    // volume terms along e, LIFT of the face terms, then the layer's updates: one thread per node
-    if (e_loc < nel) {
+    // phase 4: volume terms along e, LIFT of the face terms, the layer's updates (one thread per node)
+    if (node) {
       const T *q = sq[e_loc];
       T qr[6], qs[6];
 #pragma unroll
@@ -202,8 +246,6 @@ pml_stage_kernel(const StageArgs a, const PmlArgs p) {
         }
       }
       const T *g = sgeo[e_loc];
-      const T *pe = reinterpret_cast<const T *>(p.node) + ((l0 + e_loc) * 3) * Np;
-      const T sig = pe[n_loc], ex = pe[Np + n_loc], ey = pe[2 * Np + n_loc];
       const T *bl = sops + D::Bary + 3 * n_loc;
       const T vgx = bl[0] * g[4] + bl[1] * g[6] + bl[2] * g[8];
       const T vgy = bl[0] * g[5] + bl[1] * g[7] + bl[2] * g[9];
@@ -220,37 +262,30 @@ pml_stage_kernel(const StageArgs a, const PmlArgs p) {
       for (int m = 0; m < NFN; ++m) {
         const T lm = sops[D::LiftT + m * Np + n_loc];
 #pragma unroll
-        for (int f = 0; f < 6; ++f) R[f] += lm * sfl[e_loc][f * NFN + m];
+        for (int f = 0; f < 6; ++f) R[f] += lm * strc[e_loc][f * NFN + m];
       }
       // dF = -sigma Phi_i into the stage combinations; Phi by RK4
       const int64_t base = (l0 + e_loc) * 6 * Np + n_loc;
-      const int64_t qbase = (int64_t)p.elem[l0 + e_loc] * p.stride + n_loc;
-      T *phin = reinterpret_cast<T *>(p.phin), *phis = reinterpret_cast<T *>(p.phis);
-      T *phia = reinterpret_cast<T *>(p.phiacc);
-      T *qo = reinterpret_cast<T *>(a.qout);
-      T *st = reinterpret_cast<T *>(STAGE == 0 ? a.F0 : a.acc);
       const T dt = (T)a.dt, decay = (T)p.alpha + sig;
 #pragma unroll
       for (int f = 0; f < 6; ++f) {
         const int cl = f < 3 ? 0 : 1;
-        const int64_t i = base + f * Np;
-        const T ph = STAGE == 0 ? phin[i] : phis[i];
-        const T dF = -sig * ph;
-        const T G = R[f] - decay * ph;
-        const int64_t iq = qbase + f * Np;
-        qo[iq] += dt * (T)p.cq[cl] * dF;
-        if (STAGE < 3) st[iq] += (T)p.cs[cl] * dF;
+        const T dF = -sig * ph[f];
+        const T G = R[f] - decay * ph[f];
+        const int64_t iq = qbase + f * Np, i = base + f * Np;
+        qo[iq] = qv[f] + dt * (T)p.cq[cl] * dF;
+        if (STAGE < 3) sto[iq] = sv[f] + (T)p.cs[cl] * dF;
         if (STAGE == 0) {
-          phis[i] = phin[i] + dt * (T)0.5 * G;
+          phis[i] = pn[f] + dt * (T)0.5 * G;
           phia[i] = G / (T)6;
         } else if (STAGE == 1) {
-          phis[i] = phin[i] + dt * (T)0.5 * G;
-          phia[i] += G / (T)3;
+          phis[i] = pn[f] + dt * (T)0.5 * G;
+          phia[i] = pa[f] + G / (T)3;
         } else if (STAGE == 2) {
-          phis[i] = phin[i] + dt * G;
-          phia[i] += G / (T)3;
+          phis[i] = pn[f] + dt * G;
+          phia[i] = pa[f] + G / (T)3;
         } else {
-          phin[i] = phin[i] + dt * (phia[i] + G / (T)6);
+          phin[i] = pn[f] + dt * (pa[f] + G / (T)6);
         }
       }
     }

@@ -4,7 +4,10 @@ workload (K = 131072 jittered triangles, N = 4): set-up, `--warmup` steps, then
 
     python -m paper_2607_00199_b300.profile_case --precision mixed|fp64 [--steps 2] [--warmup 2] [--n 256] [--warps 4]
     python -m paper_2607_00199_b300.profile_case --dim 3 --precision mixed|fp64 [--nx 64 --ny 16 --nz 16] [--N 3]
+    python -m paper_2607_00199_b300.profile_case --airfoil [--no-pml] --precision mixed|fp64
 
+With --airfoil the case is the plunging NACA 0012 O-grid (256 x 192 quads, K = 98304, N = 4)
+with the outer 3-chord perfectly matched layer (r = 17..20 about mid-chord).
 With --dim 3 the case is the deforming-channel workload (periodic box [0,8]x[0,2]x[0,2]
 of nx x ny x nz hexes, 6 tetrahedra each, travelling-wave motion).
 
@@ -31,12 +34,16 @@ def main():
     p.add_argument('--nx', type=int, default=64)
     p.add_argument('--ny', type=int, default=16)
     p.add_argument('--nz', type=int, default=16)
+    p.add_argument('--airfoil', action='store_true')
+    p.add_argument('--no-pml', action='store_true')
     a = p.parse_args()
     prec = gb.GB_MIXED if a.precision == 'mixed' else gb.GB_FP64
     if a.N is None:
         a.N = 4 if a.dim == 2 else 3
     if a.dim == 3:
         return main3(a, prec)
+    if a.airfoil:
+        return main_airfoil(a, prec)
     mesh = inputs.periodic_square_mesh(a.n, jitter=0.1)
     s = gb.Solver(mesh, a.N, 0.1, 1000.0, precision=prec, stream=torch.cuda.current_stream().cuda_stream)
     s.set_motion(0.05, 1.0)
@@ -45,6 +52,30 @@ def main():
     s.set_graph(False)
     xy = s.nodes()
     rho, u, v = inputs.taylor_green(xy[..., 0], xy[..., 1], 0.1)
+    s.set_fields(state.equilibrium_fields(rho, u, v, s.c), 0.0)
+    dt = inputs.cfl_dt(mesh, a.N, s.c, 0.5)
+    s.step(dt, a.warmup)
+    s.sync()
+    ms = s.step_timed(dt, a.steps)
+    print('kernel ms per step:', [round(x / a.steps, 4) for x in ms])
+
+
+def main_airfoil(a, prec):
+    import math
+    mesh = inputs.naca_ogrid_mesh(256, 192)
+    far = (1.0, 1.0, 0.0)
+    s = gb.Solver(mesh, a.N, 0.1, 1000.0, precision=prec, stream=torch.cuda.current_stream().cuda_stream,
+                  far_state=far)
+    s.set_motion(0.25, 2.0, kind=gb.GB_MOTION_PLUNGE)
+    if not a.no_pml:
+        c = s.c
+        sigma_max = 3.0 * math.sqrt(3.0) * c * math.log(1e6) / (2.0 * 3.0)
+        s.set_pml(gb.GB_PML_RADIAL, centre=(0.5, 0.0), r0=17.0, d=3.0, sigma_max=sigma_max, power=2.0, alpha=1.0)
+    if prec == gb.GB_MIXED:
+        s.set_launch_config(a.warps)
+    s.set_graph(False)
+    xy = s.nodes()
+    rho, u, v = inputs.free_stream(xy[..., 0], xy[..., 1], far[1], far[2])
     s.set_fields(state.equilibrium_fields(rho, u, v, s.c), 0.0)
     dt = inputs.cfl_dt(mesh, a.N, s.c, 0.5)
     s.step(dt, a.warmup)

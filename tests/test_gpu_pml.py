@@ -161,3 +161,37 @@ def test_layer_state_resets_records_and_rejections():
     s3 = gb.Solver(inputs.periodic_box_tet_mesh(3, 3, 3), 2, 0.1, 100.0)
     with pytest.raises(gb.GBError):
         s3.set_pml(gb.GB_PML_UNIFORM, sigma_max=1.0)
+
+
+def test_full_size_airfoil_with_the_outer_layer():
+    """The plunging-airfoil workload at full size (256 x 192 O-grid, K = 98304, N = 4) with
+    the outer 3-chord layer (r = 17..20 about mid-chord): one SARK step of both precisions
+    against the oracle on every element, q and Phi."""
+    mesh = inputs.naca_ogrid_mesh(256, 192)
+    c = 10.0
+    pml = PML('radial', centre=(0.5, 0.0), r0=17.0, d=3.0, sigma_max=sigma_max_for_reflection(c, 3.0), alpha=1.0)
+    far = (1.0, 1.0, 0.0)
+    o = OracleSolver(mesh, 4, Ma=0.1, Re=1000.0, motion=Motion(0.25, 2.0, kind='plunge'), far_state=far, pml=pml)
+
+    def flow(x, y):
+        rho, u, v = inputs.random_flow(x, y, 5, amp=0.02)
+        return rho, 1.0 + 0.2 * u, 0.2 * v
+
+    q0 = oracle_state(o, o.X, flow)
+    dt = inputs.cfl_dt(mesh, 4, o.c, 0.5)
+    # two steps so that Phi (zero at t = 0) enters the second step's stages
+    q_or, phi_or, _, _ = o.run_pml(q0, np.zeros_like(q0), o.X.copy(), 0.0, dt, 2)
+    assert 0.02 * o.K < o.pml_layer.sum() < 0.2 * o.K
+    for precision, tq, tp in ((gb.GB_FP64, 1e-12, 1e-10), (gb.GB_MIXED, 1e-5, 1e-3)):
+        s = gb.Solver(mesh, 4, 0.1, 1000.0, precision=precision, far_state=far,
+                      stream=torch.cuda.current_stream().cuda_stream)
+        s.set_motion(0.25, 2.0, kind=gb.GB_MOTION_PLUNGE)
+        set_layer(s, pml)
+        s.set_fields(q0, 0.0)
+        s.step(dt, 2)
+        q, _ = s.fields()
+        phi, ids = s.pml_fields()
+        np.testing.assert_array_equal(ids, np.nonzero(o.pml_layer)[0])
+        assert rel_l2(q, q_or) <= tq
+        assert rel_l2(phi, phi_or[o.pml_layer]) <= tp
+        s.close()
