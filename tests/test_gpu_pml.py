@@ -195,3 +195,31 @@ def test_full_size_airfoil_with_the_outer_layer():
         assert rel_l2(q, q_or) <= tq
         assert rel_l2(phi, phi_or[o.pml_layer]) <= tp
         s.close()
+
+
+@pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
+def test_graph_replay_with_the_layer_equals_direct_launches(precision):
+    """The layer's launches join the step's CUDA graph: replayed steps equal direct launches
+    bit for bit (fields and Phi)."""
+    mesh = inputs.naca_ogrid_mesh(24, 9, R=5.0, growth=1.1)
+    far = (1.0, 1.0, 0.0)
+    o = OracleSolver(mesh, 3, Ma=0.1, Re=1000.0, far_state=far)
+    q0 = oracle_state(o, o.X, lambda x, y: (1.0 + 0.02 * np.exp(-((x - 3.0) ** 2 + y ** 2)), 1.0 + 0 * x, 0 * x))
+    dt = inputs.cfl_dt(mesh, 3, o.c, 0.5)
+    side = torch.cuda.Stream()
+    out = []
+    for graph in (True, False):
+        s = gb.Solver(mesh, 3, 0.1, 1000.0, precision=precision, far_state=far, stream=side.cuda_stream)
+        s.set_motion(0.25, 2.0, kind=gb.GB_MOTION_PLUNGE)
+        s.set_pml(gb.GB_PML_RADIAL, centre=(0.5, 0.0), r0=2.5, d=2.5, sigma_max=30.0, alpha=0.1)
+        s.set_graph(graph)
+        s.set_fields(q0, 0.0)
+        s.step(dt, 7)
+        out.append((s.fields(), s.pml_fields()[0]))
+        s.close()
+    (qa, ta), pa = out[0]
+    (qb, tb), pb = out[1]
+    assert ta == tb
+    np.testing.assert_array_equal(qa, qb)
+    np.testing.assert_array_equal(pa, pb)
+    assert np.abs(pa).max() > 0
