@@ -411,25 +411,35 @@ stage_kernel(const StageArgs a) {
         T *acc = reinterpret_cast<T *>(a.acc);
         bool bad = false;
         T qrec[3] = {0, 0, 0};
+        // every load of the node's six fields is issued before any store (q_{n+1} overwrites
+        // q_n in place at the last stage, so the compiler may not reorder them itself)
+        T xv[6], x0[6], x1[6];
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+          const int64_t idx = base + f * Np;
+          xv[f] = STAGE == 0 ? sq[e_loc * NQ + f * Np + n_loc] : qn[idx];
+          x0[f] = (STAGE == 1 || STAGE == 2) ? F0[idx] : (T)0;
+          x1[f] = STAGE >= 2 ? acc[idx] : (T)0;
+        }
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
           const int cl = f < 3 ? 0 : 1;
           const int64_t idx = base + f * Np;
           const T r = rhs[f];
           if (STAGE == 0) {
-            const T qv = sq[e_loc * NQ + f * Np + n_loc];
+            const T qv = xv[f];
             F0[idx] = r;
             qout[idx] = (T)a.co.E[cl][1] * qv + dt * ((T)a.co.A[cl][4] * r);
           } else if (STAGE == 1) {
-            const T qv = qn[idx], f0 = F0[idx];
+            const T qv = xv[f], f0 = x0[f];
             qout[idx] = (T)a.co.E[cl][2] * qv + dt * ((T)a.co.A[cl][8] * f0 + (T)a.co.A[cl][9] * r);
             acc[idx] = (T)a.co.B[cl][0] * f0 + (T)a.co.B[cl][1] * r;
           } else if (STAGE == 2) {
-            const T qv = qn[idx], f0 = F0[idx], ac = acc[idx];
+            const T qv = xv[f], f0 = x0[f], ac = x1[f];
             qout[idx] = (T)a.co.E[cl][3] * qv + dt * ((T)a.co.A[cl][12] * f0 + (T)a.co.A[cl][14] * r);
             acc[idx] = ac + (T)a.co.B[cl][2] * r;
           } else {
-            const T qv = qn[idx], ac = acc[idx];
+            const T qv = xv[f], ac = x1[f];
             const T out = (T)a.co.E[cl][4] * qv + dt * (ac + (T)a.co.B[cl][3] * r);
             qout[idx] = out;
             bad |= bad_value(out);

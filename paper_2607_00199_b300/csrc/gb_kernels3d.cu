@@ -474,26 +474,33 @@ stage3_kernel(const Stage3Args a) {
         T *F0 = reinterpret_cast<T *>(a.F0);
         T *acc = reinterpret_cast<T *>(a.acc);
         bool bad = false;
+        // every load of the node's ten fields is issued before any store (q_{n+1} overwrites
+        // q_n in place at the last stage, so the compiler may not reorder them itself): one
+        // memory round trip instead of one per field
+        T xv[10], x0[10], x1[10];
+#pragma unroll
+        for (int f = 0; f < 10; ++f) {
+          const int64_t idx = base + f * Np;
+          xv[f] = STAGE == 0 ? (L::IP_SMEM ? qin[idx] : sq[e_loc * NQ + f * Np + n_loc]) : qn[idx];   // stage 0: qin is q_n
+          x0[f] = (STAGE == 1 || STAGE == 2) ? F0[idx] : (T)0;
+          x1[f] = STAGE >= 2 ? acc[idx] : (T)0;
+        }
 #pragma unroll
         for (int f = 0; f < 10; ++f) {
           const int cl = f < 4 ? 0 : 1;
           const int64_t idx = base + f * Np;
-          const T r = rhs[f];
+          const T r = rhs[f], qv = xv[f];
           if (STAGE == 0) {
-            const T qv = L::IP_SMEM ? qin[idx] : sq[e_loc * NQ + f * Np + n_loc];   // stage 0: qin is q_n
             F0[idx] = r;
             qout[idx] = kE[cl] * qv + dt * (kA0[cl] * r);
           } else if (STAGE == 1) {
-            const T qv = qn[idx], f0 = F0[idx];
-            qout[idx] = kE[cl] * qv + dt * (kA0[cl] * f0 + kA1[cl] * r);
-            acc[idx] = kB0[cl] * f0 + kB1[cl] * r;
+            qout[idx] = kE[cl] * qv + dt * (kA0[cl] * x0[f] + kA1[cl] * r);
+            acc[idx] = kB0[cl] * x0[f] + kB1[cl] * r;
           } else if (STAGE == 2) {
-            const T qv = qn[idx], f0 = F0[idx], ac = acc[idx];
-            qout[idx] = kE[cl] * qv + dt * (kA0[cl] * f0 + kA1[cl] * r);
-            acc[idx] = ac + kB0[cl] * r;
+            qout[idx] = kE[cl] * qv + dt * (kA0[cl] * x0[f] + kA1[cl] * r);
+            acc[idx] = x1[f] + kB0[cl] * r;
           } else {
-            const T qv = qn[idx], ac = acc[idx];
-            const T out = kE[cl] * qv + dt * (ac + kB0[cl] * r);
+            const T out = kE[cl] * qv + dt * (x1[f] + kB0[cl] * r);
             qout[idx] = out;
             bad |= bad3(out);
           }
