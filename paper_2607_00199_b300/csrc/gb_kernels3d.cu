@@ -69,6 +69,29 @@ struct Op3 {
 constexpr int GEO3 = 40, GEO3_V = 9, GEO3_F = 21;
 
 
+// asynchronous global -> shared copies (cp.async): 16 bytes (both addresses 16-byte aligned)
+// or 4 bytes
+__device__ __forceinline__ void cp_async16_3(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async4_3(void *dst, const void *src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+}
+
+// the own fields of tile t (nel elements, contiguous) into shared memory, asynchronously
+template <typename T>
+__device__ __forceinline__ void prefetch_tile3(const T *qin, int64_t elem0, int nel, int NQ, T *dst, bool al16) {
+  const char *src = reinterpret_cast<const char *>(qin + elem0 * NQ);
+  char *d = reinterpret_cast<char *>(dst);
+  const int bytes = nel * NQ * (int)sizeof(T);
+  const int b16 = al16 ? (bytes & ~15) : 0;
+  for (int i = 16 * (int)threadIdx.x; i < b16; i += 16 * (int)blockDim.x) cp_async16_3(d + i, src + i);
+  for (int i = b16 + 4 * (int)threadIdx.x; i < bytes; i += 4 * (int)blockDim.x) cp_async4_3(d + i, src + i);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
 template <typename T> __device__ __forceinline__ T fma3(T a, T b, T c);
 template <> __device__ __forceinline__ double fma3<double>(double a, double b, double c) { return __fma_rn(a, b, c); }
 template <> __device__ __forceinline__ float fma3<float>(float a, float b, float c) { return __fmaf_rn(a, b, c); }
@@ -135,6 +158,11 @@ stage3_kernel(const Stage3Args a) {
   T *sflux = sq + E * NQ;          // [E][10][NFN]
   T *snt = sflux + E * 10 * NFN;   // [E][6][Nc]
   T *sgeo = snt + E * 6 * Nc;      // [E][GEO3]
+  // FP32 up to N = 3: a second own-field buffer, filled for the next tile while this one computes
+  constexpr bool DB = sizeof(T) == 4 && N <= 3;
+  static_assert(!DB || (L::SmemSize + ((L::TabInts + 3) & ~3) + E * (NQ + 10 * NFN + 6 * Nc + GEO3)) % 4 == 0,
+                "the second own-field buffer must start on a 16-byte boundary");
+  T *const sqA = sq, *const sqB = sgeo + E * GEO3;
   __shared__ double s_motion[4];
 
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -179,10 +207,28 @@ stage3_kernel(const Stage3Args a) {
   const T c = (T)a.c;
 
   const int64_t ntiles = (a.K + E - 1) / E;
+  const bool al16 = (reinterpret_cast<uintptr_t>(qin) & 15) == 0;
+  if (DB && (int64_t)blockIdx.x < ntiles) {
+    const int64_t e0 = (int64_t)blockIdx.x * E;
+    prefetch_tile3<T>(qin, e0, (int)((a.K - e0) < E ? (a.K - e0) : E), NQ, sqA, al16);
+  }
+  int cur = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t elem0 = tile * E;
     const int nel = (int)((a.K - elem0) < E ? (a.K - elem0) : E);
-    {
+    T *sq = (DB && cur) ? sqB : sqA;
+    if constexpr (DB) {
+      // this tile's fields have arrived; the other buffer (the previous tile's, released by the
+      // barrier that ended it) takes the next tile's
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncthreads();
+      const int64_t nt = tile + gridDim.x;
+      if (nt < ntiles) {
+        const int64_t e1 = nt * E;
+        prefetch_tile3<T>(qin, e1, (int)((a.K - e1) < E ? (a.K - e1) : E), NQ, cur ? sqA : sqB, al16);
+      }
+      cur ^= 1;
+    } else {
       const T *src = qin + elem0 * NQ;
       const int cnt = nel * NQ;
       for (int i = tid; i < cnt; i += nthr) sq[i] = src[i];
@@ -518,8 +564,9 @@ static size_t stage3_smem() {
   typedef Dim3<N> D;
   typedef Op3<T, N> L;
   constexpr int E = Tile3<T, N>::E;
+  constexpr bool DB = sizeof(T) == 4 && N <= 3;   // second own-field buffer (stage3_kernel)
   return sizeof(T) * (size_t)L::SmemSize + sizeof(int) * (size_t)((L::TabInts + 3) & ~3) +
-         sizeof(T) * (size_t)E * (D::NQ + 10 * D::NFN + 6 * D::Nc + GEO3);
+         sizeof(T) * (size_t)E * (D::NQ + 10 * D::NFN + 6 * D::Nc + GEO3 + (DB ? D::NQ : 0));
 }
 
 template <typename T, int N, int STAGE>
