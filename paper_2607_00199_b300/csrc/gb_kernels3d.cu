@@ -237,25 +237,30 @@ stage3_kernel(const Stage3Args a) {
     //      differences, everything after them in T (FP64 in GB_FP64) ----
     for (int e = tid; e < nel; e += nthr) {
       const MeshRec3 rec = a.mesh[elem0 + e];
+      // stage positions x_n + shift + x1 S1 + x2 S2: the vertex positions and their differences
+      // in FP64, the motion increments (small against the edges) in T
+      const T x1t = (T)x1, x2t = (T)x2, g1t = (T)g1, g2t = (T)g2;
       double P0[3];
+      T S0[3];   // x1 S1 + x2 S2 of vertex 0
       T dv[4][3], vv[4][3];   // dv[k] = P_k - P_0 (dv[0] = 0); vv[k] the grid velocity of vertex k
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int64_t v = rec.v[k];
         const double2 *sh = reinterpret_cast<const double2 *>(a.shape) + 3 * v;
         const double2 s01 = sh[0], s23 = sh[1], s45 = sh[2];
-        const double S1[3] = {s01.x, s01.y, s23.x}, S2[3] = {s23.y, s45.x, s45.y};
-        double Pk[3];
+        const T S1[3] = {(T)s01.x, (T)s01.y, (T)s23.x}, S2[3] = {(T)s23.y, (T)s45.x, (T)s45.y};
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          Pk[d] = a.xn[3 * v + d] + rec.shift[3 * k + d] * a.period[d];
-          Pk[d] += x1 * S1[d] + x2 * S2[d];
-          vv[k][d] = (T)(g1 * S1[d] + g2 * S2[d]);
-        }
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          if (k == 0) P0[d] = Pk[d];
-          dv[k][d] = k == 0 ? (T)0 : (T)(Pk[d] - P0[d]);
+          const double Pk = a.xn[3 * v + d] + rec.shift[3 * k + d] * a.period[d];
+          const T inc = fma3(x1t, S1[d], x2t * S2[d]);
+          vv[k][d] = fma3(g1t, S1[d], g2t * S2[d]);
+          if (k == 0) {
+            P0[d] = Pk;
+            S0[d] = inc;
+            dv[0][d] = (T)0;
+          } else {
+            dv[k][d] = (T)(Pk - P0[d]) + (inc - S0[d]);
+          }
         }
       }
       T G[3][3];
