@@ -141,6 +141,83 @@ __device__ __forceinline__ Motion3 stage_motion3(const Stage3Args &a, int stage)
   return m;
 }
 
+// Geometry of element `elem` at the stage (one thread): G^-1, the vertex grid velocities, the
+// outward normals and Fscale of the four faces into gout (GEO3 values).  Vertex positions and
+// their differences in FP64, the small motion increments x1 S1 + x2 S2 in T, everything after
+// the edge vectors in T (FP64 in GB_FP64).
+template <typename T>
+__device__ __forceinline__ void element_geometry3(const Stage3Args &a, int64_t elem, double x1, double x2, double g1,
+                                                  double g2, T *gout) {
+  const MeshRec3 rec = a.mesh[elem];
+  // stage positions x_n + shift + x1 S1 + x2 S2: the vertex positions and their differences
+  // in FP64, the motion increments (small against the edges) in T
+  const T x1t = (T)x1, x2t = (T)x2, g1t = (T)g1, g2t = (T)g2;
+  double P0[3];
+  T S0[3];   // x1 S1 + x2 S2 of vertex 0
+  T dv[4][3], vv[4][3];   // dv[k] = P_k - P_0 (dv[0] = 0); vv[k] the grid velocity of vertex k
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int64_t v = rec.v[k];
+    const double2 *sh = reinterpret_cast<const double2 *>(a.shape) + 3 * v;
+    const double2 s01 = sh[0], s23 = sh[1], s45 = sh[2];
+    const T S1[3] = {(T)s01.x, (T)s01.y, (T)s23.x}, S2[3] = {(T)s23.y, (T)s45.x, (T)s45.y};
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double Pk = a.xn[3 * v + d] + rec.shift[3 * k + d] * a.period[d];
+      const T inc = fma3(x1t, S1[d], x2t * S2[d]);
+      vv[k][d] = fma3(g1t, S1[d], g2t * S2[d]);
+      if (k == 0) {
+        P0[d] = Pk;
+        S0[d] = inc;
+        dv[0][d] = (T)0;
+      } else {
+        dv[k][d] = (T)(Pk - P0[d]) + (inc - S0[d]);
+      }
+    }
+  }
+  T G[3][3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) G[d][q] = (T)0.5 * dv[q + 1][d];
+  const T C00 = G[1][1] * G[2][2] - G[1][2] * G[2][1];
+  const T C01 = G[1][2] * G[2][0] - G[1][0] * G[2][2];
+  const T C02 = G[1][0] * G[2][1] - G[1][1] * G[2][0];
+  const T J = G[0][0] * C00 + G[0][1] * C01 + G[0][2] * C02;
+  if (!(J > (T)0)) atomicOr(a.status, GB_STATUS_MESH);
+  const T iJ = (T)1 / J;
+  // G^-1 = adj(G) / J; row a of G^-1 is the gradient of reference coordinate a
+  T *g = gout;
+  g[0] = C00 * iJ; g[3] = C01 * iJ; g[6] = C02 * iJ;
+  g[1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) * iJ;
+  g[4] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) * iJ;
+  g[7] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) * iJ;
+  g[2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) * iJ;
+  g[5] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) * iJ;
+  g[8] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) * iJ;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int d = 0; d < 3; ++d) g[GEO3_V + 3 * k + d] = vv[k][d];
+  // faces (local vertex triples) and the orientation of (P_b - P_a) x (P_c - P_a)
+  // relative to the outward normal; compile-time so that dv stays in registers
+  constexpr int fvt[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
+  constexpr float fsign[4] = {-1.0f, 1.0f, 1.0f, -1.0f};
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const int va = fvt[f][0], vb = fvt[f][1], vc = fvt[f][2];
+    const T ux = dv[vb][0] - dv[va][0], uy = dv[vb][1] - dv[va][1], uz = dv[vb][2] - dv[va][2];
+    const T wx = dv[vc][0] - dv[va][0], wy = dv[vc][1] - dv[va][1], wz = dv[vc][2] - dv[va][2];
+    const T nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
+    const T len = sqrt(nx * nx + ny * ny + nz * nz);
+    const T sg = (T)fsign[f] / len;
+    g[GEO3_F + 4 * f] = nx * sg;
+    g[GEO3_F + 1 + 4 * f] = ny * sg;
+    g[GEO3_F + 2 + 4 * f] = nz * sg;
+    g[GEO3_F + 3 + 4 * f] = (T)0.25 * len * iJ;   // face area / (2 J)
+  }
+}
+
 template <typename T, int N, int STAGE>
 __global__ void __launch_bounds__(((Tile3<T, N>::E * Dim3<N>::Np + 31) / 32) * 32)
 stage3_kernel(const Stage3Args a) {
@@ -163,6 +240,11 @@ stage3_kernel(const Stage3Args a) {
   static_assert(!DB || (L::SmemSize + ((L::TabInts + 3) & ~3) + E * (NQ + 10 * NFN + 6 * Nc + GEO3)) % 4 == 0,
                 "the second own-field buffer must start on a 16-byte boundary");
   T *const sqA = sq, *const sqB = sgeo + E * GEO3;
+  // FP32 at N = 3, with spare threads after the node threads: those threads form the next tile's
+  // geometry during this tile's last phase, into a second geometry buffer
+  constexpr int NODE_THREADS = E * Np, THREADS = ((E * Np + 31) / 32) * 32;
+  constexpr bool PG = DB && THREADS - NODE_THREADS >= E;
+  T *const sgA = sgeo, *const sgB = sqB + E * NQ;
   __shared__ double s_motion[4];
 
   const int tid = threadIdx.x, nthr = blockDim.x;
@@ -212,11 +294,17 @@ stage3_kernel(const Stage3Args a) {
     const int64_t e0 = (int64_t)blockIdx.x * E;
     prefetch_tile3<T>(qin, e0, (int)((a.K - e0) < E ? (a.K - e0) : E), NQ, sqA, al16);
   }
-  int cur = 0;
+  if (PG && (int64_t)blockIdx.x < ntiles) {   // the first tile's geometry
+    const int64_t e0 = (int64_t)blockIdx.x * E;
+    const int n0 = (int)((a.K - e0) < E ? (a.K - e0) : E);
+    for (int e = tid; e < n0; e += nthr) element_geometry3<T>(a, e0 + e, x1, x2, g1, g2, sgA + e * GEO3);
+  }
+  int cur = 0, gcur = 0;
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t elem0 = tile * E;
     const int nel = (int)((a.K - elem0) < E ? (a.K - elem0) : E);
     T *sq = (DB && cur) ? sqB : sqA;
+    T *sg = (PG && gcur) ? sgB : sgA;
     if constexpr (DB) {
       // this tile's fields have arrived; the other buffer (the previous tile's, released by the
       // barrier that ended it) takes the next tile's
@@ -233,78 +321,9 @@ stage3_kernel(const Stage3Args a) {
       const int cnt = nel * NQ;
       for (int i = tid; i < cnt; i += nthr) sq[i] = src[i];
     }
-    // ---- geometry, one thread per element: vertex positions in FP64, edge vectors as FP64
-    //      differences, everything after them in T (FP64 in GB_FP64) ----
-    for (int e = tid; e < nel; e += nthr) {
-      const MeshRec3 rec = a.mesh[elem0 + e];
-      // stage positions x_n + shift + x1 S1 + x2 S2: the vertex positions and their differences
-      // in FP64, the motion increments (small against the edges) in T
-      const T x1t = (T)x1, x2t = (T)x2, g1t = (T)g1, g2t = (T)g2;
-      double P0[3];
-      T S0[3];   // x1 S1 + x2 S2 of vertex 0
-      T dv[4][3], vv[4][3];   // dv[k] = P_k - P_0 (dv[0] = 0); vv[k] the grid velocity of vertex k
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int64_t v = rec.v[k];
-        const double2 *sh = reinterpret_cast<const double2 *>(a.shape) + 3 * v;
-        const double2 s01 = sh[0], s23 = sh[1], s45 = sh[2];
-        const T S1[3] = {(T)s01.x, (T)s01.y, (T)s23.x}, S2[3] = {(T)s23.y, (T)s45.x, (T)s45.y};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const double Pk = a.xn[3 * v + d] + rec.shift[3 * k + d] * a.period[d];
-          const T inc = fma3(x1t, S1[d], x2t * S2[d]);
-          vv[k][d] = fma3(g1t, S1[d], g2t * S2[d]);
-          if (k == 0) {
-            P0[d] = Pk;
-            S0[d] = inc;
-            dv[0][d] = (T)0;
-          } else {
-            dv[k][d] = (T)(Pk - P0[d]) + (inc - S0[d]);
-          }
-        }
-      }
-      T G[3][3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) G[d][q] = (T)0.5 * dv[q + 1][d];
-      const T C00 = G[1][1] * G[2][2] - G[1][2] * G[2][1];
-      const T C01 = G[1][2] * G[2][0] - G[1][0] * G[2][2];
-      const T C02 = G[1][0] * G[2][1] - G[1][1] * G[2][0];
-      const T J = G[0][0] * C00 + G[0][1] * C01 + G[0][2] * C02;
-      if (!(J > (T)0)) atomicOr(a.status, GB_STATUS_MESH);
-      const T iJ = (T)1 / J;
-      // G^-1 = adj(G) / J; row a of G^-1 is the gradient of reference coordinate a
-      T *g = sgeo + e * GEO3;
-      g[0] = C00 * iJ; g[3] = C01 * iJ; g[6] = C02 * iJ;
-      g[1] = (G[0][2] * G[2][1] - G[0][1] * G[2][2]) * iJ;
-      g[4] = (G[0][0] * G[2][2] - G[0][2] * G[2][0]) * iJ;
-      g[7] = (G[0][1] * G[2][0] - G[0][0] * G[2][1]) * iJ;
-      g[2] = (G[0][1] * G[1][2] - G[0][2] * G[1][1]) * iJ;
-      g[5] = (G[0][2] * G[1][0] - G[0][0] * G[1][2]) * iJ;
-      g[8] = (G[0][0] * G[1][1] - G[0][1] * G[1][0]) * iJ;
-#pragma unroll
-      for (int k = 0; k < 4; ++k)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) g[GEO3_V + 3 * k + d] = vv[k][d];
-      // faces (local vertex triples) and the orientation of (P_b - P_a) x (P_c - P_a)
-      // relative to the outward normal; compile-time so that dv stays in registers
-      constexpr int fvt[4][3] = {{0, 1, 2}, {0, 1, 3}, {1, 2, 3}, {0, 2, 3}};
-      constexpr float fsign[4] = {-1.0f, 1.0f, 1.0f, -1.0f};
-#pragma unroll
-      for (int f = 0; f < 4; ++f) {
-        const int va = fvt[f][0], vb = fvt[f][1], vc = fvt[f][2];
-        const T ux = dv[vb][0] - dv[va][0], uy = dv[vb][1] - dv[va][1], uz = dv[vb][2] - dv[va][2];
-        const T wx = dv[vc][0] - dv[va][0], wy = dv[vc][1] - dv[va][1], wz = dv[vc][2] - dv[va][2];
-        const T nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
-        const T len = sqrt(nx * nx + ny * ny + nz * nz);
-        const T sg = (T)fsign[f] / len;
-        g[GEO3_F + 4 * f] = nx * sg;
-        g[GEO3_F + 1 + 4 * f] = ny * sg;
-        g[GEO3_F + 2 + 4 * f] = nz * sg;
-        g[GEO3_F + 3 + 4 * f] = (T)0.25 * len * iJ;   // face area / (2 J)
-      }
-    }
+    // ---- geometry, one thread per element (with PG already formed during the previous tile) ----
+    if (!PG)
+      for (int e = tid; e < nel; e += nthr) element_geometry3<T>(a, elem0 + e, x1, x2, g1, g2, sg + e * GEO3);
     __syncthreads();
 
     // ---- volume term, one thread per node ----
@@ -325,7 +344,7 @@ stage3_kernel(const Stage3Args a) {
           qt[f] = fma3(dt, v, qt[f]);
         }
       }
-      const T *g = sgeo + e_loc * GEO3;
+      const T *g = sg + e_loc * GEO3;
       const T *bl = sops + L::Bary + 4 * n_loc;
       const T *gv = g + GEO3_V;
       const T vgx = bl[0] * gv[0] + bl[1] * gv[3] + bl[2] * gv[6] + bl[3] * gv[9];
@@ -364,7 +383,7 @@ stage3_kernel(const Stage3Args a) {
       T w[10];
 #pragma unroll
       for (int fld = 0; fld < 10; ++fld) w[fld] = qp[fld * Np] - qm[fld * Np];
-      const T *g = sgeo + e * GEO3;
+      const T *g = sg + e * GEO3;
       const T nx = g[GEO3_F + 4 * f], ny = g[GEO3_F + 1 + 4 * f], nz = g[GEO3_F + 2 + 4 * f], fs = g[GEO3_F + 3 + 4 * f];
       const T *bl = sops + L::Bary + 4 * vol;
       const T *gv = g + GEO3_V;
@@ -492,7 +511,16 @@ stage3_kernel(const Stage3Args a) {
       __syncthreads();
     }
 
-    // ---- lift, projection, SARK update ----
+    // ---- lift, projection, SARK update (node threads); the next tile's geometry (spare threads) ----
+    if (PG && tid >= NODE_THREADS) {
+      const int64_t nt = tile + gridDim.x;
+      if (nt < ntiles) {
+        const int64_t e1 = nt * E;
+        const int n1 = (int)((a.K - e1) < E ? (a.K - e1) : E);
+        for (int e = tid - NODE_THREADS; e < n1; e += nthr - NODE_THREADS)
+          element_geometry3<T>(a, e1 + e, x1, x2, g1, g2, (gcur ? sgA : sgB) + e * GEO3);
+      }
+    }
     if (node_thread && e_loc < nel) {
       const T *fl = sflux + e_loc * 10 * NFN;
 #pragma unroll 4
@@ -560,6 +588,7 @@ stage3_kernel(const Stage3Args a) {
       }
     }
     __syncthreads();
+    gcur ^= 1;
   }
 }
 
@@ -569,9 +598,11 @@ static size_t stage3_smem() {
   typedef Dim3<N> D;
   typedef Op3<T, N> L;
   constexpr int E = Tile3<T, N>::E;
-  constexpr bool DB = sizeof(T) == 4 && N <= 3;   // second own-field buffer (stage3_kernel)
+  // second own-field buffer, second geometry buffer (stage3_kernel)
+  constexpr bool DB = sizeof(T) == 4 && N <= 3;
+  constexpr bool PG = DB && ((E * D::Np + 31) / 32) * 32 - E * D::Np >= E;
   return sizeof(T) * (size_t)L::SmemSize + sizeof(int) * (size_t)((L::TabInts + 3) & ~3) +
-         sizeof(T) * (size_t)E * (D::NQ + 10 * D::NFN + 6 * D::Nc + GEO3 + (DB ? D::NQ : 0));
+         sizeof(T) * (size_t)E * (D::NQ + 10 * D::NFN + 6 * D::Nc + GEO3 + (DB ? D::NQ : 0) + (PG ? GEO3 : 0));
 }
 
 template <typename T, int N, int STAGE>
