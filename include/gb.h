@@ -140,7 +140,8 @@ typedef struct {
 /* gb_set_pml: install the layer (copied; NULL removes it) and set Phi = 0.  N <= 4.
  * Synchronises the stream.  gb_set_fields also zeroes Phi.  gb_rhs and gb_rhs_noalloc
  * leave the layer out (they take no Phi); with a layer, gb_set_diagnostics records through
- * separate reduction launches after each step.  Groups reject solvers with a layer.
+ * separate reduction launches after each step, and gb_step_timed's kernel_ms[i] includes
+ * the layer's launch that follows stage kernel i.  Groups reject solvers with a layer.
  * GB_EINVAL for a 3D solver, non-finite or out-of-range parameters. */
 int gb_set_pml(gb_solver *s, const gb_pml *p);
 
