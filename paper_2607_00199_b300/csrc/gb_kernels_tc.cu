@@ -221,24 +221,31 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
       float ex[3] = {1.f, 0.f, -1.f}, ey[3] = {0.f, 1.f, -1.f}, vx[3] = {0.f, 0.f, 0.f}, vy[3] = {0.f, 0.f, 0.f};
       if (lane < nel) {
         const MeshRec rec = a.mesh[e0 + lane];
-        double px[3], py[3], pxn[3], pyn[3];
+        // vertex positions x_n + shift and their differences in FP64; the stage's small motion
+        // increments xfac S(X) in FP32
+        double bx[3], by[3], pxn[3], pyn[3];
+        float ix[3], iy[3];
+        const float xff = (float)xfac, gff = (float)gfac;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           const double2 xv = reinterpret_cast<const double2 *>(a.xn)[rec.v[k]];
           const double2 sv = reinterpret_cast<const double2 *>(a.shape)[rec.v[k]];
-          px[k] = fma(xfac, sv.x, xv.x + rec.shift[2 * k] * a.period[0]);
-          py[k] = fma(xfac, sv.y, xv.y + rec.shift[2 * k + 1] * a.period[1]);
+          bx[k] = xv.x + rec.shift[2 * k] * a.period[0];
+          by[k] = xv.y + rec.shift[2 * k + 1] * a.period[1];
           if (REC && record) {   // x_{n+1}, where the recorded integrals are taken
-            pxn[k] = fma(fin, sv.x, xv.x + rec.shift[2 * k] * a.period[0]);
-            pyn[k] = fma(fin, sv.y, xv.y + rec.shift[2 * k + 1] * a.period[1]);
+            pxn[k] = fma(fin, sv.x, bx[k]);
+            pyn[k] = fma(fin, sv.y, by[k]);
           }
-          vx[k] = (float)(gfac * sv.x);
-          vy[k] = (float)(gfac * sv.y);
+          const float sx = (float)sv.x, sy = (float)sv.y;
+          ix[k] = xff * sx;
+          iy[k] = xff * sy;
+          vx[k] = gff * sx;
+          vy[k] = gff * sy;
         }
         if (REC && record) Jn1 = 0.25 * ((pxn[1] - pxn[0]) * (pyn[2] - pyn[0]) - (pxn[2] - pxn[0]) * (pyn[1] - pyn[0]));
-        ex[0] = (float)(px[1] - px[0]); ey[0] = (float)(py[1] - py[0]);
-        ex[1] = (float)(px[2] - px[1]); ey[1] = (float)(py[2] - py[1]);
-        ex[2] = (float)(px[0] - px[2]); ey[2] = (float)(py[0] - py[2]);
+        ex[0] = (float)(bx[1] - bx[0]) + (ix[1] - ix[0]); ey[0] = (float)(by[1] - by[0]) + (iy[1] - iy[0]);
+        ex[1] = (float)(bx[2] - bx[1]) + (ix[2] - ix[1]); ey[1] = (float)(by[2] - by[1]) + (iy[2] - iy[1]);
+        ex[2] = (float)(bx[0] - bx[2]) + (ix[0] - ix[2]); ey[2] = (float)(by[0] - by[2]) + (iy[0] - iy[2]);
       }
       const float xr = 0.5f * ex[0], yr = 0.5f * ey[0], xs = -0.5f * ex[2], ys = -0.5f * ey[2];
       const float J = xr * ys - xs * yr;
