@@ -321,10 +321,12 @@ stage3_kernel(const Stage3Args a) {
       const int cnt = nel * NQ;
       for (int i = tid; i < cnt; i += nthr) sq[i] = src[i];
     }
-    // ---- geometry, one thread per element (with PG already formed during the previous tile) ----
-    if (!PG)
+    // ---- geometry, one thread per element (with PG already formed during the previous tile and
+    //      made visible by the barrier that ended it; this tile's fields by the one above) ----
+    if constexpr (!PG) {
       for (int e = tid; e < nel; e += nthr) element_geometry3<T>(a, elem0 + e, x1, x2, g1, g2, sg + e * GEO3);
-    __syncthreads();
+      __syncthreads();
+    }
 
     // ---- volume term, one thread per node ----
     T rhs[10];
