@@ -306,8 +306,8 @@ stage3_kernel(const Stage3Args a) {
     T *sq = (DB && cur) ? sqB : sqA;
     T *sg = (PG && gcur) ? sgB : sgA;
     if constexpr (DB) {
-      // this tile's fields have arrived; the other buffer (the previous tile's, released by the
-      // barrier that ended it) takes the next tile's
+      // this tile's fields have arrived and every thread has left the previous tile; the other
+      // buffer (the previous tile's) takes the next tile's
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       __syncthreads();
       const int64_t nt = tile + gridDim.x;
@@ -322,7 +322,7 @@ stage3_kernel(const Stage3Args a) {
       for (int i = tid; i < cnt; i += nthr) sq[i] = src[i];
     }
     // ---- geometry, one thread per element (with PG already formed during the previous tile and
-    //      made visible by the barrier that ended it; this tile's fields by the one above) ----
+    //      made visible, with this tile's fields, by the barrier above) ----
     if constexpr (!PG) {
       for (int e = tid; e < nel; e += nthr) element_geometry3<T>(a, elem0 + e, x1, x2, g1, g2, sg + e * GEO3);
       __syncthreads();
@@ -589,7 +589,9 @@ stage3_kernel(const Stage3Args a) {
         if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
       }
     }
-    __syncthreads();
+    // with the double buffers the next tile's first barrier (before any of its shared-memory
+    // writes and before the next prefetch) also separates it from this tile's reads
+    if constexpr (!DB) __syncthreads();
     gcur ^= 1;
   }
 }
