@@ -45,7 +45,7 @@ FP64_FLOP_PER_CLK_SM = 4.0
 
 
 def run_serving(torch, n_req=256, steps=500, rate=50.0, budget_gib=16.0):
-    """Serving stream (configuration 5): n_req requests with Poisson
+    """Serving stream of independent moving-mesh simulations: n_req requests with Poisson
     arrivals, K in {2048 .. 131072}, N in {2 .. 5}, random motion and Re, `steps` SARK
     steps each, admitted against a device-memory budget and stepped together per
     order by the continuous-batching loop (GB_MIXED).  Baselines: the same requests
@@ -289,7 +289,7 @@ def parse():
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per element-stage ("Roofline")
+# algorithmic work per element-stage: the operations and bytes each stage kernel must do and move
 # ---------------------------------------------------------------------------
 def sizes(N):
     Np, Nfp = (N + 1) * (N + 2) // 2, N + 1
