@@ -82,8 +82,10 @@ pml_stage_kernel(const StageArgs a, const PmlArgs p) {
     if (a.motion_A != 0.0) {
       const double w = a.motion_w, Aw = a.motion_A * a.motion_w, t = a.clock[0], dt = a.dt;
       const double cst[4] = {0.0, 0.5, 0.5, 1.0};
-      gfac = Aw * cos(w * (t + cst[STAGE] * dt));
-      if (STAGE > 0) xfac = dt * cst[STAGE == 3 ? 3 : 1] * Aw * cos(w * (t + cst[STAGE - 1] * dt));
+      // the phases in FP64; their cosines in T (these factors scale FP32 terms in GB_MIXED)
+      const double p0 = w * (t + cst[STAGE] * dt), p1 = STAGE > 0 ? w * (t + cst[STAGE - 1] * dt) : 0.0;
+      gfac = Aw * (double)cos((T)p0);
+      if (STAGE > 0) xfac = dt * cst[STAGE == 3 ? 3 : 1] * Aw * (double)cos((T)p1);
     }
     s_motion[0] = gfac;
     s_motion[1] = xfac;
@@ -147,19 +149,29 @@ pml_stage_kernel(const StageArgs a, const PmlArgs p) {
     const double gfac = s_motion[0], xfac = s_motion[1];
     for (int el = tid; el < nel; el += nthr) {
       const MeshRec &rec = srec[el];
-      double px[3], py[3];
-      T vx[3], vy[3];
+      // vertex positions and their differences in FP64, the stage increments xfac S in T
+      double bx[3], by[3];
+      T vx[3], vy[3], ix[3], iy[3];
+      const T xft = (T)xfac, gft = (T)gfac;
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
         const double2 xv = reinterpret_cast<const double2 *>(a.xn)[rec.v[k]];
         const double2 sv = reinterpret_cast<const double2 *>(a.shape)[rec.v[k]];
-        px[k] = fma(xfac, sv.x, xv.x + rec.shift[2 * k] * a.period[0]);
-        py[k] = fma(xfac, sv.y, xv.y + rec.shift[2 * k + 1] * a.period[1]);
-        vx[k] = (T)(gfac * sv.x);
-        vy[k] = (T)(gfac * sv.y);
+        bx[k] = xv.x + rec.shift[2 * k] * a.period[0];
+        by[k] = xv.y + rec.shift[2 * k + 1] * a.period[1];
+        const T sx = (T)sv.x, sy = (T)sv.y;
+        ix[k] = xft * sx; iy[k] = xft * sy;
+        vx[k] = gft * sx; vy[k] = gft * sy;
       }
-      const T xr = (T)(0.5 * (px[1] - px[0])), yr = (T)(0.5 * (py[1] - py[0]));
-      const T xs = (T)(0.5 * (px[2] - px[0])), ys = (T)(0.5 * (py[2] - py[0]));
+      T ex[3], ey[3];   // edge f from vertex f to f + 1
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        const int f1 = (f + 1) % 3;
+        ex[f] = (T)(bx[f1] - bx[f]) + (ix[f1] - ix[f]);
+        ey[f] = (T)(by[f1] - by[f]) + (iy[f1] - iy[f]);
+      }
+      const T xr = (T)0.5 * ex[0], yr = (T)0.5 * ey[0];
+      const T xs = (T)-0.5 * ex[2], ys = (T)-0.5 * ey[2];
       const T J = xr * ys - xs * yr, iJ = (T)1 / J;
       T *g = sgeo[el];
       g[0] = ys * iJ; g[1] = -yr * iJ; g[2] = -xs * iJ; g[3] = xr * iJ;
@@ -168,8 +180,7 @@ pml_stage_kernel(const StageArgs a, const PmlArgs p) {
       // face f runs from vertex f to f + 1; outward normal of a counter-clockwise triangle
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
-        const int f1 = (f + 1) % 3;
-        const T dx = (T)(px[f1] - px[f]), dy = (T)(py[f1] - py[f]);
+        const T dx = ex[f], dy = ey[f];
         const T len = sqrt(dx * dx + dy * dy);
         g[10 + 3 * f] = dy / len;
         g[11 + 3 * f] = -dx / len;
