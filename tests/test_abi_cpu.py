@@ -138,3 +138,28 @@ def test_library_tet_operators_match_oracle(N):
     for k in ('Dr', 'Ds', 'Dt', 'I', 'P'):
         np.testing.assert_allclose(L[k], getattr(R, k), atol=1e-13)
     np.testing.assert_allclose(L['LIFT'], R.LIFT, atol=2e-12)
+
+
+def test_more_host_validation():
+    """Checks that return before any device work: empty meshes, 3D and bounded order limits,
+    far-field states, and NULL solvers or arguments for every later entry point."""
+    mesh = inputs.periodic_square_mesh(4)
+    empty = {'X': mesh['X'], 'EToV': mesh['EToV'][:0], 'shift': mesh['shift'][:0]}
+    _expect(gb.GB_EINVAL, lambda: gb.Solver(empty, 3, 0.1, 100))
+    box = inputs.periodic_box_tet_mesh(3, 3, 3)
+    _expect(gb.GB_EINVAL, lambda: gb.Solver(box, 5, 0.1, 100))          # dim = 3: N <= 4
+    ogrid = inputs.naca_ogrid_mesh(16, 6, R=5.0)
+    _expect(gb.GB_EINVAL, lambda: gb.Solver(ogrid, 5, 0.1, 100))        # boundary faces: N <= 4
+    _expect(gb.GB_EINVAL, lambda: gb.Solver(ogrid, 3, 0.1, 100, far_state=(0.0, 1.0, 0.0)))
+    _expect(gb.GB_EINVAL, lambda: gb.Solver(ogrid, 3, 0.1, 100, far_state=(1.0, float('nan'), 0.0)))
+    lib = gb.lib
+    out = np.zeros(8)
+    n = ctypes.c_int64()
+    assert lib.gb_set_pml(None, None) == gb.GB_EINVAL
+    assert lib.gb_pml_fields(None, None, None, ctypes.byref(n)) == gb.GB_EINVAL
+    assert lib.gb_diagnostics3d(None, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == gb.GB_EINVAL
+    assert lib.gb_diagnostics(None, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))) == gb.GB_EINVAL
+    assert lib.gb_set_diagnostics(None, 1, 4) == gb.GB_EINVAL
+    assert lib.gb_step(None, 1e-3, 1) == gb.GB_EINVAL
+    assert lib.gb_set_motion(None, None) == gb.GB_EINVAL
+    assert lib.gb_set_wave_motion(None, None) == gb.GB_EINVAL
