@@ -136,6 +136,45 @@ def serving_requests(n=256, rate=50.0, seed=1):
 _KUHN_ORDERS = ((0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0))
 
 
+def _even_permutations(n):
+    """The orientation-preserving vertex orders of a simplex with n vertices."""
+    import itertools
+    out = []
+    for p in itertools.permutations(range(n)):
+        inversions = sum(1 for a in range(n) for b in range(a + 1, n) if p[a] > p[b])
+        if inversions % 2 == 0:
+            out.append(p)
+    return np.array(out, dtype=np.int64)
+
+
+def renumber_mesh(mesh, seed=DEFAULT_SEED):
+    """The same mesh with its elements listed in a seeded random order and each element's
+    vertices in a seeded random orientation-preserving order (a cyclic rotation of a
+    triangle, an even permutation of a tetrahedron).  The geometry is unchanged; the
+    numbering of elements, of their faces and of their nodes is not, so that faces meet in
+    every pairing of local face numbers.  Returns (new mesh, order): element i of the new
+    mesh is element order[i] of the old one.  Per-face boundary tags (2D 'bc', face f
+    running from vertex f to f + 1) follow their faces.
+    Draws: splitmix64 stream `seed`, counters 2 e (order key) and 2 e + 1 (vertex order)."""
+    EToV = np.asarray(mesh['EToV'])
+    K, nv = EToV.shape
+    e = np.arange(K, dtype=np.uint64)
+    order = np.argsort(splitmix64(2 * e, seed), kind='stable')
+    perms = np.array([[(j + r) % 3 for j in range(3)] for r in range(3)]) if nv == 3 else _even_permutations(4)
+    choice = (splitmix64(2 * e + np.uint64(1), seed) % np.uint64(len(perms))).astype(np.int64)[order]
+    p = perms[choice]                                                       # (K, nv): new slot -> old slot
+    rows = np.arange(K)[:, None]
+    out = dict(mesh)
+    out['EToV'] = EToV[order][rows, p].astype(EToV.dtype)
+    out['shift'] = np.asarray(mesh['shift'])[order][rows, p]
+    if 'bc' in mesh:
+        if nv != 3:
+            raise ValueError('boundary tags are defined for triangles only')
+        # new face f joins new vertices f, f + 1 = old vertices r + f, r + f + 1: old face (f + r) mod 3
+        out['bc'] = np.asarray(mesh['bc'])[order][rows, p]
+    return out, order
+
+
 def periodic_box_tet_mesh(nx, ny, nz, L=(8.0, 2.0, 2.0), jitter=0.0, seed=DEFAULT_SEED, origin=(0.0, 0.0, 0.0)):
     """Periodic box origin + [0, Lx] x [0, Ly] x [0, Lz] with nx x ny x nz hexahedral
     cells, each split into 6 tetrahedra (Kuhn subdivision); K = 6 nx ny nz.
