@@ -58,10 +58,11 @@ struct Op3 {
   static constexpr int Size = PT + D::Nc * D::Np;
   static constexpr int SmemSize = IP_SMEM ? Size : IT;    // staged in shared memory
   static constexpr int TabInts = 4 * 4 * 6 * D::Nfp + 4 * D::Nfp;   // neighbour node table, fmask
-  // shared-memory path: cubature points per work item, nodes per projection item, vector widths
-  static constexpr int CPI = N == 3 ? 5 : (N == 2 ? 4 : 2);
+  // shared-memory path: cubature points per work item (the last item of an element may hold
+  // fewer; N = 3: 12 elements x 21 items of <= 6 of the 125 points fill a 256-thread CTA in one
+  // round), nodes per projection item, vector widths
+  static constexpr int CPI = N == 3 ? 6 : (N == 2 ? 4 : 2);
   static constexpr int NG = D::Np % 4 == 0 ? 4 : (D::Np % 2 == 0 ? 2 : 1);
-  static_assert(!IP_SMEM || D::Nc % CPI == 0, "cubature points must split evenly into work items");
 };
 
 // geometry block per element (in T): G^-1 (9, row-major r_x r_y r_z s_x ... t_z),
@@ -409,9 +410,10 @@ stage3_kernel(const Stage3Args a) {
     if constexpr (L::IP_SMEM) {
       // item = (element, group of CPI points): q1..q4 of the element in registers, one row of
       // I per point, so every operator load feeds four FMAs
-      constexpr int CPI = L::CPI, NPG = Nc / CPI;
+      constexpr int CPI = L::CPI, NPG = (Nc + CPI - 1) / CPI;
       for (int item = tid; item < E * NPG; item += nthr) {
         const int e = item / NPG, c0 = (item - NPG * (item / NPG)) * CPI;
+        const int npt = Nc - c0 < CPI ? Nc - c0 : CPI;   // points of this item
         if (e >= nel) continue;
         const T *q = sq + e * NQ;
         T qr4[4][Np];
@@ -420,7 +422,7 @@ stage3_kernel(const Stage3Args a) {
 #pragma unroll
           for (int m = 0; m < Np; ++m) qr4[f][m] = q[f * Np + m];
 #pragma unroll 1
-        for (int k = 0; k < CPI; ++k) {
+        for (int k = 0; k < npt; ++k) {
           const int cpt = c0 + k;
           const T *irow = sops + L::IT + cpt * Np;
           T im[Np];
