@@ -62,7 +62,11 @@ struct Op3 {
   // fewer; N = 3: 12 elements x 21 items of <= 6 of the 125 points fill a 256-thread CTA in one
   // round), nodes per projection item, vector widths
   static constexpr int CPI = N == 3 ? 6 : (N == 2 ? 4 : 2);
-  static constexpr int NG = D::Np % 4 == 0 ? 4 : (D::Np % 2 == 0 ? 2 : 1);
+  // projection items (element, NG nodes, FG fields); N = 3: 12 x 10 x 2 = 240 items of 2 x 3
+  // outputs in one round, instead of 360 items of 4 x 1 (104 threads ran a second one)
+  static constexpr int NG = N == 3 ? 2 : (D::Np % 4 == 0 ? 4 : (D::Np % 2 == 0 ? 2 : 1));
+  static constexpr int FG = N == 3 ? 3 : 1;
+  static_assert(D::Np % NG == 0 && 6 % FG == 0, "projection items must split the nodes and fields evenly");
 };
 
 // geometry block per element (in T): G^-1 (9, row-major r_x r_y r_z s_x ... t_z),
@@ -482,35 +486,46 @@ stage3_kernel(const Stage3Args a) {
     __syncthreads();
 
     // ---- projection P Ntilde (shared-memory path): item = (element, group of NG nodes,
-    //      field), written over the element's field tile (no longer needed) ----
+    //      group of FG fields), written over the element's field tile (no longer needed) ----
     T *sproj = sq;   // [E][6][Np]
     if constexpr (L::IP_SMEM) {
-      constexpr int NG = L::NG, NGR = Np / NG;
-      for (int item = tid; item < E * NGR * 6; item += nthr) {
-        const int f = item % 6, rest = item / 6, gq = rest % NGR, e = rest / NGR;
+      constexpr int NG = L::NG, NGR = Np / NG, FG = L::FG, NFG = 6 / FG;
+      for (int item = tid; item < E * NGR * NFG; item += nthr) {
+        const int fg = item % NFG, rest = item / NFG, gq = rest % NGR, e = rest / NGR;
         if (e >= nel) continue;
-        const T *nt = snt + e * 6 * Nc + f * Nc;
+        const T *nt = snt + e * 6 * Nc + fg * FG * Nc;
         const T *pc = sops + L::PT + gq * NG;
-        T acc[NG];
+        T acc[FG][NG];
 #pragma unroll
-        for (int i = 0; i < NG; ++i) acc[i] = 0;
+        for (int ff = 0; ff < FG; ++ff)
+#pragma unroll
+          for (int i = 0; i < NG; ++i) acc[ff][i] = 0;
 #pragma unroll 5
         for (int cpt = 0; cpt < Nc; ++cpt) {
-          const T nv = nt[cpt];
+          T pv[NG];
           if constexpr (NG == 4) {
-            const float4 pv = *reinterpret_cast<const float4 *>(pc + cpt * Np);
-            acc[0] = fma3(pv.x, nv, acc[0]);
-            acc[1] = fma3(pv.y, nv, acc[1]);
-            acc[2] = fma3(pv.z, nv, acc[2]);
-            acc[3] = fma3(pv.w, nv, acc[3]);
+            const float4 v = *reinterpret_cast<const float4 *>(pc + cpt * Np);
+            pv[0] = v.x; pv[1] = v.y; pv[2] = v.z; pv[3] = v.w;
+          } else if constexpr (NG == 2) {
+            const float2 v = *reinterpret_cast<const float2 *>(pc + cpt * Np);
+            pv[0] = v.x; pv[1] = v.y;
           } else {
 #pragma unroll
-            for (int i = 0; i < NG; ++i) acc[i] = fma3(pc[cpt * Np + i], nv, acc[i]);
+            for (int i = 0; i < NG; ++i) pv[i] = pc[cpt * Np + i];
+          }
+#pragma unroll
+          for (int ff = 0; ff < FG; ++ff) {
+            const T nv = nt[ff * Nc + cpt];
+#pragma unroll
+            for (int i = 0; i < NG; ++i) acc[ff][i] = fma3(pv[i], nv, acc[ff][i]);
           }
         }
-        T *o = sproj + e * 6 * Np + f * Np + gq * NG;
 #pragma unroll
-        for (int i = 0; i < NG; ++i) o[i] = acc[i];
+        for (int ff = 0; ff < FG; ++ff) {
+          T *o = sproj + e * 6 * Np + (fg * FG + ff) * Np + gq * NG;
+#pragma unroll
+          for (int i = 0; i < NG; ++i) o[i] = acc[ff][i];
+        }
       }
       __syncthreads();
     }
