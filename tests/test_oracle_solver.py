@@ -184,3 +184,47 @@ def test_mass_and_momentum_conserved_on_moving_mesh():
         assert abs(d1['area'] - d0['area']) < 1e-12 * d0['area']
         drift.append(max(abs(d1[k] - d0[k]) for k in ('mass', 'momentum_x', 'momentum_y')))
     assert drift[0] < 1e-7 * d0['mass'] and drift[1] < drift[0] / 8, drift
+
+
+# ---- the prescribed mesh motion (Sec. 5, Sec. 7.1) and its RK4 vertex integration --------
+
+def test_sinxy_motion_velocity_is_the_time_derivative_of_the_displacement():
+    """The free-stream motion of Sec. 7.1: d(X, t) = A sin(2 pi t / T) S(X) with
+    S = sin(2 pi X / Lx) sin(2 pi Y / Ly) on both components.  The velocity equals a central
+    difference of the displacement; closed-form values at points where S is 1, 1/2 or -1
+    (Lx != Ly, so a swapped period fails); periodic in X and Y; zero displacement at t = 0."""
+    A, T, Lx, Ly = 0.05, 1.3, 2.0 * math.pi, 4.0
+    m = Motion(A, T, Lx, Ly)
+    rng = np.random.default_rng(11)
+    X = np.stack([rng.uniform(0, Lx, 40), rng.uniform(0, Ly, 40)], axis=1)
+    h = 1e-6
+    for t in (0.0, 0.37, 0.9, 2.1):
+        fd = (m.displacement(X, t + h) - m.displacement(X, t - h)) / (2 * h)
+        np.testing.assert_allclose(m.velocity(X, t), fd, rtol=0, atol=1e-9)
+    assert np.abs(m.displacement(X, 0.0)).max() == 0.0
+    pts = np.array([[Lx / 4, Ly / 4], [Lx / 4, Ly / 12], [Lx / 4, 3 * Ly / 4]])
+    S = np.array([1.0, 0.5, -1.0])
+    np.testing.assert_allclose(m.displacement(pts, T / 4), A * np.stack([S, S], 1), rtol=1e-14, atol=1e-16)
+    np.testing.assert_allclose(m.velocity(pts, 0.0), A * 2 * math.pi / T * np.stack([S, S], 1), rtol=1e-14)
+    np.testing.assert_allclose(m.velocity(pts, T / 4), 0.0, atol=1e-16)
+    np.testing.assert_allclose(m.displacement(X + [Lx, -Ly], 0.7), m.displacement(X, 0.7), atol=1e-15)
+
+
+def _vertex_tracking_error(nsteps, t_end=0.3):
+    mesh = inputs.periodic_square_mesh(3, jitter=0.1)
+    o = OracleSolver(mesh, 1, Ma=0.1, Re=100, motion=Motion(0.05, 1.0))
+    q0 = _state(o, o.X, lambda x, y: inputs.free_stream(x, y, 1.0, 0.0))
+    _, xv, t = o.run(q0, o.X.copy(), 0.0, t_end / nsteps, nsteps)
+    assert abs(t - t_end) < 1e-14
+    return np.abs(xv - (o.X + o.motion.displacement(o.X, t_end))).max()
+
+
+def test_rk4_vertices_track_the_prescribed_displacement():
+    """Sec. 5: the vertices advance with the stages' RK4 (nodes c, weights b) and the analytic
+    velocity at the Lagrangian X.  That velocity does not depend on x, so the step is
+    Simpson's rule in time: x_n - (X + d(X, t_n)) falls like dt^4 (16x per halving).
+    A wrong weight, node time or velocity factor breaks the level or the rate."""
+    e1, e2, e3 = _vertex_tracking_error(3), _vertex_tracking_error(6), _vertex_tracking_error(12)
+    assert e3 < 1e-7, e3
+    for a, b in ((e1, e2), (e2, e3)):
+        assert 13.0 < a / b < 19.0, (e1, e2, e3)

@@ -206,3 +206,52 @@ def test_tgv_mass_and_energy():
         d1 = o.diagnostics(q, xv)
         assert abs(d1['mass'] - d0['mass']) < tol * d0['mass']
         assert d1['kinetic_energy'] < d0['kinetic_energy']
+
+
+# ---- the deforming channel's traveling wave and its RK4 vertex integration (Sec. 5) ---------
+
+def test_channel_wave_velocity_is_the_time_derivative_of_the_displacement():
+    """y += A(x) sin(k x - omega t) exp(-r^2 / r0^2), A(x) = A0 + A1 x / Lx, r the distance to
+    the centreline (yc, zc): the velocity equals a central difference of the displacement, only
+    the y component moves, and closed-form values on the centreline (x = 4: sin(8 pi - omega t))
+    and at r^2 = r0^2 (a factor 1/e) hold."""
+    m = WaveMotion(A0=0.02, A1=0.08, Lx=8.0)
+    rng = np.random.default_rng(5)
+    X = np.stack([rng.uniform(0, 8, 40), rng.uniform(0, 2, 40), rng.uniform(0, 2, 40)], axis=1)
+    h = 1e-6
+    for t in (0.0, 0.21, 0.75, 1.6):
+        fd = (m.displacement(X, t + h) - m.displacement(X, t - h)) / (2 * h)
+        np.testing.assert_allclose(m.velocity(X, t), fd, rtol=0, atol=1e-9)
+        assert np.abs(m.displacement(X, t)[:, [0, 2]]).max() == 0.0
+        assert np.abs(m.velocity(X, t)[:, [0, 2]]).max() == 0.0
+    centre = np.array([[4.0, 1.0, 1.0]])
+    amp = 0.02 + 0.08 * 0.5
+    np.testing.assert_allclose(m.displacement(centre, 0.75)[0, 1], amp, rtol=1e-14)    # sin(8 pi - 3 pi / 2) = 1
+    np.testing.assert_allclose(m.velocity(centre, 0.0)[0, 1], -TWO_PI * amp, rtol=1e-14)
+    off = np.array([[4.0, 1.5, 1.0]])                                                  # r^2 = 0.25 = r0^2
+    np.testing.assert_allclose(m.displacement(off, 0.75)[0, 1], amp / math.e, rtol=1e-14)
+    # wavelength 1: shifting x by one wavelength changes only the amplitude ramp
+    a1 = m.displacement(X, 0.4)[:, 1] / (0.02 + 0.08 * X[:, 0] / 8)
+    Xs = X + [1.0, 0.0, 0.0]
+    a2 = m.displacement(Xs, 0.4)[:, 1] / (0.02 + 0.08 * Xs[:, 0] / 8)
+    np.testing.assert_allclose(a1, a2, atol=1e-14)
+
+
+def _vertex_tracking_error_3d(nsteps, t_end=0.3):
+    mesh = inputs.periodic_box_tet_mesh(3, 3, 3, jitter=0.1)
+    motion = WaveMotion(A0=0.02, A1=0.08, Lx=8.0)
+    o = OracleSolver3D(mesh, 1, Ma=0.1, Re=500, motion=motion)
+    q0 = _state(o, o.X, lambda x, y, z: (np.ones_like(x), np.full_like(x, 0.3), np.zeros_like(x), np.zeros_like(x)))
+    _, xv, t = o.run(q0, o.X.copy(), 0.0, t_end / nsteps, nsteps)
+    # the wave does not vanish at t = 0 and the mesh starts undeformed at X, so the vertices
+    # follow X + d(X, t) - d(X, 0)
+    return np.abs(xv - (o.X + motion.displacement(o.X, t_end) - motion.displacement(o.X, 0.0))).max()
+
+
+def test_rk4_vertices_track_the_channel_wave():
+    """Sec. 5 in 3D: RK4 with the analytic velocity at the Lagrangian X is Simpson's rule in
+    time, so the vertices follow X + d(X, t) - d(X, 0) with an error falling like dt^4."""
+    e1, e2, e3 = _vertex_tracking_error_3d(3), _vertex_tracking_error_3d(6), _vertex_tracking_error_3d(12)
+    assert e3 < 1e-6, e3
+    for a, b in ((e1, e2), (e2, e3)):
+        assert 13.0 < a / b < 19.0, (e1, e2, e3)
