@@ -283,9 +283,11 @@ int gb_state_ptr(gb_solver *s, void **q_dev);
  *  - GB_EINVAL for a GB_FP64 solver (its gb_rhs needs no scratch) and for a
  *    mesh whose two internal copies exceed the array (at N = 4 about 22.8k
  *    elements, N = 3 35k, N = 2 58k), with the limit in gb_last_error.
- *  - The first call made with a given device current looks up the array's
- *    device address on that device (cudaGetSymbolAddress); make that first
- *    call before any stream capture.
+ *  - GB_EINVAL for a non-finite t, and when the current device is not the
+ *    solver's (the device current at gb_create): make it current first.
+ *  - The first call for a solver of a given device looks up the array's
+ *    device address on that device (cudaGetSymbolAddress, once per device,
+ *    under a lock); make that first call before any stream capture.
  *  - Every call, on any solver and stream, shares the one array, which keeps
  *    the last call's contents (the call clears what it needs cleared): calls
  *    that overlap on the GPU race and must be ordered by the caller. */

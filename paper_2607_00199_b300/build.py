@@ -1,6 +1,6 @@
 """Build libgb.so in-tree for sm_103a with nvcc (no GPU needed to build).
 
-    python -m paper_2607_00199_b300.build [--verbose] [--probe]
+    python -m paper_2607_00199_b300.build [--verbose]
 
 Object files go to _build/ at the repository root; the shared library is
 written next to this file, where the ctypes binding loads it.
@@ -52,16 +52,5 @@ def build(verbose=False):
     return LIB
 
 
-def build_probe():
-    """The FP64/FP32/DMMA throughput probe used for the FP64 roofline denominator."""
-    os.makedirs(BUILD, exist_ok=True)
-    exe = os.path.join(BUILD, 'peak_probe')
-    cmd = [_nvcc()] + ARCH + ['-O3', '-o', exe, os.path.join(CSRC, 'peak_probe.cu')]
-    subprocess.run(cmd, check=True)
-    return exe
-
-
 if __name__ == '__main__':
     print(build(verbose='--verbose' in sys.argv))
-    if '--probe' in sys.argv:
-        print(build_probe())

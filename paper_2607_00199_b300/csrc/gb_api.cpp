@@ -27,6 +27,7 @@ struct gb_solver {
   double c = 0, tau = 0, period[2] = {0, 0};
   cudaStream_t stream = nullptr;
   int num_sms = 1;
+  int device = 0;              // CUDA device ordinal current at gb_create: all of the solver's memory lives there
   std::string err;
   gb::RefOps ref;
   gb_motion motion{GB_MOTION_STATIC, 0, 1, 1, 1};
@@ -491,6 +492,7 @@ static int create2d(const gb_mesh *mesh, const int8_t *face_bc, const double *fa
     delete s;
     return fail(nullptr, GB_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(ce));
   }
+  s->device = dev;
   int rc = gb::upload_ops(N, s->ref, &s->d_ops, s->stream);
   if (rc == 0 && precision == GB_MIXED) rc = gb::upload_ops_mixed(N, s->ref, &s->d_ops_mixed, s->stream);
   if (rc != 0) {
@@ -1346,7 +1348,7 @@ namespace gb {
 // stage arguments of an rhs-only launch at time t, the element permutation and
 // the sizes.  Returns GB_EINVAL for a NULL solver.
 int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, int *N, int64_t *K, int *Np,
-                    int *precision, void **stream, int *num_sms) {
+                    int *precision, void **stream, int *num_sms, int *device) {
   if (!s || s->s3) return GB_EINVAL;
   *a = base_args(s);
   a->stage = -1;
@@ -1358,6 +1360,7 @@ int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, 
   *precision = s->precision;
   *stream = s->stream;
   *num_sms = s->num_sms;
+  *device = s->device;
   return GB_OK;
 }
 

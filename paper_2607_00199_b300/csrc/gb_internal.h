@@ -229,8 +229,9 @@ int launch_diagnostics_record(int N, const void *q, bool is_float, bool perturba
                               int64_t cap, void *stream);
 int launch_group_mixed(int N, int stage, const GroupArgs &g, void *stream, int num_sms);
 int launch_group_vertex_update(const GroupArgs &g, void *stream);
+// the solver's rhs-only launch arguments, its device buffers' layout, stream and device ordinal
 int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, int *N, int64_t *K, int *Np,
-                    int *precision, void **stream, int *num_sms);
+                    int *precision, void **stream, int *num_sms, int *device);
 int set_solver_error(gb_solver *s, int code, const char *msg);
 int upload_ops(int N, const RefOps &R, double **dev_ops, void *stream);
 int upload_ops_mixed(int N, const RefOps &R, float **dev_ops, void *stream);

@@ -9,7 +9,9 @@
 // until the process exits; it calls no cudaMalloc or cudaFree.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdio>
+#include <mutex>
 
 #include "gb.h"
 #include "gb_internal.h"
@@ -22,22 +24,26 @@ constexpr size_t kScratchFloats = size_t(4) << 20;
 static __device__ __align__(256) float g_rhs_scratch[kScratchFloats];
 
 // Device address of g_rhs_scratch per device ordinal, looked up on the first
-// call made with that device current.  In host code g_rhs_scratch itself only
-// names a host-side stand-in; kernels must be given this address.
+// call for a solver of that device (with that device current).  In host code
+// g_rhs_scratch itself only names a host-side stand-in; kernels must be given
+// this address.  The table is read and filled under g_scratch_mu, so first
+// calls from several host threads do not race.
 constexpr int kMaxDevices = 64;
 float *g_scratch_addr[kMaxDevices] = {nullptr};
+std::mutex g_scratch_mu;
 
 }  // namespace
 
 extern "C" int gb_rhs_noalloc(gb_solver *s, double t, const void *q_dev, void *F_dev) {
   if (!s) return GB_EINVAL;
   if (!q_dev || !F_dev) return gb::set_solver_error(s, GB_EINVAL, "gb_rhs_noalloc: NULL q or F");
+  if (!std::isfinite(t)) return gb::set_solver_error(s, GB_EINVAL, "gb_rhs_noalloc: t must be finite");
   gb::StageArgs a;
   const int32_t *perm = nullptr;
-  int N = 0, Np = 0, precision = 0, num_sms = 1;
+  int N = 0, Np = 0, precision = 0, num_sms = 1, sdev = 0;
   int64_t K = 0;
   void *stream = nullptr;
-  if (gb::rhs_launch_view(s, t, &a, &perm, &N, &K, &Np, &precision, &stream, &num_sms) != GB_OK)
+  if (gb::rhs_launch_view(s, t, &a, &perm, &N, &K, &Np, &precision, &stream, &num_sms, &sdev) != GB_OK)
     return gb::set_solver_error(s, GB_EINVAL, "gb_rhs_noalloc: not available for dim = 3 solvers");
   if (precision != GB_MIXED)
     return gb::set_solver_error(s, GB_EINVAL, "gb_rhs_noalloc: only GB_MIXED solvers use scratch; call gb_rhs");
@@ -51,18 +57,30 @@ extern "C" int gb_rhs_noalloc(gb_solver *s, double t, const void *q_dev, void *F
              2 * half, kScratchFloats, N, (long long)(kScratchFloats / 2 / S / 16 * 16));
     return gb::set_solver_error(s, GB_EINVAL, msg);
   }
+  // the scratch used is the copy of the array on the solver's device; cudaGetSymbolAddress
+  // answers for the current device, so the solver's device must be the current one
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce != cudaSuccess) return gb::set_solver_error(s, GB_ECUDA, cudaGetErrorString(ce));
-  if (dev < 0 || dev >= kMaxDevices) return gb::set_solver_error(s, GB_EINVAL, "gb_rhs_noalloc: device ordinal >= 64");
-  if (!g_scratch_addr[dev]) {
-    float *p = nullptr;
-    ce = cudaGetSymbolAddress((void **)&p, g_rhs_scratch);
-    if (ce != cudaSuccess || !p)
-      return gb::set_solver_error(s, GB_ECUDA, "gb_rhs_noalloc: cudaGetSymbolAddress of the scratch array failed");
-    g_scratch_addr[dev] = p;
+  if (dev != sdev) {
+    char msg[160];
+    snprintf(msg, sizeof(msg), "gb_rhs_noalloc: the solver lives on device %d but device %d is current; "
+             "make the solver's device current first", sdev, dev);
+    return gb::set_solver_error(s, GB_EINVAL, msg);
   }
-  float *q_int = g_scratch_addr[dev];
+  if (sdev < 0 || sdev >= kMaxDevices) return gb::set_solver_error(s, GB_EINVAL, "gb_rhs_noalloc: device ordinal >= 64");
+  float *q_int = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[sdev]) {
+      float *p = nullptr;
+      ce = cudaGetSymbolAddress((void **)&p, g_rhs_scratch);
+      if (ce != cudaSuccess || !p)
+        return gb::set_solver_error(s, GB_ECUDA, "gb_rhs_noalloc: cudaGetSymbolAddress of the scratch array failed");
+      g_scratch_addr[sdev] = p;
+    }
+    q_int = g_scratch_addr[sdev];
+  }
   float *F_int = q_int + half;
   cudaStream_t st = (cudaStream_t)stream;
   // the previous call's contents stay in the array: clear the padding slots and the

@@ -164,16 +164,6 @@ def sark_coefficients(gamma):
     return E, A.reshape(4, 4), B
 
 
-def dissipation_rate(t, kinetic_energy):
-    """epsilon = -dE_K/dt (Sec. 7.2) from a recorded series, by second-order finite
-    differences (central inside, one-sided at the ends; uneven spacing allowed)."""
-    t = np.asarray(t, dtype=np.float64)
-    e = np.asarray(kinetic_energy, dtype=np.float64)
-    if t.size < 3:
-        raise ValueError('need at least 3 records')
-    return -np.gradient(e, t, edge_order=2)
-
-
 class Solver:
     """Owns one gb_solver.  mesh is a dict with X, EToV, shift (see inputs.py); the
     dimension follows from X: (n_vert, 2) triangles with 6 fields, (n_vert, 3)

@@ -99,6 +99,10 @@ class Server:
         self.time_scale = float(time_scale)     # arrival times are divided by this (1 = real time)
         self.keep_fields = keep_fields
         self.results = {}
+        # the CUDA device current where the server is built: the worker threads that create the
+        # requests' solvers make it current too (a thread's current device defaults to 0)
+        import torch
+        self.device = torch.cuda.current_device() if torch.cuda.is_available() else None
 
     def _group(self, N):
         if N not in self.groups:
@@ -117,7 +121,11 @@ class Server:
         step_lat, done_lat = [], []
         total_dof_stages = 0
         ticks = 0
-        pool = ThreadPoolExecutor(max_workers=self.workers)
+        def _bind():
+            if self.device is not None:
+                import torch
+                torch.cuda.set_device(self.device)
+        pool = ThreadPoolExecutor(max_workers=self.workers, initializer=_bind)
         t0 = time.perf_counter()
         try:
             while pi < len(pending) or self.adm.waiting or preparing or active:

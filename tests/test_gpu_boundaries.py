@@ -9,6 +9,7 @@ import pytest
 from oracle import physics
 from oracle.solver import Motion, OracleSolver
 from paper_2607_00199_b300 import inputs
+from parity_metrics import rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -23,8 +24,6 @@ PLUNGE = (0.25, 2.0)        # h(t) = 0.25 sin(2 pi 0.5 t)
 FAR = (1.0, 1.0, 0.0)
 
 
-def rel_l2(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
 def oracle_state(o, xv, flow):
@@ -69,11 +68,11 @@ def test_rhs_parity_ogrid(N, precision):
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
     F = gpu_rhs(s, q, t)
     if precision == gb.GB_FP64:
-        assert rel_l2(F, F_or) <= 1e-12
+        assert rel_err(F, F_or) <= 1e-12
         for f in range(6):
-            assert rel_l2(F[:, f], F_or[:, f]) <= 1e-11, f
+            assert rel_err(F[:, f], F_or[:, f]) <= 1e-11, f
     else:
-        assert rel_l2(F, F_or) <= 1e-5
+        assert rel_err(F, F_or) <= 1e-5
 
 
 @pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
@@ -88,7 +87,7 @@ def test_steps_on_the_plunging_airfoil(precision):
     q_or, x_or, t_or = o.run(q0, o.X.copy(), 0.0, dt, 12)
     np.testing.assert_allclose(s.vertices(), x_or, atol=1e-14)
     assert abs(t_gpu - t_or) < 1e-14
-    assert rel_l2(q_gpu, q_or) <= (1e-10 if precision == gb.GB_FP64 else 1e-5)
+    assert rel_err(q_gpu, q_or) <= (1e-10 if precision == gb.GB_FP64 else 1e-5)
 
 
 def test_standing_wave_between_walls_gpu():
@@ -101,7 +100,7 @@ def test_standing_wave_between_walls_gpu():
     s.step(dt, 20)
     q_gpu, _ = s.fields()
     q_or, _, _ = o.run(q0, o.X.copy(), 0.0, dt, 20)
-    assert rel_l2(q_gpu, q_or) <= 1e-10
+    assert rel_err(q_gpu, q_or) <= 1e-10
     assert np.abs(q_gpu - q0).max() > 1e-5
 
 
@@ -130,13 +129,13 @@ def test_full_size_airfoil_rhs():
     s.set_vertices(xv)
     q = oracle_state(o, xv, airfoil_flow)
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
-    assert rel_l2(gpu_rhs(s, q, t), F_or) <= 1e-12
+    assert rel_err(gpu_rhs(s, q, t), F_or) <= 1e-12
     s.close()
     sm = gb.Solver(mesh, 4, 0.1, 1000.0, precision=gb.GB_MIXED, stream=torch.cuda.current_stream().cuda_stream,
                    far_state=FAR)
     sm.set_motion(*PLUNGE, kind=gb.GB_MOTION_PLUNGE)
     sm.set_vertices(xv)
-    assert rel_l2(gpu_rhs(sm, q, t), F_or) <= 1e-5
+    assert rel_err(gpu_rhs(sm, q, t), F_or) <= 1e-5
 
 
 def test_bounded_meshes_are_validated_and_not_grouped():

@@ -13,6 +13,7 @@ import pytest
 from oracle import physics
 from oracle.solver import Motion, OracleSolver
 from paper_2607_00199_b300 import inputs
+from parity_metrics import rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -25,8 +26,6 @@ from paper_2607_00199_b300 import gb  # noqa: E402  (loads libgb.so; fails loudl
 REST = np.array([1.0, 0, 0, 0, 0, 0])
 
 
-def rel_l2(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
 def oracle_state(o, xv, flow):
@@ -63,9 +62,9 @@ def test_rhs_parity_all_orders_ragged(N):
     q = oracle_state(o, xv, lambda x, y: inputs.random_flow(x, y, 11 + N))
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
     F_gpu = gpu_rhs(s, q, t)
-    assert rel_l2(F_gpu, F_or) <= 1e-12
+    assert rel_err(F_gpu, F_or) <= 1e-12
     for f in range(6):
-        assert rel_l2(F_gpu[:, f], F_or[:, f]) <= 1e-11, f
+        assert rel_err(F_gpu[:, f], F_or[:, f]) <= 1e-11, f
 
 
 def test_rhs_parity_cfg1():
@@ -76,7 +75,7 @@ def test_rhs_parity_cfg1():
     s.set_vertices(xv)
     q = oracle_state(o, xv, lambda x, y: inputs.taylor_green(x, y, 0.1))
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
-    assert rel_l2(gpu_rhs(s, q, t), F_or) <= 1e-12
+    assert rel_err(gpu_rhs(s, q, t), F_or) <= 1e-12
 
 
 def test_nodes_match_oracle():
@@ -103,8 +102,8 @@ def test_step_parity_cfg1_100_steps():
     q_gpu, q_or, x_gpu, x_or, t_gpu, t_or, q0 = run_both(16, 3, 0.1, 100.0, 0.05, 1.0, 100, tg)
     assert abs(t_gpu - t_or) <= 1e-15 * max(1.0, t_or)
     np.testing.assert_allclose(x_gpu, x_or, atol=1e-13)
-    assert rel_l2(q_gpu, q_or) <= 1e-10
-    assert rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-10
+    assert rel_err(q_gpu, q_or) <= 1e-10
+    assert rel_err(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-10
 
 
 @pytest.mark.parametrize('u0,v0', [(1.0, 0.0), (1.0, 1.0)])
@@ -125,13 +124,13 @@ def test_full_size_cfg2_rhs_and_step():
     q0 = oracle_state(o, o.X, lambda x, y: inputs.taylor_green(x, y, 0.1))
     t = 0.0
     F_or = o.rhs(q0, o.X, o.motion.velocity(o.X, t))
-    assert rel_l2(gpu_rhs(s, q0, t), F_or) <= 1e-12
+    assert rel_err(gpu_rhs(s, q0, t), F_or) <= 1e-12
     dt = inputs.cfl_dt(mesh, 4, o.c, 0.5)
     s.set_fields(q0, 0.0)
     s.step(dt, 1)
     q_gpu, _ = s.fields()
     q_or, x_or = o.step(q0, o.X.copy(), 0.0, dt)
-    assert rel_l2(q_gpu, q_or) <= 1e-11
+    assert rel_err(q_gpu, q_or) <= 1e-11
     np.testing.assert_allclose(s.vertices(), x_or, atol=1e-13)
 
 
@@ -139,22 +138,22 @@ def test_full_size_cfg2_rhs_and_step():
 def test_step_parity_other_orders(N):
     flow = lambda x, y: inputs.random_flow(x, y, 3)
     q_gpu, q_or, *_ = run_both(7, N, 0.1, 300.0, 0.04, 0.6, 20, flow, jitter=0.1)
-    assert rel_l2(q_gpu, q_or) <= 1e-10
+    assert rel_err(q_gpu, q_or) <= 1e-10
 
 
 def test_smallest_mesh():
     # n = 3: K = 18, every element is on the periodic boundary
     flow = lambda x, y: inputs.random_flow(x, y, 5)
     q_gpu, q_or, *_ = run_both(3, 3, 0.1, 100.0, 0.05, 1.0, 10, flow)
-    assert rel_l2(q_gpu, q_or) <= 1e-11
+    assert rel_err(q_gpu, q_or) <= 1e-11
 
 
 def test_mixed_precision_error_cfg1():
     tg = lambda x, y: inputs.taylor_green(x, y, 0.1)
     q_gpu, q_or, x_gpu, x_or, *_ = run_both(16, 3, 0.1, 100.0, 0.05, 1.0, 100, tg, precision=gb.GB_MIXED)
     np.testing.assert_allclose(x_gpu, x_or, atol=1e-13)     # geometry stays FP64
-    assert rel_l2(q_gpu, q_or) <= 1e-5
-    assert rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
+    assert rel_err(q_gpu, q_or) <= 1e-5
+    assert rel_err(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
 
 
 @pytest.mark.parametrize('N', [1, 2, 3, 4, 5, 6])
@@ -167,16 +166,16 @@ def test_mixed_rhs_all_orders_ragged(N):
     q = oracle_state(o, xv, lambda x, y: inputs.random_flow(x, y, 21 + N))
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
     F_gpu = gpu_rhs(s, q, t)
-    assert rel_l2(F_gpu, F_or) <= 1e-5
+    assert rel_err(F_gpu, F_or) <= 1e-5
     for f in range(6):
-        assert rel_l2(F_gpu[:, f], F_or[:, f]) <= 1e-4, f
+        assert rel_err(F_gpu[:, f], F_or[:, f]) <= 1e-4, f
 
 
 @pytest.mark.parametrize('N', [2, 4, 5])
 def test_mixed_step_other_orders(N):
     flow = lambda x, y: inputs.random_flow(x, y, 4)
     q_gpu, q_or, *_ = run_both(7, N, 0.1, 300.0, 0.04, 0.6, 20, flow, jitter=0.1, precision=gb.GB_MIXED)
-    assert rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
+    assert rel_err(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
 
 
 def test_mixed_full_size_cfg2_step():
@@ -187,7 +186,7 @@ def test_mixed_full_size_cfg2_step():
     s.step(dt, 2)
     q_gpu, _ = s.fields()
     q_or, x_or, _ = o.run(q0, o.X.copy(), 0.0, dt, 2)
-    assert rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
+    assert rel_err(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-5
     np.testing.assert_allclose(s.vertices(), x_or, atol=1e-13)
 
 
@@ -317,7 +316,7 @@ def test_mixed_rhs_matches_fp64_rhs():
     s.set_vertices(xv)
     q = oracle_state(o, xv, lambda x, y: inputs.taylor_green(x, y, 0.1))
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, 0.1))
-    assert rel_l2(gpu_rhs(s, q, 0.1), F_or) <= 1e-5
+    assert rel_err(gpu_rhs(s, q, 0.1), F_or) <= 1e-5
 
 
 def test_nan_is_reported():

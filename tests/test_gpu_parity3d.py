@@ -13,6 +13,7 @@ import pytest
 from oracle import physics3d
 from oracle.solver3d import OracleSolver3D, TGVMotion3D, WaveMotion
 from paper_2607_00199_b300 import inputs
+from parity_metrics import rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -27,8 +28,6 @@ REST[0] = 1.0
 WAVE = dict(A0=0.02, A1=0.08, Lx=8.0, wavelength=1.0, omega=2 * math.pi, r0sq=0.25, yc=1.0, zc=1.0)
 
 
-def rel_l2(a, b):
-    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
 
 
 def oracle_state(o, xv, flow):
@@ -65,9 +64,9 @@ def test_rhs_parity_all_orders_ragged(N):
     q = oracle_state(o, xv, lambda x, y, z: inputs.random_flow_3d(x, y, z, 17 + N))
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
     F_gpu = gpu_rhs(s, q, t)
-    assert rel_l2(F_gpu, F_or) <= 1e-12
+    assert rel_err(F_gpu, F_or) <= 1e-12
     for f in range(10):
-        assert rel_l2(F_gpu[:, f], F_or[:, f]) <= 1e-11, f
+        assert rel_err(F_gpu[:, f], F_or[:, f]) <= 1e-11, f
 
 
 def test_nodes_and_vertices_match_oracle():
@@ -87,7 +86,7 @@ def test_step_parity_moving_mesh(N, steps):
     q_or, x_or, t_or = o.run(q0, o.X.copy(), 0.0, dt, steps)
     assert abs(t_gpu - t_or) < 1e-14
     np.testing.assert_allclose(s.vertices(), x_or, atol=1e-14)
-    assert rel_l2(q_gpu, q_or) <= 1e-10
+    assert rel_err(q_gpu, q_or) <= 1e-10
 
 
 @pytest.mark.parametrize('vel', [(1.0, 0.0, 0.0), (1.0, 1.0, 1.0)])
@@ -110,7 +109,7 @@ def test_mixed_rhs_all_orders(N):
     s.set_vertices(xv)
     q = oracle_state(o, xv, lambda x, y, z: inputs.random_flow_3d(x, y, z, 29 + N))
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
-    assert rel_l2(gpu_rhs(s, q, t), F_or) <= 1e-5
+    assert rel_err(gpu_rhs(s, q, t), F_or) <= 1e-5
 
 
 @pytest.mark.parametrize('N', [2, 3])
@@ -122,8 +121,8 @@ def test_mixed_step_error(N):
     s.step(dt, 10)
     q_gpu, _ = s.fields()
     q_or, _, _ = o.run(q0, o.X.copy(), 0.0, dt, 10)
-    e = rel_l2(q_gpu, q_or)
-    ep = rel_l2(q_gpu - REST[None, :, None], q_or - REST[None, :, None])
+    e = rel_err(q_gpu, q_or)
+    ep = rel_err(q_gpu - REST[None, :, None], q_or - REST[None, :, None])
     print('3D mixed N=%d: fields %.2e, perturbation %.2e' % (N, e, ep))
     assert e <= 1e-5 and ep <= 1e-4
 
@@ -137,13 +136,13 @@ def test_full_size_cfg4_rhs_and_step():
     q0 = oracle_state(o, o.X, lambda x, y, z: inputs.channel_flow_3d(x, y, z, 0.1))
     t = 0.21
     F_or = o.rhs(q0, o.X, o.motion.velocity(o.X, t))
-    assert rel_l2(gpu_rhs(s, q0, t), F_or) <= 1e-12
+    assert rel_err(gpu_rhs(s, q0, t), F_or) <= 1e-12
     dt = inputs.cfl_dt_3d(mesh, 3, o.c, 0.5)
     s.set_fields(q0, 0.0)
     s.step(dt, 1)
     q_gpu, _ = s.fields()
     q_or, _ = o.step(q0, o.X.copy(), 0.0, dt)
-    assert rel_l2(q_gpu, q_or) <= 1e-12
+    assert rel_err(q_gpu, q_or) <= 1e-12
 
 
 @pytest.mark.parametrize('precision', [gb.GB_FP64, gb.GB_MIXED])
@@ -236,7 +235,7 @@ def test_tgv_rhs_parity(N):
     q = oracle_state(o, xv, tgv_flow)
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
     F = gpu_rhs(s, q, t)
-    assert rel_l2(F, F_or) <= 1e-12
+    assert rel_err(F, F_or) <= 1e-12
     # per field, against max(|F_f|, 1e-4 |F|): the relaxation of the stress moments dominates
     # this near-equilibrium state, fields 1..4 are 2e-5..1e-4 of |F|, and their rounding error
     # scales with the advection terms summed into them, not with their small sum
@@ -258,7 +257,7 @@ def test_tgv_steps_follow_oracle(precision):
     assert abs(t_gpu - t_or) < 1e-14
     np.testing.assert_allclose(s.vertices(), x_or, atol=1e-14)
     assert min(np.abs(x_or[:, d] - o.X[:, d]).max() for d in range(3)) > 1e-3
-    assert rel_l2(q_gpu, q_or) <= (1e-10 if precision == gb.GB_FP64 else 1e-5)
+    assert rel_err(q_gpu, q_or) <= (1e-10 if precision == gb.GB_FP64 else 1e-5)
 
 
 def test_tgv_free_stream_gcl_gpu():
@@ -350,7 +349,7 @@ def test_full_size_tgv_rhs_and_step():
         s = gb.Solver(mesh, 3, 0.1, 1600.0, precision=precision, stream=torch.cuda.current_stream().cuda_stream)
         s.set_tgv_motion()
         s.set_vertices(xv)
-        assert rel_l2(gpu_rhs(s, q, t), F_or) <= tol
+        assert rel_err(gpu_rhs(s, q, t), F_or) <= tol
         s.close()
     s = gb.Solver(mesh, 3, 0.1, 1600.0, stream=torch.cuda.current_stream().cuda_stream)
     s.set_tgv_motion()
@@ -360,4 +359,4 @@ def test_full_size_tgv_rhs_and_step():
     s.step(dt, 1)
     q_or, x_or = o.step(q0, o.X.copy(), 0.0, dt)
     np.testing.assert_allclose(s.vertices(), x_or, atol=1e-14)
-    assert rel_l2(s.fields()[0], q_or) <= 1e-12
+    assert rel_err(s.fields()[0], q_or) <= 1e-12
