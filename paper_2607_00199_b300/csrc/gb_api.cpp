@@ -43,6 +43,7 @@ struct gb_solver {
   // device memory
   double *d_ops = nullptr;     // FP64 operator block (canonical kernel, node coordinates)
   float *d_ops_mixed = nullptr;  // FP32 operator block of the GB_MIXED kernel
+  float *d_ops_um = nullptr;     // GB_MIXED, N <= 4, no boundary faces: tables of the tcgen05 kernel
   MeshRec *d_mesh = nullptr;     // canonical element order
   MeshRec *d_mesh_int = nullptr; // GB_MIXED: Morton element order, neighbours renumbered
   int32_t *d_perm = nullptr;     // GB_MIXED: canonical index of internal element i
@@ -91,7 +92,7 @@ static int dev_alloc(gb_solver *s, void **p, size_t bytes) {
 }
 
 static void free_all(gb_solver *s) {
-  void *ptrs[] = {s->d_ops, s->d_ops_mixed, s->d_mesh, s->d_mesh_int, s->d_perm, s->d_X, s->d_xn, s->d_shape,
+  void *ptrs[] = {s->d_ops, s->d_ops_mixed, s->d_ops_um, s->d_mesh, s->d_mesh_int, s->d_perm, s->d_X, s->d_xn, s->d_shape,
                   s->d_clock, s->d_status, s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp, s->d_diag,
                   s->d_hist, s->d_hctl, s->d_done, s->d_pml_ops, s->d_pml_node, s->d_phi, s->d_pml_elem};
   for (void *p : ptrs)
@@ -150,6 +151,7 @@ static gb::StageArgs base_args(gb_solver *s) {
   const bool mixed = s->precision == GB_MIXED;
   a.mesh = mixed ? s->d_mesh_int : s->d_mesh;
   a.ops = mixed ? reinterpret_cast<const double *>(s->d_ops_mixed) : s->d_ops;
+  a.ops_um = mixed ? s->d_ops_um : nullptr;
   a.clock = s->d_clock;
   a.status = s->d_status;
   a.K = s->K;
@@ -254,11 +256,17 @@ static int tune_launch(gb_solver *s) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
-  int best = 4;
+  // candidates: the tcgen05 kernel's 128-element CTA tiles where it applies, then the
+  // mma.sync kernel's 16-element warp tiles with 4, 2 or 1 warps per CTA; a later candidate
+  // must beat the best so far by 3%
+  int cand[4], ncand = 0;
+  if (s->d_ops_um) cand[ncand++] = gb::kShapeUm;
+  cand[ncand++] = 4;
+  cand[ncand++] = 2;
+  cand[ncand++] = 1;
+  int best = cand[0];
   float best_ms = 1e30f;
-  // later candidates must beat the best so far by 3%
-  const int cand[3] = {4, 2, 1};
-  for (int i = 0; i < 3 && ce == cudaSuccess; ++i) {
+  for (int i = 0; i < ncand && ce == cudaSuccess; ++i) {
     a.warps_per_cta = cand[i];
     int rc = gb::launch_stage_mixed(s->N, a, s->stream, s->num_sms);   // warm-up
     if (rc) { ce = (cudaError_t)rc; break; }
@@ -495,6 +503,8 @@ static int create2d(const gb_mesh *mesh, const int8_t *face_bc, const double *fa
   s->device = dev;
   int rc = gb::upload_ops(N, s->ref, &s->d_ops, s->stream);
   if (rc == 0 && precision == GB_MIXED) rc = gb::upload_ops_mixed(N, s->ref, &s->d_ops_mixed, s->stream);
+  if (rc == 0 && precision == GB_MIXED && gb::um_supported(N) && !has_bc)
+    rc = gb::upload_ops_um(N, s->ref, &s->d_ops_um, s->stream);
   if (rc != 0) {
     std::string m = std::string("operator upload: ") + cudaGetErrorString((cudaError_t)rc);
     free_all(s);
@@ -1092,8 +1102,10 @@ int gb_set_launch_config(gb_solver *s, int warps_per_cta) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
   if (s->s3) return fail(s, GB_EINVAL, "not available for dim = 3 solvers");
   if (s->precision != GB_MIXED) return fail(s, GB_EINVAL, "launch shapes apply to GB_MIXED solvers");
-  if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4)
-    return fail(s, GB_EINVAL, "warps_per_cta must be 1, 2 or 4");
+  if (warps_per_cta == gb::kShapeUm && !s->d_ops_um)
+    return fail(s, GB_EINVAL, "shape 8 (tcgen05, 128-element tiles) needs N <= 4 and a mesh without boundary faces");
+  if (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4 && warps_per_cta != gb::kShapeUm)
+    return fail(s, GB_EINVAL, "the launch shape must be 1, 2 or 4 (warps per CTA) or 8 (tcgen05 tiles)");
   s->warps = warps_per_cta;
   drop_graph(s);
   return GB_OK;

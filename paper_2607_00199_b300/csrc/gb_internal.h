@@ -14,6 +14,7 @@
 // device status bits (OR-ed by the kernels, read by gb_sync / gb_fields)
 #define GB_STATUS_NAN  1
 #define GB_STATUS_MESH 2
+#define GB_STATUS_TIMEOUT 4   // a bounded wait on the tensor cores or a bulk copy ran out
 
 namespace gb {
 
@@ -83,6 +84,7 @@ struct StageArgs {
   const double *shape;  // vertex velocity shape S(X), n_vert x 2
   const MeshRec *mesh;
   const double *ops;    // device copy of the operators (layout in gb_kernels.cu)
+  const float *ops_um;  // GB_MIXED, N <= 4: operator tables of the tcgen05 kernel (layout in gb_kernels_um.cu)
   const double *clock;  // device time t_n
   int *status;
   int64_t K;
@@ -133,6 +135,41 @@ struct PmlArgs {
 };
 int launch_pml_stage(int N, bool fp64, const StageArgs &a, const PmlArgs &p, void *stream, int num_sms);
 int pml_ops_size(int N);
+
+// element stride (floats) of the GB_MIXED field layout: the smallest s >= x with s = 4 mod 8
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int tc_round_s(int x) { return ((x - 4 + 7) / 8) * 8 + 4; }   // smallest s >= x, s = 4 mod 8
+
+#ifdef __CUDACC__
+// volume index of node k (counter-clockwise) of face f of the reference triangle of order N
+template <int N>
+__device__ __forceinline__ int tc_fmask(int f, int k) {
+  constexpr int NN = N;
+  auto rs = [](int j) { return j * (NN + 1) - j * (j - 1) / 2; };
+  return f == 0 ? k : (f == 1 ? rs(k) + (NN - k) : rs(NN - k));
+}
+
+// motion factors of a stage for one request: v_i = gfac S(X), x_i = x_n + xfac S(X),
+// and the factor of the final vertex update x_{n+1} = x_n + fin S(X) (RK4 nodes and weights)
+template <int STAGE>
+__device__ __forceinline__ void tc_stage_motion(const StageArgs &a, double &gf, double &xf, double &fin) {
+  gf = 0.0; xf = 0.0; fin = 0.0;
+  if (a.motion_A == 0.0) return;
+  const double w = a.motion_w, Aw = a.motion_A * a.motion_w;
+  if (STAGE < 0) {
+    gf = Aw * cos(w * a.rhs_time);
+    return;
+  }
+  const double tt = a.clock[0], dt = a.dt;
+  const double cst[4] = {0.0, 0.5, 0.5, 1.0};
+  gf = Aw * cos(w * (tt + cst[STAGE] * dt));
+  if (STAGE > 0) xf = dt * cst[STAGE == 3 ? 3 : 1] * Aw * cos(w * (tt + cst[STAGE - 1] * dt));
+  if (STAGE == 3) fin = dt * Aw * (cos(w * tt) / 6.0 + cos(w * (tt + 0.5 * dt)) * (2.0 / 3.0) + cos(w * (tt + dt)) / 6.0);
+}
+
+#endif
 
 // most CTAs of a launch with the fused record (the size of its partials buffer)
 constexpr int kRecMaxCtas = 1184;
@@ -228,6 +265,12 @@ int launch_diagnostics_record(int N, const void *q, bool is_float, bool perturba
                               int64_t K, double *part, const double *clock, int64_t *ctl, int every, double *hist,
                               int64_t cap, void *stream);
 int launch_group_mixed(int N, int stage, const GroupArgs &g, void *stream, int num_sms);
+// GB_MIXED on the tcgen05 tensor cores (gb_kernels_um.cu): 128-element CTA tiles, orders 1..4,
+// meshes without boundary faces, no fused diagnostics; selected by warps_per_cta == kShapeUm
+constexpr int kShapeUm = 8;
+bool um_supported(int N);
+int launch_stage_um(int N, const StageArgs &a, void *stream, int num_sms);
+int upload_ops_um(int N, const RefOps &R, float **dev_ops, void *stream);
 int launch_group_vertex_update(const GroupArgs &g, void *stream);
 // the solver's rhs-only launch arguments, its device buffers' layout, stream and device ordinal
 int rhs_launch_view(gb_solver *s, double t, StageArgs *a, const int32_t **perm, int *N, int64_t *K, int *Np,

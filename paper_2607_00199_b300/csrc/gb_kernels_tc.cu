@@ -37,7 +37,6 @@
 
 namespace gb {
 
-__host__ __device__ constexpr int tc_round_s(int x) { return ((x - 4 + 7) / 8) * 8 + 4; }   // smallest s >= x, s = 4 mod 8
 
 template <int N>
 struct TcDim {
@@ -65,12 +64,6 @@ struct TcDim {
   static constexpr int WARP_FLOATS = 16 * S + 16 * OUTS + 16 * GEOS + 4;
 };
 
-template <int N>
-__device__ __forceinline__ int tc_fmask(int f, int k) {
-  constexpr int NN = N;
-  auto rs = [](int j) { return j * (NN + 1) - j * (j - 1) / 2; };
-  return f == 0 ? k : (f == 1 ? rs(k) + (NN - k) : rs(NN - k));
-}
 
 __device__ __forceinline__ unsigned to_tf32(float x) {
   unsigned r;
@@ -660,24 +653,6 @@ __device__ __forceinline__ void tc_tile(const StageArgs &a, int64_t tile, int64_
   }
 }
 
-// motion factors of a stage for one request: v_i = gfac S(X), x_i = x_n + xfac S(X),
-// and the factor of the final vertex update x_{n+1} = x_n + fin S(X) (RK4 nodes and weights)
-template <int STAGE>
-__device__ __forceinline__ void tc_stage_motion(const StageArgs &a, double &gf, double &xf, double &fin) {
-  gf = 0.0; xf = 0.0; fin = 0.0;
-  if (a.motion_A == 0.0) return;
-  const double w = a.motion_w, Aw = a.motion_A * a.motion_w;
-  if (STAGE < 0) {
-    gf = Aw * cos(w * a.rhs_time);
-    return;
-  }
-  const double tt = a.clock[0], dt = a.dt;
-  const double cst[4] = {0.0, 0.5, 0.5, 1.0};
-  gf = Aw * cos(w * (tt + cst[STAGE] * dt));
-  if (STAGE > 0) xf = dt * cst[STAGE == 3 ? 3 : 1] * Aw * cos(w * (tt + cst[STAGE - 1] * dt));
-  if (STAGE == 3) fin = dt * Aw * (cos(w * tt) / 6.0 + cos(w * (tt + 0.5 * dt)) * (2.0 / 3.0) + cos(w * (tt + dt)) / 6.0);
-}
-
 template <int N>
 __device__ __forceinline__ void tc_load_bary(const void *ops, int lane, float (&bl)[TcDim<N>::NT][2][3]) {
   typedef TcDim<N> D;
@@ -845,6 +820,10 @@ static int tc_launch_n(const StageArgs &a, cudaStream_t st, int num_sms) {
 }
 
 int launch_stage_mixed(int N, const StageArgs &a, void *stream, int num_sms) {
+  // shape kShapeUm: the tcgen05 kernel, except where it does not apply (boundary faces, the
+  // last stage with fused diagnostics), where the 4-warp shape of this kernel runs
+  if (a.warps_per_cta == kShapeUm && a.ops_um && !a.bc && !(a.stage == 3 && a.rec_every > 0) && um_supported(N))
+    return launch_stage_um(N, a, stream, num_sms);
   cudaStream_t st = (cudaStream_t)stream;
   switch (N) {
     case 1: return tc_launch_n<1>(a, st, num_sms);

@@ -1,0 +1,918 @@
+// GB_MIXED stage kernel on the fifth-generation tensor cores (tcgen05) with the
+// accumulators in tensor memory (TMEM).
+//
+// Same right-hand side and SARK combination as the other stage kernels (Secs. 2-5):
+// F = volume + surface + P Ntilde(I q) at the stage geometry, then the stage or final
+// SARK combination.  The work is laid out one element per thread:
+//
+//   a CTA of 128 threads owns a tile of 128 consecutive (Morton-ordered) elements;
+//   thread t is element t of the tile and TMEM lane t.
+//
+// The four dense contractions of the semi-discrete form (Sec. 3) are M = 128 (elements)
+// tcgen05.mma products of kind::tf32, issued by one thread, accumulating in FP32 in TMEM:
+//   V_f  = Q_f [Dr | Ds]^T      (f = 1..6; A = the field's nodal values)
+//   C_f  = Q_f I^T              (f = 1..3; the values at the cubature points)
+//   R_f += Ntilde_f P^T         (f = 4..6; the projected collision term)
+//   R_f += Flux_f LIFT^T        (f = 1..6; the lifted face fluxes)
+// Each operand is split into a TF32 head rounded to nearest and its FP32 tail (x = hi + lo),
+// and every product is formed as hi*hi + lo*hi + hi*lo; the tail is truncated to TF32 by
+// the tensor core, so a product carries ~2^-21 relative error (the operator tables are split
+// on the host the same way, from FP64).  The heads of the field tile sit in shared memory in
+// the K-major core-matrix layout; every other A operand (the field tails, Ntilde, the
+// fluxes) is written by its element's thread straight into its TMEM lane with tcgen05.st.
+//
+// The pointwise work runs per element with the element's values in registers: the
+// geometric factors from the FP64 stage vertices (Sec. 5: FP64 positions and edge
+// differences, FP32 afterwards, as in the other mixed kernel), the chain rule with the
+// Atilde couplings and the v_G . grad q advection (Sec. 2), Ntilde at the cubature points,
+// the upwind face fluxes F_S and F_ALE (Sec. 3) with the neighbour traces read from the
+// staged tile (neighbours inside the tile) or from global memory, and the SARK combination
+// of the element's row.
+//
+// Data movement per tile is bulk copies with completion on mbarriers: the tile's own fields
+// q_i arrive while the previous tile finishes (prefetched once its fluxes are formed), F_0 and
+// the accumulator are loaded at the start of the tile, q_n once the first MMA batch has read
+// the head tile; the SARK outputs are written into those staged rows and leave as bulk
+// stores.  Three MMA batches per tile, each committed to an mbarrier.  Every wait is
+// bounded: on expiry the kernel sets GB_STATUS_TIMEOUT, waits (bounded) for what it issued,
+// frees its TMEM and returns.
+//
+// Field layout: the element-major FP32 perturbation layout of the GB_MIXED path (element
+// stride S = 4 mod 8 floats, fields of Np values), unchanged.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "gb_internal.h"
+
+namespace gb {
+
+template <int N>
+struct UmDim {
+  static constexpr int Np = (N + 1) * (N + 2) / 2;
+  static constexpr int Nfp = N + 1;
+  static constexpr int NFN = 3 * (N + 1);
+  static constexpr int Nc = ((3 * N + 2) / 2) * ((3 * N + 2) / 2);
+  static constexpr int S = tc_round_s(6 * Np);   // element stride of the field layout (floats)
+  static constexpr int S4 = S / 4;               // 16-byte chunks per element row
+  static constexpr int NPP = (Np + 3) & ~3;      // field column stride of the head tile in shared memory
+  static constexpr int KV = (Np + 7) & ~7;       // K of the Dr/Ds and I products; field stride of the TMEM tails
+  static constexpr int CA = (6 * NPP + (KV - NPP) + 3) & ~3;   // head-tile columns (the last field's K overrun included)
+  static constexpr int NV = (2 * KV + 15) & ~15; // N of the volume product: Dr rows at 0, Ds rows at KV
+  static constexpr int NCM = (Nc + 15) & ~15;    // N of the interpolation product
+  static constexpr int KC = (Nc + 7) & ~7;       // K of the projection product
+  static constexpr int NR = 16;                  // N of the projection and lift products (Np <= 15)
+  static constexpr int KL = (NFN + 7) & ~7;      // K of the lift product
+  // operator tables (floats), each as its TF32 head then its tail, core-matrix K-major layout:
+  // entry (n, k) of an R x K table at (k / 4) (4 R) + 4 n + k % 4
+  static constexpr int BV = 0;
+  static constexpr int BI = BV + 2 * NV * KV;
+  static constexpr int BP = BI + 2 * NCM * KV;
+  static constexpr int BL = BP + 2 * NR * KC;
+  static constexpr int BBAR = BL + 2 * NR * KL;  // per node ((1 + r) / 2, (1 + s) / 2)
+  static constexpr int BTOT = BBAR + 2 * 16;
+  // dynamic shared memory (floats): head tile [128 x CA] (later q_n and q_{i+1}), own
+  // fields [128 x S], F_0 [128 x S], accumulator [128 x S], tables
+  static constexpr int SM_A = 0;
+  static constexpr int SM_RAW = SM_A + 128 * CA;
+  static constexpr int SM_X1 = SM_RAW + 128 * S;
+  static constexpr int SM_X2 = SM_X1 + 128 * S;
+  static constexpr int SM_B = SM_X2 + 128 * S;
+  static constexpr int SM_END = SM_B + BTOT;
+  // TMEM columns (512 allocated): field tails, volume products (the rhs R takes their first
+  // 96 columns once they are read), interpolation products (Ntilde heads in place, then the
+  // flux heads); Ntilde tails in free 8-column slots, flux tails over the field tails
+  static constexpr uint32_t T_QL = 0, T_V = 96, T_R = 96, T_C = 288, T_FH = 288, T_FL = 0;
+  static_assert(N >= 1 && N <= 4, "the tcgen05 kernel covers orders 1..4");
+  static_assert(6 * KV <= 96 && 6 * NV <= 192 && 3 * NCM <= 192, "TMEM map");
+  static_assert(3 * (KC / 8) <= 28 && 6 * KL <= 96 && S <= CA, "TMEM slots / tile reuse");
+};
+
+// 8-column TMEM slots for the Ntilde tails: the field tails [0, 96), the volume columns
+// past R [192, 288) and [480, 512), all free once the volume products have been read
+__device__ __forceinline__ uint32_t um_slot(int s) {
+  return s < 12 ? 8u * s : (s < 24 ? 192u + 8u * (s - 12) : 480u + 8u * (s - 24));
+}
+
+// ---- PTX wrappers -----------------------------------------------------------------
+__device__ __forceinline__ uint32_t um_sa(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor, K-major without swizzle: a core matrix is 8 rows x 16
+// bytes stored as 128 contiguous bytes; lbo = byte distance between core matrices adjacent
+// in K, sbo = between core matrices adjacent in M (or N); bit 46 = descriptor version
+__device__ __forceinline__ uint64_t um_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor: kind::tf32, FP32 accumulator, A and B K-major, M = 128
+__host__ __device__ constexpr uint32_t um_idesc(int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+__device__ __forceinline__ void um_mma_ss(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+               :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void um_mma_ts(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+               :: "r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void um_commit(uint64_t *mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(um_sa(mbar)) : "memory");
+}
+__device__ __forceinline__ void um_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void um_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void um_fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void um_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void um_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ bool um_try_wait(uint64_t *mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(um_sa(mbar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// bounded wait (about a second at the SM clock); false if it ran out
+__device__ __forceinline__ bool um_wait(uint64_t *mbar, uint32_t parity) {
+  if (um_try_wait(mbar, parity)) return true;
+  const long long t0 = clock64();
+  while (!um_try_wait(mbar, parity))
+    if (clock64() - t0 > (1ll << 31)) return false;
+  return true;
+}
+__device__ __forceinline__ void um_bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *mbar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(um_sa(mbar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               :: "r"(um_sa(dst)), "l"(src), "r"(bytes), "r"(um_sa(mbar)) : "memory");
+}
+
+// tcgen05.ld / st of 8 or 16 consecutive 32-bit columns of this thread's lane
+#define UM_R8(v, o) "=r"(v[o + 0]), "=r"(v[o + 1]), "=r"(v[o + 2]), "=r"(v[o + 3]), "=r"(v[o + 4]), "=r"(v[o + 5]), \
+                    "=r"(v[o + 6]), "=r"(v[o + 7])
+#define UM_W8(v, o) "r"(v[o + 0]), "r"(v[o + 1]), "r"(v[o + 2]), "r"(v[o + 3]), "r"(v[o + 4]), "r"(v[o + 5]), \
+                    "r"(v[o + 6]), "r"(v[o + 7])
+__device__ __forceinline__ void um_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];" : UM_R8(v, 0) : "r"(taddr));
+}
+__device__ __forceinline__ void um_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : UM_R8(v, 0), UM_R8(v, 8) : "r"(taddr));
+}
+__device__ __forceinline__ void um_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" :: "r"(taddr), UM_W8(v, 0) : "memory");
+}
+__device__ __forceinline__ void um_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+               :: "r"(taddr), UM_W8(v, 0), UM_W8(v, 8) : "memory");
+}
+
+// ties the loaded registers to the preceding tcgen05.wait::ld, so that no use of them is
+// scheduled before the wait
+__device__ __forceinline__ void um_regs8(uint32_t *v) {
+  asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]));
+}
+
+__device__ __forceinline__ float um_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// volume index of node k of face f for a face index known only at run time
+template <int N>
+__device__ __forceinline__ int um_fmask_rt(int f, int k) {
+  const int j = N - k;
+  const int rs_k = k * (N + 1) - k * (k - 1) / 2, rs_j = j * (N + 1) - j * (j - 1) / 2;
+  return f == 0 ? k : (f == 1 ? rs_k + (N - k) : rs_j);
+}
+
+// ---- the kernel --------------------------------------------------------------------
+// packed FP32x2 arithmetic (two nodes or points per instruction)
+__device__ __forceinline__ float2 um_f2(uint32_t x, uint32_t y) { return make_float2(__uint_as_float(x), __uint_as_float(y)); }
+__device__ __forceinline__ float2 um_b2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 um_fma2(float a, float2 x, float2 y) { return __ffma2_rn(um_b2(a), x, y); }
+__device__ __forceinline__ float2 um_mul2(float a, float2 x) { return __fmul2_rn(um_b2(a), x); }
+__device__ __forceinline__ float um_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Shared-memory buffers of a tile (element-major rows of stride S unless noted):
+//   sA    the head tile of the own fields (core-matrix layout) for the first MMA batch;
+//         afterwards q_n, then q_{i+1} (or F in the rhs-only mode), stored back by a bulk copy
+//   sRaw  the own fields q_i (neighbour traces and q^- of the flux); the next tile's q_i is
+//         prefetched into it once this tile's fluxes are formed
+//   sX1   F_0 (read at stages 1-2; written at stage 0; the accumulator written at stage 1)
+//   sX2   the btilde accumulator (read at stages 2-3, written at stage 2)
+// Order within a tile: the heads and tails of the own fields; the volume and interpolation
+// products (two commits); the geometry while they run; the volume terms; the collision term
+// at the cubature points; the projection products while the face fluxes are formed; the lift
+// products; the SARK combination; bulk stores.
+template <int N, int STAGE>
+__global__ void __launch_bounds__(128, 1) um_stage_kernel(const StageArgs a) {
+  typedef UmDim<N> D;
+  constexpr int Np = D::Np, Nfp = D::Nfp, S = D::S, S4 = D::S4, NPP = D::NPP, KV = D::KV;
+  constexpr int CA = D::CA, NV = D::NV, NCM = D::NCM, KC = D::KC, KL = D::KL;
+  constexpr int NP2 = (Np + 1) / 2;
+  const float SQ2 = 1.41421356237309505f, ISQ2 = 0.70710678118654752f;
+  extern __shared__ __align__(1024) float um_smem[];
+  float *sA = um_smem + D::SM_A;
+  float *sRaw = um_smem + D::SM_RAW;
+  float *sX1 = um_smem + D::SM_X1;
+  float *sX2 = um_smem + D::SM_X2;
+  float *sB = um_smem + D::SM_B;
+  __shared__ __align__(8) uint64_t mbar_ld, mbar_x, mbar_qn, mbar_v, mbar_c, mbar_mma;
+  __shared__ uint32_t s_tmem;
+  __shared__ double s_motion[2];
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const float *qin = reinterpret_cast<const float *>(a.qin);
+  const int64_t ntile = (a.K + 127) >> 7;
+  auto tile_rows = [&](int64_t t_) { return (int)((a.K - t_ * 128) < 128 ? (a.K - t_ * 128) : 128); };
+
+  for (int i = tid; i < D::BTOT; i += 128) sB[i] = a.ops_um[i];
+  if (tid == 0) {
+    double gf, xf, fin;
+    tc_stage_motion<STAGE>(a, gf, xf, fin);
+    s_motion[0] = gf;
+    s_motion[1] = xf;
+    if (STAGE == 3 && blockIdx.x == 0) const_cast<double *>(a.clock)[1] = fin;
+    uint64_t *bars[6] = {&mbar_ld, &mbar_x, &mbar_qn, &mbar_v, &mbar_c, &mbar_mma};
+    for (int i = 0; i < 6; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(um_sa(bars[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if ((int64_t)blockIdx.x < ntile) {   // the first tile's own fields
+      const int64_t t0 = blockIdx.x;
+      um_bulk_load(sRaw, qin + t0 * 128 * S, (uint32_t)(tile_rows(t0) * S * sizeof(float)), &mbar_ld);
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(um_sa(&s_tmem)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  um_fence_async_smem();
+  um_fence_before();
+  __syncthreads();
+  um_fence_after();
+  const uint32_t tm = s_tmem;
+  const uint32_t tl = tm + ((uint32_t)(32 * warp) << 16);   // this warp's 32 lanes
+  const float gff = (float)s_motion[0], xff = (float)s_motion[1];
+  const float c = (float)a.c, mc = -(float)a.c, mcs = -(float)a.c * SQ2, itau = (float)a.inv_tau;
+  const float *bar = sB + D::BBAR;
+  const float dt = (float)a.dt;
+  // descriptors of the operands at their base addresses; an operand at byte offset o from
+  // the base has descriptor base + o / 16 (the 14-bit address field does not overflow)
+  const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
+  const uint64_t dA = um_desc(sA_a, 2048, 128);
+  const uint64_t dBV = um_desc(sB_a + 4 * D::BV, NV * 16, 128), dBI = um_desc(sB_a + 4 * D::BI, NCM * 16, 128);
+  const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
+  bool bad = false;
+
+  uint32_t ph_ld = 0, ph_x = 0, ph_qn = 0, ph_v = 0, ph_c = 0, ph_mma = 0;
+  bool failed = false, ld_pending = (int64_t)blockIdx.x < ntile, x_pending = false, qn_pending = false,
+       v_pending = false, c_pending = false, mma_pending = false;
+  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
+    const int64_t e0 = tile * 128;
+    const int nel = tile_rows(tile);
+    const bool live = tid < nel;
+    const int64_t e = e0 + (live ? tid : 0);
+    const uint32_t tile_bytes = (uint32_t)(nel * S * sizeof(float));
+    if (tid == 0) {
+      // the previous tile's bulk stores have read their shared sources before anything is
+      // loaded into (or written over) them
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      um_fence_async_smem();
+      if (STAGE >= 1) {
+        uint32_t bytes = 0;
+        if (STAGE == 1 || STAGE == 2) bytes += tile_bytes;
+        if (STAGE >= 2) bytes += tile_bytes;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(um_sa(&mbar_x)), "r"(bytes) : "memory");
+        if (STAGE == 1 || STAGE == 2)
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       :: "r"(um_sa(sX1)), "l"(reinterpret_cast<const float *>(a.F0) + e0 * S), "r"(tile_bytes),
+                          "r"(um_sa(&mbar_x)) : "memory");
+        if (STAGE >= 2)
+          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                       :: "r"(um_sa(sX2)), "l"(reinterpret_cast<const float *>(a.acc) + e0 * S), "r"(tile_bytes),
+                          "r"(um_sa(&mbar_x)) : "memory");
+      }
+    }
+    if (STAGE >= 1) x_pending = true;
+    // the mesh record now: its vertex loads follow the first MMA batch
+    const MeshRec rec = a.mesh[e];
+
+    if (__syncthreads_or(!um_wait(&mbar_ld, ph_ld))) { failed = true; break; }
+    ph_ld ^= 1u;
+    ld_pending = false;
+
+    // ---- heads of the own fields to the shared tile, tails to TMEM ----
+    {
+      float q[6 * Np];
+      const float4 *row = reinterpret_cast<const float4 *>(sRaw + tid * S);
+#pragma unroll
+      for (int j = 0; j < (6 * Np + 3) / 4; ++j) {
+        const float4 v = live ? row[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (4 * j + 0 < 6 * Np) q[4 * j + 0] = v.x;
+        if (4 * j + 1 < 6 * Np) q[4 * j + 1] = v.y;
+        if (4 * j + 2 < 6 * Np) q[4 * j + 2] = v.z;
+        if (4 * j + 3 < 6 * Np) q[4 * j + 3] = v.w;
+      }
+      auto colv = [&](int col) -> float {   // head-tile column: field col / NPP, node col % NPP
+        const int f = col / NPP, n = col % NPP;
+        return (f < 6 && n < Np) ? q[f * Np + n] : 0.0f;
+      };
+#pragma unroll
+      for (int g = 0; g < CA / 4; ++g) {
+        float4 h;
+        h.x = um_tf32(colv(4 * g + 0));
+        h.y = um_tf32(colv(4 * g + 1));
+        h.z = um_tf32(colv(4 * g + 2));
+        h.w = um_tf32(colv(4 * g + 3));
+        reinterpret_cast<float4 *>(sA)[g * 128 + tid] = h;
+      }
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int j = 0; j < KV; j += 8) {
+          uint32_t lo[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int n = j + i;
+            const float x = n < Np ? q[f * Np + n] : 0.0f;
+            lo[i] = __float_as_uint(x - um_tf32(x));
+          }
+          um_st8(tl + D::T_QL + f * KV + j, lo);
+        }
+    }
+    um_wait_st();
+    um_fence_async_smem();
+    um_fence_before();
+    __syncthreads();
+
+    // ---- MMA batch 1: volume products (commit), interpolation products (commit) ----
+    if (tid == 0) {
+      um_fence_after();
+      constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(NCM);
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int ks = 0; ks < KV / 8; ++ks) {
+          const uint32_t d = tm + D::T_V + f * NV;
+          const uint64_t ah = dA + (uint64_t)((((f * NPP + 8 * ks) / 4) * 2048) >> 4);
+          const uint64_t bh = dBV + (uint64_t)((4 * (2 * ks * NV * 4)) >> 4);
+          const uint64_t bl = dBV + (uint64_t)((4 * (NV * KV + 2 * ks * NV * 4)) >> 4);
+          um_mma_ts(d, tm + D::T_QL + f * KV + 8 * ks, bh, idV, ks > 0 ? 1u : 0u);
+          um_mma_ss(d, ah, bh, idV, 1u);
+          um_mma_ss(d, ah, bl, idV, 1u);
+        }
+      um_commit(&mbar_v);
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int ks = 0; ks < KV / 8; ++ks) {
+          const uint32_t d = tm + D::T_C + f * NCM;
+          const uint64_t ah = dA + (uint64_t)((((f * NPP + 8 * ks) / 4) * 2048) >> 4);
+          const uint64_t bh = dBI + (uint64_t)((4 * (2 * ks * NCM * 4)) >> 4);
+          const uint64_t bl = dBI + (uint64_t)((4 * (NCM * KV + 2 * ks * NCM * 4)) >> 4);
+          um_mma_ts(d, tm + D::T_QL + f * KV + 8 * ks, bh, idC, ks > 0 ? 1u : 0u);
+          um_mma_ss(d, ah, bh, idC, 1u);
+          um_mma_ss(d, ah, bl, idC, 1u);
+        }
+      um_commit(&mbar_c);
+    }
+    v_pending = c_pending = true;
+    __syncwarp();
+
+    // ---- geometry of this thread's element while the products run (Sec. 5) ----
+    float ex[3], ey[3], vx[3], vy[3];
+    {
+      double bx[3], by[3];
+      float ix[3], iy[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double2 xv = reinterpret_cast<const double2 *>(a.xn)[rec.v[k]];
+        const double2 sv = reinterpret_cast<const double2 *>(a.shape)[rec.v[k]];
+        bx[k] = xv.x + rec.shift[2 * k] * a.period[0];
+        by[k] = xv.y + rec.shift[2 * k + 1] * a.period[1];
+        const float sx = (float)sv.x, sy = (float)sv.y;
+        ix[k] = xff * sx;
+        iy[k] = xff * sy;
+        vx[k] = gff * sx;
+        vy[k] = gff * sy;
+      }
+      ex[0] = (float)(bx[1] - bx[0]) + (ix[1] - ix[0]); ey[0] = (float)(by[1] - by[0]) + (iy[1] - iy[0]);
+      ex[1] = (float)(bx[2] - bx[1]) + (ix[2] - ix[1]); ey[1] = (float)(by[2] - by[1]) + (iy[2] - iy[1]);
+      ex[2] = (float)(bx[0] - bx[2]) + (ix[0] - ix[2]); ey[2] = (float)(by[0] - by[2]) + (iy[0] - iy[2]);
+    }
+    const float xr = 0.5f * ex[0], yr = 0.5f * ey[0], xs = -0.5f * ex[2], ys = -0.5f * ey[2];
+    const float J = xr * ys - xs * yr;
+    if (live && !(J > 0.0f)) atomicOr(a.status, GB_STATUS_MESH);
+    const float iJ = 1.0f / J;
+    const float rx = ys * iJ, sx = -yr * iJ, ry = -xs * iJ, sy = xr * iJ;
+    // grid velocity at the nodes: P1 interpolation of the vertex velocities (Sec. 5), node pairs
+    float2 vgx2[NP2], vgy2[NP2];
+#pragma unroll
+    for (int p = 0; p < NP2; ++p) {
+      const float2 an = make_float2(bar[4 * p], bar[4 * p + 2]), bn = make_float2(bar[4 * p + 1], bar[4 * p + 3]);
+      vgx2[p] = __ffma2_rn(bn, um_b2(vx[2] - vx[0]), __ffma2_rn(an, um_b2(vx[1] - vx[0]), um_b2(vx[0])));
+      vgy2[p] = __ffma2_rn(bn, um_b2(vy[2] - vy[0]), __ffma2_rn(an, um_b2(vy[1] - vy[0]), um_b2(vy[0])));
+    }
+
+    if (__syncthreads_or(!um_wait(&mbar_v, ph_v))) { failed = true; break; }
+    ph_v ^= 1u;
+    v_pending = false;
+    um_fence_after();
+
+    // ---- volume: (A + v_G) . grad q per node pair (Sec. 2, Sec. 3) ----
+    {
+      float2 rhs[6][NP2];
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int p = 0; p < NP2; ++p) rhs[f][p] = make_float2(0.0f, 0.0f);
+#pragma unroll
+      for (int f0 = 0; f0 < 6; f0 += 2) {
+        uint32_t v[2][NV];
+#pragma unroll
+        for (int ff = 0; ff < 2; ++ff)
+#pragma unroll
+          for (int j = 0; j < NV; j += 16)
+            um_ld16(tl + D::T_V + (f0 + ff) * NV + j, *reinterpret_cast<uint32_t(*)[16]>(v[ff] + j));
+        um_wait_ld();
+#pragma unroll
+        for (int ff = 0; ff < 2; ++ff)
+#pragma unroll
+          for (int j = 0; j < NV; j += 8) um_regs8(v[ff] + j);
+#pragma unroll
+        for (int ff = 0; ff < 2; ++ff) {
+          const int f = f0 + ff;
+#pragma unroll
+          for (int p = 0; p < NP2; ++p) {
+            const int n = 2 * p;
+            const float2 d_r = um_f2(v[ff][n], v[ff][n + 1]), d_s = um_f2(v[ff][KV + n], v[ff][KV + n + 1]);
+            const float2 qx = um_fma2(sx, d_s, um_mul2(rx, d_r));
+            const float2 qy = um_fma2(sy, d_s, um_mul2(ry, d_r));
+            const float2 ale = __ffma2_rn(vgy2[p], qy, __fmul2_rn(vgx2[p], qx));
+            switch (f) {
+              case 0: rhs[0][p] = __fadd2_rn(rhs[0][p], ale); rhs[1][p] = um_fma2(mc, qx, rhs[1][p]);
+                      rhs[2][p] = um_fma2(mc, qy, rhs[2][p]); break;
+              case 1: rhs[1][p] = __fadd2_rn(rhs[1][p], ale); rhs[0][p] = um_fma2(mc, qx, rhs[0][p]);
+                      rhs[3][p] = um_fma2(mc, qy, rhs[3][p]); rhs[4][p] = um_fma2(mcs, qx, rhs[4][p]); break;
+              case 2: rhs[2][p] = __fadd2_rn(rhs[2][p], ale); rhs[0][p] = um_fma2(mc, qy, rhs[0][p]);
+                      rhs[3][p] = um_fma2(mc, qx, rhs[3][p]); rhs[5][p] = um_fma2(mcs, qy, rhs[5][p]); break;
+              case 3: rhs[3][p] = __fadd2_rn(rhs[3][p], ale); rhs[2][p] = um_fma2(mc, qx, rhs[2][p]);
+                      rhs[1][p] = um_fma2(mc, qy, rhs[1][p]); break;
+              case 4: rhs[4][p] = __fadd2_rn(rhs[4][p], ale); rhs[1][p] = um_fma2(mcs, qx, rhs[1][p]); break;
+              default: rhs[5][p] = __fadd2_rn(rhs[5][p], ale); rhs[2][p] = um_fma2(mcs, qy, rhs[2][p]); break;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        uint32_t v[16];
+#pragma unroll
+        for (int n = 0; n < 16; ++n)
+          v[n] = n < Np ? __float_as_uint((n & 1) ? rhs[f][n >> 1].y : rhs[f][n >> 1].x) : 0u;
+        um_st16(tl + D::T_R + f * 16, v);
+      }
+    }
+
+    if (__syncthreads_or(!um_wait(&mbar_c, ph_c))) { failed = true; break; }
+    ph_c ^= 1u;
+    c_pending = false;
+    um_fence_after();
+    // the head tile is read: q_n of the SARK combination goes there
+    if (STAGE >= 0 && tid == 0) {
+      um_fence_async_smem();
+      um_bulk_load(sA, reinterpret_cast<const float *>(a.qn) + e0 * S, tile_bytes, &mbar_qn);
+    }
+    if (STAGE >= 0) qn_pending = true;
+
+    // ---- collision term: Ntilde at the cubature points (Sec. 2), 16 points per batch; heads in
+    //      place, tails to the slots ----
+#pragma unroll
+    for (int c0 = 0; c0 < KC; c0 += 16) {
+      constexpr int W16 = 16;
+      const int w = (KC - c0) < W16 ? (KC - c0) : W16;   // 16, or 8 in the last batch
+      uint32_t cq[3][16];
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        if (w == 16) um_ld16(tl + D::T_C + f * NCM + c0, cq[f]);
+        else um_ld8(tl + D::T_C + f * NCM + c0, *reinterpret_cast<uint32_t(*)[8]>(cq[f]));
+      }
+      um_wait_ld();
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        um_regs8(cq[f]);
+        if (w == 16) um_regs8(cq[f] + 8);
+      }
+      uint32_t hv[3][16], lv[3][16];
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        if (i >= w) break;
+        const float2 q1 = __fadd2_rn(um_b2(1.0f), um_f2(cq[0][i], cq[0][i + 1]));
+        const float2 q2 = um_f2(cq[1][i], cq[1][i + 1]), q3 = um_f2(cq[2][i], cq[2][i + 1]);
+        const float2 r1 = um_mul2(itau, make_float2(um_rcp(q1.x), um_rcp(q1.y)));
+        const float2 rs = um_mul2(ISQ2, r1);
+        const float2 nv[3] = {__fmul2_rn(__fmul2_rn(q2, q3), r1), __fmul2_rn(__fmul2_rn(q2, q2), rs),
+                              __fmul2_rn(__fmul2_rn(q3, q3), rs)};
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          const float2 t = make_float2(um_tf32(nv[f].x), um_tf32(nv[f].y));
+          const float2 l = __fadd2_rn(nv[f], make_float2(-t.x, -t.y));
+          hv[f][i] = __float_as_uint(t.x); hv[f][i + 1] = __float_as_uint(t.y);
+          lv[f][i] = __float_as_uint(l.x); lv[f][i + 1] = __float_as_uint(l.y);
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        if (w == 16) {
+          um_st16(tl + D::T_C + f * NCM + c0, hv[f]);
+        } else {
+          um_st8(tl + D::T_C + f * NCM + c0, *reinterpret_cast<uint32_t(*)[8]>(hv[f]));
+        }
+#pragma unroll
+        for (int j = 0; j < 16; j += 8)
+          if (j < w) um_st8(tl + um_slot(f * (KC / 8) + (c0 + j) / 8), *reinterpret_cast<uint32_t(*)[8]>(lv[f] + j));
+      }
+    }
+    um_wait_st();
+    um_fence_before();
+    __syncthreads();
+
+    // ---- MMA batch 2: R_{4..6} += Ntilde P^T ----
+    if (tid == 0) {
+      um_fence_after();
+      constexpr uint32_t idR = um_idesc(16);
+#pragma unroll
+      for (int f = 0; f < 3; ++f)
+#pragma unroll
+        for (int ks = 0; ks < KC / 8; ++ks) {
+          const uint32_t d = tm + D::T_R + (3 + f) * 16;
+          const uint64_t bh = dBP + (uint64_t)((4 * (2 * ks * 16 * 4)) >> 4);
+          const uint64_t bl = dBP + (uint64_t)((4 * (16 * KC + 2 * ks * 16 * 4)) >> 4);
+          const uint32_t ah = tm + D::T_C + f * NCM + 8 * ks;
+          um_mma_ts(d, tm + um_slot(f * (KC / 8) + ks), bh, idR, 1u);
+          um_mma_ts(d, ah, bh, idR, 1u);
+          um_mma_ts(d, ah, bl, idR, 1u);
+        }
+      um_commit(&mbar_mma);
+    }
+    mma_pending = true;
+    __syncwarp();
+
+    // ---- surface: upwind F_S and F_ALE per face node (Sec. 3), the fluxes in registers ----
+    float flux[6][KL];
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+      for (int j = 0; j < KL; ++j) flux[f][j] = 0.0f;
+    if (live) {
+      const float *qm = sRaw + tid * S;
+#pragma unroll
+      for (int f = 0; f < 3; ++f) {
+        const int nb = rec.nbr[f];
+        const int64_t nbe = nb >> 2;
+        const int f2 = nb & 3;
+        const float *qp = (nbe >= e0 && nbe < e0 + nel) ? sRaw + (nbe - e0) * S : qin + nbe * S;
+        const float dx = ex[f], dy = ey[f];
+        const float len = sqrtf(dx * dx + dy * dy);
+        const float il = 1.0f / len;
+        const float nx = dy * il, ny = -dx * il;
+        const float fs = 0.5f * len * iJ;
+        const float h = 0.5f * c * fs;
+        const float al = (9.0f - 1.7320508075688772f) / 6.0f, be = (1.7320508075688772f - 3.0f) / 6.0f;
+        // |At_n| on the {1,4,5,6} block and the {2,3} block, closed form alpha At_n^2 + beta At_n^4
+        const float nn = nx * nx + ny * ny;
+        const float m00 = nn, m01 = 2.0f * nx * ny, m02 = SQ2 * nx * nx, m03 = SQ2 * ny * ny;
+        const float m12 = SQ2 * nx * ny, m22 = 2.0f * nx * nx, m33 = 2.0f * ny * ny;
+        const float q00 = m00 * m00 + m01 * m01 + m02 * m02 + m03 * m03;
+        const float q01 = m00 * m01 + m01 * m00 + m02 * m12 + m03 * m12;
+        const float q02 = m00 * m02 + m01 * m12 + m02 * m22;
+        const float q03 = m00 * m03 + m01 * m12 + m03 * m33;
+        const float q11 = m01 * m01 + m00 * m00 + m12 * m12 + m12 * m12;
+        const float q12 = m01 * m02 + m00 * m12 + m12 * m22;
+        const float q13 = m01 * m03 + m00 * m12 + m12 * m33;
+        const float q22 = m02 * m02 + m12 * m12 + m22 * m22;
+        const float q23 = m02 * m03 + m12 * m12;
+        const float q33 = m03 * m03 + m12 * m12 + m33 * m33;
+        const float M00 = h * (al * m00 + be * q00), M03 = h * (al * m01 + be * q01), M04 = h * (al * m02 + be * q02);
+        const float M05 = h * (al * m03 + be * q03), M33 = h * (al * m00 + be * q11), M34 = h * (al * m12 + be * q12);
+        const float M35 = h * (al * m12 + be * q13), M44 = h * (al * m22 + be * q22), M45 = h * (be * q23);
+        const float M55 = h * (al * m33 + be * q33);
+        const float o11 = 3.0f * nx * nx + ny * ny, o12 = 2.0f * nx * ny, o22 = nx * nx + 3.0f * ny * ny;
+        const float N11 = h * (al * o11 + be * (o11 * o11 + o12 * o12));
+        const float N12 = h * (al * o12 + be * (o11 * o12 + o12 * o22));
+        const float N22 = h * (al * o22 + be * (o12 * o12 + o22 * o22));
+        const float nhx = -h * nx, nhy = -h * ny, nsx = -h * SQ2 * nx, nsy = -h * SQ2 * ny;
+#pragma unroll
+        for (int k = 0; k < Nfp; ++k) {
+          const int vol = tc_fmask<N>(f, k), vol2 = um_fmask_rt<N>(f2, Nfp - 1 - k);
+          float w[6];
+#pragma unroll
+          for (int fld = 0; fld < 6; ++fld) w[fld] = qp[fld * Np + vol2] - qm[fld * Np + vol];
+          const float gx = (vol & 1) ? vgx2[vol >> 1].y : vgx2[vol >> 1].x;
+          const float gy = (vol & 1) ? vgy2[vol >> 1].y : vgy2[vol >> 1].x;
+          const float vn = gx * nx + gy * ny;
+          const float ale = vn > 0.0f ? vn * fs : 0.0f;
+          const int j = f * Nfp + k;
+          flux[0][j] = ale * w[0] + M00 * w[0] + M03 * w[3] + M04 * w[4] + M05 * w[5] + nhx * w[1] + nhy * w[2];
+          flux[3][j] = ale * w[3] + M03 * w[0] + M33 * w[3] + M34 * w[4] + M35 * w[5] + nhx * w[2] + nhy * w[1];
+          flux[4][j] = ale * w[4] + M04 * w[0] + M34 * w[3] + M44 * w[4] + M45 * w[5] + nsx * w[1];
+          flux[5][j] = ale * w[5] + M05 * w[0] + M35 * w[3] + M45 * w[4] + M55 * w[5] + nsy * w[2];
+          flux[1][j] = ale * w[1] + N11 * w[1] + N12 * w[2] + nhx * w[0] + nsx * w[4] + nhy * w[3];
+          flux[2][j] = ale * w[2] + N12 * w[1] + N22 * w[2] + nhy * w[0] + nsy * w[5] + nhx * w[3];
+        }
+      }
+    }
+
+    if (__syncthreads_or(!um_wait(&mbar_mma, ph_mma))) { failed = true; break; }
+    ph_mma ^= 1u;
+    mma_pending = false;
+    um_fence_after();
+    // every thread is past its flux reads of sRaw: prefetch the next tile's own fields there
+    if (tid == 0 && tile + gridDim.x < ntile) {
+      um_fence_async_smem();
+      const int64_t tn = tile + gridDim.x;
+      um_bulk_load(sRaw, qin + tn * 128 * S, (uint32_t)(tile_rows(tn) * S * sizeof(float)), &mbar_ld);
+    }
+    if (tile + gridDim.x < ntile) ld_pending = true;
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+#pragma unroll
+      for (int j = 0; j < KL; j += 8) {
+        uint32_t hv[8], lv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const float x = flux[f][j + i], t = um_tf32(x);
+          hv[i] = __float_as_uint(t);
+          lv[i] = __float_as_uint(x - t);
+        }
+        um_st8(tl + D::T_FH + f * KL + j, hv);
+        um_st8(tl + D::T_FL + f * KL + j, lv);
+      }
+    um_wait_st();
+    um_fence_before();
+    __syncthreads();
+
+    // ---- MMA batch 3: R += Flux LIFT^T ----
+    if (tid == 0) {
+      um_fence_after();
+      constexpr uint32_t idR = um_idesc(16);
+#pragma unroll
+      for (int f = 0; f < 6; ++f)
+#pragma unroll
+        for (int ks = 0; ks < KL / 8; ++ks) {
+          const uint32_t d = tm + D::T_R + f * 16;
+          const uint64_t bh = dBL + (uint64_t)((4 * (2 * ks * 16 * 4)) >> 4);
+          const uint64_t bl = dBL + (uint64_t)((4 * (16 * KL + 2 * ks * 16 * 4)) >> 4);
+          const uint32_t ah = tm + D::T_FH + f * KL + 8 * ks;
+          um_mma_ts(d, tm + D::T_FL + f * KL + 8 * ks, bh, idR, 1u);
+          um_mma_ts(d, ah, bh, idR, 1u);
+          um_mma_ts(d, ah, bl, idR, 1u);
+        }
+      um_commit(&mbar_mma);
+    }
+    mma_pending = true;
+    __syncwarp();
+    if (__syncthreads_or(!um_wait(&mbar_mma, ph_mma))) { failed = true; break; }
+    ph_mma ^= 1u;
+    mma_pending = false;
+    um_fence_after();
+    if (STAGE >= 0) {
+      bool okx = true;
+      if (STAGE >= 1) okx = um_wait(&mbar_x, ph_x);
+      okx = okx && um_wait(&mbar_qn, ph_qn);
+      if (__syncthreads_or(!okx)) { failed = true; break; }
+      if (STAGE >= 1) ph_x ^= 1u;
+      ph_qn ^= 1u;
+      x_pending = qn_pending = false;
+    }
+
+    // ---- SARK combination (Sec. 4) for this thread's element, in the staged rows ----
+    {
+      uint32_t rr[6][16];
+#pragma unroll
+      for (int f = 0; f < 6; ++f) um_ld16(tl + D::T_R + f * 16, rr[f]);
+      um_wait_ld();
+#pragma unroll
+      for (int f = 0; f < 6; ++f) {
+        um_regs8(rr[f]);
+        um_regs8(rr[f] + 8);
+      }
+      float4 *rowq = reinterpret_cast<float4 *>(sA + tid * S);
+      float4 *row1 = reinterpret_cast<float4 *>(sX1 + tid * S);
+      float4 *row2 = reinterpret_cast<float4 *>(sX2 + tid * S);
+      const float E1[2] = {a.kco[0][0], a.kco[1][0]}, A0[2] = {a.kco[0][1], a.kco[1][1]};
+      const float A1[2] = {a.kco[0][2], a.kco[1][2]}, Bc[2] = {a.kco[0][3], a.kco[1][3]};
+      const float B1[2] = {a.kco[0][4], a.kco[1][4]};
+      if (live) {
+#pragma unroll
+        for (int j = 0; j < S4; ++j) {
+          float r_[4], qv[4], f0[4], av[4], o[4], o2[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int w = 4 * j + i;
+            r_[i] = w < 6 * Np ? __uint_as_float(rr[w / Np][w % Np]) : 0.0f;
+          }
+          if (STAGE >= 0) {
+            const float4 x = rowq[j];
+            qv[0] = x.x; qv[1] = x.y; qv[2] = x.z; qv[3] = x.w;
+          }
+          if (STAGE == 1 || STAGE == 2) {
+            const float4 x = row1[j];
+            f0[0] = x.x; f0[1] = x.y; f0[2] = x.z; f0[3] = x.w;
+          }
+          if (STAGE >= 2) {
+            const float4 x = row2[j];
+            av[0] = x.x; av[1] = x.y; av[2] = x.z; av[3] = x.w;
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int w = 4 * j + i, cl = w < 3 * Np ? 0 : 1;
+            o2[i] = 0.0f;
+            if (STAGE < 0) {
+              o[i] = r_[i];
+            } else if (STAGE == 0) {
+              o2[i] = r_[i];
+              o[i] = dt * (A0[cl] * r_[i]) + E1[cl] * qv[i];
+            } else if (STAGE == 1) {
+              o[i] = dt * (A1[cl] * r_[i] + A0[cl] * f0[i]) + E1[cl] * qv[i];
+              o2[i] = B1[cl] * r_[i] + Bc[cl] * f0[i];
+            } else if (STAGE == 2) {
+              o[i] = dt * (A1[cl] * r_[i] + A0[cl] * f0[i]) + E1[cl] * qv[i];
+              o2[i] = Bc[cl] * r_[i] + av[i];
+            } else {
+              o[i] = dt * (Bc[cl] * r_[i] + av[i]) + E1[cl] * qv[i];
+              if (w < 6 * Np) bad |= (__float_as_int(o[i]) & 0x7f800000) == 0x7f800000;
+            }
+          }
+          rowq[j] = make_float4(o[0], o[1], o[2], o[3]);
+          if (STAGE == 0 || STAGE == 1) row1[j] = make_float4(o2[0], o2[1], o2[2], o2[3]);
+          if (STAGE == 2) row2[j] = make_float4(o2[0], o2[1], o2[2], o2[3]);
+        }
+      }
+    }
+    // the rows are complete: bulk stores of the tile's outputs
+    um_fence_async_smem();
+    um_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      auto store = [&](void *dst, const float *src) {
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                     :: "l"(reinterpret_cast<float *>(dst) + e0 * S), "r"(um_sa(src)), "r"(tile_bytes) : "memory");
+      };
+      store(STAGE < 0 ? a.Fout : a.qout, sA);
+      if (STAGE == 0) store(a.F0, sX1);
+      if (STAGE == 1) store(a.acc, sX1);
+      if (STAGE == 2) store(a.acc, sX2);
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
+  if (failed) {
+    // a wait ran out: flag it, wait (bounded) for what this CTA still has in flight
+    if (tid == 0) atomicOr(a.status, GB_STATUS_TIMEOUT);
+    if (ld_pending) um_wait(&mbar_ld, ph_ld);
+    if (x_pending) um_wait(&mbar_x, ph_x);
+    if (qn_pending) um_wait(&mbar_qn, ph_qn);
+    if (v_pending) um_wait(&mbar_v, ph_v);
+    if (c_pending) um_wait(&mbar_c, ph_c);
+    if (mma_pending) um_wait(&mbar_mma, ph_mma);
+  }
+  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  um_fence_before();
+  __syncthreads();
+  um_fence_after();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" :: "r"(tm) : "memory");
+}
+
+// ---- host side -------------------------------------------------------------------------
+namespace {
+
+constexpr int kUmMaxDevices = 64;
+
+template <int N, int STAGE>
+int um_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
+  typedef UmDim<N> D;
+  StageArgs a = a_in;
+  set_mixed_coefs(a);
+  // at least 116 KB, so that no two CTAs share an SM: each holds all 512 TMEM columns
+  const size_t smem = sizeof(float) * (size_t)D::SM_END > (size_t)116 * 1024 ? sizeof(float) * (size_t)D::SM_END
+                                                                                : (size_t)116 * 1024;
+  // the shared-memory opt-in is a per-device attribute: set once per device
+  static bool attr_set[kUmMaxDevices] = {};
+  int dev = 0;
+  cudaError_t err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return (int)err;
+  if (dev < 0 || dev >= kUmMaxDevices) return (int)cudaErrorInvalidDevice;
+  if (!attr_set[dev]) {
+    err = cudaFuncSetAttribute(um_stage_kernel<N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return (int)err;
+    attr_set[dev] = true;
+  }
+  const int64_t ntile = (a.K + 127) / 128;
+  int64_t grid = num_sms < ntile ? num_sms : ntile;
+  if (grid < 1) grid = 1;
+  um_stage_kernel<N, STAGE><<<(unsigned)grid, 128, smem, st>>>(a);
+  return (int)cudaGetLastError();
+}
+
+template <int N>
+int um_launch_n(const StageArgs &a, cudaStream_t st, int num_sms) {
+  switch (a.stage) {
+    case -1: return um_launch_one<N, -1>(a, st, num_sms);
+    case 0: return um_launch_one<N, 0>(a, st, num_sms);
+    case 1: return um_launch_one<N, 1>(a, st, num_sms);
+    case 2: return um_launch_one<N, 2>(a, st, num_sms);
+    case 3: return um_launch_one<N, 3>(a, st, num_sms);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+float um_tf32_host(double v) {
+  // round to nearest, ties away from zero, at 10 explicit mantissa bits (as cvt.rna.tf32.f32)
+  float x = (float)v;
+  uint32_t u;
+  memcpy(&u, &x, 4);
+  if ((u & 0x7f800000u) != 0x7f800000u) {
+    u += 0x1000u;
+    u &= 0xffffe000u;
+  }
+  float r;
+  memcpy(&r, &u, 4);
+  return r;
+}
+
+template <int N>
+void um_fill(const RefOps &Rf, std::vector<float> &h) {
+  typedef UmDim<N> D;
+  constexpr int Np = D::Np, Nc = D::Nc, NFN = D::NFN;
+  h.assign(D::BTOT, 0.0f);
+  auto put = [&](int base, int rows, int kcols, auto fn) {   // fn(n, k): entry of the rows x kcols operand
+    for (int n = 0; n < rows; ++n)
+      for (int k = 0; k < kcols; ++k) {
+        const double v = fn(n, k);
+        const float hi = um_tf32_host(v), lo = um_tf32_host(v - (double)hi);
+        const int off = (k / 4) * (rows * 4) + n * 4 + (k % 4);
+        h[base + off] = hi;
+        h[base + rows * kcols + off] = lo;
+      }
+  };
+  put(D::BV, D::NV, D::KV, [&](int n, int k) -> double {
+    if (k >= Np) return 0.0;
+    if (n < Np) return Rf.Dr[n * Np + k];
+    if (n >= D::KV && n - D::KV < Np) return Rf.Ds[(n - D::KV) * Np + k];
+    return 0.0;
+  });
+  put(D::BI, D::NCM, D::KV, [&](int n, int k) -> double { return (n < Nc && k < Np) ? Rf.I[n * Np + k] : 0.0; });
+  put(D::BP, D::NR, D::KC, [&](int o, int k) -> double { return (o < Np && k < Nc) ? Rf.P[o * Nc + k] : 0.0; });
+  put(D::BL, D::NR, D::KL, [&](int o, int k) -> double { return (o < Np && k < NFN) ? Rf.LIFT[o * NFN + k] : 0.0; });
+  for (int n = 0; n < Np; ++n) {
+    h[D::BBAR + 2 * n] = (float)(0.5 * (1.0 + Rf.r[n]));
+    h[D::BBAR + 2 * n + 1] = (float)(0.5 * (1.0 + Rf.s[n]));
+  }
+}
+
+}  // namespace
+
+bool um_supported(int N) { return N >= 1 && N <= 4; }
+
+int launch_stage_um(int N, const StageArgs &a, void *stream, int num_sms) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!a.ops_um || a.bc || (a.stage == 3 && a.rec_every > 0)) return (int)cudaErrorInvalidValue;
+  switch (N) {
+    case 1: return um_launch_n<1>(a, st, num_sms);
+    case 2: return um_launch_n<2>(a, st, num_sms);
+    case 3: return um_launch_n<3>(a, st, num_sms);
+    case 4: return um_launch_n<4>(a, st, num_sms);
+  }
+  return (int)cudaErrorInvalidValue;
+}
+
+int upload_ops_um(int N, const RefOps &Rf, float **dev_ops, void *stream) {
+  std::vector<float> h;
+  switch (N) {
+    case 1: um_fill<1>(Rf, h); break;
+    case 2: um_fill<2>(Rf, h); break;
+    case 3: um_fill<3>(Rf, h); break;
+    case 4: um_fill<4>(Rf, h); break;
+    default: return (int)cudaErrorInvalidValue;
+  }
+  void *d = nullptr;
+  cudaError_t err = cudaMalloc(&d, h.size() * sizeof(float));
+  if (err != cudaSuccess) return (int)err;
+  err = cudaMemcpyAsync(d, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (err == cudaSuccess) err = cudaStreamSynchronize((cudaStream_t)stream);
+  if (err != cudaSuccess) {
+    cudaFree(d);
+    return (int)err;
+  }
+  *dev_ops = reinterpret_cast<float *>(d);
+  return 0;
+}
+
+}  // namespace gb
