@@ -73,21 +73,28 @@ struct UmDim {
   static constexpr int BL = BP + 2 * NR * KC;
   static constexpr int BBAR = BL + 2 * NR * KL;  // per node ((1 + r) / 2, (1 + s) / 2)
   static constexpr int BTOT = BBAR + 2 * 16;
-  // dynamic shared memory (floats): head tile [128 x CA] (later q_n and q_{i+1}), own
-  // fields [128 x S], F_0 [128 x S], accumulator [128 x S], tables
+  // dynamic shared memory (floats): head tile [128 x CA] (then q_n and q_{i+1}), own fields
+  // [128 x S], F_0 [128 x S], accumulator [128 x S], tables, geometry [128 x GW], halo of the
+  // out-of-tile neighbour traces [HMAX x HW]
+  static constexpr int SAW = CA > S ? CA : S;      // columns of the head-tile region (heads, then q_n)
   static constexpr int SM_A = 0;
-  static constexpr int SM_RAW = SM_A + 128 * CA;
+  static constexpr int SM_RAW = SM_A + 128 * SAW;
   static constexpr int SM_X1 = SM_RAW + 128 * S;
   static constexpr int SM_X2 = SM_X1 + 128 * S;
   static constexpr int SM_B = SM_X2 + 128 * S;
-  static constexpr int SM_END = SM_B + BTOT;
+  static constexpr int SM_G = SM_B + BTOT;         // per element geometry of a tile [128][GW]
+  static constexpr int GW = 20;                    // rx sx ry sy 1/J, edges x3 y3, vertex velocities x3 y3, neighbours 3
+  static constexpr int HMAX = 64;                  // halo entries: out-of-tile faces of a tile
+  static constexpr int HW = 6 * Nfp;               // floats per halo entry (face node k, field fld at 6 k + fld)
+  static constexpr int SM_H = SM_G + 128 * GW;
+  static constexpr int SM_END = SM_H + HMAX * HW;
   // TMEM columns (512 allocated): field tails, volume products (the rhs R takes their first
   // 96 columns once they are read), interpolation products (Ntilde heads in place, then the
   // flux heads); Ntilde tails in free 8-column slots, flux tails over the field tails
   static constexpr uint32_t T_QL = 0, T_V = 96, T_R = 96, T_C = 288, T_FH = 288, T_FL = 0;
   static_assert(N >= 1 && N <= 4, "the tcgen05 kernel covers orders 1..4");
   static_assert(6 * KV <= 96 && 6 * NV <= 192 && 3 * NCM <= 192, "TMEM map");
-  static_assert(3 * (KC / 8) <= 28 && 6 * KL <= 96 && S <= CA, "TMEM slots / tile reuse");
+  static_assert(3 * (KC / 8) <= 28 && 6 * KL <= 96, "TMEM slots");
 };
 
 // 8-column TMEM slots for the Ntilde tails: the field tails [0, 96), the volume columns
@@ -175,10 +182,10 @@ __device__ __forceinline__ void um_regs8(uint32_t *v) {
   asm volatile("" : "+r"(v[0]), "+r"(v[1]), "+r"(v[2]), "+r"(v[3]), "+r"(v[4]), "+r"(v[5]), "+r"(v[6]), "+r"(v[7]));
 }
 
+// x rounded to TF32 (10 explicit mantissa bits, to nearest, ties away from zero: the
+// rounding of cvt.rna.tf32.f32) with two integer operations; x is finite here
 __device__ __forceinline__ float um_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xffffe000u);
 }
 
 // volume index of node k of face f for a face index known only at run time
@@ -200,321 +207,152 @@ __device__ __forceinline__ float um_rcp(float x) {
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
+__device__ __forceinline__ void um_arrive(uint64_t *mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" :: "r"(um_sa(mbar)) : "memory");
+}
 
-// Shared-memory buffers of a tile (element-major rows of stride S unless noted):
-//   sA    the head tile of the own fields (core-matrix layout) for the first MMA batch;
-//         afterwards q_n, then q_{i+1} (or F in the rhs-only mode), stored back by a bulk copy
-//   sRaw  the own fields q_i (neighbour traces and q^- of the flux); the next tile's q_i is
-//         prefetched into it once this tile's fluxes are formed
-//   sX1   F_0 (read at stages 1-2; written at stage 0; the accumulator written at stage 1)
-//   sX2   the btilde accumulator (read at stages 2-3, written at stage 2)
-// Order within a tile: the heads and tails of the own fields; the volume and interpolation
-// products (two commits); the geometry while they run; the volume terms; the collision term
-// at the cubature points; the projection products while the face fluxes are formed; the lift
-// products; the SARK combination; bulk stores.
-template <int N, int STAGE>
-__global__ void __launch_bounds__(128, 1) um_stage_kernel(const StageArgs a) {
+// per-element geometry of a stage (Sec. 5): the chain-rule factors, 1/J, the three edge
+// vectors and the grid velocity at the nodes (pairs)
+template <int N>
+struct UmGeo {
+  static constexpr int NP2 = (UmDim<N>::Np + 1) / 2;
+  float rx, sx, ry, sy, iJ;
+  float ex[3], ey[3];
+  float2 vgx2[NP2], vgy2[NP2];
+};
+
+// heads (smem tile) and tails (TMEM) of fields [3H, 3H + 3) of the element's row
+template <int N, int H>
+__device__ __forceinline__ void um_convert(const float *row, float *sA, uint32_t tl, int el, bool live) {
   typedef UmDim<N> D;
-  constexpr int Np = D::Np, Nfp = D::Nfp, S = D::S, S4 = D::S4, NPP = D::NPP, KV = D::KV;
-  constexpr int CA = D::CA, NV = D::NV, NCM = D::NCM, KC = D::KC, KL = D::KL;
-  constexpr int NP2 = (Np + 1) / 2;
-  const float SQ2 = 1.41421356237309505f, ISQ2 = 0.70710678118654752f;
-  extern __shared__ __align__(1024) float um_smem[];
-  float *sA = um_smem + D::SM_A;
-  float *sRaw = um_smem + D::SM_RAW;
-  float *sX1 = um_smem + D::SM_X1;
-  float *sX2 = um_smem + D::SM_X2;
-  float *sB = um_smem + D::SM_B;
-  __shared__ __align__(8) uint64_t mbar_ld, mbar_x, mbar_qn, mbar_v, mbar_c, mbar_mma;
-  __shared__ uint32_t s_tmem;
-  __shared__ double s_motion[2];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const float *qin = reinterpret_cast<const float *>(a.qin);
-  const int64_t ntile = (a.K + 127) >> 7;
-  auto tile_rows = [&](int64_t t_) { return (int)((a.K - t_ * 128) < 128 ? (a.K - t_ * 128) : 128); };
-
-  for (int i = tid; i < D::BTOT; i += 128) sB[i] = a.ops_um[i];
-  if (tid == 0) {
-    double gf, xf, fin;
-    tc_stage_motion<STAGE>(a, gf, xf, fin);
-    s_motion[0] = gf;
-    s_motion[1] = xf;
-    if (STAGE == 3 && blockIdx.x == 0) const_cast<double *>(a.clock)[1] = fin;
-    uint64_t *bars[6] = {&mbar_ld, &mbar_x, &mbar_qn, &mbar_v, &mbar_c, &mbar_mma};
-    for (int i = 0; i < 6; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(um_sa(bars[i])) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    if ((int64_t)blockIdx.x < ntile) {   // the first tile's own fields
-      const int64_t t0 = blockIdx.x;
-      um_bulk_load(sRaw, qin + t0 * 128 * S, (uint32_t)(tile_rows(t0) * S * sizeof(float)), &mbar_ld);
-    }
+  constexpr int Np = D::Np, NPP = D::NPP, KV = D::KV, CA = D::CA;
+  constexpr int F0 = 3 * H, W0 = F0 * Np, W1 = (F0 + 3) * Np;    // row floats [W0, W1)
+  constexpr int J0 = W0 / 4, J1 = (W1 + 3) / 4;                   // float4 chunks covering them
+  float q[4 * (J1 - J0)];
+#pragma unroll
+  for (int j = J0; j < J1; ++j) {
+    const float4 v = live ? reinterpret_cast<const float4 *>(row)[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    q[4 * (j - J0) + 0] = v.x;
+    q[4 * (j - J0) + 1] = v.y;
+    q[4 * (j - J0) + 2] = v.z;
+    q[4 * (j - J0) + 3] = v.w;
   }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(um_sa(&s_tmem)) : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  auto val = [&](int f, int n) -> float { return n < Np ? q[f * Np + n - 4 * J0] : 0.0f; };
+  // head k-groups of the three fields (the K overrun past the last field goes with H = 1)
+  constexpr int G0 = F0 * NPP / 4, G1 = H ? CA / 4 : (F0 + 3) * NPP / 4;
+#pragma unroll
+  for (int g = G0; g < G1; ++g) {
+    float hv[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int col = 4 * g + i, f = col / NPP, n = col % NPP;
+      hv[i] = f < 6 ? um_tf32(val(f, n)) : 0.0f;
+    }
+    reinterpret_cast<float4 *>(sA)[g * 128 + el] = make_float4(hv[0], hv[1], hv[2], hv[3]);
   }
-  um_fence_async_smem();
-  um_fence_before();
-  __syncthreads();
-  um_fence_after();
-  const uint32_t tm = s_tmem;
-  const uint32_t tl = tm + ((uint32_t)(32 * warp) << 16);   // this warp's 32 lanes
-  const float gff = (float)s_motion[0], xff = (float)s_motion[1];
-  const float c = (float)a.c, mc = -(float)a.c, mcs = -(float)a.c * SQ2, itau = (float)a.inv_tau;
-  const float *bar = sB + D::BBAR;
-  const float dt = (float)a.dt;
-  // descriptors of the operands at their base addresses; an operand at byte offset o from
-  // the base has descriptor base + o / 16 (the 14-bit address field does not overflow)
-  const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
-  const uint64_t dA = um_desc(sA_a, 2048, 128);
-  const uint64_t dBV = um_desc(sB_a + 4 * D::BV, NV * 16, 128), dBI = um_desc(sB_a + 4 * D::BI, NCM * 16, 128);
-  const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
-  bool bad = false;
-
-  uint32_t ph_ld = 0, ph_x = 0, ph_qn = 0, ph_v = 0, ph_c = 0, ph_mma = 0;
-  bool failed = false, ld_pending = (int64_t)blockIdx.x < ntile, x_pending = false, qn_pending = false,
-       v_pending = false, c_pending = false, mma_pending = false;
-  for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x) {
-    const int64_t e0 = tile * 128;
-    const int nel = tile_rows(tile);
-    const bool live = tid < nel;
-    const int64_t e = e0 + (live ? tid : 0);
-    const uint32_t tile_bytes = (uint32_t)(nel * S * sizeof(float));
-    if (tid == 0) {
-      // the previous tile's bulk stores have read their shared sources before anything is
-      // loaded into (or written over) them
-      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-      um_fence_async_smem();
-      if (STAGE >= 1) {
-        uint32_t bytes = 0;
-        if (STAGE == 1 || STAGE == 2) bytes += tile_bytes;
-        if (STAGE >= 2) bytes += tile_bytes;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(um_sa(&mbar_x)), "r"(bytes) : "memory");
-        if (STAGE == 1 || STAGE == 2)
-          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                       :: "r"(um_sa(sX1)), "l"(reinterpret_cast<const float *>(a.F0) + e0 * S), "r"(tile_bytes),
-                          "r"(um_sa(&mbar_x)) : "memory");
-        if (STAGE >= 2)
-          asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                       :: "r"(um_sa(sX2)), "l"(reinterpret_cast<const float *>(a.acc) + e0 * S), "r"(tile_bytes),
-                          "r"(um_sa(&mbar_x)) : "memory");
+#pragma unroll
+  for (int f = F0; f < F0 + 3; ++f)
+#pragma unroll
+    for (int j = 0; j < KV; j += 8) {
+      uint32_t lo[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const float x = val(f, j + i);
+        lo[i] = __float_as_uint(x - um_tf32(x));
       }
+      um_st8(tl + D::T_QL + f * KV + j, lo);
     }
-    if (STAGE >= 1) x_pending = true;
-    // the mesh record now: its vertex loads follow the first MMA batch
-    const MeshRec rec = a.mesh[e];
+}
 
-    if (__syncthreads_or(!um_wait(&mbar_ld, ph_ld))) { failed = true; break; }
-    ph_ld ^= 1u;
-    ld_pending = false;
-
-    // ---- heads of the own fields to the shared tile, tails to TMEM ----
-    {
-      float q[6 * Np];
-      const float4 *row = reinterpret_cast<const float4 *>(sRaw + tid * S);
+// volume terms (A + v_G) . grad q (Sec. 2, Sec. 3) at nodes [8H, 8H + 8) of the element, into R
+template <int N, int H>
+__device__ __forceinline__ void um_volume(uint32_t tl, const UmGeo<N> &G, float mc, float mcs) {
+  typedef UmDim<N> D;
+  constexpr int Np = D::Np, KV = D::KV, NV = D::NV;
+  constexpr int n0 = 8 * H;
+  if constexpr (n0 < Np) {
+    constexpr int P0 = n0 / 2;   // first node pair
+    float2 rhs[6][4];
 #pragma unroll
-      for (int j = 0; j < (6 * Np + 3) / 4; ++j) {
-        const float4 v = live ? row[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (4 * j + 0 < 6 * Np) q[4 * j + 0] = v.x;
-        if (4 * j + 1 < 6 * Np) q[4 * j + 1] = v.y;
-        if (4 * j + 2 < 6 * Np) q[4 * j + 2] = v.z;
-        if (4 * j + 3 < 6 * Np) q[4 * j + 3] = v.w;
-      }
-      auto colv = [&](int col) -> float {   // head-tile column: field col / NPP, node col % NPP
-        const int f = col / NPP, n = col % NPP;
-        return (f < 6 && n < Np) ? q[f * Np + n] : 0.0f;
-      };
+    for (int f = 0; f < 6; ++f)
 #pragma unroll
-      for (int g = 0; g < CA / 4; ++g) {
-        float4 h;
-        h.x = um_tf32(colv(4 * g + 0));
-        h.y = um_tf32(colv(4 * g + 1));
-        h.z = um_tf32(colv(4 * g + 2));
-        h.w = um_tf32(colv(4 * g + 3));
-        reinterpret_cast<float4 *>(sA)[g * 128 + tid] = h;
-      }
+      for (int p = 0; p < 4; ++p) rhs[f][p] = make_float2(0.0f, 0.0f);
 #pragma unroll
-      for (int f = 0; f < 6; ++f)
+    for (int f0 = 0; f0 < 6; f0 += 3) {
+      uint32_t vr[3][8], vs[3][8];
 #pragma unroll
-        for (int j = 0; j < KV; j += 8) {
-          uint32_t lo[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int n = j + i;
-            const float x = n < Np ? q[f * Np + n] : 0.0f;
-            lo[i] = __float_as_uint(x - um_tf32(x));
-          }
-          um_st8(tl + D::T_QL + f * KV + j, lo);
-        }
-    }
-    um_wait_st();
-    um_fence_async_smem();
-    um_fence_before();
-    __syncthreads();
-
-    // ---- MMA batch 1: volume products (commit), interpolation products (commit) ----
-    if (tid == 0) {
-      um_fence_after();
-      constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(NCM);
-#pragma unroll
-      for (int f = 0; f < 6; ++f)
-#pragma unroll
-        for (int ks = 0; ks < KV / 8; ++ks) {
-          const uint32_t d = tm + D::T_V + f * NV;
-          const uint64_t ah = dA + (uint64_t)((((f * NPP + 8 * ks) / 4) * 2048) >> 4);
-          const uint64_t bh = dBV + (uint64_t)((4 * (2 * ks * NV * 4)) >> 4);
-          const uint64_t bl = dBV + (uint64_t)((4 * (NV * KV + 2 * ks * NV * 4)) >> 4);
-          um_mma_ts(d, tm + D::T_QL + f * KV + 8 * ks, bh, idV, ks > 0 ? 1u : 0u);
-          um_mma_ss(d, ah, bh, idV, 1u);
-          um_mma_ss(d, ah, bl, idV, 1u);
-        }
-      um_commit(&mbar_v);
-#pragma unroll
-      for (int f = 0; f < 3; ++f)
-#pragma unroll
-        for (int ks = 0; ks < KV / 8; ++ks) {
-          const uint32_t d = tm + D::T_C + f * NCM;
-          const uint64_t ah = dA + (uint64_t)((((f * NPP + 8 * ks) / 4) * 2048) >> 4);
-          const uint64_t bh = dBI + (uint64_t)((4 * (2 * ks * NCM * 4)) >> 4);
-          const uint64_t bl = dBI + (uint64_t)((4 * (NCM * KV + 2 * ks * NCM * 4)) >> 4);
-          um_mma_ts(d, tm + D::T_QL + f * KV + 8 * ks, bh, idC, ks > 0 ? 1u : 0u);
-          um_mma_ss(d, ah, bh, idC, 1u);
-          um_mma_ss(d, ah, bl, idC, 1u);
-        }
-      um_commit(&mbar_c);
-    }
-    v_pending = c_pending = true;
-    __syncwarp();
-
-    // ---- geometry of this thread's element while the products run (Sec. 5) ----
-    float ex[3], ey[3], vx[3], vy[3];
-    {
-      double bx[3], by[3];
-      float ix[3], iy[3];
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const double2 xv = reinterpret_cast<const double2 *>(a.xn)[rec.v[k]];
-        const double2 sv = reinterpret_cast<const double2 *>(a.shape)[rec.v[k]];
-        bx[k] = xv.x + rec.shift[2 * k] * a.period[0];
-        by[k] = xv.y + rec.shift[2 * k + 1] * a.period[1];
-        const float sx = (float)sv.x, sy = (float)sv.y;
-        ix[k] = xff * sx;
-        iy[k] = xff * sy;
-        vx[k] = gff * sx;
-        vy[k] = gff * sy;
-      }
-      ex[0] = (float)(bx[1] - bx[0]) + (ix[1] - ix[0]); ey[0] = (float)(by[1] - by[0]) + (iy[1] - iy[0]);
-      ex[1] = (float)(bx[2] - bx[1]) + (ix[2] - ix[1]); ey[1] = (float)(by[2] - by[1]) + (iy[2] - iy[1]);
-      ex[2] = (float)(bx[0] - bx[2]) + (ix[0] - ix[2]); ey[2] = (float)(by[0] - by[2]) + (iy[0] - iy[2]);
-    }
-    const float xr = 0.5f * ex[0], yr = 0.5f * ey[0], xs = -0.5f * ex[2], ys = -0.5f * ey[2];
-    const float J = xr * ys - xs * yr;
-    if (live && !(J > 0.0f)) atomicOr(a.status, GB_STATUS_MESH);
-    const float iJ = 1.0f / J;
-    const float rx = ys * iJ, sx = -yr * iJ, ry = -xs * iJ, sy = xr * iJ;
-    // grid velocity at the nodes: P1 interpolation of the vertex velocities (Sec. 5), node pairs
-    float2 vgx2[NP2], vgy2[NP2];
-#pragma unroll
-    for (int p = 0; p < NP2; ++p) {
-      const float2 an = make_float2(bar[4 * p], bar[4 * p + 2]), bn = make_float2(bar[4 * p + 1], bar[4 * p + 3]);
-      vgx2[p] = __ffma2_rn(bn, um_b2(vx[2] - vx[0]), __ffma2_rn(an, um_b2(vx[1] - vx[0]), um_b2(vx[0])));
-      vgy2[p] = __ffma2_rn(bn, um_b2(vy[2] - vy[0]), __ffma2_rn(an, um_b2(vy[1] - vy[0]), um_b2(vy[0])));
-    }
-
-    if (__syncthreads_or(!um_wait(&mbar_v, ph_v))) { failed = true; break; }
-    ph_v ^= 1u;
-    v_pending = false;
-    um_fence_after();
-
-    // ---- volume: (A + v_G) . grad q per node pair (Sec. 2, Sec. 3) ----
-    {
-      float2 rhs[6][NP2];
-#pragma unroll
-      for (int f = 0; f < 6; ++f)
-#pragma unroll
-        for (int p = 0; p < NP2; ++p) rhs[f][p] = make_float2(0.0f, 0.0f);
-#pragma unroll
-      for (int f0 = 0; f0 < 6; f0 += 2) {
-        uint32_t v[2][NV];
-#pragma unroll
-        for (int ff = 0; ff < 2; ++ff)
-#pragma unroll
-          for (int j = 0; j < NV; j += 16)
-            um_ld16(tl + D::T_V + (f0 + ff) * NV + j, *reinterpret_cast<uint32_t(*)[16]>(v[ff] + j));
-        um_wait_ld();
-#pragma unroll
-        for (int ff = 0; ff < 2; ++ff)
-#pragma unroll
-          for (int j = 0; j < NV; j += 8) um_regs8(v[ff] + j);
-#pragma unroll
-        for (int ff = 0; ff < 2; ++ff) {
-          const int f = f0 + ff;
-#pragma unroll
-          for (int p = 0; p < NP2; ++p) {
-            const int n = 2 * p;
-            const float2 d_r = um_f2(v[ff][n], v[ff][n + 1]), d_s = um_f2(v[ff][KV + n], v[ff][KV + n + 1]);
-            const float2 qx = um_fma2(sx, d_s, um_mul2(rx, d_r));
-            const float2 qy = um_fma2(sy, d_s, um_mul2(ry, d_r));
-            const float2 ale = __ffma2_rn(vgy2[p], qy, __fmul2_rn(vgx2[p], qx));
-            switch (f) {
-              case 0: rhs[0][p] = __fadd2_rn(rhs[0][p], ale); rhs[1][p] = um_fma2(mc, qx, rhs[1][p]);
-                      rhs[2][p] = um_fma2(mc, qy, rhs[2][p]); break;
-              case 1: rhs[1][p] = __fadd2_rn(rhs[1][p], ale); rhs[0][p] = um_fma2(mc, qx, rhs[0][p]);
-                      rhs[3][p] = um_fma2(mc, qy, rhs[3][p]); rhs[4][p] = um_fma2(mcs, qx, rhs[4][p]); break;
-              case 2: rhs[2][p] = __fadd2_rn(rhs[2][p], ale); rhs[0][p] = um_fma2(mc, qy, rhs[0][p]);
-                      rhs[3][p] = um_fma2(mc, qx, rhs[3][p]); rhs[5][p] = um_fma2(mcs, qy, rhs[5][p]); break;
-              case 3: rhs[3][p] = __fadd2_rn(rhs[3][p], ale); rhs[2][p] = um_fma2(mc, qx, rhs[2][p]);
-                      rhs[1][p] = um_fma2(mc, qy, rhs[1][p]); break;
-              case 4: rhs[4][p] = __fadd2_rn(rhs[4][p], ale); rhs[1][p] = um_fma2(mcs, qx, rhs[1][p]); break;
-              default: rhs[5][p] = __fadd2_rn(rhs[5][p], ale); rhs[2][p] = um_fma2(mcs, qy, rhs[2][p]); break;
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int f = 0; f < 6; ++f) {
-        uint32_t v[16];
-#pragma unroll
-        for (int n = 0; n < 16; ++n)
-          v[n] = n < Np ? __float_as_uint((n & 1) ? rhs[f][n >> 1].y : rhs[f][n >> 1].x) : 0u;
-        um_st16(tl + D::T_R + f * 16, v);
-      }
-    }
-
-    if (__syncthreads_or(!um_wait(&mbar_c, ph_c))) { failed = true; break; }
-    ph_c ^= 1u;
-    c_pending = false;
-    um_fence_after();
-    // the head tile is read: q_n of the SARK combination goes there
-    if (STAGE >= 0 && tid == 0) {
-      um_fence_async_smem();
-      um_bulk_load(sA, reinterpret_cast<const float *>(a.qn) + e0 * S, tile_bytes, &mbar_qn);
-    }
-    if (STAGE >= 0) qn_pending = true;
-
-    // ---- collision term: Ntilde at the cubature points (Sec. 2), 16 points per batch; heads in
-    //      place, tails to the slots ----
-#pragma unroll
-    for (int c0 = 0; c0 < KC; c0 += 16) {
-      constexpr int W16 = 16;
-      const int w = (KC - c0) < W16 ? (KC - c0) : W16;   // 16, or 8 in the last batch
-      uint32_t cq[3][16];
-#pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        if (w == 16) um_ld16(tl + D::T_C + f * NCM + c0, cq[f]);
-        else um_ld8(tl + D::T_C + f * NCM + c0, *reinterpret_cast<uint32_t(*)[8]>(cq[f]));
+      for (int ff = 0; ff < 3; ++ff) {
+        um_ld8(tl + D::T_V + (f0 + ff) * NV + n0, vr[ff]);
+        um_ld8(tl + D::T_V + (f0 + ff) * NV + KV + n0, vs[ff]);
       }
       um_wait_ld();
 #pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        um_regs8(cq[f]);
-        if (w == 16) um_regs8(cq[f] + 8);
+      for (int ff = 0; ff < 3; ++ff) {
+        um_regs8(vr[ff]);
+        um_regs8(vs[ff]);
       }
-      uint32_t hv[3][16], lv[3][16];
 #pragma unroll
-      for (int i = 0; i < 16; i += 2) {
-        if (i >= w) break;
-        const float2 q1 = __fadd2_rn(um_b2(1.0f), um_f2(cq[0][i], cq[0][i + 1]));
-        const float2 q2 = um_f2(cq[1][i], cq[1][i + 1]), q3 = um_f2(cq[2][i], cq[2][i + 1]);
+      for (int ff = 0; ff < 3; ++ff) {
+        const int f = f0 + ff;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          if (n0 + 2 * p >= Np) break;
+          const float2 d_r = um_f2(vr[ff][2 * p], vr[ff][2 * p + 1]), d_s = um_f2(vs[ff][2 * p], vs[ff][2 * p + 1]);
+          const float2 qx = um_fma2(G.sx, d_s, um_mul2(G.rx, d_r));
+          const float2 qy = um_fma2(G.sy, d_s, um_mul2(G.ry, d_r));
+          const float2 ale = __ffma2_rn(G.vgy2[P0 + p], qy, __fmul2_rn(G.vgx2[P0 + p], qx));
+          switch (f) {
+            case 0: rhs[0][p] = __fadd2_rn(rhs[0][p], ale); rhs[1][p] = um_fma2(mc, qx, rhs[1][p]);
+                    rhs[2][p] = um_fma2(mc, qy, rhs[2][p]); break;
+            case 1: rhs[1][p] = __fadd2_rn(rhs[1][p], ale); rhs[0][p] = um_fma2(mc, qx, rhs[0][p]);
+                    rhs[3][p] = um_fma2(mc, qy, rhs[3][p]); rhs[4][p] = um_fma2(mcs, qx, rhs[4][p]); break;
+            case 2: rhs[2][p] = __fadd2_rn(rhs[2][p], ale); rhs[0][p] = um_fma2(mc, qy, rhs[0][p]);
+                    rhs[3][p] = um_fma2(mc, qx, rhs[3][p]); rhs[5][p] = um_fma2(mcs, qy, rhs[5][p]); break;
+            case 3: rhs[3][p] = __fadd2_rn(rhs[3][p], ale); rhs[2][p] = um_fma2(mc, qx, rhs[2][p]);
+                    rhs[1][p] = um_fma2(mc, qy, rhs[1][p]); break;
+            case 4: rhs[4][p] = __fadd2_rn(rhs[4][p], ale); rhs[1][p] = um_fma2(mcs, qx, rhs[1][p]); break;
+            default: rhs[5][p] = __fadd2_rn(rhs[5][p], ale); rhs[2][p] = um_fma2(mcs, qy, rhs[2][p]); break;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+      uint32_t v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        v[i] = n0 + i < Np ? __float_as_uint((i & 1) ? rhs[f][i >> 1].y : rhs[f][i >> 1].x) : 0u;
+      um_st8(tl + D::T_R + f * 16 + n0, v);
+    }
+  }
+}
+
+// Ntilde (Sec. 2) at the cubature points of chunks [C0, C1) (8 points each), loaded in one
+// batch: heads in place, tails to the slots
+template <int N, int H>
+__device__ __forceinline__ void um_cubature(uint32_t tl, float itau) {
+  typedef UmDim<N> D;
+  constexpr int NCM = D::NCM, NCH = D::KC / 8, HALF = (NCH + 1) / 2;
+  constexpr int C0 = H ? HALF : 0, C1 = H ? NCH : HALF, NC = C1 - C0;
+  const float ISQ2 = 0.70710678118654752f;
+  if constexpr (NC > 0) {
+    uint32_t cq[3][NC][8];
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int ch = 0; ch < NC; ++ch) um_ld8(tl + D::T_C + f * NCM + 8 * (C0 + ch), cq[f][ch]);
+    um_wait_ld();
+#pragma unroll
+    for (int f = 0; f < 3; ++f)
+#pragma unroll
+      for (int ch = 0; ch < NC; ++ch) um_regs8(cq[f][ch]);
+#pragma unroll
+    for (int ch = 0; ch < NC; ++ch) {
+      uint32_t hv[3][8], lv[3][8];
+#pragma unroll
+      for (int i = 0; i < 8; i += 2) {
+        const float2 q1 = __fadd2_rn(um_b2(1.0f), um_f2(cq[0][ch][i], cq[0][ch][i + 1]));
+        const float2 q2 = um_f2(cq[1][ch][i], cq[1][ch][i + 1]), q3 = um_f2(cq[2][ch][i], cq[2][ch][i + 1]);
         const float2 r1 = um_mul2(itau, make_float2(um_rcp(q1.x), um_rcp(q1.y)));
         const float2 rs = um_mul2(ISQ2, r1);
         const float2 nv[3] = {__fmul2_rn(__fmul2_rn(q2, q3), r1), __fmul2_rn(__fmul2_rn(q2, q2), rs),
@@ -529,261 +367,644 @@ __global__ void __launch_bounds__(128, 1) um_stage_kernel(const StageArgs a) {
       }
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
-        if (w == 16) {
-          um_st16(tl + D::T_C + f * NCM + c0, hv[f]);
-        } else {
-          um_st8(tl + D::T_C + f * NCM + c0, *reinterpret_cast<uint32_t(*)[8]>(hv[f]));
-        }
-#pragma unroll
-        for (int j = 0; j < 16; j += 8)
-          if (j < w) um_st8(tl + um_slot(f * (KC / 8) + (c0 + j) / 8), *reinterpret_cast<uint32_t(*)[8]>(lv[f] + j));
+        um_st8(tl + D::T_C + f * NCM + 8 * (C0 + ch), hv[f]);
+        um_st8(tl + um_slot(f * NCH + C0 + ch), lv[f]);
       }
     }
-    um_wait_st();
-    um_fence_before();
-    __syncthreads();
+  }
+}
 
-    // ---- MMA batch 2: R_{4..6} += Ntilde P^T ----
-    if (tid == 0) {
-      um_fence_after();
-      constexpr uint32_t idR = um_idesc(16);
+// upwind F_S and F_ALE (Sec. 3) at face nodes j = f Nfp + k in [8H, 8H + 8) of the element:
+// fl[fld][j - 8H].  qm is the element's own staged row; the trace across face f comes from
+// src[f]: the neighbour's staged row or its global row (hal[f] = false: node vol2 of field
+// fld at fld Np + vol2) or a halo entry (hal[f] = true: face node k of field fld at 6 k + fld)
+template <int N, int H>
+__device__ __forceinline__ void um_flux(const UmGeo<N> &G, const float *qm, const float *const (&src)[3],
+                                        const bool (&hal)[3], const int (&f2)[3], float c, float (&fl)[6][8]) {
+  typedef UmDim<N> D;
+  constexpr int Np = D::Np, Nfp = D::Nfp, NFN = D::NFN;
+  const float SQ2 = 1.41421356237309505f;
 #pragma unroll
-      for (int f = 0; f < 3; ++f)
+  for (int fld = 0; fld < 6; ++fld)
 #pragma unroll
-        for (int ks = 0; ks < KC / 8; ++ks) {
-          const uint32_t d = tm + D::T_R + (3 + f) * 16;
-          const uint64_t bh = dBP + (uint64_t)((4 * (2 * ks * 16 * 4)) >> 4);
-          const uint64_t bl = dBP + (uint64_t)((4 * (16 * KC + 2 * ks * 16 * 4)) >> 4);
-          const uint32_t ah = tm + D::T_C + f * NCM + 8 * ks;
-          um_mma_ts(d, tm + um_slot(f * (KC / 8) + ks), bh, idR, 1u);
-          um_mma_ts(d, ah, bh, idR, 1u);
-          um_mma_ts(d, ah, bl, idR, 1u);
-        }
-      um_commit(&mbar_mma);
+    for (int jj = 0; jj < 8; ++jj) fl[fld][jj] = 0.0f;
+  // the neighbour traces of all of this half's face nodes first (one round trip)
+  float nv[8][6];
+#pragma unroll
+  for (int f = 0; f < 3; ++f)
+#pragma unroll
+    for (int k = 0; k < Nfp; ++k) {
+      const int j = f * Nfp + k;
+      if (j < 8 * H || j >= 8 * H + 8) continue;
+      const int off = hal[f] ? 6 * k : um_fmask_rt<N>(f2[f], Nfp - 1 - k), st = hal[f] ? 1 : Np;
+#pragma unroll
+      for (int fld = 0; fld < 6; ++fld) nv[j - 8 * H][fld] = src[f][off + fld * st];
     }
-    mma_pending = true;
-    __syncwarp();
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    // faces that have a node in this half
+    if (!((f + 1) * Nfp > 8 * H && f * Nfp < 8 * H + 8 && f * Nfp < NFN)) continue;
+    const float dx = G.ex[f], dy = G.ey[f];
+    const float len = sqrtf(dx * dx + dy * dy);
+    const float il = 1.0f / len;
+    const float nx = dy * il, ny = -dx * il;
+    const float fs = 0.5f * len * G.iJ;
+    const float h = 0.5f * c * fs;
+    const float al = (9.0f - 1.7320508075688772f) / 6.0f, be = (1.7320508075688772f - 3.0f) / 6.0f;
+    // |At_n| on the {1,4,5,6} block and the {2,3} block, closed form alpha At_n^2 + beta At_n^4
+    const float nn = nx * nx + ny * ny;
+    const float m00 = nn, m01 = 2.0f * nx * ny, m02 = SQ2 * nx * nx, m03 = SQ2 * ny * ny;
+    const float m12 = SQ2 * nx * ny, m22 = 2.0f * nx * nx, m33 = 2.0f * ny * ny;
+    const float q00 = m00 * m00 + m01 * m01 + m02 * m02 + m03 * m03;
+    const float q01 = m00 * m01 + m01 * m00 + m02 * m12 + m03 * m12;
+    const float q02 = m00 * m02 + m01 * m12 + m02 * m22;
+    const float q03 = m00 * m03 + m01 * m12 + m03 * m33;
+    const float q11 = m01 * m01 + m00 * m00 + m12 * m12 + m12 * m12;
+    const float q12 = m01 * m02 + m00 * m12 + m12 * m22;
+    const float q13 = m01 * m03 + m00 * m12 + m12 * m33;
+    const float q22 = m02 * m02 + m12 * m12 + m22 * m22;
+    const float q23 = m02 * m03 + m12 * m12;
+    const float q33 = m03 * m03 + m12 * m12 + m33 * m33;
+    const float M00 = h * (al * m00 + be * q00), M03 = h * (al * m01 + be * q01), M04 = h * (al * m02 + be * q02);
+    const float M05 = h * (al * m03 + be * q03), M33 = h * (al * m00 + be * q11), M34 = h * (al * m12 + be * q12);
+    const float M35 = h * (al * m12 + be * q13), M44 = h * (al * m22 + be * q22), M45 = h * (be * q23);
+    const float M55 = h * (al * m33 + be * q33);
+    const float o11 = 3.0f * nx * nx + ny * ny, o12 = 2.0f * nx * ny, o22 = nx * nx + 3.0f * ny * ny;
+    const float N11 = h * (al * o11 + be * (o11 * o11 + o12 * o12));
+    const float N12 = h * (al * o12 + be * (o11 * o12 + o12 * o22));
+    const float N22 = h * (al * o22 + be * (o12 * o12 + o22 * o22));
+    const float nhx = -h * nx, nhy = -h * ny, nsx = -h * SQ2 * nx, nsy = -h * SQ2 * ny;
+#pragma unroll
+    for (int k = 0; k < Nfp; ++k) {
+      const int j = f * Nfp + k;
+      if (j < 8 * H || j >= 8 * H + 8) continue;
+      const int vol = tc_fmask<N>(f, k), jj = j - 8 * H;
+      float w[6];
+#pragma unroll
+      for (int fld = 0; fld < 6; ++fld) w[fld] = nv[jj][fld] - qm[fld * Np + vol];
+      const float gx = (vol & 1) ? G.vgx2[vol >> 1].y : G.vgx2[vol >> 1].x;
+      const float gy = (vol & 1) ? G.vgy2[vol >> 1].y : G.vgy2[vol >> 1].x;
+      const float vn = gx * nx + gy * ny;
+      const float ale = vn > 0.0f ? vn * fs : 0.0f;
+      fl[0][jj] = ale * w[0] + M00 * w[0] + M03 * w[3] + M04 * w[4] + M05 * w[5] + nhx * w[1] + nhy * w[2];
+      fl[3][jj] = ale * w[3] + M03 * w[0] + M33 * w[3] + M34 * w[4] + M35 * w[5] + nhx * w[2] + nhy * w[1];
+      fl[4][jj] = ale * w[4] + M04 * w[0] + M34 * w[3] + M44 * w[4] + M45 * w[5] + nsx * w[1];
+      fl[5][jj] = ale * w[5] + M05 * w[0] + M35 * w[3] + M45 * w[4] + M55 * w[5] + nsy * w[2];
+      fl[1][jj] = ale * w[1] + N11 * w[1] + N12 * w[2] + nhx * w[0] + nsx * w[4] + nhy * w[3];
+      fl[2][jj] = ale * w[2] + N12 * w[1] + N22 * w[2] + nhy * w[0] + nsy * w[5] + nhx * w[3];
+    }
+  }
+}
 
-    // ---- surface: upwind F_S and F_ALE per face node (Sec. 3), the fluxes in registers ----
-    float flux[6][KL];
+template <int N, int H>
+__device__ __forceinline__ void um_flux_store(uint32_t tl, const float (&fl)[6][8]) {
+  typedef UmDim<N> D;
+  constexpr int KL = D::KL;
+  if constexpr (8 * H < KL) {
 #pragma unroll
-    for (int f = 0; f < 6; ++f)
+    for (int f = 0; f < 6; ++f) {
+      uint32_t hv[8], lv[8];
 #pragma unroll
-      for (int j = 0; j < KL; ++j) flux[f][j] = 0.0f;
-    if (live) {
-      const float *qm = sRaw + tid * S;
-#pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        const int nb = rec.nbr[f];
-        const int64_t nbe = nb >> 2;
-        const int f2 = nb & 3;
-        const float *qp = (nbe >= e0 && nbe < e0 + nel) ? sRaw + (nbe - e0) * S : qin + nbe * S;
-        const float dx = ex[f], dy = ey[f];
-        const float len = sqrtf(dx * dx + dy * dy);
-        const float il = 1.0f / len;
-        const float nx = dy * il, ny = -dx * il;
-        const float fs = 0.5f * len * iJ;
-        const float h = 0.5f * c * fs;
-        const float al = (9.0f - 1.7320508075688772f) / 6.0f, be = (1.7320508075688772f - 3.0f) / 6.0f;
-        // |At_n| on the {1,4,5,6} block and the {2,3} block, closed form alpha At_n^2 + beta At_n^4
-        const float nn = nx * nx + ny * ny;
-        const float m00 = nn, m01 = 2.0f * nx * ny, m02 = SQ2 * nx * nx, m03 = SQ2 * ny * ny;
-        const float m12 = SQ2 * nx * ny, m22 = 2.0f * nx * nx, m33 = 2.0f * ny * ny;
-        const float q00 = m00 * m00 + m01 * m01 + m02 * m02 + m03 * m03;
-        const float q01 = m00 * m01 + m01 * m00 + m02 * m12 + m03 * m12;
-        const float q02 = m00 * m02 + m01 * m12 + m02 * m22;
-        const float q03 = m00 * m03 + m01 * m12 + m03 * m33;
-        const float q11 = m01 * m01 + m00 * m00 + m12 * m12 + m12 * m12;
-        const float q12 = m01 * m02 + m00 * m12 + m12 * m22;
-        const float q13 = m01 * m03 + m00 * m12 + m12 * m33;
-        const float q22 = m02 * m02 + m12 * m12 + m22 * m22;
-        const float q23 = m02 * m03 + m12 * m12;
-        const float q33 = m03 * m03 + m12 * m12 + m33 * m33;
-        const float M00 = h * (al * m00 + be * q00), M03 = h * (al * m01 + be * q01), M04 = h * (al * m02 + be * q02);
-        const float M05 = h * (al * m03 + be * q03), M33 = h * (al * m00 + be * q11), M34 = h * (al * m12 + be * q12);
-        const float M35 = h * (al * m12 + be * q13), M44 = h * (al * m22 + be * q22), M45 = h * (be * q23);
-        const float M55 = h * (al * m33 + be * q33);
-        const float o11 = 3.0f * nx * nx + ny * ny, o12 = 2.0f * nx * ny, o22 = nx * nx + 3.0f * ny * ny;
-        const float N11 = h * (al * o11 + be * (o11 * o11 + o12 * o12));
-        const float N12 = h * (al * o12 + be * (o11 * o12 + o12 * o22));
-        const float N22 = h * (al * o22 + be * (o12 * o12 + o22 * o22));
-        const float nhx = -h * nx, nhy = -h * ny, nsx = -h * SQ2 * nx, nsy = -h * SQ2 * ny;
-#pragma unroll
-        for (int k = 0; k < Nfp; ++k) {
-          const int vol = tc_fmask<N>(f, k), vol2 = um_fmask_rt<N>(f2, Nfp - 1 - k);
-          float w[6];
-#pragma unroll
-          for (int fld = 0; fld < 6; ++fld) w[fld] = qp[fld * Np + vol2] - qm[fld * Np + vol];
-          const float gx = (vol & 1) ? vgx2[vol >> 1].y : vgx2[vol >> 1].x;
-          const float gy = (vol & 1) ? vgy2[vol >> 1].y : vgy2[vol >> 1].x;
-          const float vn = gx * nx + gy * ny;
-          const float ale = vn > 0.0f ? vn * fs : 0.0f;
-          const int j = f * Nfp + k;
-          flux[0][j] = ale * w[0] + M00 * w[0] + M03 * w[3] + M04 * w[4] + M05 * w[5] + nhx * w[1] + nhy * w[2];
-          flux[3][j] = ale * w[3] + M03 * w[0] + M33 * w[3] + M34 * w[4] + M35 * w[5] + nhx * w[2] + nhy * w[1];
-          flux[4][j] = ale * w[4] + M04 * w[0] + M34 * w[3] + M44 * w[4] + M45 * w[5] + nsx * w[1];
-          flux[5][j] = ale * w[5] + M05 * w[0] + M35 * w[3] + M45 * w[4] + M55 * w[5] + nsy * w[2];
-          flux[1][j] = ale * w[1] + N11 * w[1] + N12 * w[2] + nhx * w[0] + nsx * w[4] + nhy * w[3];
-          flux[2][j] = ale * w[2] + N12 * w[1] + N22 * w[2] + nhy * w[0] + nsy * w[5] + nhx * w[3];
-        }
+      for (int i = 0; i < 8; ++i) {
+        const float x = fl[f][i], t = um_tf32(x);
+        hv[i] = __float_as_uint(t);
+        lv[i] = __float_as_uint(x - t);
       }
+      um_st8(tl + D::T_FH + f * KL + 8 * H, hv);
+      um_st8(tl + D::T_FL + f * KL + 8 * H, lv);
     }
+  }
+}
 
-    if (__syncthreads_or(!um_wait(&mbar_mma, ph_mma))) { failed = true; break; }
-    ph_mma ^= 1u;
-    mma_pending = false;
-    um_fence_after();
-    // every thread is past its flux reads of sRaw: prefetch the next tile's own fields there
-    if (tid == 0 && tile + gridDim.x < ntile) {
-      um_fence_async_smem();
-      const int64_t tn = tile + gridDim.x;
-      um_bulk_load(sRaw, qin + tn * 128 * S, (uint32_t)(tile_rows(tn) * S * sizeof(float)), &mbar_ld);
+// SARK combination (Sec. 4) of row chunks [J0, J1) of the element, in the staged rows
+template <int N, int STAGE, int H>
+__device__ __forceinline__ void um_sark(uint32_t tl, float4 *rowq, float4 *row1, float4 *row2, const float (&k0)[5],
+                                        const float (&k1)[5], float dt, bool &bad) {
+  typedef UmDim<N> D;
+  constexpr int Np = D::Np, S4 = D::S4, HALF = (S4 + 1) / 2;
+  constexpr int J0 = H ? HALF : 0, J1 = H ? S4 : HALF;
+  constexpr int FA = (4 * J0) / Np, FB = ((4 * J1 - 1) / Np < 5 ? (4 * J1 - 1) / Np : 5);   // fields touched
+  uint32_t rr[FB - FA + 1][16];
+#pragma unroll
+  for (int f = FA; f <= FB; ++f) um_ld16(tl + D::T_R + f * 16, rr[f - FA]);
+  um_wait_ld();
+#pragma unroll
+  for (int f = FA; f <= FB; ++f) {
+    um_regs8(rr[f - FA]);
+    um_regs8(rr[f - FA] + 8);
+  }
+#pragma unroll
+  for (int j = J0; j < J1; ++j) {
+    float r_[4], qv[4] = {0.f, 0.f, 0.f, 0.f}, f0[4] = {0.f, 0.f, 0.f, 0.f}, av[4] = {0.f, 0.f, 0.f, 0.f}, o[4], o2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int w = 4 * j + i;
+      r_[i] = w < 6 * Np ? __uint_as_float(rr[w / Np - FA][w % Np]) : 0.0f;
     }
-    if (tile + gridDim.x < ntile) ld_pending = true;
-#pragma unroll
-    for (int f = 0; f < 6; ++f)
-#pragma unroll
-      for (int j = 0; j < KL; j += 8) {
-        uint32_t hv[8], lv[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const float x = flux[f][j + i], t = um_tf32(x);
-          hv[i] = __float_as_uint(t);
-          lv[i] = __float_as_uint(x - t);
-        }
-        um_st8(tl + D::T_FH + f * KL + j, hv);
-        um_st8(tl + D::T_FL + f * KL + j, lv);
-      }
-    um_wait_st();
-    um_fence_before();
-    __syncthreads();
-
-    // ---- MMA batch 3: R += Flux LIFT^T ----
-    if (tid == 0) {
-      um_fence_after();
-      constexpr uint32_t idR = um_idesc(16);
-#pragma unroll
-      for (int f = 0; f < 6; ++f)
-#pragma unroll
-        for (int ks = 0; ks < KL / 8; ++ks) {
-          const uint32_t d = tm + D::T_R + f * 16;
-          const uint64_t bh = dBL + (uint64_t)((4 * (2 * ks * 16 * 4)) >> 4);
-          const uint64_t bl = dBL + (uint64_t)((4 * (16 * KL + 2 * ks * 16 * 4)) >> 4);
-          const uint32_t ah = tm + D::T_FH + f * KL + 8 * ks;
-          um_mma_ts(d, tm + D::T_FL + f * KL + 8 * ks, bh, idR, 1u);
-          um_mma_ts(d, ah, bh, idR, 1u);
-          um_mma_ts(d, ah, bl, idR, 1u);
-        }
-      um_commit(&mbar_mma);
-    }
-    mma_pending = true;
-    __syncwarp();
-    if (__syncthreads_or(!um_wait(&mbar_mma, ph_mma))) { failed = true; break; }
-    ph_mma ^= 1u;
-    mma_pending = false;
-    um_fence_after();
     if (STAGE >= 0) {
-      bool okx = true;
-      if (STAGE >= 1) okx = um_wait(&mbar_x, ph_x);
-      okx = okx && um_wait(&mbar_qn, ph_qn);
-      if (__syncthreads_or(!okx)) { failed = true; break; }
-      if (STAGE >= 1) ph_x ^= 1u;
-      ph_qn ^= 1u;
-      x_pending = qn_pending = false;
+      const float4 x = rowq[j];
+      qv[0] = x.x; qv[1] = x.y; qv[2] = x.z; qv[3] = x.w;
     }
-
-    // ---- SARK combination (Sec. 4) for this thread's element, in the staged rows ----
-    {
-      uint32_t rr[6][16];
+    if (STAGE == 1 || STAGE == 2) {
+      const float4 x = row1[j];
+      f0[0] = x.x; f0[1] = x.y; f0[2] = x.z; f0[3] = x.w;
+    }
+    if (STAGE >= 2) {
+      const float4 x = row2[j];
+      av[0] = x.x; av[1] = x.y; av[2] = x.z; av[3] = x.w;
+    }
 #pragma unroll
-      for (int f = 0; f < 6; ++f) um_ld16(tl + D::T_R + f * 16, rr[f]);
-      um_wait_ld();
-#pragma unroll
-      for (int f = 0; f < 6; ++f) {
-        um_regs8(rr[f]);
-        um_regs8(rr[f] + 8);
+    for (int i = 0; i < 4; ++i) {
+      const int w = 4 * j + i;
+      const float *k = w < 3 * Np ? k0 : k1;   // E, A_a, A_b, B_a, B_b of the field class
+      o2[i] = 0.0f;
+      if (STAGE < 0) {
+        o[i] = r_[i];
+      } else if (STAGE == 0) {
+        o2[i] = r_[i];
+        o[i] = dt * (k[1] * r_[i]) + k[0] * qv[i];
+      } else if (STAGE == 1) {
+        o[i] = dt * (k[2] * r_[i] + k[1] * f0[i]) + k[0] * qv[i];
+        o2[i] = k[4] * r_[i] + k[3] * f0[i];
+      } else if (STAGE == 2) {
+        o[i] = dt * (k[2] * r_[i] + k[1] * f0[i]) + k[0] * qv[i];
+        o2[i] = k[3] * r_[i] + av[i];
+      } else {
+        o[i] = dt * (k[3] * r_[i] + av[i]) + k[0] * qv[i];
+        if (w < 6 * Np) bad |= (__float_as_int(o[i]) & 0x7f800000) == 0x7f800000;
       }
-      float4 *rowq = reinterpret_cast<float4 *>(sA + tid * S);
-      float4 *row1 = reinterpret_cast<float4 *>(sX1 + tid * S);
-      float4 *row2 = reinterpret_cast<float4 *>(sX2 + tid * S);
-      const float E1[2] = {a.kco[0][0], a.kco[1][0]}, A0[2] = {a.kco[0][1], a.kco[1][1]};
-      const float A1[2] = {a.kco[0][2], a.kco[1][2]}, Bc[2] = {a.kco[0][3], a.kco[1][3]};
-      const float B1[2] = {a.kco[0][4], a.kco[1][4]};
-      if (live) {
+    }
+    rowq[j] = make_float4(o[0], o[1], o[2], o[3]);
+    if (STAGE == 0 || STAGE == 1) row1[j] = make_float4(o2[0], o2[1], o2[2], o2[3]);
+    if (STAGE == 2) row2[j] = make_float4(o2[0], o2[1], o2[2], o2[3]);
+  }
+}
+
+// Shared-memory buffers of a tile (element-major rows of stride S unless noted):
+//   sA    the head tile of the own fields (core-matrix layout) for the first MMA batch;
+//         afterwards q_n, then q_{i+1} (or F in the rhs-only mode), stored back by a bulk copy
+//   sRaw  the own fields q_i (neighbour traces and q^- of the flux); the next tile's q_i is
+//         prefetched into it once this tile's fluxes are formed
+//   sX1   F_0 (read at stages 1-2; written at stage 0; the accumulator written at stage 1)
+//   sX2   the btilde accumulator (read at stages 2-3, written at stage 2)
+//   sG    the geometry of the tile's elements, formed by the helper warps one tile ahead
+//   sH    the halo of the tile's out-of-tile neighbour traces, staged one tile ahead
+// Warps 0-7 compute (two threads per element: thread t handles element t % 128 and half
+// t / 128 of each phase's nodes, points, face nodes or row chunks).  Warps 8-11 are helpers:
+// thread 256 + i forms the geometry of element i of the next tile while the current one is
+// computed, the helpers stage the traces across the next tile's out-of-tile faces (a halo
+// of up to HMAX faces; a Morton tile of 128 triangles has about 32), and lane 0 of each
+// helper warp issues a share of every MMA batch (the products of whole fields, so that each
+// accumulator has one issuing thread and a fixed order); warp 8 also issues the bulk copies.  Hand-offs are mbarriers, one phase per tile each: the
+// copies and MMA commits complete the "data" barriers, the compute threads arrive on the
+// "operands ready" ones.
+constexpr int kUmThreads = 384;
+constexpr int kUmIssuers = 4;
+
+// the element's geometry at the stage (Sec. 5) into its row of the geometry buffer; a face
+// whose neighbour lies outside the tile [t0e, t0e + nel) gets a halo slot from the shared
+// counter while slots last (code -(slot + 1) in the row, the neighbour code in hsrc[slot]);
+// the other faces keep the neighbour code (element << 2 | face)
+template <int N>
+__device__ __forceinline__ void um_geometry(const StageArgs &a, int64_t e, bool live, int64_t t0e, int nel, float xff,
+                                            float gff, float *g, int *hcount, int *hsrc) {
+  const MeshRec rec = a.mesh[e];
+  double bx[3], by[3];
+  float ix[3], iy[3], vx[3], vy[3], ex[3], ey[3];
 #pragma unroll
-        for (int j = 0; j < S4; ++j) {
-          float r_[4], qv[4], f0[4], av[4], o[4], o2[4];
+  for (int k = 0; k < 3; ++k) {
+    const double2 xv = reinterpret_cast<const double2 *>(a.xn)[rec.v[k]];
+    const double2 sv = reinterpret_cast<const double2 *>(a.shape)[rec.v[k]];
+    bx[k] = xv.x + rec.shift[2 * k] * a.period[0];
+    by[k] = xv.y + rec.shift[2 * k + 1] * a.period[1];
+    const float sxk = (float)sv.x, syk = (float)sv.y;
+    ix[k] = xff * sxk;
+    iy[k] = xff * syk;
+    vx[k] = gff * sxk;
+    vy[k] = gff * syk;
+  }
+  // FP64 vertex positions and edge differences, the small stage increments in FP32
+  ex[0] = (float)(bx[1] - bx[0]) + (ix[1] - ix[0]); ey[0] = (float)(by[1] - by[0]) + (iy[1] - iy[0]);
+  ex[1] = (float)(bx[2] - bx[1]) + (ix[2] - ix[1]); ey[1] = (float)(by[2] - by[1]) + (iy[2] - iy[1]);
+  ex[2] = (float)(bx[0] - bx[2]) + (ix[0] - ix[2]); ey[2] = (float)(by[0] - by[2]) + (iy[0] - iy[2]);
+  const float xr = 0.5f * ex[0], yr = 0.5f * ey[0], xs = -0.5f * ex[2], ys = -0.5f * ey[2];
+  const float J = xr * ys - xs * yr;
+  if (live && !(J > 0.0f)) atomicOr(a.status, GB_STATUS_MESH);
+  const float iJ = 1.0f / J;
+  int code[3];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int w = 4 * j + i;
-            r_[i] = w < 6 * Np ? __uint_as_float(rr[w / Np][w % Np]) : 0.0f;
-          }
-          if (STAGE >= 0) {
-            const float4 x = rowq[j];
-            qv[0] = x.x; qv[1] = x.y; qv[2] = x.z; qv[3] = x.w;
-          }
-          if (STAGE == 1 || STAGE == 2) {
-            const float4 x = row1[j];
-            f0[0] = x.x; f0[1] = x.y; f0[2] = x.z; f0[3] = x.w;
-          }
-          if (STAGE >= 2) {
-            const float4 x = row2[j];
-            av[0] = x.x; av[1] = x.y; av[2] = x.z; av[3] = x.w;
-          }
+  for (int f = 0; f < 3; ++f) {
+    const int nb = rec.nbr[f];
+    const int64_t nbe = nb >> 2;
+    code[f] = nb;
+    if (live && !(nbe >= t0e && nbe < t0e + nel)) {
+      const int sl = atomicAdd(hcount, 1);
+      if (sl < UmDim<N>::HMAX) {
+        hsrc[sl] = nb;
+        code[f] = -(sl + 1);
+      }
+    }
+  }
+  float4 *g4 = reinterpret_cast<float4 *>(g);
+  g4[0] = make_float4(ys * iJ, -yr * iJ, -xs * iJ, xr * iJ);
+  g4[1] = make_float4(iJ, ex[0], ex[1], ex[2]);
+  g4[2] = make_float4(ey[0], ey[1], ey[2], vx[0]);
+  g4[3] = make_float4(vx[1], vx[2], vy[0], vy[1]);
+  g4[4] = make_float4(vy[2], __int_as_float(code[0]), __int_as_float(code[1]), __int_as_float(code[2]));
+}
+
+// the halo: the traces across the out-of-tile faces listed in hsrc[0, cnt), entry s holding
+// the neighbour's values at this side's face nodes k (field fld at 6 k + fld); helper thread
+// hi takes entries hi, hi + 128, ...
+template <int N>
+__device__ __forceinline__ void um_halo(const float *qin, const int *hsrc, int cnt, int hi, float *halo) {
+  typedef UmDim<N> D;
+  constexpr int Np = D::Np, Nfp = D::Nfp, S = D::S, HW = D::HW;
+  for (int sl = hi; sl < cnt; sl += 128) {
+    const int nb = hsrc[sl];
+    const float *qp = qin + (int64_t)(nb >> 2) * S;
+    const int f2 = nb & 3;
+    float v[HW];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            const int w = 4 * j + i, cl = w < 3 * Np ? 0 : 1;
-            o2[i] = 0.0f;
-            if (STAGE < 0) {
-              o[i] = r_[i];
-            } else if (STAGE == 0) {
-              o2[i] = r_[i];
-              o[i] = dt * (A0[cl] * r_[i]) + E1[cl] * qv[i];
-            } else if (STAGE == 1) {
-              o[i] = dt * (A1[cl] * r_[i] + A0[cl] * f0[i]) + E1[cl] * qv[i];
-              o2[i] = B1[cl] * r_[i] + Bc[cl] * f0[i];
-            } else if (STAGE == 2) {
-              o[i] = dt * (A1[cl] * r_[i] + A0[cl] * f0[i]) + E1[cl] * qv[i];
-              o2[i] = Bc[cl] * r_[i] + av[i];
-            } else {
-              o[i] = dt * (Bc[cl] * r_[i] + av[i]) + E1[cl] * qv[i];
-              if (w < 6 * Np) bad |= (__float_as_int(o[i]) & 0x7f800000) == 0x7f800000;
+    for (int k = 0; k < Nfp; ++k) {
+      const int vol2 = um_fmask_rt<N>(f2, Nfp - 1 - k);
+#pragma unroll
+      for (int fld = 0; fld < 6; ++fld) v[6 * k + fld] = qp[fld * Np + vol2];
+    }
+#pragma unroll
+    for (int i = 0; i < HW; ++i) halo[sl * HW + i] = v[i];
+  }
+}
+
+template <int N, int STAGE>
+__global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs a) {
+  typedef UmDim<N> D;
+  constexpr int S = D::S, NPP = D::NPP, KV = D::KV, GW = D::GW;
+  constexpr int NV = D::NV, NCM = D::NCM, KC = D::KC, KL = D::KL;
+  constexpr int NP2 = UmGeo<N>::NP2;
+  const float SQ2 = 1.41421356237309505f;
+  extern __shared__ __align__(1024) float um_smem[];
+  float *sA = um_smem + D::SM_A;
+  float *sRaw = um_smem + D::SM_RAW;
+  float *sX1 = um_smem + D::SM_X1;
+  float *sX2 = um_smem + D::SM_X2;
+  float *sB = um_smem + D::SM_B;
+  float *sG = um_smem + D::SM_G;
+  float *sH = um_smem + D::SM_H;
+  __shared__ int s_hcount, s_hsrc[D::HMAX];   // halo entries of the next tile and their neighbours
+  // data: q_i, F_0/accumulator, q_n loaded; shared tile free (the previous stores have read
+  // it); volume, interpolation, projection, lift products done (one commit per issuer);
+  // geometry and halo of the tile formed (128 helper threads each)
+  __shared__ __align__(8) uint64_t mb_ld, mb_x, mb_qn, mb_free, mb_v, mb_c, mb_p, mb_l, mb_geo, mb_halo;
+  // operands ready (256 compute threads): heads and tails; geometry read; R and Ntilde;
+  // fluxes; output rows
+  __shared__ __align__(8) uint64_t mb_opA, mb_gread, mb_opN, mb_opF, mb_out;
+  __shared__ uint32_t s_tmem;
+  __shared__ double s_motion[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const float *qin = reinterpret_cast<const float *>(a.qin);
+  const int64_t ntile = (a.K + 127) >> 7;
+  auto tile_rows = [&](int64_t t_) { return (int)((a.K - t_ * 128) < 128 ? (a.K - t_ * 128) : 128); };
+
+  for (int i = tid; i < D::BTOT; i += kUmThreads) sB[i] = a.ops_um[i];
+  if (tid == 0) {
+    double gf, xf, fin;
+    tc_stage_motion<STAGE>(a, gf, xf, fin);
+    s_motion[0] = gf;
+    s_motion[1] = xf;
+    if (STAGE == 3 && blockIdx.x == 0) const_cast<double *>(a.clock)[1] = fin;
+    uint64_t *one[4] = {&mb_ld, &mb_x, &mb_qn, &mb_free};
+    for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(um_sa(one[i])) : "memory");
+    uint64_t *iss[4] = {&mb_v, &mb_c, &mb_p, &mb_l};
+    for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(um_sa(iss[i])), "r"(kUmIssuers) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(um_sa(&mb_geo)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(um_sa(&mb_halo)) : "memory");
+    s_hcount = 0;
+    uint64_t *many[5] = {&mb_opA, &mb_gread, &mb_opN, &mb_opF, &mb_out};
+    for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" :: "r"(um_sa(many[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(um_sa(&s_tmem)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  um_fence_async_smem();
+  um_fence_before();
+  __syncthreads();
+  um_fence_after();
+  const uint32_t tm = s_tmem;
+  const float gff = (float)s_motion[0], xff = (float)s_motion[1];
+  bool failed = false;
+
+  if (warp >= 8) {
+    // ================= helpers: geometry one tile ahead, MMA issue, bulk copies =================
+    const int hi = tid - 256, iw = warp - 8;   // element of the next tile, issuer index
+    const bool issuer = lane == 0, copier = tid == 256;
+    const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
+    // descriptors at the operands' bases; an operand at byte offset o has descriptor base + o / 16
+    const uint64_t dA = um_desc(sA_a, 2048, 128);
+    const uint64_t dBV = um_desc(sB_a + 4 * D::BV, NV * 16, 128), dBI = um_desc(sB_a + 4 * D::BI, NCM * 16, 128);
+    const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
+    constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(NCM), idR = um_idesc(16);
+    unsigned armed = 0;   // mbarriers with a phase in flight from this thread (teardown)
+    uint32_t ld_par = 0;  // parity of the armed phase of mb_ld
+    if ((int64_t)blockIdx.x < ntile) {
+      if (copier) {
+        um_bulk_load(sRaw, qin + (int64_t)blockIdx.x * 128 * S, (uint32_t)(tile_rows(blockIdx.x) * S * sizeof(float)), &mb_ld);
+        armed |= 1u;
+      }
+      const int64_t t0 = blockIdx.x, r0 = a.K - t0 * 128;
+      um_geometry<N>(a, t0 * 128 + (hi < r0 ? hi : 0), hi < r0, t0 * 128, tile_rows(t0), xff, gff, sG + hi * GW,
+                     &s_hcount, s_hsrc);
+      um_arrive(&mb_geo);
+      asm volatile("bar.sync 1, 128;" ::: "memory");
+      um_halo<N>(qin, s_hsrc, s_hcount < D::HMAX ? s_hcount : D::HMAX, hi, sH);
+      um_arrive(&mb_halo);
+    }
+    // the MMAs of one field: K / 8 k-steps of the three split products into accumulator d
+    auto mma_field = [&](uint32_t d, uint32_t a_lo, uint64_t a_hi_s, uint32_t a_hi_t, bool hi_in_tmem, uint64_t bh,
+                         uint64_t bl, uint64_t b_step, uint32_t id, int ksteps, uint32_t a_step_t, uint64_t a_step_s,
+                         bool first_overwrites) {
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const uint64_t b0 = bh + ks * b_step, b1 = bl + ks * b_step;
+        um_mma_ts(d, a_lo + ks * a_step_t, b0, id, (first_overwrites && ks == 0) ? 0u : 1u);
+        if (hi_in_tmem) {
+          um_mma_ts(d, a_hi_t + ks * a_step_t, b0, id, 1u);
+          um_mma_ts(d, a_hi_t + ks * a_step_t, b1, id, 1u);
+        } else {
+          um_mma_ss(d, a_hi_s + ks * a_step_s, b0, id, 1u);
+          um_mma_ss(d, a_hi_s + ks * a_step_s, b1, id, 1u);
+        }
+      }
+    };
+    // A failed (timed-out) wait does not leave the loop at once: the helpers meet at named
+    // barriers, so the rest of the iteration is skipped and they leave together at its end.
+    uint32_t par = 0;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x, par ^= 1u) {
+      const int64_t e0 = tile * 128;
+      const uint32_t tile_bytes = (uint32_t)(tile_rows(tile) * S * sizeof(float));
+      const bool more = tile + gridDim.x < ntile;
+      if (copier) {
+        // the previous tile's stores have read the shared tile and the staged rows
+        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        um_arrive(&mb_free);
+        if (STAGE >= 1) {
+          uint32_t bytes = 0;
+          if (STAGE == 1 || STAGE == 2) bytes += tile_bytes;
+          if (STAGE >= 2) bytes += tile_bytes;
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(um_sa(&mb_x)), "r"(bytes) : "memory");
+          if (STAGE == 1 || STAGE == 2)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(um_sa(sX1)), "l"(reinterpret_cast<const float *>(a.F0) + e0 * S), "r"(tile_bytes),
+                            "r"(um_sa(&mb_x)) : "memory");
+          if (STAGE >= 2)
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(um_sa(sX2)), "l"(reinterpret_cast<const float *>(a.acc) + e0 * S), "r"(tile_bytes),
+                            "r"(um_sa(&mb_x)) : "memory");
+          armed |= 2u;
+        }
+      }
+      // ---- batch 1: volume products of fields {iw, iw + 4}, interpolation of a field ----
+      if (issuer && !failed) {
+        if (!um_wait(&mb_opA, par)) {
+          failed = true;
+        } else {
+          um_fence_after();
+          for (int f = iw; f < 6; f += 4)
+            mma_field(tm + D::T_V + f * NV, tm + D::T_QL + f * KV, dA + (uint64_t)(((f * NPP / 4) * 2048) >> 4), 0u,
+                      false, dBV, dBV + (uint64_t)((4 * NV * KV) >> 4), (uint64_t)((4 * 2 * NV * 4) >> 4), idV, KV / 8,
+                      8u, (uint64_t)((2 * 2048) >> 4), true);
+          um_commit(&mb_v);
+          const int fc = iw == 0 ? 2 : (iw == 2 ? 0 : (iw == 3 ? 1 : -1));
+          if (fc >= 0)
+            mma_field(tm + D::T_C + fc * NCM, tm + D::T_QL + fc * KV, dA + (uint64_t)(((fc * NPP / 4) * 2048) >> 4), 0u,
+                      false, dBI, dBI + (uint64_t)((4 * NCM * KV) >> 4), (uint64_t)((4 * 2 * NCM * 4) >> 4), idC, KV / 8,
+                      8u, (uint64_t)((2 * 2048) >> 4), true);
+          um_commit(&mb_c);
+          armed |= 8u | 16u;
+        }
+      }
+      // ---- q_n into the shared tile once the first batch has read it ----
+      if (copier && STAGE >= 0 && !failed) {
+        if (!um_wait(&mb_c, par)) {
+          failed = true;
+        } else {
+          um_bulk_load(sA, reinterpret_cast<const float *>(a.qn) + e0 * S, tile_bytes, &mb_qn);
+          armed |= 4u;
+        }
+      }
+      // ---- the next tile's geometry and halo slots, once the compute threads have read this
+      //      tile's geometry ----
+      if (more) {
+        if (!failed && !um_wait(&mb_gread, par)) failed = true;
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // this tile's halo entries are all staged
+        if (hi == 0) s_hcount = 0;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (!failed) {
+          const int64_t tn = tile + gridDim.x, rn = a.K - tn * 128;
+          um_geometry<N>(a, tn * 128 + (hi < rn ? hi : 0), hi < rn, tn * 128, tile_rows(tn), xff, gff, sG + hi * GW,
+                         &s_hcount, s_hsrc);
+          um_arrive(&mb_geo);
+        }
+      }
+      // ---- batch 2: R_{4..6} += Ntilde P^T, field iw ----
+      if (issuer && !failed) {
+        if (!um_wait(&mb_opN, par)) {
+          failed = true;
+        } else {
+          um_fence_after();
+          if (iw < 3) {
+            // the tails sit in 8-column slots that are not contiguous across k-steps
+            const uint32_t d = tm + D::T_R + (3 + iw) * 16;
+#pragma unroll
+            for (int ks = 0; ks < KC / 8; ++ks) {
+              const uint64_t b0 = dBP + (uint64_t)((4 * 2 * ks * 16 * 4) >> 4);
+              const uint64_t b1 = dBP + (uint64_t)((4 * (16 * KC + 2 * ks * 16 * 4)) >> 4);
+              const uint32_t ah = tm + D::T_C + iw * NCM + 8 * ks;
+              um_mma_ts(d, tm + um_slot(iw * (KC / 8) + ks), b0, idR, 1u);
+              um_mma_ts(d, ah, b0, idR, 1u);
+              um_mma_ts(d, ah, b1, idR, 1u);
             }
           }
-          rowq[j] = make_float4(o[0], o[1], o[2], o[3]);
-          if (STAGE == 0 || STAGE == 1) row1[j] = make_float4(o2[0], o2[1], o2[2], o2[3]);
-          if (STAGE == 2) row2[j] = make_float4(o2[0], o2[1], o2[2], o2[3]);
+          um_commit(&mb_p);
+          armed |= 32u;
         }
       }
+      // ---- batch 3: R += Flux LIFT^T, fields {iw, iw + 4}; then the next tile's own fields ----
+      if (issuer && !failed) {
+        if (!um_wait(&mb_opF, par)) {
+          failed = true;
+        } else {
+          um_fence_after();
+          for (int f = iw; f < 6; f += 4)
+            mma_field(tm + D::T_R + f * 16, tm + D::T_FL + f * KL, 0, tm + D::T_FH + f * KL, true, dBL,
+                      dBL + (uint64_t)((4 * 16 * KL) >> 4), (uint64_t)((4 * 2 * 16 * 4) >> 4), idR, KL / 8, 8u, 0, false);
+          um_commit(&mb_l);
+          armed |= 64u;
+          if (copier && more) {
+            const int64_t tn = tile + gridDim.x;
+            um_fence_async_smem();
+            um_bulk_load(sRaw, qin + tn * 128 * S, (uint32_t)(tile_rows(tn) * S * sizeof(float)), &mb_ld);
+            ld_par = par ^ 1u;
+          }
+        }
+      }
+      // ---- the next tile's halo, once this tile's fluxes have read the current one ----
+      if (more) {
+        if (!failed && !um_wait(&mb_opF, par)) failed = true;
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // the next tile's slots are all assigned
+        if (!failed) {
+          um_halo<N>(qin, s_hsrc, s_hcount < D::HMAX ? s_hcount : D::HMAX, hi, sH);
+          um_arrive(&mb_halo);
+        }
+      }
+      // ---- stores of the output rows ----
+      if (copier && !failed) {
+        if (!um_wait(&mb_out, par)) {
+          failed = true;
+        } else {
+          auto store = [&](void *dst, const float *src) {
+            asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                         :: "l"(reinterpret_cast<float *>(dst) + e0 * S), "r"(um_sa(src)), "r"(tile_bytes) : "memory");
+          };
+          store(STAGE < 0 ? a.Fout : a.qout, sA);
+          if (STAGE == 0) store(a.F0, sX1);
+          if (STAGE == 1) store(a.acc, sX1);
+          if (STAGE == 2) store(a.acc, sX2);
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+      }
+      // all helpers leave together if any of them saw a wait run out
+      {
+        uint32_t any;
+        asm volatile("{\n\t.reg .pred pi, po;\n\tsetp.ne.u32 pi, %1, 0;\n\tbar.red.or.pred po, 1, 128, pi;\n\t"
+                     "selp.u32 %0, 1, 0, po;\n\t}" : "=r"(any) : "r"((uint32_t)failed) : "memory");
+        if (any) {
+          failed = true;
+          break;
+        }
+      }
+      armed = (copier && more) ? 1u : 0u;   // the other phases of this tile are complete
     }
-    // the rows are complete: bulk stores of the tile's outputs
-    um_fence_async_smem();
-    um_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      auto store = [&](void *dst, const float *src) {
-        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
-                     :: "l"(reinterpret_cast<float *>(dst) + e0 * S), "r"(um_sa(src)), "r"(tile_bytes) : "memory");
-      };
-      store(STAGE < 0 ? a.Fout : a.qout, sA);
-      if (STAGE == 0) store(a.F0, sX1);
-      if (STAGE == 1) store(a.acc, sX1);
-      if (STAGE == 2) store(a.acc, sX2);
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    if (failed) {
+      // wait (bounded) for everything this thread started in the current phase
+      uint64_t *bars[7] = {&mb_ld, &mb_x, &mb_qn, &mb_v, &mb_c, &mb_p, &mb_l};   // bulk copies and MMA commits
+      for (int i = 0; i < 7; ++i)
+        if (armed & (1u << i)) um_wait(bars[i], i == 0 ? ld_par : par);
+      atomicOr(a.status, GB_STATUS_TIMEOUT);
     }
+    if (copier) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+  } else {
+    // ================= compute: warps 0-7 =================
+    const int el = tid & 127, h = tid >> 7;
+    const uint32_t tl = tm + ((uint32_t)(32 * (warp & 3)) << 16);   // this warp's 32 lanes
+    const float c = (float)a.c, mc = -(float)a.c, mcs = -(float)a.c * SQ2, itau = (float)a.inv_tau;
+    const float *bar = sB + D::BBAR;
+    const float dt = (float)a.dt;
+    const float k0[5] = {a.kco[0][0], a.kco[0][1], a.kco[0][2], a.kco[0][3], a.kco[0][4]};
+    const float k1[5] = {a.kco[1][0], a.kco[1][1], a.kco[1][2], a.kco[1][3], a.kco[1][4]};
+    bool bad = false;
+    uint32_t par = 0;
+    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x, par ^= 1u) {
+      const int64_t e0 = tile * 128;
+      const int nel = tile_rows(tile);
+      const bool live = el < nel;
+      if (!__all_sync(0xffffffffu, um_wait(&mb_ld, par) && um_wait(&mb_free, par))) { failed = true; break; }
+      // ---- heads and tails of the own fields ----
+      const float *row = sRaw + el * S;
+      if (h == 0) um_convert<N, 0>(row, sA, tl, el, live);
+      else um_convert<N, 1>(row, sA, tl, el, live);
+      um_wait_st();
+      um_fence_async_smem();
+      um_fence_before();
+      um_arrive(&mb_opA);
+      // ---- the tile's geometry, formed by the helpers ----
+      if (!__all_sync(0xffffffffu, um_wait(&mb_geo, par))) { failed = true; break; }
+      UmGeo<N> G;
+      int code[3];
+      {
+        const float4 *g4 = reinterpret_cast<const float4 *>(sG + el * GW);
+        const float4 w0 = g4[0], w1 = g4[1], w2 = g4[2], w3 = g4[3], w4 = g4[4];
+        G.rx = w0.x; G.sx = w0.y; G.ry = w0.z; G.sy = w0.w;
+        G.iJ = w1.x; G.ex[0] = w1.y; G.ex[1] = w1.z; G.ex[2] = w1.w;
+        G.ey[0] = w2.x; G.ey[1] = w2.y; G.ey[2] = w2.z;
+        const float vx[3] = {w2.w, w3.x, w3.y}, vy[3] = {w3.z, w3.w, w4.x};
+        code[0] = __float_as_int(w4.y); code[1] = __float_as_int(w4.z); code[2] = __float_as_int(w4.w);
+        um_arrive(&mb_gread);
+        // grid velocity at the nodes: P1 interpolation of the vertex velocities, node pairs
+#pragma unroll
+        for (int p = 0; p < NP2; ++p) {
+          const float2 an = make_float2(bar[4 * p], bar[4 * p + 2]), bn = make_float2(bar[4 * p + 1], bar[4 * p + 3]);
+          G.vgx2[p] = __ffma2_rn(bn, um_b2(vx[2] - vx[0]), __ffma2_rn(an, um_b2(vx[1] - vx[0]), um_b2(vx[0])));
+          G.vgy2[p] = __ffma2_rn(bn, um_b2(vy[2] - vy[0]), __ffma2_rn(an, um_b2(vy[1] - vy[0]), um_b2(vy[0])));
+        }
+      }
+      // ---- volume terms, into R ----
+      if (!__all_sync(0xffffffffu, um_wait(&mb_v, par))) { failed = true; break; }
+      um_fence_after();
+      if (h == 0) um_volume<N, 0>(tl, G, mc, mcs);
+      else um_volume<N, 1>(tl, G, mc, mcs);
+      // ---- collision term at the cubature points ----
+      if (!__all_sync(0xffffffffu, um_wait(&mb_c, par))) { failed = true; break; }
+      um_fence_after();
+      if (h == 0) um_cubature<N, 0>(tl, itau);
+      else um_cubature<N, 1>(tl, itau);
+      um_wait_st();
+      um_fence_before();
+      um_arrive(&mb_opN);
+      // ---- face fluxes while the projection runs: neighbour traces from the staged tile, the
+      //      halo, or (past the halo's capacity) global memory ----
+      if (!__all_sync(0xffffffffu, um_wait(&mb_halo, par))) { failed = true; break; }
+      float fl[6][8];
+      {
+        const float *src[3];
+        bool hal[3];
+        int f2[3];
+#pragma unroll
+        for (int f = 0; f < 3; ++f) {
+          hal[f] = code[f] < 0;
+          const int64_t nbe = code[f] >> 2;
+          f2[f] = code[f] & 3;
+          src[f] = hal[f] ? sH + (-code[f] - 1) * D::HW
+                          : ((nbe >= e0 && nbe < e0 + nel) ? sRaw + (nbe - e0) * S : qin + nbe * S);
+        }
+        if (h == 0) um_flux<N, 0>(G, row, src, hal, f2, c, fl);
+        else um_flux<N, 1>(G, row, src, hal, f2, c, fl);
+        if (!live) {
+#pragma unroll
+          for (int f = 0; f < 6; ++f)
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) fl[f][jj] = 0.0f;
+        }
+      }
+      if (!__all_sync(0xffffffffu, um_wait(&mb_p, par))) { failed = true; break; }
+      um_fence_after();
+      if (h == 0) um_flux_store<N, 0>(tl, fl);
+      else um_flux_store<N, 1>(tl, fl);
+      um_wait_st();
+      um_fence_before();
+      um_arrive(&mb_opF);
+      // ---- SARK combination once the lift and the staged rows are in ----
+      if (!__all_sync(0xffffffffu, um_wait(&mb_l, par))) { failed = true; break; }
+      if (STAGE >= 0 && !__all_sync(0xffffffffu, um_wait(&mb_qn, par))) { failed = true; break; }
+      if (STAGE >= 1 && !__all_sync(0xffffffffu, um_wait(&mb_x, par))) { failed = true; break; }
+      um_fence_after();
+      {
+        float4 *rowq = reinterpret_cast<float4 *>(sA + el * S);
+        float4 *row1 = reinterpret_cast<float4 *>(sX1 + el * S);
+        float4 *row2 = reinterpret_cast<float4 *>(sX2 + el * S);
+        bool bd = false;
+        if (h == 0) um_sark<N, STAGE, 0>(tl, rowq, row1, row2, k0, k1, dt, bd);
+        else um_sark<N, STAGE, 1>(tl, rowq, row1, row2, k0, k1, dt, bd);
+        bad |= live && bd;
+      }
+      um_fence_async_smem();
+      um_fence_before();
+      um_arrive(&mb_out);
+    }
+    if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
+    if (failed) atomicOr(a.status, GB_STATUS_TIMEOUT);
   }
-  if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
-  if (failed) {
-    // a wait ran out: flag it, wait (bounded) for what this CTA still has in flight
-    if (tid == 0) atomicOr(a.status, GB_STATUS_TIMEOUT);
-    if (ld_pending) um_wait(&mbar_ld, ph_ld);
-    if (x_pending) um_wait(&mbar_x, ph_x);
-    if (qn_pending) um_wait(&mbar_qn, ph_qn);
-    if (v_pending) um_wait(&mbar_v, ph_v);
-    if (c_pending) um_wait(&mbar_c, ph_c);
-    if (mma_pending) um_wait(&mbar_mma, ph_mma);
-  }
-  if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   um_fence_before();
   __syncthreads();
   um_fence_after();
@@ -817,7 +1038,7 @@ int um_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
   const int64_t ntile = (a.K + 127) / 128;
   int64_t grid = num_sms < ntile ? num_sms : ntile;
   if (grid < 1) grid = 1;
-  um_stage_kernel<N, STAGE><<<(unsigned)grid, 128, smem, st>>>(a);
+  um_stage_kernel<N, STAGE><<<(unsigned)grid, kUmThreads, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
