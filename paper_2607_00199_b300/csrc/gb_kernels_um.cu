@@ -540,6 +540,30 @@ __device__ __forceinline__ void um_sark(uint32_t tl, float4 *rowq, float4 *row1,
   }
 }
 
+// motion factors of the stage (Sec. 5, RK4 nodes c = (0, 1/2, 1/2, 1) and weights): grid velocity
+// v_i = gf S(X), stage position x_i = x_n + xf S(X), final vertex factor x_{n+1} = x_n + fin S(X).
+// Called by a whole warp: lanes 0..2 evaluate cos(w (t_n + k dt / 2)) (one FP64 cosine each,
+// in parallel), lane 0 combines them.
+__device__ __forceinline__ void um_stage_motion_warp(const StageArgs &a, int stage, int lane, double &gf, double &xf,
+                                                     double &fin) {
+  gf = 0.0; xf = 0.0; fin = 0.0;
+  if (a.motion_A == 0.0) return;
+  const double w = a.motion_w, Aw = a.motion_A * a.motion_w, dt = a.dt;
+  double ck = 0.0;
+  if (lane < 3) ck = stage < 0 ? cos(w * a.rhs_time) : cos(w * (a.clock[0] + 0.5 * lane * dt));
+  const double c0 = __shfl_sync(0xffffffffu, ck, 0), c1 = __shfl_sync(0xffffffffu, ck, 1),
+               c2 = __shfl_sync(0xffffffffu, ck, 2);
+  if (stage < 0) {
+    gf = Aw * c0;
+    return;
+  }
+  const double cs[3] = {c0, c1, c2};   // at t_n, t_n + dt / 2, t_n + dt
+  const int node[4] = {0, 1, 1, 2};    // c_i = node[i] / 2
+  gf = Aw * cs[node[stage]];
+  if (stage > 0) xf = dt * (stage == 3 ? 1.0 : 0.5) * Aw * cs[node[stage - 1]];
+  if (stage == 3) fin = dt * Aw * (c0 / 6.0 + c1 * (2.0 / 3.0) + c2 / 6.0);
+}
+
 // Shared-memory buffers of a tile (element-major rows of stride S unless noted):
 //   sA    the head tile of the own fields (core-matrix layout) for the first MMA batch;
 //         afterwards q_n, then q_{i+1} (or F in the rhs-only mode), stored back by a bulk copy
@@ -561,23 +585,38 @@ __device__ __forceinline__ void um_sark(uint32_t tl, float4 *rowq, float4 *row1,
 constexpr int kUmThreads = 384;
 constexpr int kUmIssuers = 4;
 
+// inputs of an element's geometry: its mesh record and the current positions and motion
+// shapes of its vertices (loaded ahead of their use)
+struct UmGeoIn {
+  MeshRec rec;
+  double2 xv[3];
+  float2 sv[3];
+};
+__device__ __forceinline__ MeshRec um_rec(const StageArgs &a, int64_t e) { return a.mesh[e]; }
+__device__ __forceinline__ void um_vertices(const StageArgs &a, UmGeoIn &in) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    in.xv[k] = reinterpret_cast<const double2 *>(a.xn)[in.rec.v[k]];
+    const double2 sv = reinterpret_cast<const double2 *>(a.shape)[in.rec.v[k]];
+    in.sv[k] = make_float2((float)sv.x, (float)sv.y);
+  }
+}
+
 // the element's geometry at the stage (Sec. 5) into its row of the geometry buffer; a face
 // whose neighbour lies outside the tile [t0e, t0e + nel) gets a halo slot from the shared
 // counter while slots last (code -(slot + 1) in the row, the neighbour code in hsrc[slot]);
 // the other faces keep the neighbour code (element << 2 | face)
 template <int N>
-__device__ __forceinline__ void um_geometry(const StageArgs &a, int64_t e, bool live, int64_t t0e, int nel, float xff,
-                                            float gff, float *g, int *hcount, int *hsrc) {
-  const MeshRec rec = a.mesh[e];
+__device__ __forceinline__ void um_geometry(const StageArgs &a, const UmGeoIn &in, bool live, int64_t t0e, int nel,
+                                            float xff, float gff, float *g, int *hcount, int *hsrc) {
+  const MeshRec &rec = in.rec;
   double bx[3], by[3];
   float ix[3], iy[3], vx[3], vy[3], ex[3], ey[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const double2 xv = reinterpret_cast<const double2 *>(a.xn)[rec.v[k]];
-    const double2 sv = reinterpret_cast<const double2 *>(a.shape)[rec.v[k]];
-    bx[k] = xv.x + rec.shift[2 * k] * a.period[0];
-    by[k] = xv.y + rec.shift[2 * k + 1] * a.period[1];
-    const float sxk = (float)sv.x, syk = (float)sv.y;
+    bx[k] = in.xv[k].x + rec.shift[2 * k] * a.period[0];
+    by[k] = in.xv[k].y + rec.shift[2 * k + 1] * a.period[1];
+    const float sxk = in.sv[k].x, syk = in.sv[k].y;
     ix[k] = xff * sxk;
     iy[k] = xff * syk;
     vx[k] = gff * sxk;
@@ -636,8 +675,11 @@ __device__ __forceinline__ void um_halo(const float *qin, const int *hsrc, int c
   }
 }
 
-template <int N, int STAGE>
+// one kernel for every stage (the stage is a run-time argument), so that the launches of a
+// step share their code
+template <int N>
 __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs a) {
+  const int STAGE = a.stage;
   typedef UmDim<N> D;
   constexpr int S = D::S, NPP = D::NPP, KV = D::KV, GW = D::GW;
   constexpr int NV = D::NV, NCM = D::NCM, KC = D::KC, KL = D::KL;
@@ -666,13 +708,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   const int64_t ntile = (a.K + 127) >> 7;
   auto tile_rows = [&](int64_t t_) { return (int)((a.K - t_ * 128) < 128 ? (a.K - t_ * 128) : 128); };
 
-  for (int i = tid; i < D::BTOT; i += kUmThreads) sB[i] = a.ops_um[i];
+  __shared__ __align__(8) uint64_t mb_tab;   // operator tables staged
   if (tid == 0) {
-    double gf, xf, fin;
-    tc_stage_motion<STAGE>(a, gf, xf, fin);
-    s_motion[0] = gf;
-    s_motion[1] = xf;
-    if (STAGE == 3 && blockIdx.x == 0) const_cast<double *>(a.clock)[1] = fin;
     uint64_t *one[4] = {&mb_ld, &mb_x, &mb_qn, &mb_free};
     for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(um_sa(one[i])) : "memory");
     uint64_t *iss[4] = {&mb_v, &mb_c, &mb_p, &mb_l};
@@ -682,7 +719,12 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     s_hcount = 0;
     uint64_t *many[5] = {&mb_opA, &mb_gread, &mb_opN, &mb_opF, &mb_out};
     for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" :: "r"(um_sa(many[i])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(um_sa(&mb_tab)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    // the operator tables and the first tile's own fields, in flight during the set-up
+    um_bulk_load(sB, a.ops_um, (uint32_t)(D::BTOT * sizeof(float)), &mb_tab);
+    if ((int64_t)blockIdx.x < ntile)
+      um_bulk_load(sRaw, qin + (int64_t)blockIdx.x * 128 * S, (uint32_t)(tile_rows(blockIdx.x) * S * sizeof(float)), &mb_ld);
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" :: "r"(um_sa(&s_tmem)) : "memory");
@@ -693,29 +735,39 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   __syncthreads();
   um_fence_after();
   const uint32_t tm = s_tmem;
-  const float gff = (float)s_motion[0], xff = (float)s_motion[1];
-  bool failed = false;
+  bool failed = !__all_sync(0xffffffffu, um_wait(&mb_tab, 0));
 
   if (warp >= 8) {
     // ================= helpers: geometry one tile ahead, MMA issue, bulk copies =================
     const int hi = tid - 256, iw = warp - 8;   // element of the next tile, issuer index
     const bool issuer = lane == 0, copier = tid == 256;
+    // the stage's motion factors (FP64 cosines) after the set-up barrier, so that the compute
+    // warps and the first bulk copy do not wait for them
+    unsigned armed = (copier && (int64_t)blockIdx.x < ntile) ? 1u : 0u;   // phases in flight from this thread
+    uint32_t ld_par = 0;  // parity of the armed phase of mb_ld
+    if (warp == 11) {
+      double gf, xf, fin;
+      um_stage_motion_warp(a, STAGE, lane, gf, xf, fin);
+      if (lane == 0) {
+        s_motion[0] = gf;
+        s_motion[1] = xf;
+        if (STAGE == 3 && blockIdx.x == 0) const_cast<double *>(a.clock)[1] = fin;
+      }
+    }
+    asm volatile("bar.sync 1, 128;" ::: "memory");
+    const float gff = (float)s_motion[0], xff = (float)s_motion[1];
     const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
     // descriptors at the operands' bases; an operand at byte offset o has descriptor base + o / 16
     const uint64_t dA = um_desc(sA_a, 2048, 128);
     const uint64_t dBV = um_desc(sB_a + 4 * D::BV, NV * 16, 128), dBI = um_desc(sB_a + 4 * D::BI, NCM * 16, 128);
     const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
     constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(NCM), idR = um_idesc(16);
-    unsigned armed = 0;   // mbarriers with a phase in flight from this thread (teardown)
-    uint32_t ld_par = 0;  // parity of the armed phase of mb_ld
     if ((int64_t)blockIdx.x < ntile) {
-      if (copier) {
-        um_bulk_load(sRaw, qin + (int64_t)blockIdx.x * 128 * S, (uint32_t)(tile_rows(blockIdx.x) * S * sizeof(float)), &mb_ld);
-        armed |= 1u;
-      }
       const int64_t t0 = blockIdx.x, r0 = a.K - t0 * 128;
-      um_geometry<N>(a, t0 * 128 + (hi < r0 ? hi : 0), hi < r0, t0 * 128, tile_rows(t0), xff, gff, sG + hi * GW,
-                     &s_hcount, s_hsrc);
+      UmGeoIn in0;
+      in0.rec = um_rec(a, t0 * 128 + (hi < r0 ? hi : 0));
+      um_vertices(a, in0);
+      um_geometry<N>(a, in0, hi < r0, t0 * 128, tile_rows(t0), xff, gff, sG + hi * GW, &s_hcount, s_hsrc);
       um_arrive(&mb_geo);
       asm volatile("bar.sync 1, 128;" ::: "memory");
       um_halo<N>(qin, s_hsrc, s_hcount < D::HMAX ? s_hcount : D::HMAX, hi, sH);
@@ -744,6 +796,11 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       const int64_t e0 = tile * 128;
       const uint32_t tile_bytes = (uint32_t)(tile_rows(tile) * S * sizeof(float));
       const bool more = tile + gridDim.x < ntile;
+      // the next tile's geometry inputs: its mesh record now, its vertex data after the first
+      // batch is issued, the arithmetic once the projection batch is issued
+      const int64_t tn = tile + gridDim.x, rn = a.K - tn * 128;
+      UmGeoIn gin;
+      if (more) gin.rec = um_rec(a, tn * 128 + (hi < rn ? hi : 0));
       if (copier) {
         // the previous tile's stores have read the shared tile and the staged rows
         asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
@@ -793,20 +850,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
           armed |= 4u;
         }
       }
-      // ---- the next tile's geometry and halo slots, once the compute threads have read this
-      //      tile's geometry ----
-      if (more) {
-        if (!failed && !um_wait(&mb_gread, par)) failed = true;
-        asm volatile("bar.sync 1, 128;" ::: "memory");   // this tile's halo entries are all staged
-        if (hi == 0) s_hcount = 0;
-        asm volatile("bar.sync 1, 128;" ::: "memory");
-        if (!failed) {
-          const int64_t tn = tile + gridDim.x, rn = a.K - tn * 128;
-          um_geometry<N>(a, tn * 128 + (hi < rn ? hi : 0), hi < rn, tn * 128, tile_rows(tn), xff, gff, sG + hi * GW,
-                         &s_hcount, s_hsrc);
-          um_arrive(&mb_geo);
-        }
-      }
+      if (more) um_vertices(a, gin);
       // ---- batch 2: R_{4..6} += Ntilde P^T, field iw ----
       if (issuer && !failed) {
         if (!um_wait(&mb_opN, par)) {
@@ -830,6 +874,18 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
           armed |= 32u;
         }
       }
+      // ---- the next tile's geometry and halo slots, once the compute threads have read this
+      //      tile's geometry ----
+      if (more) {
+        if (!failed && !um_wait(&mb_gread, par)) failed = true;
+        asm volatile("bar.sync 1, 128;" ::: "memory");   // this tile's halo entries are all staged
+        if (hi == 0) s_hcount = 0;
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        if (!failed) {
+          um_geometry<N>(a, gin, hi < rn, tn * 128, tile_rows(tn), xff, gff, sG + hi * GW, &s_hcount, s_hsrc);
+          um_arrive(&mb_geo);
+        }
+      }
       // ---- batch 3: R += Flux LIFT^T, fields {iw, iw + 4}; then the next tile's own fields ----
       if (issuer && !failed) {
         if (!um_wait(&mb_opF, par)) {
@@ -842,7 +898,6 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
           um_commit(&mb_l);
           armed |= 64u;
           if (copier && more) {
-            const int64_t tn = tile + gridDim.x;
             um_fence_async_smem();
             um_bulk_load(sRaw, qin + tn * 128 * S, (uint32_t)(tile_rows(tn) * S * sizeof(float)), &mb_ld);
             ld_par = par ^ 1u;
@@ -905,7 +960,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     const float k1[5] = {a.kco[1][0], a.kco[1][1], a.kco[1][2], a.kco[1][3], a.kco[1][4]};
     bool bad = false;
     uint32_t par = 0;
-    for (int64_t tile = blockIdx.x; tile < ntile; tile += gridDim.x, par ^= 1u) {
+    for (int64_t tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x, par ^= 1u) {
       const int64_t e0 = tile * 128;
       const int nel = tile_rows(tile);
       const bool live = el < nel;
@@ -994,8 +1049,17 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
         float4 *row1 = reinterpret_cast<float4 *>(sX1 + el * S);
         float4 *row2 = reinterpret_cast<float4 *>(sX2 + el * S);
         bool bd = false;
-        if (h == 0) um_sark<N, STAGE, 0>(tl, rowq, row1, row2, k0, k1, dt, bd);
-        else um_sark<N, STAGE, 1>(tl, rowq, row1, row2, k0, k1, dt, bd);
+#define UM_SARK(ST)                                                                          \
+  if (h == 0) um_sark<N, ST, 0>(tl, rowq, row1, row2, k0, k1, dt, bd);                       \
+  else um_sark<N, ST, 1>(tl, rowq, row1, row2, k0, k1, dt, bd);
+        switch (STAGE) {
+          case -1: UM_SARK(-1) break;
+          case 0: UM_SARK(0) break;
+          case 1: UM_SARK(1) break;
+          case 2: UM_SARK(2) break;
+          default: UM_SARK(3) break;
+        }
+#undef UM_SARK
         bad |= live && bd;
       }
       um_fence_async_smem();
@@ -1004,6 +1068,10 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     }
     if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
     if (failed) atomicOr(a.status, GB_STATUS_TIMEOUT);
+  }
+  if (tid == 0) {   // the set-up copies have landed (at once, unless a wait ran out)
+    um_wait(&mb_tab, 0);
+    if ((int64_t)blockIdx.x < ntile && failed) um_wait(&mb_ld, 0);
   }
   um_fence_before();
   __syncthreads();
@@ -1016,7 +1084,7 @@ namespace {
 
 constexpr int kUmMaxDevices = 64;
 
-template <int N, int STAGE>
+template <int N>
 int um_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
   typedef UmDim<N> D;
   StageArgs a = a_in;
@@ -1031,27 +1099,21 @@ int um_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
   if (err != cudaSuccess) return (int)err;
   if (dev < 0 || dev >= kUmMaxDevices) return (int)cudaErrorInvalidDevice;
   if (!attr_set[dev]) {
-    err = cudaFuncSetAttribute(um_stage_kernel<N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    err = cudaFuncSetAttribute(um_stage_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
     attr_set[dev] = true;
   }
   const int64_t ntile = (a.K + 127) / 128;
   int64_t grid = num_sms < ntile ? num_sms : ntile;
   if (grid < 1) grid = 1;
-  um_stage_kernel<N, STAGE><<<(unsigned)grid, kUmThreads, smem, st>>>(a);
+  um_stage_kernel<N><<<(unsigned)grid, kUmThreads, smem, st>>>(a);
   return (int)cudaGetLastError();
 }
 
 template <int N>
 int um_launch_n(const StageArgs &a, cudaStream_t st, int num_sms) {
-  switch (a.stage) {
-    case -1: return um_launch_one<N, -1>(a, st, num_sms);
-    case 0: return um_launch_one<N, 0>(a, st, num_sms);
-    case 1: return um_launch_one<N, 1>(a, st, num_sms);
-    case 2: return um_launch_one<N, 2>(a, st, num_sms);
-    case 3: return um_launch_one<N, 3>(a, st, num_sms);
-  }
-  return (int)cudaErrorInvalidValue;
+  if (a.stage < -1 || a.stage > 3) return (int)cudaErrorInvalidValue;
+  return um_launch_one<N>(a, st, num_sms);
 }
 
 float um_tf32_host(double v) {
