@@ -127,6 +127,23 @@ __device__ __forceinline__ void um_mma_ts(uint32_t d, uint32_t a, uint64_t b, ui
                "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
                :: "r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc) : "memory");
 }
+// the same, issued by the calling thread only where `issue` is set: a whole warp runs the
+// issue code (its descriptors stay warp-uniform) and one lane executes the instruction
+__device__ __forceinline__ void um_mma_ss_p(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc, uint32_t issue) {
+  asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 q, %5, 0;\n\t"
+               "@q tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+               :: "r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc), "r"(issue) : "memory");
+}
+__device__ __forceinline__ void um_mma_ts_p(uint32_t d, uint32_t a, uint64_t b, uint32_t idesc, uint32_t acc, uint32_t issue) {
+  asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.b32 p, %4, 0;\n\tsetp.ne.b32 q, %5, 0;\n\t"
+               "@q tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+               :: "r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc), "r"(issue) : "memory");
+}
+__device__ __forceinline__ void um_commit_p(uint64_t *mbar, uint32_t issue) {
+  asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %1, 0;\n\t"
+               "@q tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n\t}"
+               :: "r"(um_sa(mbar)), "r"(issue) : "memory");
+}
 __device__ __forceinline__ void um_commit(uint64_t *mbar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(um_sa(mbar)) : "memory");
 }
@@ -723,6 +740,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // the operator tables and the first tile's own fields, in flight during the set-up
     um_bulk_load(sB, a.ops_um, (uint32_t)(D::BTOT * sizeof(float)), &mb_tab);
+    um_arrive(&mb_free);   // the shared tile of the first tile is free
     if ((int64_t)blockIdx.x < ntile)
       um_bulk_load(sRaw, qin + (int64_t)blockIdx.x * 128 * S, (uint32_t)(tile_rows(blockIdx.x) * S * sizeof(float)), &mb_ld);
   }
@@ -740,11 +758,17 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   if (warp >= 8) {
     // ================= helpers: geometry one tile ahead, MMA issue, bulk copies =================
     const int hi = tid - 256, iw = warp - 8;   // element of the next tile, issuer index
-    const bool issuer = lane == 0, copier = tid == 256;
-    // the stage's motion factors (FP64 cosines) after the set-up barrier, so that the compute
-    // warps and the first bulk copy do not wait for them
+    const bool copier = tid == 256;
     unsigned armed = (copier && (int64_t)blockIdx.x < ntile) ? 1u : 0u;   // phases in flight from this thread
     uint32_t ld_par = 0;  // parity of the armed phase of mb_ld
+    const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
+    // descriptors at the operands' bases; an operand at byte offset o has descriptor base + o / 16
+    const uint64_t dA = um_desc(sA_a, 2048, 128);
+    const uint64_t dBV = um_desc(sB_a + 4 * D::BV, NV * 16, 128), dBI = um_desc(sB_a + 4 * D::BI, NCM * 16, 128);
+    const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
+    constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(NCM), idR = um_idesc(16);
+    // the stage's motion factors (FP64 cosines: three lanes of warp 11 in parallel) after the
+    // set-up barrier, so that the compute warps and the first bulk copies do not wait for them
     if (warp == 11) {
       double gf, xf, fin;
       um_stage_motion_warp(a, STAGE, lane, gf, xf, fin);
@@ -756,12 +780,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
     const float gff = (float)s_motion[0], xff = (float)s_motion[1];
-    const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
-    // descriptors at the operands' bases; an operand at byte offset o has descriptor base + o / 16
-    const uint64_t dA = um_desc(sA_a, 2048, 128);
-    const uint64_t dBV = um_desc(sB_a + 4 * D::BV, NV * 16, 128), dBI = um_desc(sB_a + 4 * D::BI, NCM * 16, 128);
-    const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
-    constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(NCM), idR = um_idesc(16);
+    // the first tile's geometry and halo
     if ((int64_t)blockIdx.x < ntile) {
       const int64_t t0 = blockIdx.x, r0 = a.K - t0 * 128;
       UmGeoIn in0;
@@ -774,18 +793,19 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       um_arrive(&mb_halo);
     }
     // the MMAs of one field: K / 8 k-steps of the three split products into accumulator d
+    const uint32_t one = lane == 0 ? 1u : 0u;   // the lane that executes this warp's MMAs and commits
     auto mma_field = [&](uint32_t d, uint32_t a_lo, uint64_t a_hi_s, uint32_t a_hi_t, bool hi_in_tmem, uint64_t bh,
                          uint64_t bl, uint64_t b_step, uint32_t id, int ksteps, uint32_t a_step_t, uint64_t a_step_s,
                          bool first_overwrites) {
       for (int ks = 0; ks < ksteps; ++ks) {
         const uint64_t b0 = bh + ks * b_step, b1 = bl + ks * b_step;
-        um_mma_ts(d, a_lo + ks * a_step_t, b0, id, (first_overwrites && ks == 0) ? 0u : 1u);
+        um_mma_ts_p(d, a_lo + ks * a_step_t, b0, id, (first_overwrites && ks == 0) ? 0u : 1u, one);
         if (hi_in_tmem) {
-          um_mma_ts(d, a_hi_t + ks * a_step_t, b0, id, 1u);
-          um_mma_ts(d, a_hi_t + ks * a_step_t, b1, id, 1u);
+          um_mma_ts_p(d, a_hi_t + ks * a_step_t, b0, id, 1u, one);
+          um_mma_ts_p(d, a_hi_t + ks * a_step_t, b1, id, 1u, one);
         } else {
-          um_mma_ss(d, a_hi_s + ks * a_step_s, b0, id, 1u);
-          um_mma_ss(d, a_hi_s + ks * a_step_s, b1, id, 1u);
+          um_mma_ss_p(d, a_hi_s + ks * a_step_s, b0, id, 1u, one);
+          um_mma_ss_p(d, a_hi_s + ks * a_step_s, b1, id, 1u, one);
         }
       }
     };
@@ -802,9 +822,12 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       UmGeoIn gin;
       if (more) gin.rec = um_rec(a, tn * 128 + (hi < rn ? hi : 0));
       if (copier) {
-        // the previous tile's stores have read the shared tile and the staged rows
-        asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-        um_arrive(&mb_free);
+        // the previous tile's stores have read the shared tile and the staged rows (the first
+        // tile's is free from the set-up)
+        if (tile != (int64_t)blockIdx.x) {
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          um_arrive(&mb_free);
+        }
         if (STAGE >= 1) {
           uint32_t bytes = 0;
           if (STAGE == 1 || STAGE == 2) bytes += tile_bytes;
@@ -822,8 +845,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
         }
       }
       // ---- batch 1: volume products of fields {iw, iw + 4}, interpolation of a field ----
-      if (issuer && !failed) {
-        if (!um_wait(&mb_opA, par)) {
+      if (!failed) {
+        if (!__all_sync(0xffffffffu, um_wait(&mb_opA, par))) {
           failed = true;
         } else {
           um_fence_after();
@@ -831,14 +854,14 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
             mma_field(tm + D::T_V + f * NV, tm + D::T_QL + f * KV, dA + (uint64_t)(((f * NPP / 4) * 2048) >> 4), 0u,
                       false, dBV, dBV + (uint64_t)((4 * NV * KV) >> 4), (uint64_t)((4 * 2 * NV * 4) >> 4), idV, KV / 8,
                       8u, (uint64_t)((2 * 2048) >> 4), true);
-          um_commit(&mb_v);
+          um_commit_p(&mb_v, one);
           const int fc = iw == 0 ? 2 : (iw == 2 ? 0 : (iw == 3 ? 1 : -1));
           if (fc >= 0)
             mma_field(tm + D::T_C + fc * NCM, tm + D::T_QL + fc * KV, dA + (uint64_t)(((fc * NPP / 4) * 2048) >> 4), 0u,
                       false, dBI, dBI + (uint64_t)((4 * NCM * KV) >> 4), (uint64_t)((4 * 2 * NCM * 4) >> 4), idC, KV / 8,
                       8u, (uint64_t)((2 * 2048) >> 4), true);
-          um_commit(&mb_c);
-          armed |= 8u | 16u;
+          um_commit_p(&mb_c, one);
+          if (one) armed |= 8u | 16u;
         }
       }
       // ---- q_n into the shared tile once the first batch has read it ----
@@ -852,8 +875,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       }
       if (more) um_vertices(a, gin);
       // ---- batch 2: R_{4..6} += Ntilde P^T, field iw ----
-      if (issuer && !failed) {
-        if (!um_wait(&mb_opN, par)) {
+      if (!failed) {
+        if (!__all_sync(0xffffffffu, um_wait(&mb_opN, par))) {
           failed = true;
         } else {
           um_fence_after();
@@ -865,13 +888,13 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
               const uint64_t b0 = dBP + (uint64_t)((4 * 2 * ks * 16 * 4) >> 4);
               const uint64_t b1 = dBP + (uint64_t)((4 * (16 * KC + 2 * ks * 16 * 4)) >> 4);
               const uint32_t ah = tm + D::T_C + iw * NCM + 8 * ks;
-              um_mma_ts(d, tm + um_slot(iw * (KC / 8) + ks), b0, idR, 1u);
-              um_mma_ts(d, ah, b0, idR, 1u);
-              um_mma_ts(d, ah, b1, idR, 1u);
+              um_mma_ts_p(d, tm + um_slot(iw * (KC / 8) + ks), b0, idR, 1u, one);
+              um_mma_ts_p(d, ah, b0, idR, 1u, one);
+              um_mma_ts_p(d, ah, b1, idR, 1u, one);
             }
           }
-          um_commit(&mb_p);
-          armed |= 32u;
+          um_commit_p(&mb_p, one);
+          if (one) armed |= 32u;
         }
       }
       // ---- the next tile's geometry and halo slots, once the compute threads have read this
@@ -887,16 +910,16 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
         }
       }
       // ---- batch 3: R += Flux LIFT^T, fields {iw, iw + 4}; then the next tile's own fields ----
-      if (issuer && !failed) {
-        if (!um_wait(&mb_opF, par)) {
+      if (!failed) {
+        if (!__all_sync(0xffffffffu, um_wait(&mb_opF, par))) {
           failed = true;
         } else {
           um_fence_after();
           for (int f = iw; f < 6; f += 4)
             mma_field(tm + D::T_R + f * 16, tm + D::T_FL + f * KL, 0, tm + D::T_FH + f * KL, true, dBL,
                       dBL + (uint64_t)((4 * 16 * KL) >> 4), (uint64_t)((4 * 2 * 16 * 4) >> 4), idR, KL / 8, 8u, 0, false);
-          um_commit(&mb_l);
-          armed |= 64u;
+          um_commit_p(&mb_l, one);
+          if (one) armed |= 64u;
           if (copier && more) {
             um_fence_async_smem();
             um_bulk_load(sRaw, qin + tn * 128 * S, (uint32_t)(tile_rows(tn) * S * sizeof(float)), &mb_ld);
