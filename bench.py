@@ -278,6 +278,7 @@ def parse():
     p.add_argument('--warmup', type=int, default=5)
     p.add_argument('--impl', choices=['ours', 'reference'], default='ours')
     p.add_argument('--no-cpu-baseline', action='store_true')
+    p.add_argument('--no-long-error', action='store_true', help='skip the 1000-step mixed-vs-FP64 error run')
     p.add_argument('--no-serve', action='store_true', help='skip the serving-stream measurement')
     p.add_argument('--serve-only', action='store_true', help='only the serving-stream measurement')
     p.add_argument('--no-3d', action='store_true',
@@ -409,13 +410,14 @@ def load_peaks():
         return 6400.0, 2032.0, 'fallback'
 
 
-def recorded_traffic(precision):
+def recorded_traffic(key):
     """DRAM bytes per launch (average over the 4 stage launches of a step) of the
-    stage kernel from a committed ncu capture, or None if that kernel's source file
+    stage kernel from a committed ncu capture ('mixed': the warp-tile mma.sync kernel,
+    'mixed_um': the tcgen05 kernel, 'fp64'), or None if that kernel's source file
     changed since the capture was taken."""
     try:
         with open(TRAFFIC_FILE) as f:
-            d = json.load(f)[precision]
+            d = json.load(f)[key]
         src = os.path.join(ROOT, d['kernel_source'])
         if hashlib.sha256(open(src, 'rb').read()).hexdigest() != d['kernel_source_sha256']:
             return None
@@ -482,17 +484,26 @@ class _SingleThreadBLAS:
             self._ctx.__exit__(*exc)
 
 
+class _NoLimit:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        return False
+
+
 def _cores_used(cpu_s, wall_s):
     return max(1, int(round(cpu_s / max(wall_s, 1e-9))))
 
 
-def cpu_baseline(steps_sample=2, n_sample=128):
-    """The oracle, as it stands, on a bounded sample of the workload (host cores)."""
+def cpu_baseline(steps_sample=2, n_sample=128, all_cores=False):
+    """The oracle, as it stands, on a bounded sample of the workload (host cores): with its
+    numpy calls held to one thread, or (all_cores) with numpy's own threading on every core."""
     from oracle import physics
     from oracle.solver import Motion, OracleSolver
     from paper_2607_00199_b300 import inputs
     W = WORKLOAD
-    with _SingleThreadBLAS():
+    with (_NoLimit() if all_cores else _SingleThreadBLAS()):
         mesh = inputs.periodic_square_mesh(n_sample, jitter=W['jitter'])
         o = OracleSolver(mesh, W['N'], Ma=W['Ma'], Re=W['Re'], motion=Motion(W['A'], W['T']))
         xn = o.node_coords(o.X)
@@ -506,9 +517,38 @@ def cpu_baseline(steps_sample=2, n_sample=128):
     dof = o.K * Np * 6
     return {'value': dof * 4 * steps_sample / el, 'unit': 'DOF-stage updates/s', 'cores': _cores_used(cpu, el),
             'kind': 'oracle',
-            'sample': '%d SARK steps of the same method on a %dx%d jittered mesh (K=%d, N=%d), numpy FP64; '
+            'nproc': os.cpu_count(),
+            'sample': '%d SARK steps of the same method on a %dx%d jittered mesh (K=%d, N=%d), numpy FP64%s; '
                       '%.1f s wall, %.1f s CPU (cores = CPU/wall, rounded)' % (steps_sample, n_sample, n_sample,
-                                                                           o.K, W['N'], el, cpu)}
+                                                                           o.K, W['N'],
+                                                                           ', numpy threads on all cores'
+                                                                           if all_cores else ', one thread',
+                                                                           el, cpu)}
+
+
+def long_error(results, steps):
+    """The error of the mixed path after `steps` SARK steps of the benchmark workload,
+    against the FP64 path run from the same initial state (the FP64 path matches the oracle
+    to 1e-10 after 100 steps and at full size per step, in the GPU parity tests)."""
+    out = {}
+    q = {}
+    for name in ('mixed', 'fp64'):
+        r = results[name]
+        s = r['solver']
+        s.set_fields(r['q0'], 0.0)
+        t0 = time.perf_counter()
+        s.step(r['dt'], steps)
+        q[name], _ = s.fields()
+        out['%s_s' % name] = time.perf_counter() - t0
+    qm, qf = q['mixed'], q['fp64']
+    rest = np.zeros_like(qf)
+    rest[:, 0, :] = 1.0
+    dq = qm - qf
+    out.update({'steps': steps, 'rel_l2_fields': float(np.linalg.norm(dq) / np.linalg.norm(qf)),
+                'rel_l2_perturbation': float(np.linalg.norm(dq) / np.linalg.norm(qf - rest)),
+                'max_abs_over_max_perturbation': float(np.abs(dq).max() / np.abs(qf - rest).max()),
+                'against': 'GB_FP64 path from the same state'})
+    return out
 
 
 def run_ours(args):
@@ -551,13 +591,24 @@ def run_ours(args):
         v = aggregate_rate(ws, dof * 4 * args.steps, ms / 1e3)
         ebytes = 4 if name == 'mixed' else 8
         if name == 'mixed':
+            # the stage kernels' time inside the graph-timed steps: ms_per_step times the
+            # stage kernels' share of the per-launch event pass (the vertex update is the rest),
+            # so that the kernel time never exceeds the step it is part of
+            event_ms = float(sum(r['kernel_ms']))
+            share = stage_ms / event_ms if event_ms > 0 else 1.0
+            kern_ms = ms * share
             alg = bytes_per_step(K, W['N'], nv, ebytes) * args.steps
-            achieved = alg / (stage_ms / 1e3) / 1e9
-            traffic = recorded_traffic('mixed')
+            achieved = alg / (kern_ms / 1e3) / 1e9
+            um = r['warps'] == 8
+            traffic = recorded_traffic('mixed_um' if um else 'mixed')
+            kname = ('um_stage_kernel<4> (tcgen05, 128-element CTA tiles; 4 launches per step)' if um
+                     else 'tc_stage_kernel<4,*> (mma.sync, %d-warp CTAs; 4 launches per step)' % r['warps'])
             roof = {'bound': 'hbm', 'achieved': achieved, 'peak': hbm, 'unit': 'GB/s', 'frac': achieved / hbm,
-                    'traffic': traffic, 'kernel': 'tc_stage_kernel<4,*> (4 launches per step)',
+                    'traffic': traffic, 'kernel': kname,
                     'algorithmic_bytes_per_launch_avg': bytes_per_step(K, W['N'], nv, ebytes) / 4,
-                    'mean_launch_ms': stage_ms / (4 * args.steps),
+                    'mean_launch_ms': kern_ms / (4 * args.steps),
+                    'mean_launch_ms_event_pass': stage_ms / (4 * args.steps),
+                    'kernel_time': 'graph-timed steps x the stage kernels\' share of the event-per-launch pass',
                     'peak_source': '%s hbm_gbs (MEASURED_PEAKS.json)' % peak_kind if peak_kind == 'measured'
                     else 'fallback 6400 GB/s',
                     'algorithmic_bytes_per_step': bytes_per_step(K, W['N'], nv, ebytes)}
@@ -574,13 +625,17 @@ def run_ours(args):
                      'kernel_ms_per_step': [x / args.steps for x in r['kernel_ms']],
                      'stage_kernel_share': min(1.0, stage_ms / ms),
                      'timing': 'ms_per_step: gb_step (CUDA graph replay); kernel_ms_per_step: gb_step_timed',
-                     'warps_per_cta': r['warps'] if name == 'mixed' else None}
+                     'launch_shape': (('tcgen05 128-element CTA tiles (shape 8)' if r['warps'] == 8 else
+                                       'mma.sync 16-element warp tiles, %d warps per CTA' % r['warps'])
+                                      if name == 'mixed' else None)}
     qm, qf = results['mixed']['q_end'], results['fp64']['q_end']
     rest = np.zeros_like(qf)
     rest[:, 0, :] = 1.0
     err = {'rel_l2_fields': float(np.linalg.norm(qm - qf) / np.linalg.norm(qf)),
            'rel_l2_perturbation': float(np.linalg.norm(qm - qf) / np.linalg.norm(qf - rest)),
            'steps': args.warmup + args.steps, 'against': 'GB_FP64 path (oracle-parity-tested) from the same state'}
+    if not args.no_long_error:
+        err['run_1000'] = long_error(results, 1000)
 
     # end to end through the public API: pinned host state in, steps, pinned host state out
     s = results['mixed']['solver']
@@ -629,6 +684,7 @@ def run_ours(args):
         line['serving'] = run_serving(torch, args.serve_requests, args.serve_steps)
     if ws == 1 and not args.no_cpu_baseline:
         line['cpu_baseline'] = cpu_baseline()
+        line['cpu_baseline_all_cores'] = cpu_baseline(all_cores=True)
     print(json.dumps(line))
 
 

@@ -190,13 +190,20 @@ int gb_rhs(gb_solver *s, double t, const void *q_dev, void *F_dev);
 int gb_step(gb_solver *s, double dt, int64_t nsteps);
 int gb_set_graph(gb_solver *s, int enable);
 
-/* gb_launch_config: the GB_MIXED kernel's warps per CTA (1, 2 or 4; 0 for GB_FP64).
- * The first gb_step / gb_step_timed of a GB_MIXED solver tunes it: it times the
- * right-hand-side kernel on the solver's own data for each shape (the state is not
- * changed) and keeps the fastest; the choice is cached per (N, K) in the process. */
+/* gb_launch_config: the GB_MIXED launch shape (0 for GB_FP64):
+ *   1, 2, 4  the mma.sync kernel: 16-element warp tiles, that many warps per CTA;
+ *   8        the tcgen05 kernel: 128-element CTA tiles, accumulators in tensor
+ *            memory (orders 1..4, meshes without boundary faces).
+ * Both compute the same right-hand side and SARK step (they agree to rounding; the
+ * three warp-tile shapes agree bit for bit).  With the fused diagnostics the last
+ * stage of shape 8 runs on the 4-warp kernel.  The first gb_step / gb_step_timed of
+ * a GB_MIXED solver tunes the shape: it times the right-hand-side kernel on the
+ * solver's own data for each applicable shape (the state is not changed) and keeps
+ * the fastest; the choice is cached per (N, K) in the process. */
 int gb_launch_config(gb_solver *s, int *warps_per_cta);
-/* gb_set_launch_config: fix the GB_MIXED warps per CTA (1, 2 or 4) and skip the
- * tuner.  GB_EINVAL for other values and for GB_FP64 solvers. */
+/* gb_set_launch_config: fix the GB_MIXED launch shape (1, 2, 4 or 8) and skip the
+ * tuner.  GB_EINVAL for other values, for 8 where it does not apply, and for
+ * GB_FP64 solvers. */
 int gb_set_launch_config(gb_solver *s, int warps_per_cta);
 
 /* gb_step_timed: gb_step that also records a CUDA event pair around every kernel

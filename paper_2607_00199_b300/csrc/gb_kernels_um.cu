@@ -718,6 +718,9 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   // operands ready (256 compute threads): heads and tails; geometry read; R and Ntilde;
   // fluxes; output rows
   __shared__ __align__(8) uint64_t mb_opA, mb_gread, mb_opN, mb_opF, mb_out;
+  // the volume products read (256 compute threads): the Ntilde tails go into columns that held
+  // them, and the two threads of an element read and write them at their own pace
+  __shared__ __align__(8) uint64_t mb_vread;
   __shared__ uint32_t s_tmem;
   __shared__ double s_motion[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -734,8 +737,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(um_sa(&mb_geo)) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(um_sa(&mb_halo)) : "memory");
     s_hcount = 0;
-    uint64_t *many[5] = {&mb_opA, &mb_gread, &mb_opN, &mb_opF, &mb_out};
-    for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" :: "r"(um_sa(many[i])) : "memory");
+    uint64_t *many[6] = {&mb_opA, &mb_gread, &mb_opN, &mb_opF, &mb_out, &mb_vread};
+    for (int i = 0; i < 6; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" :: "r"(um_sa(many[i])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(um_sa(&mb_tab)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // the operator tables and the first tile's own fields, in flight during the set-up
@@ -1022,7 +1025,11 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       um_fence_after();
       if (h == 0) um_volume<N, 0>(tl, G, mc, mcs);
       else um_volume<N, 1>(tl, G, mc, mcs);
-      // ---- collision term at the cubature points ----
+      um_fence_before();
+      um_arrive(&mb_vread);
+      // ---- collision term at the cubature points (its tails overwrite volume columns: after
+      //      both threads of every element have read them) ----
+      if (!__all_sync(0xffffffffu, um_wait(&mb_vread, par))) { failed = true; break; }
       if (!__all_sync(0xffffffffu, um_wait(&mb_c, par))) { failed = true; break; }
       um_fence_after();
       if (h == 0) um_cubature<N, 0>(tl, itau);

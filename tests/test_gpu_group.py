@@ -23,9 +23,12 @@ def _stream():
     return STREAM.cuda_stream
 
 
-def _solver(n, N, A, T, Re, jitter=0.1, precision=gb.GB_MIXED):
+def _solver(n, N, A, T, Re, jitter=0.1, precision=gb.GB_MIXED, shape=None):
+    # shape 4: alone on the same warp-tile kernel as the group (bitwise comparable)
     mesh = inputs.periodic_square_mesh(n, jitter=jitter)
     s = gb.Solver(mesh, N, 0.1, Re, precision=precision, stream=_stream())
+    if shape is not None:
+        s.set_launch_config(shape)
     s.set_motion(A, T)
     xy = s.nodes()
     rho, u, v = inputs.taylor_green(xy[..., 0], xy[..., 1], 0.1)
@@ -43,7 +46,7 @@ def test_group_step_is_bitwise_equal_to_alone(N):
     for (n, A, T, Re), (sg, q0, dt) in zip(specs, grouped):
         qg, tg = sg.fields()
         xg = sg.vertices()
-        sa, _, dta = _solver(n, N, A, T, Re)
+        sa, _, dta = _solver(n, N, A, T, Re, shape=4)
         assert dta == dt
         sa.step(dt, 15)
         qa, ta = sa.fields()
@@ -63,7 +66,7 @@ def test_group_records_diagnostics_like_alone():
     g = gb.Group(4, _stream())
     g.step([s for s, _, _ in grouped], [dt for _, _, dt in grouped], 6)
     for (n, A, T, Re), (sg, _, dt), every in zip(specs, grouped, (1, 2)):
-        sa, _, _ = _solver(n, 3, A, T, Re)
+        sa, _, _ = _solver(n, 3, A, T, Re, shape=4)
         sa.set_diagnostics(every, 32)
         sa.step(dt, 6)
         hg, ha = sg.diagnostics_history(), sa.diagnostics_history()
@@ -120,6 +123,7 @@ def test_serving_results_equal_alone_and_budget_respected():
     assert set(srv.results) == set(range(len(reqs)))
     for spec in reqs:
         rq = serve.Request(spec, _stream())
+        rq.solver.set_launch_config(4)   # the warp-tile kernel of the groups
         rq.solver.step(rq.dt, 12)
         q_alone, _ = rq.solver.fields()
         rq.solver.close()
