@@ -250,10 +250,15 @@ int gb_info(gb_solver *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *
 
 /* ---- groups (batched stepping of many simulations) --------------------------
  * A group steps several GB_MIXED solvers of the same order N with one launch
- * per SARK stage (a persistent kernel over the 16-element tiles of all of them)
- * plus one vertex-update launch per step.  Every solver keeps its own fields,
- * mesh, motion, time and step size; the result of each solver is bitwise the
- * same as stepping it alone with gb_step.  gb_group_create allocates the
+ * per SARK stage (a persistent kernel over the 16-element tiles of all of them,
+ * the mma.sync kernel) plus one vertex-update launch per step.  Every solver
+ * keeps its own fields, mesh, motion, time and step size; the result of each
+ * solver is bitwise the same as stepping it alone with gb_step on a warp-tile
+ * launch shape (1, 2 or 4).  The first gb_group_step of an order and size class
+ * (the group's tile count, in powers of two) times the group kernel with 4, 2
+ * and 1 warps per CTA on the group's own data (stage-0 launches, which only write
+ * buffers the step rewrites) and keeps the fastest, cached for the process.
+ * gb_group_create allocates the
  * descriptor buffers for up to `capacity` solvers (device and pinned host
  * memory) and uses `cuda_stream` for all its work; the solvers of a group must
  * have been created on that same stream.  gb_group_step enqueues nsteps steps
@@ -264,6 +269,14 @@ int gb_group_create(int capacity, void *cuda_stream, gb_group **out);
 int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int n, int64_t nsteps);
 int gb_group_destroy(gb_group *g);
 const char *gb_group_last_error(gb_group *g);
+/* gb_group_launch_config: the group kernel's warps per CTA last used for order N
+ * (0 before the first gb_group_step of that order).  GB_EINVAL for NULL or N out of
+ * 1..6. */
+int gb_group_launch_config(gb_group *g, int N, int *warps_per_cta);
+/* gb_group_set_launch_config: fix the group kernel's warps per CTA (1, 2 or 4) for
+ * order N and skip its tuner (all shapes give bitwise-equal results).  GB_EINVAL for
+ * other values or N out of 1..6. */
+int gb_group_set_launch_config(gb_group *g, int N, int warps_per_cta);
 
 /* gb_state_ptr: the device address of the current fields, owned by the solver and
  * valid until gb_destroy: the canonical FP64 layout in GB_FP64 mode; in GB_MIXED

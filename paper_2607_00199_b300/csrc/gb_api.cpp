@@ -209,6 +209,8 @@ static int launch_pml(gb_solver *s, const gb::StageArgs &a) {
 
 struct gb_group {
   int capacity = 0, num_sms = 1;
+  int warps[GB_MAX_N + 1] = {};   // group-kernel warps per CTA last used for each order (0: none yet)
+  bool fixed[GB_MAX_N + 1] = {};  // set by gb_group_set_launch_config: no tuning for that order
   cudaStream_t stream = nullptr;
   gb::StageArgs *d_args = nullptr, *h_args = nullptr;   // [4][capacity]
   int64_t *d_prefix = nullptr, *h_prefix = nullptr;     // tile prefix (n+1), then vertex prefix (n+1)
@@ -232,13 +234,21 @@ static void set_coefficients(gb_solver *s, double dt) {
 // copy of the operator tables.  The tuner times the rhs-only stage
 // kernel (which writes only the scratch buffer b2 and leaves the state alone) on
 // the solver's own data for each shape and keeps the fastest; a candidate after
-// the first must win by 3%.  Choices are cached per (N, K) for the process.
+// the first must win by 3%.  Choices are cached per (N, size class of K) for the process.
 static std::mutex g_tune_mu;
-static std::map<std::pair<int, int64_t>, int> g_tuned;
+static std::map<std::pair<int, int64_t>, int> g_tuned;        // (N, K class) -> solver launch shape
+static std::map<std::pair<int, int64_t>, int> g_group_tuned;  // (N, tile-count class) -> group warps per CTA
+
+// size class of a mesh or a group: the bit length of (count - 1), i.e. counts in (2^(c-1), 2^c]
+static int64_t k_class(int64_t count) {
+  int64_t c = 0;
+  for (int64_t x = count - 1; x > 0; x >>= 1) ++c;
+  return c;
+}
 
 static int tune_launch(gb_solver *s) {
   if (s->precision != GB_MIXED || s->warps != 0) return GB_OK;
-  const std::pair<int, int64_t> key(s->N, s->K);
+  const std::pair<int, int64_t> key(s->N, k_class(s->K));
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
@@ -901,6 +911,75 @@ int gb_group_create(int capacity, void *cuda_stream, gb_group **out) {
   return GB_OK;
 }
 
+// Group launch-shape tuner: warps per CTA of the group kernel (4, 2 or 1) for the group's
+// order and size class (tile count), timed on the group's own data with stage-0 launches, which
+// only write the stage buffer b1 and F_0 of each member (both rewritten by the step's own stage
+// 0); a later candidate must win by 3%.  Choices are cached per (N, tile-count class).
+static int group_tune(gb_group *g, int N, gb::GroupArgs &ga) {
+  if (g->fixed[N]) {
+    ga.warps = g->warps[N];
+    return GB_OK;
+  }
+  const std::pair<int, int64_t> key(N, k_class(ga.total_tiles));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_group_tuned.find(key);
+    if (it != g_group_tuned.end()) {
+      ga.warps = g->warps[N] = it->second;
+      return GB_OK;
+    }
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  const int cand[3] = {4, 2, 1};
+  int best = 4;
+  float best_ms = 1e30f;
+  ga.args = g->d_args;   // stage 0
+  for (int i = 0; i < 3 && ce == cudaSuccess; ++i) {
+    ga.warps = cand[i];
+    int rc = gb::launch_group_mixed(N, 0, ga, g->stream, g->num_sms);   // warm-up
+    if (rc) { ce = (cudaError_t)rc; break; }
+    ce = cudaEventRecord(e0, g->stream);
+    for (int r = 0; r < 2 && ce == cudaSuccess; ++r) {
+      rc = gb::launch_group_mixed(N, 0, ga, g->stream, g->num_sms);
+      if (rc) ce = (cudaError_t)rc;
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, g->stream);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce == cudaSuccess && ms < 0.97f * best_ms) {
+      best_ms = ms;
+      best = cand[i];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (ce != cudaSuccess) {
+    g->err = std::string("gb_group_step tuning: ") + cudaGetErrorString(ce);
+    return GB_ECUDA;
+  }
+  ga.warps = g->warps[N] = best;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_group_tuned[key] = best;
+  return GB_OK;
+}
+
+int gb_group_set_launch_config(gb_group *g, int N, int warps_per_cta) {
+  if (!g || N < 1 || N > GB_MAX_N || (warps_per_cta != 1 && warps_per_cta != 2 && warps_per_cta != 4))
+    return GB_EINVAL;
+  g->warps[N] = warps_per_cta;
+  g->fixed[N] = true;
+  return GB_OK;
+}
+
+int gb_group_launch_config(gb_group *g, int N, int *warps_per_cta) {
+  if (!g || !warps_per_cta || N < 1 || N > GB_MAX_N) return GB_EINVAL;
+  *warps_per_cta = g->warps[N];
+  return GB_OK;
+}
+
 int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int n, int64_t nsteps) {
   if (!g) return fail(nullptr, GB_EINVAL, "gb_group_step: NULL group");
   auto gfail = [&](int code, const std::string &m) { g->err = m; return code; };
@@ -956,6 +1035,11 @@ int gb_group_step(gb_group *g, gb_solver *const *solvers, const double *dt, int 
   ga.total_tiles = tstart[n];
   ga.total_vertices = vstart[n];
   ga.ops = solvers[0]->d_ops_mixed;
+  ga.warps = 4;
+  if (nsteps > 0) {
+    int rc = group_tune(g, N, ga);
+    if (rc) return rc;
+  }
   for (int64_t k = 0; k < nsteps; ++k) {
     for (int st = 0; st < 4; ++st) {
       ga.args = g->d_args + (size_t)st * g->capacity;

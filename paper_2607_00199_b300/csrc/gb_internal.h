@@ -237,6 +237,7 @@ struct GroupArgs {
   int64_t total_tiles;
   int64_t total_vertices;
   const void *ops;
+  int warps;   // warps per CTA of the group kernel (1, 2 or 4), chosen by the group tuner
 };
 
 // Launchers (gb_kernels.cu).  Return a cudaError_t value as int.

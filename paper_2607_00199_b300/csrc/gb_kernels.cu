@@ -478,13 +478,19 @@ static int launch_one(const StageArgs &a, cudaStream_t st, int num_sms) {
   constexpr int E = Tile<T, N>::E;
   const int threads = ((E * Dim<N>::Np + 31) / 32) * 32;
   const size_t smem = stage_smem<T, N>();
-  static bool attr_set = false;   // per template instance (one device per process assumed)
-  if (!attr_set) {
+  // the shared-memory opt-in and the occupancy are per-device facts, cached per device ordinal
+  int dev = 0;
+  cudaError_t derr = cudaGetDevice(&dev);
+  if (derr != cudaSuccess) return (int)derr;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  static bool attr_set[64] = {};
+  if (!attr_set[dev]) {
     cudaError_t err = cudaFuncSetAttribute(stage_kernel<T, N, STAGE, BC, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
-    attr_set = true;
+    attr_set[dev] = true;
   }
-  static int per_sm = 0;   // cached: no runtime queries while a graph is being captured
+  static int per_sm_d[64] = {};
+  int &per_sm = per_sm_d[dev];
   if (per_sm == 0) {
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage_kernel<T, N, STAGE, BC, REC>, threads, smem);
     if (err != cudaSuccess) return (int)err;

@@ -631,13 +631,19 @@ static int launch3_one(const Stage3Args &a, cudaStream_t st, int num_sms) {
   constexpr int E = Tile3<T, N>::E;
   const int threads = ((E * Dim3<N>::Np + 31) / 32) * 32;
   const size_t smem = stage3_smem<T, N>();
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the shared-memory opt-in and the occupancy are per-device facts, cached per device ordinal
+  int dev = 0;
+  cudaError_t derr = cudaGetDevice(&dev);
+  if (derr != cudaSuccess) return (int)derr;
+  if (dev < 0 || dev >= 64) return (int)cudaErrorInvalidDevice;
+  static bool attr_set[64] = {};
+  if (!attr_set[dev]) {
     cudaError_t err = cudaFuncSetAttribute(stage3_kernel<T, N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return (int)err;
-    attr_set = true;
+    attr_set[dev] = true;
   }
-  static int per_sm = 0;   // cached: no runtime queries while a graph is being captured
+  static int per_sm_d[64] = {};
+  int &per_sm = per_sm_d[dev];
   if (per_sm == 0) {
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, stage3_kernel<T, N, STAGE>, threads, smem);
     if (err != cudaSuccess) return (int)err;

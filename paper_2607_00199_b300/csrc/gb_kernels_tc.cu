@@ -711,7 +711,7 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_stage_k
 template <int N, int STAGE>
 __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_group_kernel(const GroupArgs gd) {
   typedef TcDim<N> D;
-  constexpr int W = D::W;
+  const int W = blockDim.x >> 5;                // warps per CTA: a launch parameter (1, 2 or 4)
   extern __shared__ float4 tc_smem4[];
   const float4 *btab = reinterpret_cast<const float4 *>(gd.ops);
   float *wbase = reinterpret_cast<float *>(tc_smem4);
@@ -744,6 +744,8 @@ __global__ void __launch_bounds__(32 * TcDim<N>::W, (N <= 4 ? 3 : 1)) tc_group_k
 }
 
 // ---------------------------------------------------------------------------
+constexpr int kTcMaxDevices = 64;
+
 template <int N>
 static size_t tc_smem(int W = TcDim<N>::W) {
   typedef TcDim<N> D;
@@ -774,14 +776,20 @@ static int tc_launch_one(const StageArgs &a_in, cudaStream_t st, int num_sms) {
   const int W = (a.warps_per_cta == 1 || a.warps_per_cta == 2) ? a.warps_per_cta : D::W;
   const size_t smem = tc_smem<N>(W);
   const int threads = 32 * W;
-  static bool attr_set = false;
-  if (!attr_set) {
+  // the shared-memory opt-in and the occupancy are per-device facts: cached per device ordinal
+  // (the first launch on a device queries them; none happen during a graph capture after it)
+  int dev = 0;
+  cudaError_t derr = cudaGetDevice(&dev);
+  if (derr != cudaSuccess) return (int)derr;
+  if (dev < 0 || dev >= kTcMaxDevices) return (int)cudaErrorInvalidDevice;
+  static bool attr_set[kTcMaxDevices] = {};
+  if (!attr_set[dev]) {
     cudaError_t err = cudaFuncSetAttribute(tc_stage_kernel<N, STAGE, BC, REC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<N>());
     if (err != cudaSuccess) return (int)err;
-    attr_set = true;
+    attr_set[dev] = true;
   }
-  static int per_sm_w[5] = {0, 0, 0, 0, 0};   // cached: no runtime queries while a graph is being captured
-  int &per_sm = per_sm_w[W];
+  static int per_sm_w[kTcMaxDevices][5] = {};
+  int &per_sm = per_sm_w[dev][W];
   if (per_sm == 0) {
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_stage_kernel<N, STAGE, BC, REC>, threads, smem);
     if (err != cudaSuccess) return (int)err;
@@ -839,22 +847,28 @@ int launch_stage_mixed(int N, const StageArgs &a, void *stream, int num_sms) {
 template <int N, int STAGE>
 static int tc_group_launch_one(const GroupArgs &g, cudaStream_t st, int num_sms) {
   typedef TcDim<N> D;
-  const size_t smem = tc_smem<N>();
-  constexpr int threads = 32 * D::W;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t err = cudaFuncSetAttribute(tc_group_kernel<N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int W = (g.warps == 1 || g.warps == 2) ? g.warps : D::W;
+  const size_t smem = tc_smem<N>(W);
+  const int threads = 32 * W;
+  int dev = 0;
+  cudaError_t derr = cudaGetDevice(&dev);
+  if (derr != cudaSuccess) return (int)derr;
+  if (dev < 0 || dev >= kTcMaxDevices) return (int)cudaErrorInvalidDevice;
+  static bool attr_set[kTcMaxDevices] = {};   // per device ordinal, like the single-solver launcher
+  if (!attr_set[dev]) {
+    cudaError_t err = cudaFuncSetAttribute(tc_group_kernel<N, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem<N>());
     if (err != cudaSuccess) return (int)err;
-    attr_set = true;
+    attr_set[dev] = true;
   }
-  static int per_sm = 0;   // cached: no runtime queries while a graph is being captured
+  static int per_sm_d[kTcMaxDevices][5] = {};
+  int &per_sm = per_sm_d[dev][W];
   if (per_sm == 0) {
     cudaError_t err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tc_group_kernel<N, STAGE>, threads, smem);
     if (err != cudaSuccess) return (int)err;
   }
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)num_sms * per_sm;
-  const int64_t need = (g.total_tiles + D::W - 1) / D::W;
+  const int64_t need = (g.total_tiles + W - 1) / W;
   if (grid > need) grid = need;
   if (grid < 1) grid = 1;
   tc_group_kernel<N, STAGE><<<(unsigned)grid, threads, smem, st>>>(g);

@@ -82,6 +82,8 @@ def _load():
         'gb_diagnostics_history': ([vp, _dp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_int64)], c_int),
         'gb_launch_config': ([vp, ctypes.POINTER(c_int)], c_int),
+        'gb_group_launch_config': ([vp, c_int, ctypes.POINTER(c_int)], c_int),
+        'gb_group_set_launch_config': ([vp, c_int, c_int], c_int),
         'gb_set_launch_config': ([vp, c_int], c_int),
         'gb_info': ([vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int),
                      ctypes.POINTER(i64), ctypes.POINTER(i64), _dp, _dp, ctypes.POINTER(i64)], c_int),
@@ -373,6 +375,20 @@ class Group:
         rc = lib.gb_group_step(self.h, arr, _ptr(d), n, int(nsteps))
         if rc != GB_OK:
             raise GBError(rc, lib.gb_group_last_error(self.h).decode())
+
+    def launch_config(self, N):
+        """Warps per CTA of the group kernel last used for order N (0: not stepped yet)."""
+        w = ctypes.c_int(0)
+        rc = lib.gb_group_launch_config(self.h, int(N), ctypes.byref(w))
+        if rc != GB_OK:
+            raise GBError(rc, 'gb_group_launch_config: bad order')
+        return w.value
+
+    def set_launch_config(self, N, warps_per_cta):
+        """Fix the group kernel's warps per CTA (1, 2 or 4) for order N and skip its tuner."""
+        rc = lib.gb_group_set_launch_config(self.h, int(N), int(warps_per_cta))
+        if rc != GB_OK:
+            raise GBError(rc, 'gb_group_set_launch_config: bad order or shape')
 
     def close(self):
         if getattr(self, 'h', None) is not None and self.h.value is not None:

@@ -132,3 +132,30 @@ def test_serving_results_equal_alone_and_budget_respected():
         assert rel <= 1e-5, (spec['id'], rel)
         assert np.array_equal(q_mix, q_alone)
     assert stats['step_latency_ms']['p99'] >= stats['step_latency_ms']['p50'] > 0
+
+
+
+@pytest.mark.parametrize('N', [2, 4])
+def test_group_shapes_are_bitwise_equal_and_tuned(N):
+    # the group kernel's warps per CTA (4, 2, 1) change only which warp takes which tile: the
+    # same results bit for bit; untuned, the group picks one of them
+    specs = [(5, 0.05, 1.0, 100.0), (9, 0.03, 0.7, 500.0)]
+    outs = []
+    for w in (4, 2, 1, None):
+        grouped = [_solver(n, N, A, T, Re) for (n, A, T, Re) in specs]
+        g = gb.Group(4, _stream())
+        if w:
+            g.set_launch_config(N, w)
+        g.step([s for s, _, _ in grouped], [dt for _, _, dt in grouped], 5)
+        assert g.launch_config(N) == w if w else g.launch_config(N) in (1, 2, 4)
+        outs.append([s.fields()[0] for s, _, _ in grouped])
+        for s, _, _ in grouped:
+            s.close()
+        g.close()
+    for o in outs[1:]:
+        for qa, qb in zip(o, outs[0]):
+            assert np.array_equal(qa, qb)
+    g = gb.Group(2, _stream())
+    with pytest.raises(gb.GBError):
+        g.set_launch_config(N, 3)
+    g.close()
