@@ -44,20 +44,19 @@ TRAFFIC_FILE = os.path.join(ROOT, 'profiles', 'stage_kernel_traffic.json')
 FP64_FLOP_PER_CLK_SM = 4.0
 
 
-def run_serving(torch, n_req=256, steps=500, rate=50.0, budget_gib=16.0):
+def run_serving(torch, n_req=256, steps=500, rate=50.0, budget_gib=None):
     """Serving stream of independent moving-mesh simulations: n_req requests with Poisson
     arrivals, K in {2048 .. 131072}, N in {2 .. 5}, random motion and Re, `steps` SARK
-    steps each, admitted against a device-memory budget and stepped together per
-    order by the continuous-batching loop (GB_MIXED).  Baselines: the same requests
-    run one after another alone, in GB_FP64 and in GB_MIXED, from per-(K, N) step
-    times measured here."""
+    steps each (GB_MIXED), admitted against a device-memory budget (default: 80% of the
+    free device memory) and stepped by the continuous-batching loop: small requests in
+    groups per (N, size class), large ones alone, every unit on its own stream at its own
+    cadence.  Baselines: the same requests run one after another alone, in GB_FP64 and in
+    GB_MIXED (tuned launch shape), from per-(K, N) step times measured here first; each
+    request's slowdown is its completion latency over its time alone in GB_MIXED."""
     from paper_2607_00199_b300 import gb, inputs, serve, state
     reqs = inputs.serving_requests(n_req, rate=rate, seed=1)
     stream = torch.cuda.Stream()
     setup = torch.cuda.Stream()
-    srv = serve.Server(int(budget_gib * 2 ** 30), stream.cuda_stream, steps_per_request=steps,
-                       setup_stream=setup.cuda_stream)
-    stats = srv.run(reqs, sync=stream.synchronize)
     # per-bucket step times of a request running alone
     alone = {}
     for prec, name, nst in ((gb.GB_FP64, 'fp64', 2), (gb.GB_MIXED, 'mixed', 10)):
@@ -66,26 +65,37 @@ def run_serving(torch, n_req=256, steps=500, rate=50.0, budget_gib=16.0):
                 spec = {'id': -1, 'arrival': 0.0, 'n': int(round(math.sqrt(K / 2))), 'N': N, 'A': 0.05, 'T': 1.0,
                         'Re': 1000.0, 'Ma': 0.1}
                 rq = serve.Request(spec, stream.cuda_stream, precision=prec)
-                rq.solver.step(rq.dt, 1)
+                rq.solver.step(rq.dt, 2)
                 stream.synchronize()
                 t0 = time.perf_counter()
                 rq.solver.step(rq.dt, nst)
                 rq.solver.sync()
                 alone[(name, K, N)] = (time.perf_counter() - t0) / nst
                 rq.solver.close()
+    alone_ms = {(K, N): alone[('mixed', K, N)] * 1e3 for (nm, K, N) in alone if nm == 'mixed'}
+    budget = None if budget_gib is None else int(budget_gib * 2 ** 30)
+    srv = serve.Server(budget, stream.cuda_stream, steps_per_request=steps, setup_stream=setup.cuda_stream,
+                       alone_ms=alone_ms)
+    stats = srv.run(reqs)
     work = sum(2 * r['n'] ** 2 * ((r['N'] + 1) * (r['N'] + 2) // 2) * 6 * 4 * steps for r in reqs)
     t_fp64 = sum(alone[('fp64', r['K'], r['N'])] * steps for r in reqs)
     t_mixed = sum(alone[('mixed', r['K'], r['N'])] * steps for r in reqs)
     return {'workload': '%d requests, Poisson %.0f/s (seed 1), K in {2048,8192,32768,131072}, N in {2,3,4,5}, '
-                        'A~U[0.01,0.08], T~U[0.5,2], Re~U[100,2000], Ma 0.1, %d SARK steps each, '
-                        'HBM budget %.0f GiB, GB_MIXED grouped by N' % (n_req, rate, steps, budget_gib),
-            'dof_stage_per_s': stats['dof_stage_per_s'], 'wall_s': stats['wall_s'], 'ticks': stats['ticks'],
+                        'A~U[0.01,0.08], T~U[0.5,2], Re~U[100,2000], Ma 0.1, %d SARK steps each, GB_MIXED; '
+                        'device-memory budget %.1f GiB (%s); small requests grouped per (N, size class), '
+                        'K >= 32768 alone, every unit on its own stream'
+                        % (n_req, rate, steps, stats['budget_bytes'] / 2 ** 30,
+                           'given' if budget_gib is not None else '80% of the free device memory'),
+            'dof_stage_per_s': stats['dof_stage_per_s'], 'wall_s': stats['wall_s'], 'launches': stats['launches'],
             'step_latency_ms': stats['step_latency_ms'], 'completion_latency_s': stats['completion_latency_s'],
+            'slowdown_vs_alone': stats.get('slowdown_vs_alone'),
             'peak_device_bytes': stats['peak_device_bytes'], 'budget_bytes': stats['budget_bytes'],
             'alone_fp64_dof_stage_per_s': work / t_fp64, 'alone_mixed_dof_stage_per_s': work / t_mixed,
             'speedup_vs_alone_fp64': (work / stats['wall_s']) / (work / t_fp64),
+            'speedup_vs_alone_mixed': (work / stats['wall_s']) / (work / t_mixed),
             'note': 'aggregate rate = all DOF-stage updates / wall time from the first arrival to the last '
-                    'completion (includes set-up of each request and idle time before arrivals)'}
+                    'completion (includes set-up of each request and idle time before arrivals); slowdown = '
+                    'completion latency (arrival to last step) / the request\'s steps x its alone step time'}
 
 
 WORKLOAD3 = dict(dims=(64, 16, 16), L=(8.0, 2.0, 2.0), N=3, Ma=0.1, Re=500.0, cfl=0.5,

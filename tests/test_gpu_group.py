@@ -110,20 +110,24 @@ def test_predicted_footprint_is_conservative():
 def test_serving_results_equal_alone_and_budget_respected():
     # a small stream: several sizes and orders, arrivals spread over ~30 ms, some
     # requests arrive while others run; the budget holds about three at a time
+    # (the last one is large: a unit of its own, stepped with gb_step on its tuned shape)
     reqs = []
-    sizes = [(8, 2), (12, 3), (6, 2), (10, 3), (16, 4), (8, 4), (14, 2)]
+    sizes = [(8, 2), (12, 3), (6, 2), (10, 3), (16, 4), (8, 4), (14, 2), (128, 3)]
     for i, (n, N) in enumerate(sizes):
         reqs.append({'id': i, 'arrival': 0.005 * i, 'n': n, 'N': N, 'A': 0.02 + 0.01 * i,
                      'T': 0.6 + 0.2 * i, 'Re': 150.0 + 200.0 * i, 'Ma': 0.1, 'K': 2 * n * n})
-    budget = 3 * serve.predicted_device_bytes(2 * 16 * 16, 4)
+    budget = 3 * serve.predicted_device_bytes(2 * 16 * 16, 4) + serve.predicted_device_bytes(2 * 128 * 128, 3)
     setup = torch.cuda.Stream()
-    srv = serve.Server(budget, _stream(), steps_per_request=12, keep_fields=True, setup_stream=setup.cuda_stream)
-    stats = srv.run(reqs, sync=torch.cuda.synchronize)
+    srv = serve.Server(budget, _stream(), steps_per_request=12, keep_fields=True, setup_stream=setup.cuda_stream,
+                       alone_ms={(2 * n * n, N): 1.0 for n, N in sizes})
+    stats = srv.run(reqs)
     assert stats['peak_device_bytes'] <= budget
     assert set(srv.results) == set(range(len(reqs)))
+    assert stats['slowdown_vs_alone']['p50'] > 0
     for spec in reqs:
         rq = serve.Request(spec, _stream())
-        rq.solver.set_launch_config(4)   # the warp-tile kernel of the groups
+        if spec['K'] < srv.large_k:
+            rq.solver.set_launch_config(4)   # the warp-tile kernel of the groups
         rq.solver.step(rq.dt, 12)
         q_alone, _ = rq.solver.fields()
         rq.solver.close()
