@@ -3,13 +3,16 @@
 //
 // Same right-hand side and SARK combination as the other stage kernels (Secs. 2-5):
 // F = volume + surface + P Ntilde(I q) at the stage geometry, then the stage or final
-// SARK combination.  The work is laid out one element per thread:
+// SARK combination.  The work is laid out by element tiles:
 //
-//   a CTA of 128 threads owns a tile of 128 consecutive (Morton-ordered) elements;
-//   thread t is element t of the tile and TMEM lane t.
+//   a CTA (one per SM, persistent) owns tiles of 128 consecutive (Morton-ordered)
+//   elements in turn; element e of a tile is TMEM lane e, and two compute threads
+//   (t and t + 128) share its pointwise work; four helper warps form the next tile's
+//   geometry and halo, issue the MMAs and the bulk copies.
 //
 // The four dense contractions of the semi-discrete form (Sec. 3) are M = 128 (elements)
-// tcgen05.mma products of kind::tf32, issued by one thread, accumulating in FP32 in TMEM:
+// tcgen05.mma products of kind::tf32, each issued by one lane of a helper warp,
+// accumulating in FP32 in TMEM:
 //   V_f  = Q_f [Dr | Ds]^T      (f = 1..6; A = the field's nodal values)
 //   C_f  = Q_f I^T              (f = 1..3; the values at the cubature points)
 //   R_f += Ntilde_f P^T         (f = 4..6; the projected collision term)
@@ -19,23 +22,24 @@
 // the tensor core, so a product carries ~2^-21 relative error (the operator tables are split
 // on the host the same way, from FP64).  The heads of the field tile sit in shared memory in
 // the K-major core-matrix layout; every other A operand (the field tails, Ntilde, the
-// fluxes) is written by its element's thread straight into its TMEM lane with tcgen05.st.
+// fluxes) is written by its element's threads straight into its TMEM lane with tcgen05.st.
 //
 // The pointwise work runs per element with the element's values in registers: the
 // geometric factors from the FP64 stage vertices (Sec. 5: FP64 positions and edge
 // differences, FP32 afterwards, as in the other mixed kernel), the chain rule with the
 // Atilde couplings and the v_G . grad q advection (Sec. 2), Ntilde at the cubature points,
 // the upwind face fluxes F_S and F_ALE (Sec. 3) with the neighbour traces read from the
-// staged tile (neighbours inside the tile) or from global memory, and the SARK combination
-// of the element's row.
+// staged tile (neighbours inside the tile), from the halo the helpers staged (the tile's
+// out-of-tile faces) or, past the halo's capacity, from global memory, and the SARK
+// combination of the element's row.
 //
 // Data movement per tile is bulk copies with completion on mbarriers: the tile's own fields
 // q_i arrive while the previous tile finishes (prefetched once its fluxes are formed), F_0 and
 // the accumulator are loaded at the start of the tile, q_n once the first MMA batch has read
 // the head tile; the SARK outputs are written into those staged rows and leave as bulk
-// stores.  Three MMA batches per tile, each committed to an mbarrier.  Every wait is
-// bounded: on expiry the kernel sets GB_STATUS_TIMEOUT, waits (bounded) for what it issued,
-// frees its TMEM and returns.
+// stores.  Four MMA batches per tile (volume, interpolation, projection, lift), each
+// committed to an mbarrier.  Every wait is bounded: on expiry the kernel sets
+// GB_STATUS_TIMEOUT, waits (bounded) for what it issued, frees its TMEM and returns.
 //
 // Field layout: the element-major FP32 perturbation layout of the GB_MIXED path (element
 // stride S = 4 mod 8 floats, fields of Np values), unchanged.
@@ -90,17 +94,32 @@ struct UmDim {
   static constexpr int SM_END = SM_H + HMAX * HW;
   // TMEM columns (512 allocated): field tails, volume products (the rhs R takes their first
   // 96 columns once they are read), interpolation products (Ntilde heads in place, then the
-  // flux heads); Ntilde tails in free 8-column slots, flux tails over the field tails
+  // flux heads); Ntilde tails in 8-column slots (see um_nslot), flux tails over the field tails
   static constexpr uint32_t T_QL = 0, T_V = 96, T_R = 96, T_C = 288, T_FH = 288, T_FL = 0;
+  static constexpr int NCH = KC / 8, HALF = (NCH + 1) / 2;        // cubature chunks; those of thread half 0
+  static constexpr int NOWN = 6;                                  // volume-region slots of each half
+  static constexpr int NQL = 6 * KV / 8;                          // slots over the field tails
   static_assert(N >= 1 && N <= 4, "the tcgen05 kernel covers orders 1..4");
   static_assert(6 * KV <= 96 && 6 * NV <= 192 && 3 * NCM <= 192, "TMEM map");
-  static_assert(3 * (KC / 8) <= 28 && 6 * KL <= 96, "TMEM slots");
+  static_assert(3 * HALF <= NOWN + NQL / 2 && 3 * (NCH - HALF) <= NOWN + (NQL - NQL / 2) && 6 * KL <= 96,
+                "TMEM slots");
+  static_assert(NV == 32 ? Np > 8 : 6 * NV <= 96, "volume-region slots");
 };
 
-// 8-column TMEM slots for the Ntilde tails: the field tails [0, 96), the volume columns
-// past R [192, 288) and [480, 512), all free once the volume products have been read
-__device__ __forceinline__ uint32_t um_slot(int s) {
-  return s < 12 ? 8u * s : (s < 24 ? 192u + 8u * (s - 12) : 480u + 8u * (s - 24));
+// 8-column TMEM slot of the Ntilde tails of field f, cubature chunk ks.  Chunk ks is formed by
+// thread half h = (ks >= HALF); its first six slots lie in [192, 288): at N >= 3 these are the
+// volume columns of fields 3..5 that the same half read itself (Vr and Vs of its nodes
+// [8h, 8h + 8)), at N <= 2 columns past the volume products; the rest are a half of the
+// field-tail columns (free once the first MMA batch is complete).  So no thread overwrites
+// columns that the other thread of its element may still have to read.
+template <int N>
+__host__ __device__ constexpr uint32_t um_nslot(int f, int ks) {
+  typedef UmDim<N> D;
+  const int h = ks >= D::HALF ? 1 : 0;
+  const int i = f * (h ? D::NCH - D::HALF : D::HALF) + (ks - (h ? D::HALF : 0));
+  if (i < D::NOWN)
+    return D::NV == 32 ? D::T_V + (3 + i / 2) * D::NV + (i % 2) * D::KV + 8 * h : 192u + 8 * (D::NOWN * h + i);
+  return D::T_QL + 8 * ((h ? D::NQL / 2 : 0) + (i - D::NOWN));
 }
 
 // ---- PTX wrappers -----------------------------------------------------------------
@@ -385,7 +404,7 @@ __device__ __forceinline__ void um_cubature(uint32_t tl, float itau) {
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
         um_st8(tl + D::T_C + f * NCM + 8 * (C0 + ch), hv[f]);
-        um_st8(tl + um_slot(f * NCH + C0 + ch), lv[f]);
+        um_st8(tl + um_nslot<N>(f, C0 + ch), lv[f]);
       }
     }
   }
@@ -591,31 +610,51 @@ __device__ __forceinline__ void um_stage_motion_warp(const StageArgs &a, int sta
 //   sG    the geometry of the tile's elements, formed by the helper warps one tile ahead
 //   sH    the halo of the tile's out-of-tile neighbour traces, staged one tile ahead
 // Warps 0-7 compute (two threads per element: thread t handles element t % 128 and half
-// t / 128 of each phase's nodes, points, face nodes or row chunks).  Warps 8-11 are helpers:
-// thread 256 + i forms the geometry of element i of the next tile while the current one is
-// computed, the helpers stage the traces across the next tile's out-of-tile faces (a halo
-// of up to HMAX faces; a Morton tile of 128 triangles has about 32), and lane 0 of each
-// helper warp issues a share of every MMA batch (the products of whole fields, so that each
-// accumulator has one issuing thread and a fixed order); warp 8 also issues the bulk copies.  Hand-offs are mbarriers, one phase per tile each: the
-// copies and MMA commits complete the "data" barriers, the compute threads arrive on the
-// "operands ready" ones.
+// t / 128 of each phase's nodes, points, face nodes or row chunks); lane 0 of compute warp
+// w < 6 also issues the volume and the lift products of field w, at the two points where the
+// compute warps would otherwise wait for them.  Warps 8-11 are helpers: thread 256 + i forms
+// the geometry of element i of the next tile while the current one is computed, the helpers
+// stage the traces across the next tile's out-of-tile faces (a halo of up to HMAX faces; a
+// Morton tile of 128 triangles has about 32), and lane 0 of helper warp 8 + f (f < 3) issues
+// the interpolation and projection products of field f; warp 8 also issues the bulk copies.
+// Every accumulator has one issuing thread, so its sums run in a fixed order.  Hand-offs are
+// mbarriers, one phase per tile each: the copies and MMA commits complete the "data"
+// barriers, the compute threads arrive on the "operands ready" ones.
 constexpr int kUmThreads = 384;
-constexpr int kUmIssuers = 4;
+constexpr int kUmIssuers = 4;       // helper warps committing the interpolation and projection batches
+constexpr int kUmFieldIssuers = 6;  // compute warps committing the volume and lift batches
+
+// the MMAs of one field: K / 8 k-steps of the three split products hi*hi + lo*hi + hi*lo into
+// accumulator d (A tails in TMEM at a_lo; A heads in shared memory at descriptor a_hi_s or in
+// TMEM at a_hi_t; B heads and tails at descriptors bh, bl), issued by the lane with `issue` set
+__device__ __forceinline__ void um_mma_field(uint32_t d, uint32_t a_lo, uint64_t a_hi_s, uint32_t a_hi_t, bool hi_in_tmem,
+                                             uint64_t bh, uint64_t bl, uint64_t b_step, uint32_t id, int ksteps,
+                                             uint32_t a_step_t, uint64_t a_step_s, bool first_overwrites, uint32_t issue) {
+  for (int ks = 0; ks < ksteps; ++ks) {
+    const uint64_t b0 = bh + ks * b_step, b1 = bl + ks * b_step;
+    um_mma_ts_p(d, a_lo + ks * a_step_t, b0, id, (first_overwrites && ks == 0) ? 0u : 1u, issue);
+    if (hi_in_tmem) {
+      um_mma_ts_p(d, a_hi_t + ks * a_step_t, b0, id, 1u, issue);
+      um_mma_ts_p(d, a_hi_t + ks * a_step_t, b1, id, 1u, issue);
+    } else {
+      um_mma_ss_p(d, a_hi_s + ks * a_step_s, b0, id, 1u, issue);
+      um_mma_ss_p(d, a_hi_s + ks * a_step_s, b1, id, 1u, issue);
+    }
+  }
+}
 
 // inputs of an element's geometry: its mesh record and the current positions and motion
 // shapes of its vertices (loaded ahead of their use)
 struct UmGeoIn {
   MeshRec rec;
-  double2 xv[3];
-  float2 sv[3];
+  double2 xv[3], sv[3];   // as loaded: nothing waits for the loads until the geometry is formed
 };
 __device__ __forceinline__ MeshRec um_rec(const StageArgs &a, int64_t e) { return a.mesh[e]; }
 __device__ __forceinline__ void um_vertices(const StageArgs &a, UmGeoIn &in) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     in.xv[k] = reinterpret_cast<const double2 *>(a.xn)[in.rec.v[k]];
-    const double2 sv = reinterpret_cast<const double2 *>(a.shape)[in.rec.v[k]];
-    in.sv[k] = make_float2((float)sv.x, (float)sv.y);
+    in.sv[k] = reinterpret_cast<const double2 *>(a.shape)[in.rec.v[k]];
   }
 }
 
@@ -633,7 +672,7 @@ __device__ __forceinline__ void um_geometry(const StageArgs &a, const UmGeoIn &i
   for (int k = 0; k < 3; ++k) {
     bx[k] = in.xv[k].x + rec.shift[2 * k] * a.period[0];
     by[k] = in.xv[k].y + rec.shift[2 * k + 1] * a.period[1];
-    const float sxk = in.sv[k].x, syk = in.sv[k].y;
+    const float sxk = (float)in.sv[k].x, syk = (float)in.sv[k].y;
     ix[k] = xff * sxk;
     iy[k] = xff * syk;
     vx[k] = gff * sxk;
@@ -718,9 +757,6 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   // operands ready (256 compute threads): heads and tails; geometry read; R and Ntilde;
   // fluxes; output rows
   __shared__ __align__(8) uint64_t mb_opA, mb_gread, mb_opN, mb_opF, mb_out;
-  // the volume products read (256 compute threads): the Ntilde tails go into columns that held
-  // them, and the two threads of an element read and write them at their own pace
-  __shared__ __align__(8) uint64_t mb_vread;
   __shared__ uint32_t s_tmem;
   __shared__ double s_motion[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -733,12 +769,14 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     uint64_t *one[4] = {&mb_ld, &mb_x, &mb_qn, &mb_free};
     for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(um_sa(one[i])) : "memory");
     uint64_t *iss[4] = {&mb_v, &mb_c, &mb_p, &mb_l};
-    for (int i = 0; i < 4; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(um_sa(iss[i])), "r"(kUmIssuers) : "memory");
+    for (int i = 0; i < 4; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;"
+                   :: "r"(um_sa(iss[i])), "r"((i == 0 || i == 3) ? kUmFieldIssuers : kUmIssuers) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(um_sa(&mb_geo)) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 128;" :: "r"(um_sa(&mb_halo)) : "memory");
     s_hcount = 0;
-    uint64_t *many[6] = {&mb_opA, &mb_gread, &mb_opN, &mb_opF, &mb_out, &mb_vread};
-    for (int i = 0; i < 6; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" :: "r"(um_sa(many[i])) : "memory");
+    uint64_t *many[5] = {&mb_opA, &mb_gread, &mb_opN, &mb_opF, &mb_out};
+    for (int i = 0; i < 5; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 256;" :: "r"(um_sa(many[i])) : "memory");
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(um_sa(&mb_tab)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     // the operator tables and the first tile's own fields, in flight during the set-up
@@ -757,6 +795,13 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   um_fence_after();
   const uint32_t tm = s_tmem;
   bool failed = !__all_sync(0xffffffffu, um_wait(&mb_tab, 0));
+  const uint32_t one = lane == 0 ? 1u : 0u;   // the lane that executes its warp's MMAs and commits
+  const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
+  // descriptors at the operands' bases; an operand at byte offset o has descriptor base + o / 16
+  const uint64_t dA = um_desc(sA_a, 2048, 128);
+  const uint64_t dBV = um_desc(sB_a + 4 * D::BV, NV * 16, 128), dBI = um_desc(sB_a + 4 * D::BI, NCM * 16, 128);
+  const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
+  constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(NCM), idR = um_idesc(16);
 
   if (warp >= 8) {
     // ================= helpers: geometry one tile ahead, MMA issue, bulk copies =================
@@ -764,12 +809,20 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     const bool copier = tid == 256;
     unsigned armed = (copier && (int64_t)blockIdx.x < ntile) ? 1u : 0u;   // phases in flight from this thread
     uint32_t ld_par = 0;  // parity of the armed phase of mb_ld
-    const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
-    // descriptors at the operands' bases; an operand at byte offset o has descriptor base + o / 16
-    const uint64_t dA = um_desc(sA_a, 2048, 128);
-    const uint64_t dBV = um_desc(sB_a + 4 * D::BV, NV * 16, 128), dBI = um_desc(sB_a + 4 * D::BI, NCM * 16, 128);
-    const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
-    constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(NCM), idR = um_idesc(16);
+    // the interpolation products of field iw < 3 (A heads in shared memory, tails in TMEM)
+    auto issue_interp = [&]() {
+      if (iw < 3)
+        um_mma_field(tm + D::T_C + iw * NCM, tm + D::T_QL + iw * KV, dA + (uint64_t)(((iw * NPP / 4) * 2048) >> 4), 0u,
+                     false, dBI, dBI + (uint64_t)((4 * NCM * KV) >> 4), (uint64_t)((4 * 2 * NCM * 4) >> 4), idC, KV / 8,
+                     8u, (uint64_t)((2 * 2048) >> 4), true, one);
+      um_commit_p(&mb_c, one);
+      if (one) armed |= 16u;
+    };
+    // the first tile's geometry inputs: the mesh records first, before anything waits
+    const bool first = (int64_t)blockIdx.x < ntile;
+    const int64_t t0 = blockIdx.x, r0 = a.K - t0 * 128;
+    UmGeoIn in0;
+    if (first) in0.rec = um_rec(a, t0 * 128 + (hi < r0 ? hi : 0));
     // the stage's motion factors (FP64 cosines: three lanes of warp 11 in parallel) after the
     // set-up barrier, so that the compute warps and the first bulk copies do not wait for them
     if (warp == 11) {
@@ -783,35 +836,22 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
     const float gff = (float)s_motion[0], xff = (float)s_motion[1];
-    // the first tile's geometry and halo
-    if ((int64_t)blockIdx.x < ntile) {
-      const int64_t t0 = blockIdx.x, r0 = a.K - t0 * 128;
-      UmGeoIn in0;
-      in0.rec = um_rec(a, t0 * 128 + (hi < r0 ? hi : 0));
+    // the first tile: its vertex data in flight while its interpolation products are issued,
+    // then its geometry and halo
+    if (first) {
       um_vertices(a, in0);
+      if (!__all_sync(0xffffffffu, um_wait(&mb_opA, 0))) {
+        failed = true;
+      } else {
+        um_fence_after();
+        issue_interp();
+      }
       um_geometry<N>(a, in0, hi < r0, t0 * 128, tile_rows(t0), xff, gff, sG + hi * GW, &s_hcount, s_hsrc);
       um_arrive(&mb_geo);
       asm volatile("bar.sync 1, 128;" ::: "memory");
       um_halo<N>(qin, s_hsrc, s_hcount < D::HMAX ? s_hcount : D::HMAX, hi, sH);
       um_arrive(&mb_halo);
     }
-    // the MMAs of one field: K / 8 k-steps of the three split products into accumulator d
-    const uint32_t one = lane == 0 ? 1u : 0u;   // the lane that executes this warp's MMAs and commits
-    auto mma_field = [&](uint32_t d, uint32_t a_lo, uint64_t a_hi_s, uint32_t a_hi_t, bool hi_in_tmem, uint64_t bh,
-                         uint64_t bl, uint64_t b_step, uint32_t id, int ksteps, uint32_t a_step_t, uint64_t a_step_s,
-                         bool first_overwrites) {
-      for (int ks = 0; ks < ksteps; ++ks) {
-        const uint64_t b0 = bh + ks * b_step, b1 = bl + ks * b_step;
-        um_mma_ts_p(d, a_lo + ks * a_step_t, b0, id, (first_overwrites && ks == 0) ? 0u : 1u, one);
-        if (hi_in_tmem) {
-          um_mma_ts_p(d, a_hi_t + ks * a_step_t, b0, id, 1u, one);
-          um_mma_ts_p(d, a_hi_t + ks * a_step_t, b1, id, 1u, one);
-        } else {
-          um_mma_ss_p(d, a_hi_s + ks * a_step_s, b0, id, 1u, one);
-          um_mma_ss_p(d, a_hi_s + ks * a_step_s, b1, id, 1u, one);
-        }
-      }
-    };
     // A failed (timed-out) wait does not leave the loop at once: the helpers meet at named
     // barriers, so the rest of the iteration is skipped and they leave together at its end.
     uint32_t par = 0;
@@ -819,8 +859,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       const int64_t e0 = tile * 128;
       const uint32_t tile_bytes = (uint32_t)(tile_rows(tile) * S * sizeof(float));
       const bool more = tile + gridDim.x < ntile;
-      // the next tile's geometry inputs: its mesh record now, its vertex data after the first
-      // batch is issued, the arithmetic once the projection batch is issued
+      // the next tile's geometry inputs: its mesh record now, its vertex data after the
+      // interpolation batch is issued, the arithmetic once the projection batch is issued
       const int64_t tn = tile + gridDim.x, rn = a.K - tn * 128;
       UmGeoIn gin;
       if (more) gin.rec = um_rec(a, tn * 128 + (hi < rn ? hi : 0));
@@ -828,10 +868,13 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
         // the previous tile's stores have read the shared tile and the staged rows (the first
         // tile's is free from the set-up)
         if (tile != (int64_t)blockIdx.x) {
-          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          // the output rows leave in the first bulk group, F_0 or the accumulator in a second
+          if (STAGE >= 0 && STAGE <= 2) asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
+          else asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
           um_arrive(&mb_free);
         }
         if (STAGE >= 1) {
+          if (tile != (int64_t)blockIdx.x) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
           uint32_t bytes = 0;
           if (STAGE == 1 || STAGE == 2) bytes += tile_bytes;
           if (STAGE >= 2) bytes += tile_bytes;
@@ -847,37 +890,29 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
           armed |= 2u;
         }
       }
-      // ---- batch 1: volume products of fields {iw, iw + 4}, interpolation of a field ----
-      if (!failed) {
+      // ---- interpolation products (the first tile's were issued before its geometry) ----
+      if (!failed && tile != (int64_t)blockIdx.x) {
         if (!__all_sync(0xffffffffu, um_wait(&mb_opA, par))) {
           failed = true;
         } else {
           um_fence_after();
-          for (int f = iw; f < 6; f += 4)
-            mma_field(tm + D::T_V + f * NV, tm + D::T_QL + f * KV, dA + (uint64_t)(((f * NPP / 4) * 2048) >> 4), 0u,
-                      false, dBV, dBV + (uint64_t)((4 * NV * KV) >> 4), (uint64_t)((4 * 2 * NV * 4) >> 4), idV, KV / 8,
-                      8u, (uint64_t)((2 * 2048) >> 4), true);
-          um_commit_p(&mb_v, one);
-          const int fc = iw == 0 ? 2 : (iw == 2 ? 0 : (iw == 3 ? 1 : -1));
-          if (fc >= 0)
-            mma_field(tm + D::T_C + fc * NCM, tm + D::T_QL + fc * KV, dA + (uint64_t)(((fc * NPP / 4) * 2048) >> 4), 0u,
-                      false, dBI, dBI + (uint64_t)((4 * NCM * KV) >> 4), (uint64_t)((4 * 2 * NCM * 4) >> 4), idC, KV / 8,
-                      8u, (uint64_t)((2 * 2048) >> 4), true);
-          um_commit_p(&mb_c, one);
-          if (one) armed |= 8u | 16u;
+          issue_interp();
         }
       }
-      // ---- q_n into the shared tile once the first batch has read it ----
+      // ---- q_n into the shared tile once the volume and interpolation products have read it ----
       if (copier && STAGE >= 0 && !failed) {
-        if (!um_wait(&mb_c, par)) {
+        if (!um_wait(&mb_v, par) || !um_wait(&mb_c, par)) {
           failed = true;
         } else {
+          // (at stage 0 the SARK pass writes F_0 into sX1 once q_n is in: the previous F_0 store
+          // has read it by then)
+          asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
           um_bulk_load(sA, reinterpret_cast<const float *>(a.qn) + e0 * S, tile_bytes, &mb_qn);
           armed |= 4u;
         }
       }
       if (more) um_vertices(a, gin);
-      // ---- batch 2: R_{4..6} += Ntilde P^T, field iw ----
+      // ---- projection products: R_{4..6} += Ntilde P^T, field iw ----
       if (!failed) {
         if (!__all_sync(0xffffffffu, um_wait(&mb_opN, par))) {
           failed = true;
@@ -891,7 +926,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
               const uint64_t b0 = dBP + (uint64_t)((4 * 2 * ks * 16 * 4) >> 4);
               const uint64_t b1 = dBP + (uint64_t)((4 * (16 * KC + 2 * ks * 16 * 4)) >> 4);
               const uint32_t ah = tm + D::T_C + iw * NCM + 8 * ks;
-              um_mma_ts_p(d, tm + um_slot(iw * (KC / 8) + ks), b0, idR, 1u, one);
+              um_mma_ts_p(d, tm + um_nslot<N>(iw, ks), b0, idR, 1u, one);
               um_mma_ts_p(d, ah, b0, idR, 1u, one);
               um_mma_ts_p(d, ah, b1, idR, 1u, one);
             }
@@ -912,22 +947,14 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
           um_arrive(&mb_geo);
         }
       }
-      // ---- batch 3: R += Flux LIFT^T, fields {iw, iw + 4}; then the next tile's own fields ----
-      if (!failed) {
-        if (!__all_sync(0xffffffffu, um_wait(&mb_opF, par))) {
+      // ---- the next tile's own fields, once this tile's fluxes have read the current ones ----
+      if (copier && more && !failed) {
+        if (!um_wait(&mb_opF, par)) {
           failed = true;
         } else {
-          um_fence_after();
-          for (int f = iw; f < 6; f += 4)
-            mma_field(tm + D::T_R + f * 16, tm + D::T_FL + f * KL, 0, tm + D::T_FH + f * KL, true, dBL,
-                      dBL + (uint64_t)((4 * 16 * KL) >> 4), (uint64_t)((4 * 2 * 16 * 4) >> 4), idR, KL / 8, 8u, 0, false);
-          um_commit_p(&mb_l, one);
-          if (one) armed |= 64u;
-          if (copier && more) {
-            um_fence_async_smem();
-            um_bulk_load(sRaw, qin + tn * 128 * S, (uint32_t)(tile_rows(tn) * S * sizeof(float)), &mb_ld);
-            ld_par = par ^ 1u;
-          }
+          um_fence_async_smem();
+          um_bulk_load(sRaw, qin + tn * 128 * S, (uint32_t)(tile_rows(tn) * S * sizeof(float)), &mb_ld);
+          ld_par = par ^ 1u;
         }
       }
       // ---- the next tile's halo, once this tile's fluxes have read the current one ----
@@ -949,10 +976,11 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
                          :: "l"(reinterpret_cast<float *>(dst) + e0 * S), "r"(um_sa(src)), "r"(tile_bytes) : "memory");
           };
           store(STAGE < 0 ? a.Fout : a.qout, sA);
+          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
           if (STAGE == 0) store(a.F0, sX1);
           if (STAGE == 1) store(a.acc, sX1);
           if (STAGE == 2) store(a.acc, sX2);
-          asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          if (STAGE >= 0 && STAGE <= 2) asm volatile("cp.async.bulk.commit_group;" ::: "memory");
         }
       }
       // all helpers leave together if any of them saw a wait run out
@@ -986,6 +1014,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     const float k1[5] = {a.kco[1][0], a.kco[1][1], a.kco[1][2], a.kco[1][3], a.kco[1][4]};
     bool bad = false;
     uint32_t par = 0;
+    uint32_t carmed = 0;   // this lane's MMA commits in flight: 1 volume, 2 lift
     for (int64_t tile = blockIdx.x; tile < ntile && !failed; tile += gridDim.x, par ^= 1u) {
       const int64_t e0 = tile * 128;
       const int nel = tile_rows(tile);
@@ -999,6 +1028,16 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       um_fence_async_smem();
       um_fence_before();
       um_arrive(&mb_opA);
+      // ---- volume products of field `warp` (warps 0-5), once every element's operands are in ----
+      if (warp < kUmFieldIssuers) {
+        if (!__all_sync(0xffffffffu, um_wait(&mb_opA, par))) { failed = true; break; }
+        um_fence_after();
+        um_mma_field(tm + D::T_V + warp * NV, tm + D::T_QL + warp * KV, dA + (uint64_t)(((warp * NPP / 4) * 2048) >> 4),
+                     0u, false, dBV, dBV + (uint64_t)((4 * NV * KV) >> 4), (uint64_t)((4 * 2 * NV * 4) >> 4), idV,
+                     KV / 8, 8u, (uint64_t)((2 * 2048) >> 4), true, one);
+        um_commit_p(&mb_v, one);
+        carmed = one;
+      }
       // ---- the tile's geometry, formed by the helpers ----
       if (!__all_sync(0xffffffffu, um_wait(&mb_geo, par))) { failed = true; break; }
       UmGeo<N> G;
@@ -1023,13 +1062,11 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       // ---- volume terms, into R ----
       if (!__all_sync(0xffffffffu, um_wait(&mb_v, par))) { failed = true; break; }
       um_fence_after();
+      carmed &= ~1u;
       if (h == 0) um_volume<N, 0>(tl, G, mc, mcs);
       else um_volume<N, 1>(tl, G, mc, mcs);
-      um_fence_before();
-      um_arrive(&mb_vread);
-      // ---- collision term at the cubature points (its tails overwrite volume columns: after
-      //      both threads of every element have read them) ----
-      if (!__all_sync(0xffffffffu, um_wait(&mb_vread, par))) { failed = true; break; }
+      // ---- collision term at the cubature points (its tails go to columns that this thread
+      //      has read itself, or that no thread reads any more) ----
       if (!__all_sync(0xffffffffu, um_wait(&mb_c, par))) { failed = true; break; }
       um_fence_after();
       if (h == 0) um_cubature<N, 0>(tl, itau);
@@ -1069,8 +1106,19 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       um_wait_st();
       um_fence_before();
       um_arrive(&mb_opF);
+      // ---- lift products of field `warp` (warps 0-5), once every element's fluxes are in ----
+      if (warp < kUmFieldIssuers) {
+        if (!__all_sync(0xffffffffu, um_wait(&mb_opF, par))) { failed = true; break; }
+        um_fence_after();
+        um_mma_field(tm + D::T_R + warp * 16, tm + D::T_FL + warp * KL, 0, tm + D::T_FH + warp * KL, true, dBL,
+                     dBL + (uint64_t)((4 * 16 * KL) >> 4), (uint64_t)((4 * 2 * 16 * 4) >> 4), idR, KL / 8, 8u, 0,
+                     false, one);
+        um_commit_p(&mb_l, one);
+        carmed = 2u * one;
+      }
       // ---- SARK combination once the lift and the staged rows are in ----
       if (!__all_sync(0xffffffffu, um_wait(&mb_l, par))) { failed = true; break; }
+      carmed = 0u;
       if (STAGE >= 0 && !__all_sync(0xffffffffu, um_wait(&mb_qn, par))) { failed = true; break; }
       if (STAGE >= 1 && !__all_sync(0xffffffffu, um_wait(&mb_x, par))) { failed = true; break; }
       um_fence_after();
@@ -1097,7 +1145,12 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       um_arrive(&mb_out);
     }
     if (STAGE == 3 && bad) atomicOr(a.status, GB_STATUS_NAN);
-    if (failed) atomicOr(a.status, GB_STATUS_TIMEOUT);
+    if (failed) {
+      // wait (bounded) for the products this lane issued in the current tile
+      if (carmed & 1u) um_wait(&mb_v, par);
+      if (carmed & 2u) um_wait(&mb_l, par);
+      atomicOr(a.status, GB_STATUS_TIMEOUT);
+    }
   }
   if (tid == 0) {   // the set-up copies have landed (at once, unless a wait ran out)
     um_wait(&mb_tab, 0);
