@@ -8,21 +8,23 @@
 //   a CTA (one per SM, persistent) owns tiles of 128 consecutive (Morton-ordered)
 //   elements in turn; element e of a tile is TMEM lane e, and two compute threads
 //   (t and t + 128) share its pointwise work; four helper warps form the next tile's
-//   geometry and halo, issue the MMAs and the bulk copies.
+//   geometry and halo, issue the projection products and the bulk copies.
 //
 // The four dense contractions of the semi-discrete form (Sec. 3) are M = 128 (elements)
-// tcgen05.mma products of kind::tf32, each issued by one lane of a helper warp,
-// accumulating in FP32 in TMEM:
-//   V_f  = Q_f [Dr | Ds]^T      (f = 1..6; A = the field's nodal values)
-//   C_f  = Q_f I^T              (f = 1..3; the values at the cubature points)
+// tcgen05.mma products of kind::tf32, each accumulator fed by one lane, accumulating in
+// FP32 in TMEM:
+//   [V_f | C_f] = Q_f [Dr | Ds | I]^T  (f = 1..3: the volume products and the values at the
+//                                       cubature points in one product; A = the field's nodes)
+//   V_f  = Q_f [Dr | Ds]^T      (f = 4..6)
 //   R_f += Ntilde_f P^T         (f = 4..6; the projected collision term)
 //   R_f += Flux_f LIFT^T        (f = 1..6; the lifted face fluxes)
 // Each operand is split into a TF32 head rounded to nearest and its FP32 tail (x = hi + lo),
-// and every product is formed as hi*hi + lo*hi + hi*lo; the tail is truncated to TF32 by
+// and every product is formed as hi*hi + hi*lo + lo*hi; the tail is truncated to TF32 by
 // the tensor core, so a product carries ~2^-21 relative error (the operator tables are split
-// on the host the same way, from FP64).  The heads of the field tile sit in shared memory in
-// the K-major core-matrix layout; every other A operand (the field tails, Ntilde, the
-// fluxes) is written by its element's threads straight into its TMEM lane with tcgen05.st.
+// on the host the same way, from FP64).  The tails of the field tile sit in shared memory in
+// the K-major core-matrix layout (one of the three products reads them there); every other
+// A operand (the field heads, Ntilde, the fluxes) is written by its element's threads
+// straight into its TMEM lane with tcgen05.st.
 //
 // The pointwise work runs per element with the element's values in registers: the
 // geometric factors from the FP64 stage vertices (Sec. 5: FP64 positions and edge
@@ -36,8 +38,8 @@
 // Data movement per tile is bulk copies with completion on mbarriers: the tile's own fields
 // q_i arrive while the previous tile finishes (prefetched once its fluxes are formed), F_0 and
 // the accumulator are loaded at the start of the tile, q_n once the first MMA batch has read
-// the head tile; the SARK outputs are written into those staged rows and leave as bulk
-// stores.  Four MMA batches per tile (volume, interpolation, projection, lift), each
+// the tail tile; the SARK outputs are written into those staged rows and leave as bulk
+// stores.  Three MMA batches per tile (volume with interpolation, projection, lift), each
 // committed to an mbarrier.  Every wait is bounded: on expiry the kernel sets
 // GB_STATUS_TIMEOUT, waits (bounded) for what it issued, frees its TMEM and returns.
 //
@@ -61,26 +63,27 @@ struct UmDim {
   static constexpr int Nc = ((3 * N + 2) / 2) * ((3 * N + 2) / 2);
   static constexpr int S = tc_round_s(6 * Np);   // element stride of the field layout (floats)
   static constexpr int S4 = S / 4;               // 16-byte chunks per element row
-  static constexpr int NPP = (Np + 3) & ~3;      // field column stride of the head tile in shared memory
-  static constexpr int KV = (Np + 7) & ~7;       // K of the Dr/Ds and I products; field stride of the TMEM tails
-  static constexpr int CA = (6 * NPP + (KV - NPP) + 3) & ~3;   // head-tile columns (the last field's K overrun included)
+  static constexpr int NPP = (Np + 3) & ~3;      // field column stride of the tail tile in shared memory
+  static constexpr int KV = (Np + 7) & ~7;       // K of the Dr/Ds and I products; field stride of the TMEM heads
+  static constexpr int CA = (6 * NPP + (KV - NPP) + 3) & ~3;   // tail-tile columns (the last field's K overrun included)
   static constexpr int NV = (2 * KV + 15) & ~15; // N of the volume product: Dr rows at 0, Ds rows at KV
   static constexpr int NCM = (Nc + 15) & ~15;    // N of the interpolation product
   static constexpr int KC = (Nc + 7) & ~7;       // K of the projection product
   static constexpr int NR = 16;                  // N of the projection and lift products (Np <= 15)
   static constexpr int KL = (NFN + 7) & ~7;      // K of the lift product
+  static constexpr int NVC = NV + NCM;           // N of the merged volume and interpolation product (fields 1..3)
   // operator tables (floats), each as its TF32 head then its tail, core-matrix K-major layout:
-  // entry (n, k) of an R x K table at (k / 4) (4 R) + 4 n + k % 4
+  // entry (n, k) of an R x K table at (k / 4) (4 R) + 4 n + k % 4.  BV: the rows of Dr (at 0),
+  // Ds (at KV) and I (at NV), NVC x KV; the volume product of fields 4..6 reads its first NV rows
   static constexpr int BV = 0;
-  static constexpr int BI = BV + 2 * NV * KV;
-  static constexpr int BP = BI + 2 * NCM * KV;
+  static constexpr int BP = BV + 2 * NVC * KV;
   static constexpr int BL = BP + 2 * NR * KC;
   static constexpr int BBAR = BL + 2 * NR * KL;  // per node ((1 + r) / 2, (1 + s) / 2)
   static constexpr int BTOT = BBAR + 2 * 16;
-  // dynamic shared memory (floats): head tile [128 x CA] (then q_n and q_{i+1}), own fields
-  // [128 x S], F_0 [128 x S], accumulator [128 x S], tables, geometry [128 x GW], halo of the
-  // out-of-tile neighbour traces [HMAX x HW]
-  static constexpr int SAW = CA > S ? CA : S;      // columns of the head-tile region (heads, then q_n)
+  // dynamic shared memory (floats): field-tail tile [128 x CA] (then q_n and q_{i+1}), own
+  // fields [128 x S], F_0 [128 x S], accumulator [128 x S], tables, geometry [128 x GW], halo
+  // of the out-of-tile neighbour traces [HMAX x HW]
+  static constexpr int SAW = CA > S ? CA : S;      // columns of the tail-tile region (tails, then q_n)
   static constexpr int SM_A = 0;
   static constexpr int SM_RAW = SM_A + 128 * SAW;
   static constexpr int SM_X1 = SM_RAW + 128 * S;
@@ -92,34 +95,56 @@ struct UmDim {
   static constexpr int HW = 6 * Nfp;               // floats per halo entry (face node k, field fld at 6 k + fld)
   static constexpr int SM_H = SM_G + 128 * GW;
   static constexpr int SM_END = SM_H + HMAX * HW;
-  // TMEM columns (512 allocated): field tails, volume products (the rhs R takes their first
-  // 96 columns once they are read), interpolation products (Ntilde heads in place, then the
-  // flux heads); Ntilde tails in 8-column slots (see um_nslot), flux tails over the field tails
-  static constexpr uint32_t T_QL = 0, T_V = 96, T_R = 96, T_C = 288, T_FH = 288, T_FL = 0;
+  // TMEM columns (512 allocated), per field f (see um_tv and the functions after it):
+  //   [0, 96)        field heads (KV columns per field); later Ntilde tails and flux tails
+  //   from T_V0      fields 1..3: [Vr | Vs | C] (NVC columns), then fields 4..6: [Vr | Vs] (NV);
+  //                  R_f takes the Vr columns of field f once they are read, the Ntilde heads
+  //                  replace C in place, and at N >= 3 the flux heads take the Vs columns
+  //   from T_END     free: Ntilde tails where they fit (N <= 3), flux heads at N <= 2
+  static constexpr uint32_t T_QH = 0, T_V0 = 96;
+  static constexpr uint32_t T_END = T_V0 + 3 * NVC + 3 * NV;
   static constexpr int NCH = KC / 8, HALF = (NCH + 1) / 2;        // cubature chunks; those of thread half 0
-  static constexpr int NOWN = 6;                                  // volume-region slots of each half
-  static constexpr int NQL = 6 * KV / 8;                          // slots over the field tails
+  static constexpr bool SLOTS_FREE = (512 - (int)T_END) / 8 >= 3 * NCH;
+  static constexpr int NQL = 6 * KV / 8;                          // 8-column slots over the field heads
   static_assert(N >= 1 && N <= 4, "the tcgen05 kernel covers orders 1..4");
-  static_assert(6 * KV <= 96 && 6 * NV <= 192 && 3 * NCM <= 192, "TMEM map");
-  static_assert(3 * HALF <= NOWN + NQL / 2 && 3 * (NCH - HALF) <= NOWN + (NQL - NQL / 2) && 6 * KL <= 96,
-                "TMEM slots");
-  static_assert(NV == 32 ? Np > 8 : 6 * NV <= 96, "volume-region slots");
+  static_assert(6 * KV <= 96 && 6 * KL <= 96 && T_END <= 512 && KC <= NCM && NVC <= 256, "TMEM map");
+  static_assert(NV == 32 ? (Np > 8 && KL <= KV) : T_END + 6 * KL <= 512, "flux heads");
+  static_assert(SLOTS_FREE || (NV == 32 && 3 * HALF <= 6 + NQL / 2 && 3 * (NCH - HALF) <= 6 + (NQL - NQL / 2)),
+                "Ntilde tail slots");
 };
 
-// 8-column TMEM slot of the Ntilde tails of field f, cubature chunk ks.  Chunk ks is formed by
-// thread half h = (ks >= HALF); its first six slots lie in [192, 288): at N >= 3 these are the
-// volume columns of fields 3..5 that the same half read itself (Vr and Vs of its nodes
-// [8h, 8h + 8)), at N <= 2 columns past the volume products; the rest are a half of the
-// field-tail columns (free once the first MMA batch is complete).  So no thread overwrites
-// columns that the other thread of its element may still have to read.
+// TMEM column of the volume products of field f (Vr at +0, Vs at +KV; C at +NV for f < 3)
+template <int N>
+__host__ __device__ constexpr uint32_t um_tv(int f) {
+  typedef UmDim<N> D;
+  return f < 3 ? D::T_V0 + f * D::NVC : D::T_V0 + 3 * D::NVC + (f - 3) * D::NV;
+}
+template <int N>
+__host__ __device__ constexpr uint32_t um_tc(int f) { return um_tv<N>(f) + UmDim<N>::NV; }   // f < 3
+template <int N>
+__host__ __device__ constexpr uint32_t um_tr(int f) { return um_tv<N>(f); }                  // R_f, 16 columns
+template <int N>
+__host__ __device__ constexpr uint32_t um_tfl(int f) { return UmDim<N>::T_QH + f * UmDim<N>::KL; }
+template <int N>
+__host__ __device__ constexpr uint32_t um_tfh(int f) {
+  typedef UmDim<N> D;
+  return D::NV == 32 ? um_tv<N>(f) + D::KV : D::T_END + f * D::KL;
+}
+
+// 8-column TMEM slot of the Ntilde tails of field f, cubature chunk ks.  Where there is room
+// past the products they go there.  Otherwise chunk ks, formed by thread half h = (ks >= HALF),
+// goes first to the Vs columns of nodes [8h, 8h + 8) of a field (read by the same half
+// itself), then to a half of the field-head columns (free once the first MMA batch is
+// complete).  So no thread overwrites columns that the other thread of its element may still
+// have to read.
 template <int N>
 __host__ __device__ constexpr uint32_t um_nslot(int f, int ks) {
   typedef UmDim<N> D;
+  if (D::SLOTS_FREE) return D::T_END + 8 * (f * D::NCH + ks);
   const int h = ks >= D::HALF ? 1 : 0;
   const int i = f * (h ? D::NCH - D::HALF : D::HALF) + (ks - (h ? D::HALF : 0));
-  if (i < D::NOWN)
-    return D::NV == 32 ? D::T_V + (3 + i / 2) * D::NV + (i % 2) * D::KV + 8 * h : 192u + 8 * (D::NOWN * h + i);
-  return D::T_QL + 8 * ((h ? D::NQL / 2 : 0) + (i - D::NOWN));
+  if (i < 6) return um_tv<N>(i) + D::KV + 8 * h;
+  return D::T_QH + 8 * ((h ? D::NQL / 2 : 0) + (i - 6));
 }
 
 // ---- PTX wrappers -----------------------------------------------------------------
@@ -257,7 +282,7 @@ struct UmGeo {
   float2 vgx2[NP2], vgy2[NP2];
 };
 
-// heads (smem tile) and tails (TMEM) of fields [3H, 3H + 3) of the element's row
+// tails (smem tile) and heads (TMEM) of fields [3H, 3H + 3) of the element's row
 template <int N, int H>
 __device__ __forceinline__ void um_convert(const float *row, float *sA, uint32_t tl, int el, bool live) {
   typedef UmDim<N> D;
@@ -274,29 +299,27 @@ __device__ __forceinline__ void um_convert(const float *row, float *sA, uint32_t
     q[4 * (j - J0) + 3] = v.w;
   }
   auto val = [&](int f, int n) -> float { return n < Np ? q[f * Np + n - 4 * J0] : 0.0f; };
-  // head k-groups of the three fields (the K overrun past the last field goes with H = 1)
+  // tail k-groups of the three fields (the K overrun past the last field goes with H = 1)
   constexpr int G0 = F0 * NPP / 4, G1 = H ? CA / 4 : (F0 + 3) * NPP / 4;
 #pragma unroll
   for (int g = G0; g < G1; ++g) {
-    float hv[4];
+    float lv[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
       const int col = 4 * g + i, f = col / NPP, n = col % NPP;
-      hv[i] = f < 6 ? um_tf32(val(f, n)) : 0.0f;
+      const float x = f < 6 ? val(f, n) : 0.0f;
+      lv[i] = x - um_tf32(x);
     }
-    reinterpret_cast<float4 *>(sA)[g * 128 + el] = make_float4(hv[0], hv[1], hv[2], hv[3]);
+    reinterpret_cast<float4 *>(sA)[g * 128 + el] = make_float4(lv[0], lv[1], lv[2], lv[3]);
   }
 #pragma unroll
   for (int f = F0; f < F0 + 3; ++f)
 #pragma unroll
     for (int j = 0; j < KV; j += 8) {
-      uint32_t lo[8];
+      uint32_t hv[8];
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const float x = val(f, j + i);
-        lo[i] = __float_as_uint(x - um_tf32(x));
-      }
-      um_st8(tl + D::T_QL + f * KV + j, lo);
+      for (int i = 0; i < 8; ++i) hv[i] = __float_as_uint(um_tf32(val(f, j + i)));
+      um_st8(tl + D::T_QH + f * KV + j, hv);
     }
 }
 
@@ -304,7 +327,7 @@ __device__ __forceinline__ void um_convert(const float *row, float *sA, uint32_t
 template <int N, int H>
 __device__ __forceinline__ void um_volume(uint32_t tl, const UmGeo<N> &G, float mc, float mcs) {
   typedef UmDim<N> D;
-  constexpr int Np = D::Np, KV = D::KV, NV = D::NV;
+  constexpr int Np = D::Np, KV = D::KV;
   constexpr int n0 = 8 * H;
   if constexpr (n0 < Np) {
     constexpr int P0 = n0 / 2;   // first node pair
@@ -318,8 +341,8 @@ __device__ __forceinline__ void um_volume(uint32_t tl, const UmGeo<N> &G, float 
       uint32_t vr[3][8], vs[3][8];
 #pragma unroll
       for (int ff = 0; ff < 3; ++ff) {
-        um_ld8(tl + D::T_V + (f0 + ff) * NV + n0, vr[ff]);
-        um_ld8(tl + D::T_V + (f0 + ff) * NV + KV + n0, vs[ff]);
+        um_ld8(tl + um_tv<N>(f0 + ff) + n0, vr[ff]);
+        um_ld8(tl + um_tv<N>(f0 + ff) + KV + n0, vs[ff]);
       }
       um_wait_ld();
 #pragma unroll
@@ -358,7 +381,7 @@ __device__ __forceinline__ void um_volume(uint32_t tl, const UmGeo<N> &G, float 
 #pragma unroll
       for (int i = 0; i < 8; ++i)
         v[i] = n0 + i < Np ? __float_as_uint((i & 1) ? rhs[f][i >> 1].y : rhs[f][i >> 1].x) : 0u;
-      um_st8(tl + D::T_R + f * 16 + n0, v);
+      um_st8(tl + um_tr<N>(f) + n0, v);
     }
   }
 }
@@ -368,7 +391,7 @@ __device__ __forceinline__ void um_volume(uint32_t tl, const UmGeo<N> &G, float 
 template <int N, int H>
 __device__ __forceinline__ void um_cubature(uint32_t tl, float itau) {
   typedef UmDim<N> D;
-  constexpr int NCM = D::NCM, NCH = D::KC / 8, HALF = (NCH + 1) / 2;
+  constexpr int NCH = D::KC / 8, HALF = (NCH + 1) / 2;
   constexpr int C0 = H ? HALF : 0, C1 = H ? NCH : HALF, NC = C1 - C0;
   const float ISQ2 = 0.70710678118654752f;
   if constexpr (NC > 0) {
@@ -376,7 +399,7 @@ __device__ __forceinline__ void um_cubature(uint32_t tl, float itau) {
 #pragma unroll
     for (int f = 0; f < 3; ++f)
 #pragma unroll
-      for (int ch = 0; ch < NC; ++ch) um_ld8(tl + D::T_C + f * NCM + 8 * (C0 + ch), cq[f][ch]);
+      for (int ch = 0; ch < NC; ++ch) um_ld8(tl + um_tc<N>(f) + 8 * (C0 + ch), cq[f][ch]);
     um_wait_ld();
 #pragma unroll
     for (int f = 0; f < 3; ++f)
@@ -403,7 +426,7 @@ __device__ __forceinline__ void um_cubature(uint32_t tl, float itau) {
       }
 #pragma unroll
       for (int f = 0; f < 3; ++f) {
-        um_st8(tl + D::T_C + f * NCM + 8 * (C0 + ch), hv[f]);
+        um_st8(tl + um_tc<N>(f) + 8 * (C0 + ch), hv[f]);
         um_st8(tl + um_nslot<N>(f, C0 + ch), lv[f]);
       }
     }
@@ -506,8 +529,8 @@ __device__ __forceinline__ void um_flux_store(uint32_t tl, const float (&fl)[6][
         hv[i] = __float_as_uint(t);
         lv[i] = __float_as_uint(x - t);
       }
-      um_st8(tl + D::T_FH + f * KL + 8 * H, hv);
-      um_st8(tl + D::T_FL + f * KL + 8 * H, lv);
+      um_st8(tl + um_tfh<N>(f) + 8 * H, hv);
+      um_st8(tl + um_tfl<N>(f) + 8 * H, lv);
     }
   }
 }
@@ -522,7 +545,7 @@ __device__ __forceinline__ void um_sark(uint32_t tl, float4 *rowq, float4 *row1,
   constexpr int FA = (4 * J0) / Np, FB = ((4 * J1 - 1) / Np < 5 ? (4 * J1 - 1) / Np : 5);   // fields touched
   uint32_t rr[FB - FA + 1][16];
 #pragma unroll
-  for (int f = FA; f <= FB; ++f) um_ld16(tl + D::T_R + f * 16, rr[f - FA]);
+  for (int f = FA; f <= FB; ++f) um_ld16(tl + um_tr<N>(f), rr[f - FA]);
   um_wait_ld();
 #pragma unroll
   for (int f = FA; f <= FB; ++f) {
@@ -611,35 +634,34 @@ __device__ __forceinline__ void um_stage_motion_warp(const StageArgs &a, int sta
 //   sH    the halo of the tile's out-of-tile neighbour traces, staged one tile ahead
 // Warps 0-7 compute (two threads per element: thread t handles element t % 128 and half
 // t / 128 of each phase's nodes, points, face nodes or row chunks); lane 0 of compute warp
-// w < 6 also issues the volume and the lift products of field w, at the two points where the
-// compute warps would otherwise wait for them.  Warps 8-11 are helpers: thread 256 + i forms
-// the geometry of element i of the next tile while the current one is computed, the helpers
-// stage the traces across the next tile's out-of-tile faces (a halo of up to HMAX faces; a
-// Morton tile of 128 triangles has about 32), and lane 0 of helper warp 8 + f (f < 3) issues
-// the interpolation and projection products of field f; warp 8 also issues the bulk copies.
-// Every accumulator has one issuing thread, so its sums run in a fixed order.  Hand-offs are
-// mbarriers, one phase per tile each: the copies and MMA commits complete the "data"
-// barriers, the compute threads arrive on the "operands ready" ones.
+// w < 6 also issues the first products (volume, and for w < 3 the interpolation in the same
+// instruction) and the lift products of field w, at the two points where the compute warps
+// would otherwise wait for them.  Warps 8-11 are helpers: thread 256 + i forms the geometry of
+// element i of the next tile while the current one is computed, the helpers stage the traces
+// across the next tile's out-of-tile faces (a halo of up to HMAX faces; a Morton tile of 128
+// triangles has about 32), and lane 0 of helper warp 8 + f (f < 3) issues the projection
+// products of field f; warp 8 also issues the bulk copies.  Every accumulator has one issuing
+// thread, so its sums run in a fixed order.  Hand-offs are mbarriers, one phase per tile
+// each: the copies and MMA commits complete the "data" barriers, the compute threads arrive
+// on the "operands ready" ones.
 constexpr int kUmThreads = 384;
-constexpr int kUmIssuers = 4;       // helper warps committing the interpolation and projection batches
-constexpr int kUmFieldIssuers = 6;  // compute warps committing the volume and lift batches
+constexpr int kUmIssuers = 4;       // helper warps committing the projection batch
+constexpr int kUmFieldIssuers = 6;  // compute warps committing the first and the lift batches
 
-// the MMAs of one field: K / 8 k-steps of the three split products hi*hi + lo*hi + hi*lo into
-// accumulator d (A tails in TMEM at a_lo; A heads in shared memory at descriptor a_hi_s or in
-// TMEM at a_hi_t; B heads and tails at descriptors bh, bl), issued by the lane with `issue` set
-__device__ __forceinline__ void um_mma_field(uint32_t d, uint32_t a_lo, uint64_t a_hi_s, uint32_t a_hi_t, bool hi_in_tmem,
+// K / 8 k-steps of the three split products hi*hi + hi*lo + lo*hi of one field into
+// accumulator d, issued by the lane with `issue` set.  A heads in TMEM at a_hi; A tails in TMEM
+// at a_lo_t, or (lo_in_smem) in shared memory at descriptor a_lo_s; B heads and tails at
+// descriptors bh, bl, advancing by b_step per k-step.  The first product overwrites d when
+// `overwrite` is set.
+__device__ __forceinline__ void um_mma_field(uint32_t d, uint32_t a_hi, uint32_t a_lo_t, uint64_t a_lo_s, bool lo_in_smem,
                                              uint64_t bh, uint64_t bl, uint64_t b_step, uint32_t id, int ksteps,
-                                             uint32_t a_step_t, uint64_t a_step_s, bool first_overwrites, uint32_t issue) {
+                                             bool overwrite, uint32_t issue) {
   for (int ks = 0; ks < ksteps; ++ks) {
     const uint64_t b0 = bh + ks * b_step, b1 = bl + ks * b_step;
-    um_mma_ts_p(d, a_lo + ks * a_step_t, b0, id, (first_overwrites && ks == 0) ? 0u : 1u, issue);
-    if (hi_in_tmem) {
-      um_mma_ts_p(d, a_hi_t + ks * a_step_t, b0, id, 1u, issue);
-      um_mma_ts_p(d, a_hi_t + ks * a_step_t, b1, id, 1u, issue);
-    } else {
-      um_mma_ss_p(d, a_hi_s + ks * a_step_s, b0, id, 1u, issue);
-      um_mma_ss_p(d, a_hi_s + ks * a_step_s, b1, id, 1u, issue);
-    }
+    um_mma_ts_p(d, a_hi + 8 * ks, b0, id, (overwrite && ks == 0) ? 0u : 1u, issue);
+    um_mma_ts_p(d, a_hi + 8 * ks, b1, id, 1u, issue);
+    if (lo_in_smem) um_mma_ss_p(d, a_lo_s + ks * (uint64_t)((2 * 2048) >> 4), b0, id, 1u, issue);
+    else um_mma_ts_p(d, a_lo_t + 8 * ks, b0, id, 1u, issue);
   }
 }
 
@@ -738,7 +760,7 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   const int STAGE = a.stage;
   typedef UmDim<N> D;
   constexpr int S = D::S, NPP = D::NPP, KV = D::KV, GW = D::GW;
-  constexpr int NV = D::NV, NCM = D::NCM, KC = D::KC, KL = D::KL;
+  constexpr int NV = D::NV, KC = D::KC, KL = D::KL;
   constexpr int NP2 = UmGeo<N>::NP2;
   const float SQ2 = 1.41421356237309505f;
   extern __shared__ __align__(1024) float um_smem[];
@@ -799,9 +821,9 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
   // descriptors at the operands' bases; an operand at byte offset o has descriptor base + o / 16
   const uint64_t dA = um_desc(sA_a, 2048, 128);
-  const uint64_t dBV = um_desc(sB_a + 4 * D::BV, NV * 16, 128), dBI = um_desc(sB_a + 4 * D::BI, NCM * 16, 128);
+  const uint64_t dBV = um_desc(sB_a + 4 * D::BV, D::NVC * 16, 128);
   const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
-  constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(NCM), idR = um_idesc(16);
+  constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(D::NCM), idR = um_idesc(16);
 
   if (warp >= 8) {
     // ================= helpers: geometry one tile ahead, MMA issue, bulk copies =================
@@ -809,15 +831,6 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     const bool copier = tid == 256;
     unsigned armed = (copier && (int64_t)blockIdx.x < ntile) ? 1u : 0u;   // phases in flight from this thread
     uint32_t ld_par = 0;  // parity of the armed phase of mb_ld
-    // the interpolation products of field iw < 3 (A heads in shared memory, tails in TMEM)
-    auto issue_interp = [&]() {
-      if (iw < 3)
-        um_mma_field(tm + D::T_C + iw * NCM, tm + D::T_QL + iw * KV, dA + (uint64_t)(((iw * NPP / 4) * 2048) >> 4), 0u,
-                     false, dBI, dBI + (uint64_t)((4 * NCM * KV) >> 4), (uint64_t)((4 * 2 * NCM * 4) >> 4), idC, KV / 8,
-                     8u, (uint64_t)((2 * 2048) >> 4), true, one);
-      um_commit_p(&mb_c, one);
-      if (one) armed |= 16u;
-    };
     // the first tile's geometry inputs: the mesh records first, before anything waits
     const bool first = (int64_t)blockIdx.x < ntile;
     const int64_t t0 = blockIdx.x, r0 = a.K - t0 * 128;
@@ -836,16 +849,9 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
     }
     asm volatile("bar.sync 1, 128;" ::: "memory");
     const float gff = (float)s_motion[0], xff = (float)s_motion[1];
-    // the first tile: its vertex data in flight while its interpolation products are issued,
-    // then its geometry and halo
+    // the first tile's geometry and halo
     if (first) {
       um_vertices(a, in0);
-      if (!__all_sync(0xffffffffu, um_wait(&mb_opA, 0))) {
-        failed = true;
-      } else {
-        um_fence_after();
-        issue_interp();
-      }
       um_geometry<N>(a, in0, hi < r0, t0 * 128, tile_rows(t0), xff, gff, sG + hi * GW, &s_hcount, s_hsrc);
       um_arrive(&mb_geo);
       asm volatile("bar.sync 1, 128;" ::: "memory");
@@ -890,18 +896,24 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
           armed |= 2u;
         }
       }
-      // ---- interpolation products (the first tile's were issued before its geometry) ----
-      if (!failed && tile != (int64_t)blockIdx.x) {
-        if (!__all_sync(0xffffffffu, um_wait(&mb_opA, par))) {
+      // ---- interpolation products of field iw < 3, once the volume products are complete (they
+      //      go first: the compute threads need them first) ----
+      if (!failed) {
+        if (!__all_sync(0xffffffffu, um_wait(&mb_v, par))) {
           failed = true;
         } else {
           um_fence_after();
-          issue_interp();
+          if (iw < 3)
+            um_mma_field(tm + um_tc<N>(iw), tm + D::T_QH + iw * KV, 0u, dA + (uint64_t)(((iw * NPP / 4) * 2048) >> 4), true,
+                         dBV + (uint64_t)NV, dBV + (uint64_t)NV + (uint64_t)((D::NVC * KV) >> 2), (uint64_t)(2 * D::NVC),
+                         idC, KV / 8, true, one);
+          um_commit_p(&mb_c, one);
+          if (one) armed |= 16u;
         }
       }
       // ---- q_n into the shared tile once the volume and interpolation products have read it ----
       if (copier && STAGE >= 0 && !failed) {
-        if (!um_wait(&mb_v, par) || !um_wait(&mb_c, par)) {
+        if (!um_wait(&mb_c, par)) {
           failed = true;
         } else {
           // (at stage 0 the SARK pass writes F_0 into sX1 once q_n is in: the previous F_0 store
@@ -920,12 +932,12 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
           um_fence_after();
           if (iw < 3) {
             // the tails sit in 8-column slots that are not contiguous across k-steps
-            const uint32_t d = tm + D::T_R + (3 + iw) * 16;
+            const uint32_t d = tm + um_tr<N>(3 + iw);
 #pragma unroll
             for (int ks = 0; ks < KC / 8; ++ks) {
               const uint64_t b0 = dBP + (uint64_t)((4 * 2 * ks * 16 * 4) >> 4);
               const uint64_t b1 = dBP + (uint64_t)((4 * (16 * KC + 2 * ks * 16 * 4)) >> 4);
-              const uint32_t ah = tm + D::T_C + iw * NCM + 8 * ks;
+              const uint32_t ah = tm + um_tc<N>(iw) + 8 * ks;
               um_mma_ts_p(d, tm + um_nslot<N>(iw, ks), b0, idR, 1u, one);
               um_mma_ts_p(d, ah, b0, idR, 1u, one);
               um_mma_ts_p(d, ah, b1, idR, 1u, one);
@@ -1032,9 +1044,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       if (warp < kUmFieldIssuers) {
         if (!__all_sync(0xffffffffu, um_wait(&mb_opA, par))) { failed = true; break; }
         um_fence_after();
-        um_mma_field(tm + D::T_V + warp * NV, tm + D::T_QL + warp * KV, dA + (uint64_t)(((warp * NPP / 4) * 2048) >> 4),
-                     0u, false, dBV, dBV + (uint64_t)((4 * NV * KV) >> 4), (uint64_t)((4 * 2 * NV * 4) >> 4), idV,
-                     KV / 8, 8u, (uint64_t)((2 * 2048) >> 4), true, one);
+        um_mma_field(tm + um_tv<N>(warp), tm + D::T_QH + warp * KV, 0u, dA + (uint64_t)(((warp * NPP / 4) * 2048) >> 4),
+                     true, dBV, dBV + (uint64_t)((D::NVC * KV) >> 2), (uint64_t)(2 * D::NVC), idV, KV / 8, true, one);
         um_commit_p(&mb_v, one);
         carmed = one;
       }
@@ -1110,9 +1121,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       if (warp < kUmFieldIssuers) {
         if (!__all_sync(0xffffffffu, um_wait(&mb_opF, par))) { failed = true; break; }
         um_fence_after();
-        um_mma_field(tm + D::T_R + warp * 16, tm + D::T_FL + warp * KL, 0, tm + D::T_FH + warp * KL, true, dBL,
-                     dBL + (uint64_t)((4 * 16 * KL) >> 4), (uint64_t)((4 * 2 * 16 * 4) >> 4), idR, KL / 8, 8u, 0,
-                     false, one);
+        um_mma_field(tm + um_tr<N>(warp), tm + um_tfh<N>(warp), tm + um_tfl<N>(warp), 0u, false, dBL,
+                     dBL + (uint64_t)((4 * 16 * KL) >> 4), (uint64_t)((4 * 2 * 16 * 4) >> 4), idR, KL / 8, false, one);
         um_commit_p(&mb_l, one);
         carmed = 2u * one;
       }
@@ -1228,13 +1238,13 @@ void um_fill(const RefOps &Rf, std::vector<float> &h) {
         h[base + rows * kcols + off] = lo;
       }
   };
-  put(D::BV, D::NV, D::KV, [&](int n, int k) -> double {
+  put(D::BV, D::NVC, D::KV, [&](int n, int k) -> double {   // rows: Dr, Ds, I
     if (k >= Np) return 0.0;
     if (n < Np) return Rf.Dr[n * Np + k];
     if (n >= D::KV && n - D::KV < Np) return Rf.Ds[(n - D::KV) * Np + k];
+    if (n >= D::NV && n - D::NV < Nc) return Rf.I[(n - D::NV) * Np + k];
     return 0.0;
   });
-  put(D::BI, D::NCM, D::KV, [&](int n, int k) -> double { return (n < Nc && k < Np) ? Rf.I[n * Np + k] : 0.0; });
   put(D::BP, D::NR, D::KC, [&](int o, int k) -> double { return (o < Np && k < Nc) ? Rf.P[o * Nc + k] : 0.0; });
   put(D::BL, D::NR, D::KL, [&](int o, int k) -> double { return (o < Np && k < NFN) ? Rf.LIFT[o * NFN + k] : 0.0; });
   for (int n = 0; n < Np; ++n) {
