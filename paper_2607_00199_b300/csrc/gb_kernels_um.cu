@@ -80,18 +80,19 @@ struct UmDim {
   static constexpr int BL = BP + 2 * NR * KC;
   static constexpr int BBAR = BL + 2 * NR * KL;  // per node ((1 + r) / 2, (1 + s) / 2)
   static constexpr int BTOT = BBAR + 2 * 16;
-  // dynamic shared memory (floats): field-tail tile [128 x CA] (then q_n and q_{i+1}), own
-  // fields [128 x S], F_0 [128 x S], accumulator [128 x S], tables, geometry [128 x GW], halo
-  // of the out-of-tile neighbour traces [HMAX x HW]
-  static constexpr int SAW = CA > S ? CA : S;      // columns of the tail-tile region (tails, then q_n)
+  // dynamic shared memory (floats): q_n then q_{i+1} [128 x S], own fields [128 x S], F_0 and
+  // the accumulator [128 x SAW each: rows of S, or the field-tail tile of 128 x CA in the one
+  // that the stage leaves free], tables, geometry [128 x GW], halo of the out-of-tile
+  // neighbour traces [HMAX x HW]
+  static constexpr int SAW = CA > S ? CA : S;
   static constexpr int SM_A = 0;
-  static constexpr int SM_RAW = SM_A + 128 * SAW;
+  static constexpr int SM_RAW = SM_A + 128 * S;
   static constexpr int SM_X1 = SM_RAW + 128 * S;
-  static constexpr int SM_X2 = SM_X1 + 128 * S;
-  static constexpr int SM_B = SM_X2 + 128 * S;
+  static constexpr int SM_X2 = SM_X1 + 128 * SAW;
+  static constexpr int SM_B = SM_X2 + 128 * SAW;
   static constexpr int SM_G = SM_B + BTOT;         // per element geometry of a tile [128][GW]
   static constexpr int GW = 20;                    // rx sx ry sy 1/J, edges x3 y3, vertex velocities x3 y3, neighbours 3
-  static constexpr int HMAX = 64;                  // halo entries: out-of-tile faces of a tile
+  static constexpr int HMAX = 48;                  // halo entries: out-of-tile faces of a tile
   static constexpr int HW = 6 * Nfp;               // floats per halo entry (face node k, field fld at 6 k + fld)
   static constexpr int SM_H = SM_G + 128 * GW;
   static constexpr int SM_END = SM_H + HMAX * HW;
@@ -818,9 +819,13 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   const uint32_t tm = s_tmem;
   bool failed = !__all_sync(0xffffffffu, um_wait(&mb_tab, 0));
   const uint32_t one = lane == 0 ? 1u : 0u;   // the lane that executes its warp's MMAs and commits
-  const uint32_t sA_a = um_sa(sA), sB_a = um_sa(sB);
+  // the field-tail tile: in the F_0 / accumulator buffer that the stage does not use (stages
+  // 0, 1: the accumulator's; stages 2, 3 and the rhs: F_0's, loaded at stage 2 only once the
+  // first products have read the tails)
+  float *sT = (STAGE == 0 || STAGE == 1) ? sX2 : sX1;
+  const uint32_t sB_a = um_sa(sB);
   // descriptors at the operands' bases; an operand at byte offset o has descriptor base + o / 16
-  const uint64_t dA = um_desc(sA_a, 2048, 128);
+  const uint64_t dA = um_desc(um_sa(sT), 2048, 128);
   const uint64_t dBV = um_desc(sB_a + 4 * D::BV, D::NVC * 16, 128);
   const uint64_t dBP = um_desc(sB_a + 4 * D::BP, 256, 128), dBL = um_desc(sB_a + 4 * D::BL, 256, 128);
   constexpr uint32_t idV = um_idesc(NV), idC = um_idesc(D::NCM), idR = um_idesc(16);
@@ -880,12 +885,10 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
           um_arrive(&mb_free);
         }
         if (STAGE >= 1) {
+          // F_0 at stage 1, the accumulator at stages 2 and 3 (F_0 at stage 2 comes with q_n)
           if (tile != (int64_t)blockIdx.x) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-          uint32_t bytes = 0;
-          if (STAGE == 1 || STAGE == 2) bytes += tile_bytes;
-          if (STAGE >= 2) bytes += tile_bytes;
-          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(um_sa(&mb_x)), "r"(bytes) : "memory");
-          if (STAGE == 1 || STAGE == 2)
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(um_sa(&mb_x)), "r"(tile_bytes) : "memory");
+          if (STAGE == 1)
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                          :: "r"(um_sa(sX1)), "l"(reinterpret_cast<const float *>(a.F0) + e0 * S), "r"(tile_bytes),
                             "r"(um_sa(&mb_x)) : "memory");
@@ -919,7 +922,17 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
           // (at stage 0 the SARK pass writes F_0 into sX1 once q_n is in: the previous F_0 store
           // has read it by then)
           asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-          um_bulk_load(sA, reinterpret_cast<const float *>(a.qn) + e0 * S, tile_bytes, &mb_qn);
+          if (STAGE == 2) {   // q_n and F_0, the latter over the tails that the products have read
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(um_sa(&mb_qn)), "r"(2 * tile_bytes) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(um_sa(sA)), "l"(reinterpret_cast<const float *>(a.qn) + e0 * S), "r"(tile_bytes),
+                            "r"(um_sa(&mb_qn)) : "memory");
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         :: "r"(um_sa(sX1)), "l"(reinterpret_cast<const float *>(a.F0) + e0 * S), "r"(tile_bytes),
+                            "r"(um_sa(&mb_qn)) : "memory");
+          } else {
+            um_bulk_load(sA, reinterpret_cast<const float *>(a.qn) + e0 * S, tile_bytes, &mb_qn);
+          }
           armed |= 4u;
         }
       }
@@ -1031,11 +1044,17 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       const int64_t e0 = tile * 128;
       const int nel = tile_rows(tile);
       const bool live = el < nel;
-      if (!__all_sync(0xffffffffu, um_wait(&mb_ld, par) && um_wait(&mb_free, par))) { failed = true; break; }
+      // the own fields in; at stage 2 the tails go over F_0, which the previous tile's SARK pass
+      // has read once all its threads have arrived
+      if (!__all_sync(0xffffffffu, um_wait(&mb_ld, par) &&
+                                       (STAGE != 2 || tile == (int64_t)blockIdx.x || um_wait(&mb_out, par ^ 1u)))) {
+        failed = true;
+        break;
+      }
       // ---- heads and tails of the own fields ----
       const float *row = sRaw + el * S;
-      if (h == 0) um_convert<N, 0>(row, sA, tl, el, live);
-      else um_convert<N, 1>(row, sA, tl, el, live);
+      if (h == 0) um_convert<N, 0>(row, sT, tl, el, live);
+      else um_convert<N, 1>(row, sT, tl, el, live);
       um_wait_st();
       um_fence_async_smem();
       um_fence_before();
@@ -1130,6 +1149,8 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
       if (!__all_sync(0xffffffffu, um_wait(&mb_l, par))) { failed = true; break; }
       carmed = 0u;
       if (STAGE >= 0 && !__all_sync(0xffffffffu, um_wait(&mb_qn, par))) { failed = true; break; }
+      // (the rhs rows go into sA: the previous tile's stores have read it)
+      if (STAGE < 0 && !__all_sync(0xffffffffu, um_wait(&mb_free, par))) { failed = true; break; }
       if (STAGE >= 1 && !__all_sync(0xffffffffu, um_wait(&mb_x, par))) { failed = true; break; }
       um_fence_after();
       {
