@@ -274,13 +274,15 @@ __device__ __forceinline__ void um_arrive(uint64_t *mbar) {
 }
 
 // per-element geometry of a stage (Sec. 5): the chain-rule factors, 1/J, the three edge
-// vectors and the grid velocity at the nodes (pairs)
+// vectors and the vertex grid velocities (v_0 and the differences v_1 - v_0, v_2 - v_0), from
+// which the grid velocity at a node is interpolated where it is used, with the node's
+// barycentrics ((1 + r) / 2, (1 + s) / 2) from the shared tables
 template <int N>
 struct UmGeo {
-  static constexpr int NP2 = (UmDim<N>::Np + 1) / 2;
   float rx, sx, ry, sy, iJ;
   float ex[3], ey[3];
-  float2 vgx2[NP2], vgy2[NP2];
+  float vx0, vy0, dvx1, dvy1, dvx2, dvy2;
+  const float *bar;
 };
 
 // tails (smem tile) and heads (TMEM) of fields [3H, 3H + 3) of the element's row
@@ -332,6 +334,16 @@ __device__ __forceinline__ void um_volume(uint32_t tl, const UmGeo<N> &G, float 
   constexpr int n0 = 8 * H;
   if constexpr (n0 < Np) {
     constexpr int P0 = n0 / 2;   // first node pair
+    // the grid velocity at the node pairs of this half (P1 interpolation of the vertex values)
+    float2 vgx[4], vgy[4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      if (n0 + 2 * p >= Np) break;
+      const float4 b4 = reinterpret_cast<const float4 *>(G.bar)[P0 + p];
+      const float2 an = make_float2(b4.x, b4.z), bn = make_float2(b4.y, b4.w);
+      vgx[p] = __ffma2_rn(bn, um_b2(G.dvx2), __ffma2_rn(an, um_b2(G.dvx1), um_b2(G.vx0)));
+      vgy[p] = __ffma2_rn(bn, um_b2(G.dvy2), __ffma2_rn(an, um_b2(G.dvy1), um_b2(G.vy0)));
+    }
     float2 rhs[6][4];
 #pragma unroll
     for (int f = 0; f < 6; ++f)
@@ -360,7 +372,7 @@ __device__ __forceinline__ void um_volume(uint32_t tl, const UmGeo<N> &G, float 
           const float2 d_r = um_f2(vr[ff][2 * p], vr[ff][2 * p + 1]), d_s = um_f2(vs[ff][2 * p], vs[ff][2 * p + 1]);
           const float2 qx = um_fma2(G.sx, d_s, um_mul2(G.rx, d_r));
           const float2 qy = um_fma2(G.sy, d_s, um_mul2(G.ry, d_r));
-          const float2 ale = __ffma2_rn(G.vgy2[P0 + p], qy, __fmul2_rn(G.vgx2[P0 + p], qx));
+          const float2 ale = __ffma2_rn(vgy[p], qy, __fmul2_rn(vgx[p], qx));
           switch (f) {
             case 0: rhs[0][p] = __fadd2_rn(rhs[0][p], ale); rhs[1][p] = um_fma2(mc, qx, rhs[1][p]);
                     rhs[2][p] = um_fma2(mc, qy, rhs[2][p]); break;
@@ -502,8 +514,9 @@ __device__ __forceinline__ void um_flux(const UmGeo<N> &G, const float *qm, cons
       float w[6];
 #pragma unroll
       for (int fld = 0; fld < 6; ++fld) w[fld] = nv[jj][fld] - qm[fld * Np + vol];
-      const float gx = (vol & 1) ? G.vgx2[vol >> 1].y : G.vgx2[vol >> 1].x;
-      const float gy = (vol & 1) ? G.vgy2[vol >> 1].y : G.vgy2[vol >> 1].x;
+      const float2 ab = reinterpret_cast<const float2 *>(G.bar)[vol];
+      const float gx = fmaf(ab.y, G.dvx2, fmaf(ab.x, G.dvx1, G.vx0));
+      const float gy = fmaf(ab.y, G.dvy2, fmaf(ab.x, G.dvy1, G.vy0));
       const float vn = gx * nx + gy * ny;
       const float ale = vn > 0.0f ? vn * fs : 0.0f;
       fl[0][jj] = ale * w[0] + M00 * w[0] + M03 * w[3] + M04 * w[4] + M05 * w[5] + nhx * w[1] + nhy * w[2];
@@ -762,7 +775,6 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
   typedef UmDim<N> D;
   constexpr int S = D::S, NPP = D::NPP, KV = D::KV, GW = D::GW;
   constexpr int NV = D::NV, KC = D::KC, KL = D::KL;
-  constexpr int NP2 = UmGeo<N>::NP2;
   const float SQ2 = 1.41421356237309505f;
   extern __shared__ __align__(1024) float um_smem[];
   float *sA = um_smem + D::SM_A;
@@ -1081,13 +1093,9 @@ __global__ void __launch_bounds__(kUmThreads, 1) um_stage_kernel(const StageArgs
         const float vx[3] = {w2.w, w3.x, w3.y}, vy[3] = {w3.z, w3.w, w4.x};
         code[0] = __float_as_int(w4.y); code[1] = __float_as_int(w4.z); code[2] = __float_as_int(w4.w);
         um_arrive(&mb_gread);
-        // grid velocity at the nodes: P1 interpolation of the vertex velocities, node pairs
-#pragma unroll
-        for (int p = 0; p < NP2; ++p) {
-          const float2 an = make_float2(bar[4 * p], bar[4 * p + 2]), bn = make_float2(bar[4 * p + 1], bar[4 * p + 3]);
-          G.vgx2[p] = __ffma2_rn(bn, um_b2(vx[2] - vx[0]), __ffma2_rn(an, um_b2(vx[1] - vx[0]), um_b2(vx[0])));
-          G.vgy2[p] = __ffma2_rn(bn, um_b2(vy[2] - vy[0]), __ffma2_rn(an, um_b2(vy[1] - vy[0]), um_b2(vy[0])));
-        }
+        G.vx0 = vx[0]; G.dvx1 = vx[1] - vx[0]; G.dvx2 = vx[2] - vx[0];
+        G.vy0 = vy[0]; G.dvy1 = vy[1] - vy[0]; G.dvy2 = vy[2] - vy[0];
+        G.bar = bar;
       }
       // ---- volume terms, into R ----
       if (!__all_sync(0xffffffffu, um_wait(&mb_v, par))) { failed = true; break; }
