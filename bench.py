@@ -714,6 +714,7 @@ def run_ours(args):
         'roofline': out['mixed']['roofline'],
         'e2e': e2e,
         'gpu_launches': 5 * args.steps,
+        'launch_shape': out['mixed']['launch_shape'],   # the tuner's pick for this (N, size class)
         'clocks': clocks,
         'fp64': out['fp64'],
         'mixed': {k: v for k, v in out['mixed'].items() if k != 'roofline'},
