@@ -506,25 +506,38 @@ __device__ __forceinline__ void um_flux(const UmGeo<N> &G, const float *qm, cons
     const float N12 = h * (al * o12 + be * (o11 * o12 + o12 * o22));
     const float N22 = h * (al * o22 + be * (o12 * o12 + o22 * o22));
     const float nhx = -h * nx, nhy = -h * ny, nsx = -h * SQ2 * nx, nsy = -h * SQ2 * ny;
+    // the face's nodes in this half, two at a time in packed FP32x2 arithmetic (the face
+    // constants are shared; a node left over at the end goes in the .x lane alone)
+    const int kA = 8 * H - f * Nfp > 0 ? 8 * H - f * Nfp : 0;
+    const int kB = 8 * H + 8 - f * Nfp < Nfp ? 8 * H + 8 - f * Nfp : Nfp;
 #pragma unroll
-    for (int k = 0; k < Nfp; ++k) {
-      const int j = f * Nfp + k;
-      if (j < 8 * H || j >= 8 * H + 8) continue;
-      const int vol = tc_fmask<N>(f, k), jj = j - 8 * H;
-      float w[6];
+    for (int k = kA; k < kB; k += 2) {
+      const bool two = k + 1 < kB;
+      const int jA = f * Nfp + k - 8 * H, jB = two ? jA + 1 : jA;
+      const int volA = tc_fmask<N>(f, k), volB = two ? tc_fmask<N>(f, k + 1) : volA;
+      float2 w[6];
 #pragma unroll
-      for (int fld = 0; fld < 6; ++fld) w[fld] = nv[jj][fld] - qm[fld * Np + vol];
-      const float2 ab = reinterpret_cast<const float2 *>(G.bar)[vol];
-      const float gx = fmaf(ab.y, G.dvx2, fmaf(ab.x, G.dvx1, G.vx0));
-      const float gy = fmaf(ab.y, G.dvy2, fmaf(ab.x, G.dvy1, G.vy0));
-      const float vn = gx * nx + gy * ny;
-      const float ale = vn > 0.0f ? vn * fs : 0.0f;
-      fl[0][jj] = ale * w[0] + M00 * w[0] + M03 * w[3] + M04 * w[4] + M05 * w[5] + nhx * w[1] + nhy * w[2];
-      fl[3][jj] = ale * w[3] + M03 * w[0] + M33 * w[3] + M34 * w[4] + M35 * w[5] + nhx * w[2] + nhy * w[1];
-      fl[4][jj] = ale * w[4] + M04 * w[0] + M34 * w[3] + M44 * w[4] + M45 * w[5] + nsx * w[1];
-      fl[5][jj] = ale * w[5] + M05 * w[0] + M35 * w[3] + M45 * w[4] + M55 * w[5] + nsy * w[2];
-      fl[1][jj] = ale * w[1] + N11 * w[1] + N12 * w[2] + nhx * w[0] + nsx * w[4] + nhy * w[3];
-      fl[2][jj] = ale * w[2] + N12 * w[1] + N22 * w[2] + nhy * w[0] + nsy * w[5] + nhx * w[3];
+      for (int fld = 0; fld < 6; ++fld)
+        w[fld] = make_float2(nv[jA][fld] - qm[fld * Np + volA], nv[jB][fld] - qm[fld * Np + volB]);
+      const float2 abA = reinterpret_cast<const float2 *>(G.bar)[volA], abB = reinterpret_cast<const float2 *>(G.bar)[volB];
+      const float2 ra = make_float2(abA.x, abB.x), sb = make_float2(abA.y, abB.y);
+      const float2 gx = __ffma2_rn(sb, um_b2(G.dvx2), __ffma2_rn(ra, um_b2(G.dvx1), um_b2(G.vx0)));
+      const float2 gy = __ffma2_rn(sb, um_b2(G.dvy2), __ffma2_rn(ra, um_b2(G.dvy1), um_b2(G.vy0)));
+      const float2 vn = __ffma2_rn(um_b2(ny), gy, __fmul2_rn(um_b2(nx), gx));
+      const float2 ale = make_float2(vn.x > 0.0f ? vn.x * fs : 0.0f, vn.y > 0.0f ? vn.y * fs : 0.0f);
+      auto acc = [](float2 s, float c, float2 x) { return __ffma2_rn(um_b2(c), x, s); };
+      float2 o[6];
+      o[0] = acc(acc(acc(acc(acc(acc(__fmul2_rn(ale, w[0]), M00, w[0]), M03, w[3]), M04, w[4]), M05, w[5]), nhx, w[1]), nhy, w[2]);
+      o[3] = acc(acc(acc(acc(acc(acc(__fmul2_rn(ale, w[3]), M03, w[0]), M33, w[3]), M34, w[4]), M35, w[5]), nhx, w[2]), nhy, w[1]);
+      o[4] = acc(acc(acc(acc(acc(__fmul2_rn(ale, w[4]), M04, w[0]), M34, w[3]), M44, w[4]), M45, w[5]), nsx, w[1]);
+      o[5] = acc(acc(acc(acc(acc(__fmul2_rn(ale, w[5]), M05, w[0]), M35, w[3]), M45, w[4]), M55, w[5]), nsy, w[2]);
+      o[1] = acc(acc(acc(acc(acc(__fmul2_rn(ale, w[1]), N11, w[1]), N12, w[2]), nhx, w[0]), nsx, w[4]), nhy, w[3]);
+      o[2] = acc(acc(acc(acc(acc(__fmul2_rn(ale, w[2]), N12, w[1]), N22, w[2]), nhy, w[0]), nsy, w[5]), nhx, w[3]);
+#pragma unroll
+      for (int fld = 0; fld < 6; ++fld) {
+        fl[fld][jA] = o[fld].x;
+        if (two) fl[fld][jB] = o[fld].y;
+      }
     }
   }
 }
