@@ -199,7 +199,9 @@ int gb_set_graph(gb_solver *s, int enable);
  * stage of shape 8 runs on the 4-warp kernel.  The first gb_step / gb_step_timed of
  * a GB_MIXED solver tunes the shape: it times the right-hand-side kernel on the
  * solver's own data for each applicable shape (the state is not changed) and keeps
- * the fastest; the choice is cached per (N, K) in the process. */
+ * the fastest (a smaller shape must win by 3%); the choice is cached in the process
+ * per device and per (N, size class of K), the size class being the bit length of
+ * K - 1. */
 int gb_launch_config(gb_solver *s, int *warps_per_cta);
 /* gb_set_launch_config: fix the GB_MIXED launch shape (1, 2, 4 or 8) and skip the
  * tuner.  GB_EINVAL for other values, for 8 where it does not apply, and for

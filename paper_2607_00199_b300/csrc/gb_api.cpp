@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <map>
+#include <tuple>
 #include <mutex>
 
 using gb::MeshRec;
@@ -208,7 +209,7 @@ static int launch_pml(gb_solver *s, const gb::StageArgs &a) {
 }
 
 struct gb_group {
-  int capacity = 0, num_sms = 1;
+  int capacity = 0, num_sms = 1, device = 0;
   int warps[GB_MAX_N + 1] = {};   // group-kernel warps per CTA last used for each order (0: none yet)
   bool fixed[GB_MAX_N + 1] = {};  // set by gb_group_set_launch_config: no tuning for that order
   cudaStream_t stream = nullptr;
@@ -234,10 +235,11 @@ static void set_coefficients(gb_solver *s, double dt) {
 // copy of the operator tables.  The tuner times the rhs-only stage
 // kernel (which writes only the scratch buffer b2 and leaves the state alone) on
 // the solver's own data for each shape and keeps the fastest; a candidate after
-// the first must win by 3%.  Choices are cached per (N, size class of K) for the process.
+// the first must win by 3%.  Choices are cached per (device, N, size class of K) for the process.
 static std::mutex g_tune_mu;
-static std::map<std::pair<int, int64_t>, int> g_tuned;        // (N, K class) -> solver launch shape
-static std::map<std::pair<int, int64_t>, int> g_group_tuned;  // (N, tile-count class) -> group warps per CTA
+typedef std::tuple<int, int, int64_t> TuneKey;   // (device, N, size class)
+static std::map<TuneKey, int> g_tuned;           // -> solver launch shape
+static std::map<TuneKey, int> g_group_tuned;     // (device, N, tile-count class) -> group warps per CTA
 
 // size class of a mesh or a group: the bit length of (count - 1), i.e. counts in (2^(c-1), 2^c]
 static int64_t k_class(int64_t count) {
@@ -248,7 +250,7 @@ static int64_t k_class(int64_t count) {
 
 static int tune_launch(gb_solver *s) {
   if (s->precision != GB_MIXED || s->warps != 0) return GB_OK;
-  const std::pair<int, int64_t> key(s->N, k_class(s->K));
+  const TuneKey key(s->device, s->N, k_class(s->K));
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(key);
@@ -894,6 +896,7 @@ int gb_group_create(int capacity, void *cuda_stream, gb_group **out) {
   g->stream = (cudaStream_t)cuda_stream;
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
+  g->device = dev;
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&g->num_sms, cudaDevAttrMultiProcessorCount, dev);
   const size_t args_bytes = sizeof(gb::StageArgs) * 4 * (size_t)capacity;
   const size_t pre_bytes = sizeof(int64_t) * 2 * (size_t)(capacity + 1);
@@ -914,13 +917,13 @@ int gb_group_create(int capacity, void *cuda_stream, gb_group **out) {
 // Group launch-shape tuner: warps per CTA of the group kernel (4, 2 or 1) for the group's
 // order and size class (tile count), timed on the group's own data with stage-0 launches, which
 // only write the stage buffer b1 and F_0 of each member (both rewritten by the step's own stage
-// 0); a later candidate must win by 3%.  Choices are cached per (N, tile-count class).
+// 0); a later candidate must win by 3%.  Choices are cached per (device, N, tile-count class).
 static int group_tune(gb_group *g, int N, gb::GroupArgs &ga) {
   if (g->fixed[N]) {
     ga.warps = g->warps[N];
     return GB_OK;
   }
-  const std::pair<int, int64_t> key(N, k_class(ga.total_tiles));
+  const TuneKey key(g->device, N, k_class(ga.total_tiles));
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_group_tuned.find(key);

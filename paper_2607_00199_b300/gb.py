@@ -325,7 +325,8 @@ class Solver:
         return w.value
 
     def set_launch_config(self, warps_per_cta):
-        """Fix the GB_MIXED warps per CTA (1, 2 or 4) instead of tuning."""
+        """Fix the GB_MIXED launch shape instead of tuning: 1, 2 or 4 warps per CTA of the
+        mma.sync kernel, or 8 for the tcgen05 kernel (N <= 4, no boundary faces)."""
         self._c(lib.gb_set_launch_config(self.h, int(warps_per_cta)))
 
     def set_graph(self, enable):
