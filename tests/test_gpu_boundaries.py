@@ -149,6 +149,9 @@ def test_bounded_meshes_are_validated_and_not_grouped():
     g = gb.Group(2)
     with pytest.raises(gb.GBError):
         g.step([s], [1e-4], 1)
+    with pytest.raises(gb.GBError):   # the tcgen05 kernel has no boundary-face variant
+        s.set_launch_config(8)
+    s.set_launch_config(4)
     with pytest.raises(gb.GBError) as ei:
         gb.Solver(mesh, 5, 0.1, 100.0)
     assert ei.value.code == gb.GB_EINVAL
