@@ -8,14 +8,13 @@
 //   a CTA (one per SM, persistent) owns tiles of 128 consecutive (Morton-ordered)
 //   elements in turn; element e of a tile is TMEM lane e, and two compute threads
 //   (t and t + 128) share its pointwise work; four helper warps form the next tile's
-//   geometry and halo, issue the projection products and the bulk copies.
+//   geometry and halo, issue the interpolation and projection products and the bulk copies.
 //
 // The four dense contractions of the semi-discrete form (Sec. 3) are M = 128 (elements)
 // tcgen05.mma products of kind::tf32, each accumulator fed by one lane, accumulating in
 // FP32 in TMEM:
-//   [V_f | C_f] = Q_f [Dr | Ds | I]^T  (f = 1..3: the volume products and the values at the
-//                                       cubature points in one product; A = the field's nodes)
-//   V_f  = Q_f [Dr | Ds]^T      (f = 4..6)
+//   V_f  = Q_f [Dr | Ds]^T      (f = 1..6; A = the field's nodal values)
+//   C_f  = Q_f I^T              (f = 1..3; the values at the cubature points)
 //   R_f += Ntilde_f P^T         (f = 4..6; the projected collision term)
 //   R_f += Flux_f LIFT^T        (f = 1..6; the lifted face fluxes)
 // Each operand is split into a TF32 head rounded to nearest and its FP32 tail (x = hi + lo),
@@ -37,10 +36,10 @@
 //
 // Data movement per tile is bulk copies with completion on mbarriers: the tile's own fields
 // q_i arrive while the previous tile finishes (prefetched once its fluxes are formed), F_0 and
-// the accumulator are loaded at the start of the tile, q_n once the first MMA batch has read
-// the tail tile; the SARK outputs are written into those staged rows and leave as bulk
-// stores.  Three MMA batches per tile (volume with interpolation, projection, lift), each
-// committed to an mbarrier.  Every wait is bounded: on expiry the kernel sets
+// the accumulator are loaded at the start of the tile, q_n once the volume and interpolation
+// products have read the tail tile; the SARK outputs are written into those staged rows and
+// leave as bulk stores.  Four MMA batches per tile (volume, then interpolation, projection,
+// lift), each committed to an mbarrier.  Every wait is bounded: on expiry the kernel sets
 // GB_STATUS_TIMEOUT, waits (bounded) for what it issued, frees its TMEM and returns.
 //
 // Field layout: the element-major FP32 perturbation layout of the GB_MIXED path (element
@@ -71,10 +70,11 @@ struct UmDim {
   static constexpr int KC = (Nc + 7) & ~7;       // K of the projection product
   static constexpr int NR = 16;                  // N of the projection and lift products (Np <= 15)
   static constexpr int KL = (NFN + 7) & ~7;      // K of the lift product
-  static constexpr int NVC = NV + NCM;           // N of the merged volume and interpolation product (fields 1..3)
+  static constexpr int NVC = NV + NCM;           // rows of the [Dr | Ds | I] table; TMEM columns of fields 1..3
   // operator tables (floats), each as its TF32 head then its tail, core-matrix K-major layout:
   // entry (n, k) of an R x K table at (k / 4) (4 R) + 4 n + k % 4.  BV: the rows of Dr (at 0),
-  // Ds (at KV) and I (at NV), NVC x KV; the volume product of fields 4..6 reads its first NV rows
+  // Ds (at KV) and I (at NV), NVC x KV; the volume products read its first NV rows, the
+  // interpolation products the NCM rows from NV
   static constexpr int BV = 0;
   static constexpr int BP = BV + 2 * NVC * KV;
   static constexpr int BL = BP + 2 * NR * KC;
