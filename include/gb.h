@@ -201,11 +201,21 @@ int gb_set_graph(gb_solver *s, int enable);
  * solver's own data for each applicable shape (the state is not changed) and keeps
  * the fastest (a smaller shape must win by 3%); the choice is cached in the process
  * per device and per (N, size class of K), the size class being the bit length of
- * K - 1. */
+ * K - 1.
+ * For dim = 3 solvers (GB_MIXED; 0 for GB_FP64):
+ *   1..8     the tensor-core kernel: 16-element warp tiles on mma.sync TF32 split
+ *            products, that many warps per CTA sharing the operator table in shared
+ *            memory (orders 1..3; at most as many as fit, 7 at N = 3 and 8 at N <= 2);
+ *   16       the FP32 one-thread-per-node kernel (every order; the only one at N = 4).
+ * Before the first step of an untuned solver this reports the tensor-core kernel with
+ * the most warps; that step then times a stage launch of it against shape 16 on the
+ * solver's own data and keeps the faster (shape 16 must win by 3%), cached per device
+ * and (N, size class of K) like the 2D choice.  The two agree to rounding; all warp
+ * counts agree bit for bit. */
 int gb_launch_config(gb_solver *s, int *warps_per_cta);
-/* gb_set_launch_config: fix the GB_MIXED launch shape (1, 2, 4 or 8) and skip the
- * tuner.  GB_EINVAL for other values, for 8 where it does not apply, and for
- * GB_FP64 solvers. */
+/* gb_set_launch_config: fix the GB_MIXED launch shape (1, 2, 4 or 8; for dim = 3:
+ * 1..8 as above or 16) and skip the tuner.  GB_EINVAL for other values, for a shape that
+ * does not apply to the solver's order or mesh, and for GB_FP64 solvers. */
 int gb_set_launch_config(gb_solver *s, int warps_per_cta);
 
 /* gb_step_timed: gb_step that also records a CUDA event pair around every kernel

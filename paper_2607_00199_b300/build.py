@@ -18,7 +18,7 @@ BUILD = os.path.join(ROOT, '_build')
 LIB = os.path.join(HERE, 'libgb.so')
 
 SOURCES = ['gb_api.cpp', 'gb_reference.cpp', 'gb_kernels.cu', 'gb_kernels_tc.cu', 'gb_kernels_um.cu', 'gb_diagnostics.cu', 'gb_noalloc.cu',
-           'gb3d.cpp', 'gb_kernels3d.cu', 'gb_pml.cu']
+           'gb3d.cpp', 'gb_kernels3d.cu', 'gb_kernels3d_tc.cu', 'gb_pml.cu']
 ARCH = ['-gencode', 'arch=compute_103a,code=sm_103a']
 FLAGS = ['-O3', '-lineinfo', '-std=c++17', '-Xcompiler', '-fPIC', '-I', INCLUDE, '-I', CSRC]
 

@@ -9,8 +9,12 @@
 #include <array>
 #include <cmath>
 #include <cstdio>
+#include <cstdint>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -25,6 +29,7 @@ struct Solver3 {
   double c = 0, tau = 0, period[3] = {0, 0, 0};
   cudaStream_t stream = nullptr;
   int num_sms = 1;
+  int device = 0;
   std::string err;
   RefOps3 ref;
   Wave3 wave{0, 0, 1, 1, 0, 1, 0, 0};
@@ -37,6 +42,8 @@ struct Solver3 {
   bool graph_warm = false, use_graph = true;
   size_t elem_bytes = 8;
   void *d_ops = nullptr;
+  void *d_ops_tc = nullptr;     // GB_MIXED, N <= 3: the tensor-core kernel's operator table
+  int shape = 0;                // GB_MIXED launch shape (kShape3*); 0 = the default
   int *d_tab = nullptr;
   double *d_bary = nullptr;
   MeshRec3 *d_mesh = nullptr;
@@ -75,7 +82,7 @@ static int alloc3(Solver3 *s, void **p, size_t bytes) {
 }
 
 static void free3(Solver3 *s) {
-  void *ptrs[] = {s->d_ops, s->d_tab, s->d_bary, s->d_mesh, s->d_X, s->d_xn, s->d_shape, s->d_clock, s->d_status,
+  void *ptrs[] = {s->d_ops, s->d_ops_tc, s->d_tab, s->d_bary, s->d_mesh, s->d_X, s->d_xn, s->d_shape, s->d_clock, s->d_status,
                   s->d_qn, s->d_b1, s->d_b2, s->d_F0, s->d_acc, s->d_tmp, s->d_diag, s->d_hist, s->d_hctl};
   for (void *p : ptrs)
     if (p) cudaFree(p);
@@ -223,6 +230,7 @@ int s3_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
   int dev = 0;
   cudaError_t ce = cudaGetDevice(&dev);
   if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  s->device = dev;
   if (ce != cudaSuccess) {
     delete s;
     return fail3(nullptr, &err, GB_ECUDA, std::string("no usable CUDA device: ") + cudaGetErrorString(ce));
@@ -236,6 +244,17 @@ int s3_create(const gb_mesh *mesh, int N, double Ma, double Re, int precision, v
     return fail3(nullptr, &err, GB_ECUDA, m);
   }
   s->device_bytes += (int64_t)opbytes;
+  if (precision == GB_MIXED && stage3_tc_supported(N)) {
+    size_t tcbytes = 0;
+    rc = upload_ops3_tc(N, s->ref, &s->d_ops_tc, &tcbytes, s->stream);
+    if (rc) {
+      std::string m = std::string("operator upload (tensor-core table): ") + cudaGetErrorString((cudaError_t)rc);
+      free3(s);
+      delete s;
+      return fail3(nullptr, &err, GB_ECUDA, m);
+    }
+    s->device_bytes += (int64_t)tcbytes;
+  }
   const size_t fbytes = (size_t)K * 10 * s->Np * s->elem_bytes;
   void **fields[] = {&s->d_qn, &s->d_b1, &s->d_b2, &s->d_F0, &s->d_acc};
   int arc = GB_OK;
@@ -490,6 +509,17 @@ int s3_diag_ring(Solver3 *s, const double **hist, const int64_t **ctl, int *ever
   return GB_OK;
 }
 
+// the stage kernel of the solver's precision and launch shape: GB_FP64 and the FP32
+// one-thread-per-node kernel (gb_kernels3d.cu), or the tensor-core kernel (gb_kernels3d_tc.cu)
+static int launch3(Solver3 *s, const Stage3Args &a) {
+  // (the tensor-core kernel stores the right-hand side as node pairs: an F_dev that is not
+  // 8-byte aligned goes to the one-thread-per-node kernel)
+  const bool fout_ok = a.stage >= 0 || (reinterpret_cast<uintptr_t>(a.Fout) & 7) == 0;
+  if (s->precision == GB_MIXED && s->d_ops_tc && s->shape != kShape3Simt && fout_ok)
+    return launch_stage3_tc(s->N, a, s->stream, s->shape ? s->shape : stage3_tc_max_warps(s->N), s->num_sms);
+  return launch_stage3(s->N, s->precision == GB_FP64, a, s->stream, s->num_sms);
+}
+
 static Stage3Args base3(Solver3 *s) {
   Stage3Args a;
   memset(&a, 0, sizeof(a));
@@ -497,6 +527,7 @@ static Stage3Args base3(Solver3 *s) {
   a.shape = s->d_shape;
   a.mesh = s->d_mesh;
   a.ops = s->d_ops;
+  a.ops_tc = s->d_ops_tc;
   a.tab = s->d_tab;
   a.clock = s->d_clock;
   a.status = s->d_status;
@@ -517,7 +548,7 @@ int s3_rhs(Solver3 *s, double t, const void *q_dev, void *F_dev) {
   a.qn = q_dev;
   a.Fout = F_dev;
   a.rhs_time = t;
-  int rc = launch_stage3(s->N, s->precision == GB_FP64, a, s->stream, s->num_sms);
+  int rc = launch3(s, a);
   return rc ? cuda_fail3(s, (cudaError_t)rc, "stage kernel launch (dim = 3)") : GB_OK;
 }
 
@@ -536,7 +567,7 @@ static int step_once3(Solver3 *s, double dt, cudaEvent_t *ev) {
     a.qin = in[i];
     a.qout = outp[i];
     if (ev) cudaEventRecord(ev[2 * i], s->stream);
-    int rc = launch_stage3(s->N, s->precision == GB_FP64, a, s->stream, s->num_sms);
+    int rc = launch3(s, a);
     if (rc) return cuda_fail3(s, (cudaError_t)rc, "stage kernel launch (dim = 3)");
     if (ev) cudaEventRecord(ev[2 * i + 1], s->stream);
   }
@@ -553,8 +584,76 @@ static int step_once3(Solver3 *s, double dt, cudaEvent_t *ev) {
   return GB_OK;
 }
 
+// GB_MIXED launch tuner (N <= 3): time a stage kernel on the solver's own state (into the
+// stage buffers; the state is not changed) for the tensor-core kernel with the most
+// warps per CTA and for the one-thread-per-node kernel, keep the faster (the second must win
+// by 3%); the choice is cached per device and (N, size class of K), the size class being
+// the bit length of K - 1
+static std::mutex g_tune3_mu;
+static std::map<std::tuple<int, int, int>, int> g_tuned3;
+
+static int tune3(Solver3 *s) {
+  if (s->precision != GB_MIXED || !s->d_ops_tc || s->shape != 0) return GB_OK;
+  int kc = 0;
+  for (int64_t v = s->K - 1; v > 0; v >>= 1) ++kc;
+  const auto key = std::make_tuple(s->device, s->N, kc);
+  {
+    std::lock_guard<std::mutex> lk(g_tune3_mu);
+    auto it = g_tuned3.find(key);
+    if (it != g_tuned3.end()) {
+      s->shape = it->second;
+      return GB_OK;
+    }
+  }
+  // a middle stage (it reads q_n, q_i and F_0 and writes q_{i+1} and the accumulator, as most
+  // launches of a step do), into the stage buffers that hold nothing between steps
+  Stage3Args a = base3(s);
+  a.stage = 1;
+  a.qin = s->d_qn;
+  a.qn = s->d_qn;
+  a.F0 = s->d_F0;
+  a.acc = s->d_b1;
+  a.qout = s->d_b2;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t ce = cudaEventCreate(&e0);
+  if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+  const int cand[2] = {stage3_tc_max_warps(s->N), kShape3Simt};
+  int best = cand[0];
+  float best_ms = 1e30f;
+  for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
+    s->shape = cand[i];
+    int rc = launch3(s, a);   // warm-up
+    if (rc) { ce = (cudaError_t)rc; break; }
+    ce = cudaEventRecord(e0, s->stream);
+    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) {
+      rc = launch3(s, a);
+      if (rc) ce = (cudaError_t)rc;
+    }
+    if (ce == cudaSuccess) ce = cudaEventRecord(e1, s->stream);
+    if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
+    float ms = 0.0f;
+    if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, e0, e1);
+    if (ce == cudaSuccess && ms < 0.97f * best_ms) {
+      best_ms = ms;
+      best = cand[i];
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  s->shape = 0;
+  if (ce != cudaSuccess) return cuda_fail3(s, ce, "launch tuning (dim = 3)");
+  s->shape = best;
+  std::lock_guard<std::mutex> lk(g_tune3_mu);
+  g_tuned3[key] = best;
+  return GB_OK;
+}
+
 int s3_step(Solver3 *s, double dt, int64_t nsteps) {
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail3(s, nullptr, GB_EINVAL, "dt must be positive and nsteps >= 0");
+  if (nsteps > 0) {
+    const int trc = tune3(s);
+    if (trc) return trc;
+  }
   set_coef3(s, dt);
   if (dt != s->graph_dt) drop_graph3(s);
   const bool can_graph = s->use_graph && s->stream != nullptr && nsteps >= 2;
@@ -595,6 +694,10 @@ int s3_step(Solver3 *s, double dt, int64_t nsteps) {
 
 int s3_step_timed(Solver3 *s, double dt, int64_t nsteps, double *kernel_ms) {
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail3(s, nullptr, GB_EINVAL, "dt must be positive and nsteps >= 0");
+  if (nsteps > 0) {
+    const int trc = tune3(s);
+    if (trc) return trc;
+  }
   set_coef3(s, dt);
   cudaEvent_t ev[10];
   for (auto &e : ev) e = nullptr;
@@ -634,6 +737,26 @@ int s3_info(Solver3 *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *n_
 
 int s3_state_ptr(Solver3 *s, void **q) {
   *q = s->d_qn;
+  return GB_OK;
+}
+
+int s3_launch_config(Solver3 *s, int *shape) {
+  if (s->precision != GB_MIXED) *shape = 0;
+  else if (!s->d_ops_tc) *shape = kShape3Simt;
+  else *shape = s->shape ? s->shape : stage3_tc_max_warps(s->N);
+  return GB_OK;
+}
+
+int s3_set_launch_config(Solver3 *s, int shape) {
+  if (s->precision != GB_MIXED) return fail3(s, nullptr, GB_EINVAL, "launch shapes apply to GB_MIXED solvers");
+  if (shape != kShape3Simt) {
+    if (!s->d_ops_tc) return fail3(s, nullptr, GB_EINVAL, "the tensor-core kernel needs N <= 3 (dim = 3); shape 16 is the one-thread-per-node kernel");
+    if (shape < 1 || shape > stage3_tc_max_warps(s->N))
+      return fail3(s, nullptr, GB_EINVAL, "the launch shape must be 1.." + std::to_string(stage3_tc_max_warps(s->N)) +
+                                              " (tensor-core kernel, warps per CTA) or 16 (one thread per node) for dim = 3");
+  }
+  s->shape = shape;
+  drop_graph3(s);
   return GB_OK;
 }
 

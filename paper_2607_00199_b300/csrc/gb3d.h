@@ -39,6 +39,12 @@ int s3_info(Solver3 *s, int *Np, int *Nfp, int *Nc, int64_t *n_elem, int64_t *n_
             int64_t *device_bytes);
 int s3_state_ptr(Solver3 *s, void **q);
 int s3_set_graph(Solver3 *s, int enable);
+// GB_MIXED launch shapes: 1..stage3_tc_max_warps(N) the tensor-core kernel with that many warps
+// per CTA (N <= 3; the default, until the first step tunes it, is the most that fit), kShape3Simt the FP32
+// one-thread-per-node kernel (every order)
+constexpr int kShape3Simt = 16;
+int s3_launch_config(Solver3 *s, int *shape);
+int s3_set_launch_config(Solver3 *s, int shape);
 int s3_set_stream(Solver3 *s, void *stream);
 
 }  // namespace gb

@@ -32,6 +32,7 @@ struct Stage3Args {
   const double *shape;   // n_vert x 6: velocity shapes S1 (xyz), S2 (xyz)
   const MeshRec3 *mesh;
   const void *ops;       // operator block (T), layout in gb_kernels3d.cu
+  const void *ops_tc;    // GB_MIXED, N <= 3: the tensor-core kernel's table (gb_kernels3d_tc.cu), else NULL
   const int *tab;        // neighbour face-node table [4][4][6][Nfp], then fmask [4][Nfp]
   double *clock;         // t_n, then the final vertex-update factors f1, f2
   int *status;
@@ -62,6 +63,12 @@ struct Diag3Args {
 constexpr int kDiag3MaxBlocks = 1184;
 
 int launch_stage3(int N, bool fp64, const Stage3Args &a, void *stream, int num_sms);
+// the GB_MIXED tensor-core stage kernel (16-element warp tiles, CTAs of
+// 1..stage3_tc_max_warps(N) warps)
+bool stage3_tc_supported(int N);
+int stage3_tc_max_warps(int N);
+int launch_stage3_tc(int N, const Stage3Args &a, void *stream, int warps_per_cta, int num_sms);
+int upload_ops3_tc(int N, const RefOps3 &R, void **dev, size_t *bytes, void *stream);
 int diagnostics3_blocks(int64_t K);
 int launch_diagnostics3(const Diag3Args &d, double *out, void *stream);
 int launch_diagnostics3_record(const Diag3Args &d, const double *clock, int64_t *ctl, int every, double *hist,

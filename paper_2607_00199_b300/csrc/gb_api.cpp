@@ -1177,17 +1177,14 @@ int gb_diagnostics(gb_solver *s, double *out) {
 
 int gb_launch_config(gb_solver *s, int *warps_per_cta) {
   if (!s || !warps_per_cta) return fail(s, GB_EINVAL, "NULL argument");
-  if (s->s3) {
-    *warps_per_cta = 0;
-    return GB_OK;
-  }
+  if (s->s3) return gb::s3_launch_config(s->s3, warps_per_cta);
   *warps_per_cta = s->precision == GB_MIXED ? (s->warps ? s->warps : 4) : 0;
   return GB_OK;
 }
 
 int gb_set_launch_config(gb_solver *s, int warps_per_cta) {
   if (!s) return fail(s, GB_EINVAL, "NULL solver");
-  if (s->s3) return fail(s, GB_EINVAL, "not available for dim = 3 solvers");
+  if (s->s3) return gb::s3_set_launch_config(s->s3, warps_per_cta);
   if (s->precision != GB_MIXED) return fail(s, GB_EINVAL, "launch shapes apply to GB_MIXED solvers");
   if (warps_per_cta == gb::kShapeUm && !s->d_ops_um)
     return fail(s, GB_EINVAL, "shape 8 (tcgen05, 128-element tiles) needs N <= 4 and a mesh without boundary faces");
