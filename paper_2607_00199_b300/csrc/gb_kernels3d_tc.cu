@@ -58,7 +58,6 @@ struct Tc3Dim {
   static constexpr int NQ = 10 * Np;
   static constexpr int KS = (Np + 7) / 8;   // k-steps over nodes
   static constexpr int NT = KS;             // n-tiles over output nodes
-  static constexpr int NT8 = 8 * NT;
   static constexpr int KF = (NFN + 7) / 8;  // k-steps over face nodes
   static constexpr int CH = (Nc + 7) / 8;   // cubature chunks of 8 points
   static constexpr int S = NQ + (12 - NQ % 8) % 8;   // element stride of the shared tile, S = 4 mod 8
@@ -113,7 +112,7 @@ __device__ __forceinline__ void t3_split(float x, unsigned &hi, unsigned &lo) {
 }
 
 __device__ __forceinline__ void t3_mma(float (&c)[4], const unsigned (&a)[4], float b0, float b1) {
-  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)));
 }
@@ -253,7 +252,7 @@ __device__ __forceinline__ void t3_flux(const float *own, const float *geo, cons
 template <int N, int STAGE>
 __global__ void __launch_bounds__(32 * Tc3Dim<N>::MAX_WARPS) tc3_stage_kernel(const Stage3Args a) {
   typedef Tc3Dim<N> D;
-  constexpr int Np = D::Np, NFN = D::NFN, NQ = D::NQ, KS = D::KS, NT = D::NT, NT8 = D::NT8, KF = D::KF, CH = D::CH;
+  constexpr int Np = D::Np, NFN = D::NFN, NQ = D::NQ, KS = D::KS, NT = D::NT, KF = D::KF, CH = D::CH;
   constexpr int S = D::S, GEO = D::GEO;
   const float SQ2 = 1.41421356237309505f, ISQ2 = 0.70710678118654752f;
   extern __shared__ __align__(16) float t3_smem[];
@@ -374,7 +373,7 @@ __global__ void __launch_bounds__(32 * Tc3Dim<N>::MAX_WARPS) tc3_stage_kernel(co
   // ---- 3. collision term: I q at the cubature points, Ntilde there, P back (fields 5..10) ----
   {
     const float itau = (float)a.inv_tau;
-#pragma unroll 1
+#pragma unroll 2
     for (int ch = 0; ch < CH; ++ch) {
       float qc[4][4];
 #pragma unroll

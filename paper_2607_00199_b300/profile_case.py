@@ -3,7 +3,7 @@ workload (K = 131072 jittered triangles, N = 4): set-up, `--warmup` steps, then
 `--steps` steps, with as few other launches as possible.
 
     python -m paper_2607_00199_b300.profile_case --precision mixed|fp64 [--steps 2] [--warmup 2] [--n 256] [--warps 8]
-    python -m paper_2607_00199_b300.profile_case --dim 3 --precision mixed|fp64 [--nx 64 --ny 16 --nz 16] [--N 3] [--shape3 1|2|4|16]
+    python -m paper_2607_00199_b300.profile_case --dim 3 --precision mixed|fp64 [--nx 64 --ny 16 --nz 16] [--N 3] [--shape3 1..8|16]
     python -m paper_2607_00199_b300.profile_case --airfoil [--no-pml] --precision mixed|fp64
 
 With --airfoil the case is the plunging NACA 0012 O-grid (256 x 192 quads, K = 98304, N = 4)
@@ -32,8 +32,8 @@ def main():
     p.add_argument('--N', type=int, default=None, help='order (default 4 in 2D, 3 in 3D)')
     p.add_argument('--warps', type=int, default=8, choices=[1, 2, 4, 8], help='launch shape of the mixed kernel (8: tcgen05)')
     p.add_argument('--dim', type=int, default=2, choices=[2, 3])
-    p.add_argument('--shape3', type=int, default=None, choices=[1, 2, 4, 16],
-                   help='dim 3, mixed: launch shape (1, 2, 4 the tensor-core kernel; 16 one thread per node)')
+    p.add_argument('--shape3', type=int, default=None, choices=[1, 2, 3, 4, 5, 6, 7, 8, 16],
+                   help='dim 3, mixed: launch shape (1..8 the tensor-core kernel, warps per CTA; 16 one thread per node)')
     p.add_argument('--nx', type=int, default=64)
     p.add_argument('--ny', type=int, default=16)
     p.add_argument('--nz', type=int, default=16)
