@@ -208,10 +208,10 @@ int gb_set_graph(gb_solver *s, int enable);
  *            memory (orders 1..3; at most as many as fit, 7 at N = 3 and 8 at N <= 2);
  *   16       the FP32 one-thread-per-node kernel (every order; the only one at N = 4).
  * Before the first step of an untuned solver this reports the tensor-core kernel with
- * the most warps; that step then times a stage launch of it against shape 16 on the
- * solver's own data and keeps the faster (shape 16 must win by 3%), cached per device
- * and (N, size class of K) like the 2D choice.  The two agree to rounding; all warp
- * counts agree bit for bit. */
+ * the most warps; that step then times stages 0..2 of it against shape 16 on the
+ * solver's own data and keeps the faster (shape 16 must win by 3%), for that solver
+ * (not cached: which one wins depends on the mesh and motion).  The two agree to
+ * rounding; all warp counts agree bit for bit. */
 int gb_launch_config(gb_solver *s, int *warps_per_cta);
 /* gb_set_launch_config: fix the GB_MIXED launch shape (1, 2, 4 or 8; for dim = 3:
  * 1..8 as above or 16) and skip the tuner.  GB_EINVAL for other values, for a shape that

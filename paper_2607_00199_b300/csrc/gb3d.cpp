@@ -11,10 +11,7 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
-#include <map>
-#include <mutex>
 #include <string>
-#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -584,36 +581,21 @@ static int step_once3(Solver3 *s, double dt, cudaEvent_t *ev) {
   return GB_OK;
 }
 
-// GB_MIXED launch tuner (N <= 3): time a stage kernel on the solver's own state (into the
-// stage buffers; the state is not changed) for the tensor-core kernel with the most
-// warps per CTA and for the one-thread-per-node kernel, keep the faster (the second must win
-// by 3%); the choice is cached per device and (N, size class of K), the size class being
-// the bit length of K - 1
-static std::mutex g_tune3_mu;
-static std::map<std::tuple<int, int, int>, int> g_tuned3;
-
+// GB_MIXED launch tuner (N <= 3), once per solver: time stages 0, 1 and 2 on the solver's own
+// state (outputs into F_0 and the stage buffers, which hold nothing between steps; the state
+// is not changed) for the tensor-core kernel with the most warps per CTA and for the
+// one-thread-per-node kernel, and keep the faster (the second must win by 3%).  Not cached
+// across solvers: the two kernels are close, and which wins depends on the mesh and motion,
+// not only on N and K.
 static int tune3(Solver3 *s) {
   if (s->precision != GB_MIXED || !s->d_ops_tc || s->shape != 0) return GB_OK;
-  int kc = 0;
-  for (int64_t v = s->K - 1; v > 0; v >>= 1) ++kc;
-  const auto key = std::make_tuple(s->device, s->N, kc);
-  {
-    std::lock_guard<std::mutex> lk(g_tune3_mu);
-    auto it = g_tuned3.find(key);
-    if (it != g_tuned3.end()) {
-      s->shape = it->second;
-      return GB_OK;
-    }
-  }
-  // a middle stage (it reads q_n, q_i and F_0 and writes q_{i+1} and the accumulator, as most
-  // launches of a step do), into the stage buffers that hold nothing between steps
   Stage3Args a = base3(s);
-  a.stage = 1;
-  a.qin = s->d_qn;
+  a.dt = s->coef_dt;
   a.qn = s->d_qn;
   a.F0 = s->d_F0;
-  a.acc = s->d_b1;
-  a.qout = s->d_b2;
+  a.acc = s->d_acc;
+  const void *in[3] = {s->d_qn, s->d_b1, s->d_b2};
+  void *outp[3] = {s->d_b1, s->d_b2, s->d_b1};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t ce = cudaEventCreate(&e0);
   if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
@@ -622,12 +604,15 @@ static int tune3(Solver3 *s) {
   float best_ms = 1e30f;
   for (int i = 0; i < 2 && ce == cudaSuccess; ++i) {
     s->shape = cand[i];
-    int rc = launch3(s, a);   // warm-up
-    if (rc) { ce = (cudaError_t)rc; break; }
-    ce = cudaEventRecord(e0, s->stream);
-    for (int r = 0; r < 3 && ce == cudaSuccess; ++r) {
-      rc = launch3(s, a);
-      if (rc) ce = (cudaError_t)rc;
+    for (int rep = 0; rep < 2 && ce == cudaSuccess; ++rep) {   // warm-up, then timed
+      if (rep == 1) ce = cudaEventRecord(e0, s->stream);
+      for (int st = 0; st < 3 && ce == cudaSuccess; ++st) {
+        a.stage = st;
+        a.qin = in[st];
+        a.qout = outp[st];
+        const int rc = launch3(s, a);
+        if (rc) ce = (cudaError_t)rc;
+      }
     }
     if (ce == cudaSuccess) ce = cudaEventRecord(e1, s->stream);
     if (ce == cudaSuccess) ce = cudaEventSynchronize(e1);
@@ -643,18 +628,16 @@ static int tune3(Solver3 *s) {
   s->shape = 0;
   if (ce != cudaSuccess) return cuda_fail3(s, ce, "launch tuning (dim = 3)");
   s->shape = best;
-  std::lock_guard<std::mutex> lk(g_tune3_mu);
-  g_tuned3[key] = best;
   return GB_OK;
 }
 
 int s3_step(Solver3 *s, double dt, int64_t nsteps) {
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail3(s, nullptr, GB_EINVAL, "dt must be positive and nsteps >= 0");
+  set_coef3(s, dt);
   if (nsteps > 0) {
     const int trc = tune3(s);
     if (trc) return trc;
   }
-  set_coef3(s, dt);
   if (dt != s->graph_dt) drop_graph3(s);
   const bool can_graph = s->use_graph && s->stream != nullptr && nsteps >= 2;
   int64_t done = 0;
@@ -694,11 +677,11 @@ int s3_step(Solver3 *s, double dt, int64_t nsteps) {
 
 int s3_step_timed(Solver3 *s, double dt, int64_t nsteps, double *kernel_ms) {
   if (!(dt > 0.0) || !std::isfinite(dt) || nsteps < 0) return fail3(s, nullptr, GB_EINVAL, "dt must be positive and nsteps >= 0");
+  set_coef3(s, dt);
   if (nsteps > 0) {
     const int trc = tune3(s);
     if (trc) return trc;
   }
-  set_coef3(s, dt);
   cudaEvent_t ev[10];
   for (auto &e : ev) e = nullptr;
   cudaError_t ce = cudaSuccess;
