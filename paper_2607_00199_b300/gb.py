@@ -319,14 +319,18 @@ class Solver:
         return d
 
     def launch_config(self):
-        """Warps per CTA of the GB_MIXED kernel (tuned at the first step; 0 for GB_FP64)."""
+        """The GB_MIXED launch shape (tuned at the first step; 0 for GB_FP64): in 2D the
+        mma.sync kernel's warps per CTA (1, 2, 4) or 8 for the tcgen05 kernel; in 3D the
+        tensor-core kernel's warps per CTA (1..8, N <= 3) or 16 for the FP32 kernel."""
         w = ctypes.c_int()
         self._c(lib.gb_launch_config(self.h, ctypes.byref(w)))
         return w.value
 
     def set_launch_config(self, warps_per_cta):
-        """Fix the GB_MIXED launch shape instead of tuning: 1, 2 or 4 warps per CTA of the
-        mma.sync kernel, or 8 for the tcgen05 kernel (N <= 4, no boundary faces)."""
+        """Fix the GB_MIXED launch shape instead of tuning.  2D: 1, 2 or 4 warps per CTA of
+        the mma.sync kernel, or 8 for the tcgen05 kernel (N <= 4, no boundary faces).  3D: 1..8
+        warps per CTA of the tensor-core kernel (N <= 3, at most as many as fit: 7 at N = 3),
+        or 16 for the FP32 one-thread-per-node kernel."""
         self._c(lib.gb_set_launch_config(self.h, int(warps_per_cta)))
 
     def set_graph(self, enable):
