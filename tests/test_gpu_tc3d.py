@@ -226,3 +226,27 @@ def test_tc3_full_size_channel_rhs_and_step():
     q_gpu = s.fields()[0]
     assert rel_err(q_gpu, q_or) <= 1e-5
     assert rel_err(q_gpu - REST[None, :, None], q_or - REST[None, :, None]) <= 1e-4
+
+
+def test_tc3_tuner_choice_is_one_of_the_two_kernels():
+    """The first step of an untuned GB_MIXED solver times both 3D kernels on its own state and
+    keeps one; the tuning launches leave the state alone, so the fields equal a solver fixed to
+    the chosen kernel bit for bit."""
+    mesh, o = channel((5, 3, 3), 3, jitter=0.05)
+    q0 = oracle_state(o, o.X, lambda x, y, z: inputs.channel_flow_3d(x, y, z, 0.1))
+    dt = inputs.cfl_dt_3d(mesh, 3, o.c, 0.5)
+    tuned = mixed_solver(mesh, 3)
+    assert tuned.launch_config() == TC_DEFAULT[3]      # before the first step
+    tuned.set_fields(q0, 0.0)
+    tuned.step(dt, 4)
+    pick = tuned.launch_config()
+    assert pick in (TC_DEFAULT[3], SIMT)
+    fixed = mixed_solver(mesh, 3, pick)
+    fixed.set_fields(q0, 0.0)
+    fixed.step(dt, 4)
+    qa, ta = tuned.fields()
+    qb, tb = fixed.fields()
+    assert ta == tb
+    np.testing.assert_array_equal(qa, qb)
+    q_or, _, _ = o.run(q0, o.X.copy(), 0.0, dt, 4)
+    assert rel_err(qa, q_or) <= 1e-5
