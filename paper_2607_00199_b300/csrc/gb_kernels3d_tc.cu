@@ -22,20 +22,22 @@
 //      stride S = 4 mod 8, so that A-fragment loads are free of bank conflicts) while
 //      lanes 0..15 form one element's geometry each (FP64 vertex positions and
 //      differences, FP32 afterwards; the same routine as the FP32 kernel);
-//   2. the grid velocity enters as vt_a(n) = (G^-1 v_G(n))_a per node, so that
-//      v_G . grad q_f = sum_a vt_a D_a q_f needs no physical gradient;
+//   2. the neighbour traces of the first face-node k-step are requested (cp.async into
+//      this lane's slots), to arrive during the cubature;
 //   3. cubature chain, chunk by chunk: the accumulator fragment of I q is reused directly
 //      as the A fragment of P Ntilde (the chunk's 8 points taken in the order
 //      0,2,4,6,1,3,5,7, folded into the P table); the result seeds the accumulators of
 //      fields 5..10;
-//   4. volume: per field the three derivative fragments, then the chain rule, the grid
-//      velocity term and the Atilde couplings, all in the thread that holds the node;
-//   5. surface: each lane forms the upwind flux exactly at the four (element, face node)
-//      slots of the A fragment it feeds to the lift product, so the fluxes never go
-//      through shared memory (neighbour traces read through L1/L2);
-//   6. SARK combination straight from the accumulators (8-byte accesses, node pairs).
+//   4. surface: each lane forms the upwind flux exactly at the four (element, face node)
+//      slots of the A fragment it feeds to the lift product, from the traces in its slots
+//      (the next k-step's traces arrive in a second slot set meanwhile);
+//   5. the accumulators of n-tiles 1.. are parked in shared memory (fragment order);
+//   6. per n-tile: volume (the three derivative fragments of each field, then the chain
+//      rule, the grid velocity term v_G . grad q_f = sum_a vt_a D_a q_f with
+//      vt_a = (G^-1 v_G)_a, and the Atilde couplings, all in the thread that holds the
+//      node), then the SARK combination straight from the accumulators (node pairs).
 // The rhs accumulators of all 10 fields (10 x ceil(Np/8) fragments) stay in registers
-// from step 3 to step 6.
+// through steps 3 and 4; step 6 holds one n-tile's at a time.
 #include <cuda_runtime.h>
 
 #include <atomic>
