@@ -192,15 +192,33 @@ def test_rhs_on_a_renumbered_tetrahedral_mesh(N):
         assert rel_err(F[:, f], F_or[:, f]) <= 1e-11, f
 
 
-@pytest.mark.parametrize('N', [2, 3])
-def test_mixed_rhs_on_a_renumbered_tetrahedral_mesh(N):
+@pytest.mark.parametrize('N,shape', [(1, 8), (2, 8), (3, 7), (2, 16), (3, 16)])
+def test_mixed_rhs_on_a_renumbered_tetrahedral_mesh(N, shape):
+    """Both 3D mixed kernels (the tensor-core kernel with its most warps per CTA, and the
+    one-thread-per-node kernel, shape 16) on a mesh whose faces meet in every pairing and
+    orientation."""
     mesh, o, s = periodic3((5, 3, 3), N, gb.GB_MIXED)
+    s.set_launch_config(shape)
     t = 0.3
     xv = o.X + o.motion.displacement(o.X, t)
     s.set_vertices(xv)
     q = state3(o, xv, 70 + N)
     F_or = o.rhs(q, xv, o.motion.velocity(o.X, t))
     assert rel_err(gpu_rhs(s, q, t), F_or) <= 1e-5
+
+
+@pytest.mark.parametrize('shape', [7, 16])
+def test_mixed_steps_on_a_renumbered_tetrahedral_mesh(shape):
+    mesh, o, s = periodic3((6, 3, 3), 3, gb.GB_MIXED, seed=5)
+    s.set_launch_config(shape)
+    q0 = np.ascontiguousarray(state3(o, o.X, 90))
+    dt = inputs.cfl_dt_3d(mesh, 3, o.c, 0.5)
+    s.set_fields(q0, 0.0)
+    s.step(dt, 6)
+    q, _ = s.fields()
+    q_or, x_or, _ = o.run(q0, o.X.copy(), 0.0, dt, 6)
+    np.testing.assert_allclose(s.vertices(), x_or, atol=1e-14)
+    assert rel_err(q, q_or) <= 1e-5
 
 
 def test_steps_on_a_renumbered_tetrahedral_mesh():
